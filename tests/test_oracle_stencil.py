@@ -1,0 +1,92 @@
+"""Pins for the oracle's operator (closed forms and an independent dense assembly)."""
+import numpy as np
+import pytest
+
+from oracle import dense, stencil
+
+
+def grid_coords(shape):
+    N = shape[0]
+    h = 1.0 / (N + 1)
+    axes = [np.arange(1, n + 1) * h for n in shape]
+    # flat order x fastest
+    mesh = np.meshgrid(*axes[::-1], indexing="ij")[::-1]
+    return [m.reshape(-1) for m in mesh], h
+
+
+@pytest.mark.parametrize("shape,beta", [((9, 9), (20.0, -7.0)), ((7, 7, 7), (30.0, 20.0, 10.0)), ((12, 12), (0.0, 0.0))])
+def test_quadratic_closed_form(shape, beta):
+    """P1: centred differences are exact for u quadratic in each variable.
+
+    u = prod_d x_d (1 - x_d) vanishes on the boundary, so the Dirichlet rows
+    need no correction: (A u)_p = h^2 [ -Lap u + beta . grad u ](x_p).
+    """
+    X, h = grid_coords(shape)
+    dim = len(shape)
+    q = [x * (1 - x) for x in X]
+    u = np.prod(q, axis=0)
+    lap = np.zeros_like(u)
+    grad_term = np.zeros_like(u)
+    for d in range(dim):
+        others = np.prod([q[e] for e in range(dim) if e != d], axis=0)
+        lap += -2.0 * others                     # d^2/dx_d^2 of x(1-x) = -2
+        grad_term += beta[d] * (1 - 2 * X[d]) * others
+    expect = h * h * (-lap + grad_term)
+    A = stencil.convdiff(shape, beta)
+    got = A.apply(u)
+    assert np.max(np.abs(got - expect)) <= 1e-14 * np.max(np.abs(expect))
+
+
+@pytest.mark.parametrize("shape,beta", [((10, 10), (20.0, 20.0)), ((6, 6, 6), (10.0, 6.0, -3.0))])
+def test_eigenpairs_closed_form(shape, beta):
+    """P2: A is diagonally similar to a symmetric matrix with known eigenpairs.
+
+    In 1-D, tridiag(-1-c, 2, -1+c) has eigenvectors rho^i sin(i p pi h),
+    rho = sqrt((1+c)/(1-c)), and eigenvalues 2 - 2 sqrt(1-c^2) cos(p pi h);
+    the d-dimensional operator is the Kronecker sum (needs |c| < 1).
+    """
+    N = shape[0]
+    dim = len(shape)
+    h = 1.0 / (N + 1)
+    A = stencil.convdiff(shape, beta)
+    idx = [np.arange(1, N + 1)] * dim
+    mesh = [m.reshape(-1) for m in np.meshgrid(*idx[::-1], indexing="ij")[::-1]]
+    rng = np.random.default_rng(1)
+    for _ in range(4):
+        p = rng.integers(1, N + 1, size=dim)
+        u = np.ones(A.n)
+        lam = 0.0
+        for d in range(dim):
+            c = beta[d] * h / 2
+            rho = np.sqrt((1 + c) / (1 - c))
+            u *= rho ** mesh[d] * np.sin(mesh[d] * p[d] * np.pi * h)
+            lam += 2 - 2 * np.sqrt(1 - c * c) * np.cos(p[d] * np.pi * h)
+        res = A.apply(u) - lam * u
+        assert np.linalg.norm(res) <= 1e-12 * np.linalg.norm(lam * u)
+
+
+def test_dense_assembly_matches_apply():
+    """Two independent formulations of the same rows agree, constant and variable coefficients."""
+    rng = np.random.default_rng(2)
+    for St in [stencil.convdiff((5, 5), (20.0, 20.0)), stencil.convdiff((4, 4, 4), (30.0, 20.0, 10.0)),
+               stencil.convdiff_variable(6, rng.uniform(-40, 40, 36)),
+               stencil.Stencil((5, 3, 4), rng.uniform(1, 2, 60), [rng.uniform(-1, 0, 60) for _ in range(3)],
+                               [rng.uniform(-1, 0, 60) for _ in range(3)])]:
+        D = dense.dense_matrix(St)
+        for _ in range(3):
+            x = rng.standard_normal(St.n)
+            assert np.allclose(D @ x, St.apply(x), rtol=0, atol=1e-13)
+        assert abs(St.norm_inf() - np.abs(D).sum(axis=1).max()) <= 1e-13
+
+
+def test_norm_inf_is_4d():
+    # holds while every cell Peclet number |c_d| = |beta_d| h / 2 is at most 1
+    for shape, beta in [((8, 8), (17.0, 17.0)), ((5, 5, 5), (5.0, 4.0, -3.0))]:
+        assert abs(stencil.convdiff(shape, beta).norm_inf() - 4 * len(shape)) < 1e-14
+
+
+def test_gauss_solve_matches_library():
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((30, 30)) + 5 * np.eye(30)
+    b = rng.standard_normal(30)
+    assert np.allclose(dense.gauss_solve(M, b), np.linalg.solve(M, b), rtol=1e-12, atol=1e-12)
