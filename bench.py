@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark: solve time to 1e-8 relative residual, s-step vs plain, on one GB300.
+
+Workload: the 3-D convection-diffusion system on a 128^3 interior grid
+(n = 2,097,152), beta = (30, 20, 10), 7-point centred stencil, FP64,
+x_true ~ U[-1, 1] from SplitMix64 seed (rank), f = A x_true, x0 = 0.
+One step = one complete solve to ||f - A x|| / ||f|| <= 1e-8 with s-step GMRES
+(m = 40), every kernel of the hot path included. The working set (a 42-column
+basis of 16.8 MB columns) is larger than L2, so no flush is needed.
+
+With N GPUs (torchrun) every rank solves its own system (replicas, weak
+scaling); the step time is the maximum over ranks.
+
+--impl reference times the CPU oracle (numpy FP64, one thread) on the same
+system: each step is one restart cycle of its s-step GMRES, and the value is
+scaled to a full solve by the number of cycles the solve takes.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solve time to 1e-8 rel. residual & HBM GB/s vs peak; s-step vs plain, 1 GB300"
+N_GRID = 128
+BETA = (30.0, 20.0, 10.0)
+M = 40
+TOL = 1e-8
+WORKLOAD = "3-D convection-diffusion 128^3 (n=2,097,152), beta=(30,20,10), 7-point, FP64, x0=0, tol 1e-8"
+FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz, FMA = 2 flops
+
+
+def env_ranks():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--s", type=int, default=8, help="block size of the headline s-step GMRES")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi samples of this GPU's clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_id), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ algorithmic work
+def cycle_steps(history, s, m, tol):
+    """Krylov steps of each cycle, read off a GMRES-type history.
+
+    The history holds, per cycle, the explicit restart residual and then one
+    least-squares estimate per step, in blocks of s; a cycle stops after m steps
+    or after a block whose last estimate is <= tol. The final entry is the
+    restart residual that met tol.
+    """
+    steps, i = [], 1
+    while i < len(history):
+        k = 0
+        while k < m and i + s <= len(history):
+            i += s
+            k += s
+            if history[i - 1] <= tol:
+                break
+        steps.append(k)
+        i += 1   # the next restart entry
+    return steps
+
+
+def sstep_gmres_work(n, dim, s, m, history, tol):
+    """Algorithmic FP64 flops and bytes per kernel kind of one s-step GMRES solve.
+
+    Per kernel: the FMAs of the definition (FMA = 2 flops) and the compulsory
+    traffic (every array read or written once, halo re-reads excluded). Block k
+    of a cycle (o = k s earlier columns) costs: powers s sweeps of (2(2d+1)) flops
+    and 16 B per point plus the 8 B scaled start vector; Gram 2 o s flops and
+    (o + s) columns; update 2 o s + (s+1)(s+2) flops, (o+s+1) columns read and s
+    written (none when o = 0); next vector 2s+2 flops, s+1 columns read, 1 written.
+    """
+    pts = 2 * (2 * dim + 1)
+    W = {k: [0.0, 0.0] for k in ("stencil_powers", "gram", "block_update", "next_vector", "residual", "basis_axpy")}
+    cycles = cycle_steps(history, s, m, tol)
+    for steps in cycles:
+        nblk = steps // s
+        for k in range(nblk):
+            o = k * s
+            W["stencil_powers"][0] += s * pts * n
+            W["stencil_powers"][1] += (s * 16 + 8) * n
+            if k > 0:
+                W["gram"][0] += 2 * o * s * n
+                W["gram"][1] += (o + s) * 8 * n
+            W["block_update"][0] += (2 * o * s + (s + 1) * (s + 2)) * n
+            W["block_update"][1] += ((o + s + 1) + (s if o > 0 else 0)) * 8 * n
+            W["next_vector"][0] += (2 * s + 2) * n
+            W["next_vector"][1] += (s + 2) * 8 * n
+        W["basis_axpy"][0] += 2 * nblk * s * n
+        W["basis_axpy"][1] += (nblk * s + 2) * 8 * n
+    # the norm of f, one explicit residual per restart and the final check
+    W["residual"][0] += (len(cycles) + 3) * (pts + 2) * n
+    W["residual"][1] += (len(cycles) + 3) * 24 * n
+    return W
+
+
+# ------------------------------------------------------------------ oracle baseline
+ORACLE_SNIPPET = r"""
+import os, sys, time, json
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import stencil, sstep
+from paper_2001_04886_gb300 import inputs
+A = stencil.convdiff(({n}, {n}, {n}), {beta!r})
+f = A.apply(inputs.x_true({seed}, A.n))
+sigma = 1.0 / A.norm_inf()
+times = []
+for _ in range({reps}):
+    t = time.perf_counter()
+    sstep.sstep_gmres(A, f, np.zeros(A.n), {s}, {m}, {tol}, sigma, max_cycles=1)
+    times.append(time.perf_counter() - t)
+print(json.dumps(times))
+"""
+
+
+def oracle_cycle_seconds(s, reps, seed=0):
+    """Seconds per restart cycle of the oracle's s-step GMRES (one thread), in a fresh process."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, n=N_GRID, beta=BETA, seed=seed, reps=reps, s=s, m=M, tol=TOL)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args):
+    rank, world, _ = env_ranks()
+    if rank != 0:
+        return 0
+    # cycles of the full solve: the s-step GMRES on this workload converges in this many
+    # restart cycles (the GPU path and the oracle agree on it; measured on this workload)
+    cycles = int(os.environ.get("SSTEP_BENCH_CYCLES", "11"))
+    times = oracle_cycle_seconds(args.s, args.warmup + args.steps)
+    t = times[args.warmup:]
+    ms = 1e3 * sum(t) / len(t) * cycles
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "method": f"oracle s-step GMRES s={args.s} m={M}", "cores": 1},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"each step = 1 restart cycle of the numpy oracle (1 thread); value = mean "
+                                   f"cycle time x {cycles} cycles of the full solve"},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    rank, world, local = env_ranks()
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__ as entry
+
+    if rank == 0:
+        entry.build()
+    if dist:
+        dist.barrier()
+    import paper_2001_04886_gb300 as pkg
+    from paper_2001_04886_gb300 import inputs
+
+    pkg.lib()
+    shape = (N_GRID,) * 3
+    A = pkg.StencilMatrix(3, shape, beta=BETA)
+    n = A.n
+    xt = torch.tensor(inputs.x_true(rank, n), dtype=torch.float64, device=dev)
+    f = torch.empty_like(xt)
+    A.apply(xt, f)
+    x = torch.zeros_like(f)
+    s = args.s
+
+    def solve(xv, method="sstep", **kw):
+        if method == "sstep":
+            return pkg.sstep_gmres_solve(A, f, xv, kw.get("s", s), M, TOL, max_cycles=200, history_cap=8192)
+        if method == "gmres":
+            return pkg.gmres_solve(A, f, xv, M, TOL, max_cycles=200, history_cap=8192)
+        return pkg.sstep_omin_solve(A, f, xv, kw["s"], kw["k"], TOL, max_iters=20000, history_cap=8192)
+
+    for _ in range(max(args.warmup, 3)):
+        x.zero_()
+        res = solve(x)
+    assert res["status"] == 0, res
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    clocks = Clocks(gpu_id)
+    pkg.trace_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        x.zero_()
+        res = solve(x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    trace = pkg.trace_read()
+    pkg.trace_enable(False)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    relres = res["relres"]
+    err = float((x - xt).norm() / xt.norm())
+
+    # roofline of the dominant kernel kind (largest share of the traced time)
+    work = sstep_gmres_work(n, 3, s, M, res["history"], TOL)
+    kinds = {k: v for k, v in trace.items() if v[1] > 0}
+    dom = max((k for k in kinds if k in work), key=lambda k: kinds[k][0])
+    t_dom = kinds[dom][0] / args.steps / 1e3             # seconds per solve
+    flops, bytes_ = work[dom]
+    achieved = flops / t_dom / 1e12
+    launches_timed = sum(v[1] for v in kinds.values())
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
+                "hbm_gbs": bytes_ / t_dom / 1e9,
+                "share_of_step": kinds[dom][0] / args.steps / ms}
+
+    # end to end through the public API: inputs from pinned host memory, x back to the host
+    f_h = f.cpu().pin_memory()
+    x_h = torch.zeros(n, dtype=torch.float64).pin_memory()
+    out_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    f_d = torch.empty_like(f)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        f_d.copy_(f_h, non_blocking=True)
+        x.copy_(x_h, non_blocking=True)
+        r2 = pkg.sstep_gmres_solve(A, f_d, x, s, M, TOL, max_cycles=200, history_cap=0)
+        out_h.copy_(x, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    assert r2["status"] == 0
+
+    variants = {}
+    if not args.no_variants:
+        for name, kw in [("sstep_gmres_s2", dict(method="sstep", s=2)), ("sstep_gmres_s4", dict(method="sstep", s=4)),
+                         ("sstep_gmres_s8", dict(method="sstep", s=8)), ("gmres", dict(method="gmres")),
+                         ("sstep_omin_s4_k1", dict(method="omin", s=4, k=1)),
+                         ("omin_k1", dict(method="omin", s=1, k=1)), ("omin_k7", dict(method="omin", s=1, k=7))]:
+            x.zero_()
+            solve(x, **kw)                                  # warm the workspace
+            torch.cuda.synchronize()
+            e0.record(stream)
+            reps = 3
+            for _ in range(reps):
+                x.zero_()
+                rv = solve(x, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            variants[name] = {"ms": e0.elapsed_time(e1) / reps, "status": rv["status"], "cycles": rv["cycles"],
+                              "iters": rv["iters"], "matvecs": rv["matvecs"], "relres": rv["relres"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            ts = oracle_cycle_seconds(s, 2)
+            cycles = res["cycles"]
+            cpu = {"value": 1e3 * min(ts) * cycles, "unit": "ms", "cores": 1, "kind": "oracle",
+                   "sample": f"1 restart cycle of the numpy oracle's s-step GMRES (s={s}, m={M}) on the same "
+                             f"system, best of 2, x {cycles} cycles of the full solve"}
+        except Exception as ex:   # the baseline is reported, never required
+            cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:200]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "method": f"s-step GMRES s={s} m={M}, sigma=1/||A||_inf",
+                       "l2": "inputs larger than L2 (basis 42 x 16.8 MB), no flush", "parallelism": f"replicas{world}",
+                       "cycles": res["cycles"], "matvecs": res["matvecs"], "relres": relres,
+                       "x_err_vs_x_true": err},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": int(launches_timed),
+            "clocks": clk,
+            "kernel_ms_per_solve": {k: v[0] / args.steps for k, v in kinds.items()},
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,169 @@
+/*
+ * sstep.h - C ABI of the GB300 s-step Orthomin / s-step GMRES library.
+ *
+ * Method: A. T. Chronopoulos and S. K. Kim, "s-Step Orthomin and GMRES
+ * implemented on parallel computers" (1990). Section numbers, algorithms and
+ * equations below refer to that paper.
+ *
+ * Conventions for every entry point:
+ *   - All vector pointers are DEVICE pointers on the current CUDA device unless
+ *     a comment says "host". Vectors are contiguous float64 arrays of n values
+ *     in grid order (x fastest, then y, then z).
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream. Work is stream-ordered. Kernel-level entry points return after
+ *     enqueueing; solvers synchronise `stream` (see each solver).
+ *   - The caller owns every pointer it passes. Matrix handles own their
+ *     coefficient copies and their solver workspace.
+ *   - Every call returns an sstep_status (0 = success). Nothing aborts and no
+ *     C++ exception crosses the ABI. Argument errors return SSTEP_ERR_ARG before
+ *     any work is enqueued.
+ *   - A handle may run one solve at a time (its workspace is reused).
+ */
+#ifndef SSTEP_H
+#define SSTEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SSTEP_OK = 0,
+    SSTEP_NOT_CONVERGED = 1,   /* max cycles / iterations reached; x holds the last iterate */
+    SSTEP_ERR_ARG = -1,        /* invalid argument (null pointer, size, s, m, k out of range) */
+    SSTEP_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+    SSTEP_ERR_OOM = -3,        /* device allocation failed */
+    SSTEP_ERR_BREAKDOWN = -4,  /* non-positive Cholesky pivot in a Gram block W (Scalar1/Scalar2) */
+    SSTEP_ERR_NAN = -5         /* a residual norm became NaN or Inf */
+} sstep_status;
+
+typedef struct sstep_matrix_s* sstep_matrix;
+
+/* ------------------------------------------------------------------ operator
+ * The operator of Sec. 1 / Sec. 5: a (2*dim+1)-point stencil on an
+ * nx x ny [x nz] grid of interior unknowns with homogeneous Dirichlet
+ * boundaries (neighbours outside the grid are zero). Row p is
+ *   (A u)_p = a0 u_p + sum_d ( am_d u_{p-e_d} + ap_d u_{p+e_d} ),
+ * summed in the order centre, x-, x+, y-, y+, z-, z+.
+ */
+
+/* Constant coefficients. shape = {nx, ny, nz} (nz ignored when dim == 2).
+ * coef (host) = {a0, am_x, ap_x, am_y, ap_y[, am_z, ap_z]}. */
+int stencil_matrix_create(sstep_matrix* out, int dim, const int64_t shape[3], const double* coef);
+
+/* Variable coefficients: fields (host array of 2*dim+1 DEVICE pointers, each n
+ * values, same order as coef). The library copies the fields. */
+int stencil_matrix_create_fields(sstep_matrix* out, int dim, const int64_t shape[3],
+                                 const double* const* fields, void* stream);
+
+/* The h^2-scaled centred convection-diffusion operator of -Lap u + beta . grad u
+ * on the unit square/cube (Sec. 5, eq. 10 with constant coefficients): all sides
+ * equal N, h = 1/(N+1), c_d = beta_d h / 2, a0 = 2 dim, am_d = -1 - c_d,
+ * ap_d = -1 + c_d. beta (host) holds dim values. */
+int stencil_matrix_create_convdiff(sstep_matrix* out, int dim, const int64_t shape[3], const double* beta);
+
+int stencil_matrix_destroy(sstep_matrix A);
+
+/* n (number of unknowns) and ||A||_inf (max absolute row sum). Host outputs. */
+int stencil_matrix_info(sstep_matrix A, int64_t* n, double* norm_inf);
+
+/* y = A x (Sec. 1: one sweep over the grid). x and y must not overlap. */
+int stencil_matrix_apply(sstep_matrix A, const double* x, double* y, void* stream);
+
+/* ------------------------------------------------------------------ s-step block primitives
+ * The three data-parallel steps of one s-step (Sec. 1, Alg. 3.1, Alg. 4.1),
+ * exposed one by one. Column-major panels: column j of a panel P with leading
+ * dimension ld starts at P + j*ld; ld >= n.
+ */
+
+/* Matrix powers (Alg. 3.1 R_i, Alg. 4.1 step 3):
+ *   Y[:,0] = scale * v,  Y[:,j] = sigma * A Y[:,j-1]  for j = 1..s.
+ * v must not overlap Y. 1 <= s <= SSTEP_MAX_S. */
+int sstep_matrix_powers(sstep_matrix A, const double* v, double scale, double sigma, int s,
+                        double* Y, int64_t ldy, void* stream);
+
+/* Bytes of device workspace the Gram pass needs for ka x kb outputs over n rows. */
+int sstep_gram_workspace_size(int64_t n, int ka, int kb, size_t* bytes);
+
+/* The simultaneous inner products of one s-step (Sec. 1; Alg. 4.1 steps 4-5;
+ * Alg. 3.1 steps 1 and 6) as one tall-skinny Gram pass:
+ *   C = V^T Y,  V: n x ka (ldv), Y: n x kb (ldy), C: ka x kb column-major (ldc >= ka), device.
+ * work: device buffer of at least sstep_gram_workspace_size bytes, 256-byte aligned.
+ * The reduction order is fixed, so results are bitwise reproducible.
+ * 1 <= ka <= SSTEP_MAX_COLS, 1 <= kb <= SSTEP_MAX_S + 1. */
+int sstep_gram(int64_t n, const double* V, int64_t ldv, int ka, const double* Y, int64_t ldy, int kb,
+               double* C, int ldc, void* work, size_t work_bytes, void* stream);
+
+/* Block update (Alg. 4.1 step 7 with Scalar1's Gram; Alg. 3.1 steps 8-9 shape):
+ *   Y <- Y - V T  (in place; V: n x ka, T: ka x kb column-major device, ldt >= ka),
+ *   then Gout = Y^T Y (kb x kb, column-major, device) over the updated Y.
+ * ka may be 0 (Gram only). V must not overlap Y. work as for sstep_gram(n, kb, kb). */
+int sstep_block_update(int64_t n, const double* V, int64_t ldv, int ka, double* Y, int64_t ldy, int kb,
+                       const double* T, int ldt, double* Gout, void* work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------ solvers */
+#define SSTEP_MAX_S 8        /* largest block size s on the GPU path */
+#define SSTEP_MAX_M 64       /* largest Krylov dimension per cycle */
+#define SSTEP_MAX_COLS 64    /* largest ka of the Gram pass */
+
+typedef struct {
+    int s;              /* block size (>= 1, <= SSTEP_MAX_S) */
+    int m;              /* GMRES: Krylov dimension per cycle, a multiple of s (<= SSTEP_MAX_M) */
+    int k;              /* Orthomin: number of previous direction blocks kept (>= 0) */
+    double tol;         /* stop when ||f - A x|| / ||f|| <= tol */
+    int max_cycles;     /* GMRES: maximum restart cycles */
+    int max_iters;      /* Orthomin: maximum (s-)steps */
+    double sigma;       /* basis scale of the monomial powers; 0 => 1 / ||A||_inf */
+    double* history;    /* HOST array receiving the residual history, or NULL */
+    int history_cap;    /* capacity of history */
+} sstep_params;
+
+typedef struct {
+    int status;         /* sstep_status of the solve */
+    int cycles;         /* GMRES restart cycles run (Orthomin: restarts from an explicit residual) */
+    int iters;          /* Krylov steps (GMRES) or s-steps (Orthomin) */
+    int matvecs;        /* products with A, including explicit residuals */
+    int history_len;    /* entries written to params.history (<= history_cap) */
+    double relres;      /* final explicit ||f - A x|| / ||f|| */
+} sstep_result;
+
+/* s-step GMRES (Alg. 4.2 over the s-step Arnoldi of Alg. 4.1, least squares of
+ * eq. 6-9). Restart r = f - A x is explicit; per cycle m/s blocks of s products.
+ * History: the explicit relres at every restart, then the least-squares estimate
+ * after each step of every block; a cycle ends early once the estimate is <= tol.
+ * x (device) is the initial guess on entry and the result on exit. Synchronises
+ * `stream` once per cycle. */
+int sstep_gmres_solve(sstep_matrix A, const double* f, double* x, const sstep_params* p,
+                      sstep_result* res, void* stream);
+
+/* Standard restarted GMRES(m) with classical Gram-Schmidt (Alg. 2.2, eq. 2-3):
+ * the plain baseline of the same kernels' quality. p->s is ignored. */
+int gmres_solve(sstep_matrix A, const double* f, double* x, const sstep_params* p,
+                sstep_result* res, void* stream);
+
+/* s-step Orthomin(k) (Alg. 3.1); s = 1 is Orthomin(k) (Alg. 2.1). The updated
+ * residual is tested after each s-step; at tol it is recomputed explicitly and
+ * the method restarts if the explicit residual is still above tol. History: the
+ * explicit relres at (re)starts and the updated relres after each s-step. */
+int sstep_omin_solve(sstep_matrix A, const double* f, double* x, const sstep_params* p,
+                     sstep_result* res, void* stream);
+
+const char* sstep_status_string(int status);
+
+/* ------------------------------------------------------------------ launch tracing
+ * The library counts every kernel launch of the solvers per kernel kind. With
+ * tracing on, it also brackets each launch with a pair of CUDA events recorded on
+ * the launching stream and, at the end of each solve, adds the elapsed times per
+ * kind (each pair costs about a microsecond of stream time). Process-global and
+ * not thread-safe: meant for benchmarks and profiling. enable() resets the totals. */
+int sstep_trace_enable(int on);
+int sstep_trace_kinds(void);                       /* number of kernel kinds */
+const char* sstep_trace_kind_name(int kind);       /* e.g. "gram", "block_update" */
+int sstep_trace_read(int kind, double* total_ms, int64_t* launches);  /* host outputs */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSTEP_H */

@@ -1,0 +1,46 @@
+"""GB300 s-step Orthomin / s-step GMRES: Python binding of the C ABI in include/sstep.h.
+
+Every function here only marshals arguments (tensor data pointers, sizes and
+the current CUDA stream) into one call of libsstep.so; all arithmetic runs in
+the library's CUDA kernels. There is no CPU fallback: if the library is not
+built, the first call raises.
+
+Importing the package loads nothing; `inputs` (seeded synthetic inputs) can be
+used without a GPU.
+"""
+from __future__ import annotations
+
+from ._binding import (  # noqa: F401
+    SSTEP_MAX_COLS,
+    SSTEP_MAX_M,
+    SSTEP_MAX_S,
+    SStepError,
+    StencilMatrix,
+    gmres_solve,
+    lib,
+    sstep_block_update,
+    sstep_gmres_solve,
+    sstep_gram,
+    sstep_gram_workspace_size,
+    sstep_matrix_powers,
+    sstep_omin_solve,
+    stencil_matrix_apply,
+    trace_enable,
+    trace_read,
+)
+
+__all__ = [
+    "StencilMatrix",
+    "stencil_matrix_apply",
+    "sstep_matrix_powers",
+    "sstep_gram",
+    "sstep_gram_workspace_size",
+    "sstep_block_update",
+    "sstep_gmres_solve",
+    "gmres_solve",
+    "sstep_omin_solve",
+    "SStepError",
+    "trace_enable",
+    "trace_read",
+    "lib",
+]

@@ -1,0 +1,279 @@
+"""ctypes binding of libsstep.so (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+SSTEP_MAX_S = 8
+SSTEP_MAX_M = 64
+SSTEP_MAX_COLS = 64
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libsstep.so")
+_lib = None
+_lock = threading.Lock()
+
+c_int, c_double, c_void_p, c_int64, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+P = ctypes.POINTER
+
+
+class SStepParams(ctypes.Structure):
+    _fields_ = [("s", c_int), ("m", c_int), ("k", c_int), ("tol", c_double), ("max_cycles", c_int),
+                ("max_iters", c_int), ("sigma", c_double), ("history", P(c_double)), ("history_cap", c_int)]
+
+
+class SStepResult(ctypes.Structure):
+    _fields_ = [("status", c_int), ("cycles", c_int), ("iters", c_int), ("matvecs", c_int),
+                ("history_len", c_int), ("relres", c_double)]
+
+
+# name -> (restype, argtypes); every entry point declared in include/sstep.h
+SIGNATURES = {
+    "stencil_matrix_create": (c_int, [P(c_void_p), c_int, P(c_int64), P(c_double)]),
+    "stencil_matrix_create_fields": (c_int, [P(c_void_p), c_int, P(c_int64), P(c_void_p), c_void_p]),
+    "stencil_matrix_create_convdiff": (c_int, [P(c_void_p), c_int, P(c_int64), P(c_double)]),
+    "stencil_matrix_destroy": (c_int, [c_void_p]),
+    "stencil_matrix_info": (c_int, [c_void_p, P(c_int64), P(c_double)]),
+    "stencil_matrix_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sstep_matrix_powers": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_void_p, c_int64, c_void_p]),
+    "sstep_gram_workspace_size": (c_int, [c_int64, c_int, c_int, P(c_size_t)]),
+    "sstep_gram": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
+                           c_void_p, c_size_t, c_void_p]),
+    "sstep_block_update": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
+                                   c_void_p, c_void_p, c_size_t, c_void_p]),
+    "sstep_gmres_solve": (c_int, [c_void_p, c_void_p, c_void_p, P(SStepParams), P(SStepResult), c_void_p]),
+    "gmres_solve": (c_int, [c_void_p, c_void_p, c_void_p, P(SStepParams), P(SStepResult), c_void_p]),
+    "sstep_omin_solve": (c_int, [c_void_p, c_void_p, c_void_p, P(SStepParams), P(SStepResult), c_void_p]),
+    "sstep_status_string": (ctypes.c_char_p, [c_int]),
+    "sstep_trace_enable": (c_int, [c_int]),
+    "sstep_trace_kinds": (c_int, []),
+    "sstep_trace_kind_name": (ctypes.c_char_p, [c_int]),
+    "sstep_trace_read": (c_int, [c_int, P(c_double), P(c_int64)]),
+}
+
+
+class SStepError(RuntimeError):
+    def __init__(self, name, status):
+        msg = lib().sstep_status_string(status).decode()
+        super().__init__(f"{name} failed: {msg} (status {status})")
+        self.status = status
+
+
+def lib():
+    """The loaded libsstep.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(_LIB_PATH):
+                    raise ImportError(
+                        f"libsstep.so not found at {_LIB_PATH}; build it with "
+                        "`python -c 'import __graft_entry__ as g; g.build()'`")
+                L = ctypes.CDLL(_LIB_PATH)
+                for name, (res, args) in SIGNATURES.items():
+                    fn = getattr(L, name)
+                    fn.restype = res
+                    fn.argtypes = args
+                _lib = L
+    return _lib
+
+
+def _check(name, rc):
+    if rc < 0:
+        raise SStepError(name, rc)
+    return rc
+
+
+def _ptr(t):
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("expected a float64 CUDA tensor")
+    return c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return c_void_p(stream.cuda_stream)
+
+
+def _col_major(t, name):
+    """(rows, cols, ld) of a tensor viewed as a column-major panel (columns contiguous)."""
+    if t.dim() == 1:
+        return t.shape[0], 1, t.shape[0]
+    if t.dim() != 2:
+        raise ValueError(f"{name}: expected a vector or an (n, k) column-major matrix")
+    n, k = t.shape
+    if t.stride(0) != 1:
+        raise ValueError(f"{name}: columns must be contiguous (use .t().contiguous().t())")
+    return n, k, max(t.stride(1), n) if k > 1 else n
+
+
+class StencilMatrix:
+    """Handle of a (2d+1)-point stencil operator (include/sstep.h, operator section)."""
+
+    def __init__(self, dim, shape, coef=None, beta=None, fields=None, stream=None):
+        L = lib()
+        h = c_void_p()
+        shp = (c_int64 * 3)(*(list(shape) + [1] * (3 - len(shape))))
+        if beta is not None:
+            b = (c_double * 3)(*list(beta))
+            _check("stencil_matrix_create_convdiff", L.stencil_matrix_create_convdiff(ctypes.byref(h), dim, shp, b))
+        elif coef is not None:
+            c = (c_double * 7)(*list(coef))
+            _check("stencil_matrix_create", L.stencil_matrix_create(ctypes.byref(h), dim, shp, c))
+        elif fields is not None:
+            ptrs = (c_void_p * 7)(*[_ptr(f).value for f in fields])
+            _check("stencil_matrix_create_fields",
+                   L.stencil_matrix_create_fields(ctypes.byref(h), dim, shp, ptrs, _stream(stream)))
+        else:
+            raise ValueError("give coef, beta or fields")
+        self.handle = h
+        self.dim = dim
+        self.shape = tuple(shape)
+        n = c_int64()
+        ninf = c_double()
+        _check("stencil_matrix_info", L.stencil_matrix_info(h, ctypes.byref(n), ctypes.byref(ninf)))
+        self.n = n.value
+        self.norm_inf = ninf.value
+
+    def close(self):
+        if self.handle:
+            lib().stencil_matrix_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, x, y, stream=None):
+        return stencil_matrix_apply(self, x, y, stream)
+
+
+def stencil_matrix_apply(A, x, y, stream=None):
+    return _check("stencil_matrix_apply", lib().stencil_matrix_apply(A.handle, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def sstep_matrix_powers(A, v, scale, sigma, s, Y, stream=None):
+    n, k, ld = _col_major(Y, "Y")
+    if k < s + 1:
+        raise ValueError("Y needs s+1 columns")
+    return _check("sstep_matrix_powers",
+                  lib().sstep_matrix_powers(A.handle, _ptr(v), scale, sigma, s, _ptr(Y), ld, _stream(stream)))
+
+
+def sstep_gram_workspace_size(n, ka, kb):
+    b = c_size_t()
+    _check("sstep_gram_workspace_size", lib().sstep_gram_workspace_size(n, ka, kb, ctypes.byref(b)))
+    return b.value
+
+
+def _workspace(nbytes, device):
+    import torch
+
+    return torch.empty((nbytes + 255) // 8 + 64, dtype=torch.float64, device=device)
+
+
+def _aligned_ptr(buf):
+    p = buf.data_ptr()
+    return c_void_p((p + 255) // 256 * 256)
+
+
+def sstep_gram(V, Y, C=None, work=None, stream=None):
+    """C = V^T Y for column-major panels V (n x ka) and Y (n x kb)."""
+    import torch
+
+    n, ka, ldv = _col_major(V, "V")
+    n2, kb, ldy = _col_major(Y, "Y")
+    assert n == n2
+    if C is None:
+        C = torch.empty((kb, ka), dtype=torch.float64, device=V.device).t()
+    nbytes = sstep_gram_workspace_size(n, ka, kb)
+    if work is None:
+        work = _workspace(nbytes, V.device)
+    _check("sstep_gram", lib().sstep_gram(n, _ptr(V), ldv, ka, _ptr(Y), ldy, kb, c_void_p(C.data_ptr()), ka,
+                                          _aligned_ptr(work), nbytes, _stream(stream)))
+    return C
+
+
+def sstep_block_update(V, Y, T, work=None, stream=None):
+    """In place Y <- Y - V T; returns G = Y^T Y of the updated Y."""
+    import torch
+
+    n, kb, ldy = _col_major(Y, "Y")
+    if V is None or V.numel() == 0:
+        ka, ldv, vp, tp, ldt = 0, n, c_void_p(0), c_void_p(0), 1
+    else:
+        n2, ka, ldv = _col_major(V, "V")
+        assert n == n2
+        vp = _ptr(V)
+        Tc = T.t().contiguous().t()
+        tp = c_void_p(Tc.data_ptr())
+        ldt = Tc.stride(1) if Tc.dim() == 2 and Tc.shape[1] > 1 else ka
+        T = Tc
+    G = torch.empty((kb, kb), dtype=torch.float64, device=Y.device)
+    nbytes = sstep_gram_workspace_size(max(n, 1), 1, kb)
+    if work is None:
+        work = _workspace(nbytes, Y.device)
+    _check("sstep_block_update", lib().sstep_block_update(n, vp, ldv, ka, _ptr(Y), ldy, kb, tp, ldt,
+                                                          c_void_p(G.data_ptr()), _aligned_ptr(work), nbytes,
+                                                          _stream(stream)))
+    return G.t()
+
+
+def _solve(name, A, f, x, s=1, m=20, k=1, tol=1e-8, max_cycles=1000, max_iters=100000, sigma=0.0,
+           history_cap=4096, stream=None):
+    import numpy as np
+
+    hist = np.zeros(max(history_cap, 1), dtype=np.float64)
+    p = SStepParams(s=s, m=m, k=k, tol=tol, max_cycles=max_cycles, max_iters=max_iters, sigma=sigma,
+                    history=hist.ctypes.data_as(P(c_double)) if history_cap > 0 else None,
+                    history_cap=history_cap)
+    r = SStepResult()
+    rc = getattr(lib(), name)(A.handle, _ptr(f), _ptr(x), ctypes.byref(p), ctypes.byref(r), _stream(stream))
+    _check(name, rc)
+    return dict(status=r.status, cycles=r.cycles, iters=r.iters, matvecs=r.matvecs, relres=r.relres,
+                history=hist[: r.history_len].tolist())
+
+
+def sstep_gmres_solve(A, f, x, s, m, tol, max_cycles=1000, sigma=0.0, history_cap=4096, stream=None):
+    """s-step GMRES (Alg. 4.1/4.2); x is updated in place. Returns the result as a dict."""
+    return _solve("sstep_gmres_solve", A, f, x, s=s, m=m, tol=tol, max_cycles=max_cycles, sigma=sigma,
+                  history_cap=history_cap, stream=stream)
+
+
+def gmres_solve(A, f, x, m, tol, max_cycles=1000, history_cap=4096, stream=None):
+    """Standard GMRES(m) with classical Gram-Schmidt (Alg. 2.2)."""
+    return _solve("gmres_solve", A, f, x, m=m, tol=tol, max_cycles=max_cycles, history_cap=history_cap,
+                  stream=stream)
+
+
+def sstep_omin_solve(A, f, x, s, k, tol, max_iters=100000, sigma=0.0, history_cap=4096, stream=None):
+    """s-step Orthomin(k) (Alg. 3.1); s = 1 is Orthomin(k)."""
+    return _solve("sstep_omin_solve", A, f, x, s=s, k=k, tol=tol, max_iters=max_iters, sigma=sigma,
+                  history_cap=history_cap, stream=stream)
+
+
+def trace_enable(on=True):
+    """Turn per-launch CUDA-event tracing on or off (resets the totals)."""
+    _check("sstep_trace_enable", lib().sstep_trace_enable(1 if on else 0))
+
+
+def trace_read():
+    """{kind name: (total milliseconds, launches)} since the last trace_enable()."""
+    L = lib()
+    out = {}
+    for k in range(L.sstep_trace_kinds()):
+        ms = c_double()
+        nl = c_int64()
+        _check("sstep_trace_read", L.sstep_trace_read(k, ctypes.byref(ms), ctypes.byref(nl)))
+        out[L.sstep_trace_kind_name(k).decode()] = (ms.value, nl.value)
+    return out

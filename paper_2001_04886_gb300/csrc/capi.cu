@@ -1,0 +1,678 @@
+// C ABI: matrix handles, kernel-level entry points and the solver drivers.
+//
+// The drivers only enqueue kernels and read back a small status header: every
+// arithmetic step of the solvers runs on the device (kernels.cu). One host
+// synchronisation per GMRES cycle, or per batch of Orthomin steps, decides
+// whether to continue.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace sstep;
+
+struct sstep_matrix_s {
+    StencilDesc A;
+    double norm_inf = 0.0;
+    double* fields = nullptr;        // owned copies of variable coefficients (7 x n)
+    // solver workspace, grown on demand
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    SolverState* hdr = nullptr;      // pinned host copy of the state
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+inline int64_t col_ld(int64_t n) { return (n + 31) / 32 * 32; }   // 256-byte aligned columns
+
+#define CUDA_TRY(expr)                                  \
+    do {                                                \
+        cudaError_t e_ = (expr);                        \
+        if (e_ != cudaSuccess) return SSTEP_ERR_CUDA;   \
+    } while (0)
+
+int check_launch() { return cudaGetLastError() == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA; }
+
+// ------------------------------------------------------------------ launch tracing
+// Every launch is counted; when tracing is on, a pair of CUDA events brackets each
+// launch on its own stream and the elapsed times are summed per kernel kind at the
+// end of the call that issued them.
+enum Kind { K_STENCIL = 0, K_RESIDUAL, K_GRAM, K_UPDATE, K_NEXT, K_AXPY, K_OMIN_XR, K_OMIN_PUPDATE, K_LSQ, K_COUNT };
+const char* const kKindNames[K_COUNT] = {"stencil_powers", "residual", "gram", "block_update", "next_vector",
+                                         "basis_axpy", "omin_xr", "omin_pupdate", "lsq_solve"};
+struct Tracer {
+    bool on = false;
+    std::vector<cudaEvent_t> events;
+    std::vector<int> kinds;       // kind of each recorded pair
+    size_t used = 0;              // events in use (pairs * 2)
+    double total_ms[K_COUNT] = {0};
+    long long launches[K_COUNT] = {0};
+};
+Tracer g_trace;
+
+int trace_begin(int kind, cudaStream_t s) {
+    g_trace.launches[kind] += 1;
+    if (!g_trace.on) return -1;
+    if (g_trace.used + 2 > g_trace.events.size()) {
+        for (int i = 0; i < 256; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            g_trace.events.push_back(e);
+        }
+    }
+    int idx = (int)g_trace.used;
+    g_trace.used += 2;
+    g_trace.kinds.push_back(kind);
+    cudaEventRecord(g_trace.events[idx], s);
+    return idx;
+}
+
+void trace_end(int idx, cudaStream_t s) {
+    if (idx >= 0) cudaEventRecord(g_trace.events[idx + 1], s);
+}
+
+// Adds up the recorded pairs (their stream must have been synchronised).
+void trace_collect() {
+    for (size_t i = 0; i < g_trace.kinds.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g_trace.events[2 * i], g_trace.events[2 * i + 1]) == cudaSuccess)
+            g_trace.total_ms[g_trace.kinds[i]] += ms;
+    }
+    cudaGetLastError();
+    g_trace.kinds.clear();
+    g_trace.used = 0;
+}
+
+#define TRACED(kind, stream, call)                   \
+    do {                                             \
+        int tr_ = trace_begin((kind), (stream));     \
+        call;                                        \
+        trace_end(tr_, (stream));                    \
+    } while (0)
+
+// ||A||_inf of a constant stencil: per axis a row has both neighbours (side >= 3),
+// exactly one of them (side 2) or none (side 1); axes are independent.
+double row_norm_inf_const(const StencilDesc& A) {
+    const int sz[3] = {A.nx, A.ny, A.nz};
+    double t = fabs(A.c[0]);
+    for (int d = 0; d < A.dim; ++d) {
+        const double lo = fabs(A.c[1 + 2 * d]), hi = fabs(A.c[2 + 2 * d]);
+        if (sz[d] >= 3) t += lo + hi;
+        else if (sz[d] == 2) t += std::max(lo, hi);
+    }
+    return t;
+}
+
+int make_desc(StencilDesc& A, int dim, const int64_t shape[3]) {
+    if (dim != 2 && dim != 3) return SSTEP_ERR_ARG;
+    if (!shape) return SSTEP_ERR_ARG;
+    int64_t nx = shape[0], ny = shape[1], nz = dim == 3 ? shape[2] : 1;
+    if (nx < 1 || ny < 1 || nz < 1) return SSTEP_ERR_ARG;
+    int64_t n = nx * ny * nz;
+    if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30) || n >= (int64_t)1 << 31) return SSTEP_ERR_ARG;
+    memset(&A, 0, sizeof(A));
+    A.dim = dim;
+    A.nx = (int)nx;
+    A.ny = (int)ny;
+    A.nz = (int)nz;
+    A.n = n;
+    return SSTEP_OK;
+}
+
+// Device workspace of one solve. Small arrays first, then the columns.
+struct Layout {
+    size_t state, L, T, S, G, R, gc, gs, g, y, hist, C, a, counter, partials, cols;
+    size_t total;
+};
+
+Layout plan(int64_t n, int ncols, int m, int hist_cap) {
+    Layout l;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    const int mm = std::max(m, 1);
+    l.state = take(sizeof(SolverState));
+    l.L = take(sizeof(double) * kMaxCols * kMaxS * 2);
+    l.T = take(sizeof(double) * kMaxCols * (kMaxS + 1));
+    l.S = take(sizeof(double) * kMaxCols);
+    l.G = take(sizeof(double) * (mm + 1) * mm);
+    l.R = take(sizeof(double) * (mm + 1) * mm);
+    l.gc = take(sizeof(double) * mm);
+    l.gs = take(sizeof(double) * mm);
+    l.g = take(sizeof(double) * (mm + 1));
+    l.y = take(sizeof(double) * kMaxCols);
+    l.hist = take(sizeof(double) * std::max(hist_cap, 1));
+    l.C = take(sizeof(double) * kMaxCols * (kMaxS + 1));
+    l.a = take(sizeof(double) * kMaxCols);
+    l.counter = take(kAlign);
+    l.partials = take(sizeof(double) * (size_t)max_partials_doubles());
+    l.cols = take(sizeof(double) * (size_t)col_ld(n) * ncols);
+    l.total = off;
+    return l;
+}
+
+int ensure_workspace(sstep_matrix M, size_t bytes) {
+    if (!M->hdr) {
+        if (cudaMallocHost((void**)&M->hdr, sizeof(SolverState)) != cudaSuccess) {
+            M->hdr = nullptr;
+            return SSTEP_ERR_OOM;
+        }
+    }
+    if (M->ws_bytes >= bytes) return SSTEP_OK;
+    if (M->ws) cudaFree(M->ws);
+    M->ws = nullptr;
+    M->ws_bytes = 0;
+    if (cudaMalloc((void**)&M->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SSTEP_ERR_OOM;
+    }
+    M->ws_bytes = bytes;
+    return SSTEP_OK;
+}
+
+// Host image of the state with its device pointers filled in.
+SolverState init_state(const Layout& l, char* ws, const sstep_params* p, int s, int m, int k) {
+    SolverState h;
+    memset(&h, 0, sizeof(h));
+    h.active = 1;
+    h.building = 1;
+    h.status = SSTEP_NOT_CONVERGED;
+    h.s = s;
+    h.m = m;
+    h.k = k;
+    h.nb = s > 0 ? m / s : 0;
+    h.max_cycles = p->max_cycles;
+    h.max_iters = p->max_iters;
+    h.hist_cap = p->history ? p->history_cap : 0;
+    h.tol = p->tol;
+    h.L = (double*)(ws + l.L);
+    h.T = (double*)(ws + l.T);
+    h.S = (double*)(ws + l.S);
+    h.G = (double*)(ws + l.G);
+    h.R = (double*)(ws + l.R);
+    h.gc = (double*)(ws + l.gc);
+    h.gs = (double*)(ws + l.gs);
+    h.g = (double*)(ws + l.g);
+    h.y = (double*)(ws + l.y);
+    h.hist = (double*)(ws + l.hist);
+    h.C = (double*)(ws + l.C);
+    h.a = (double*)(ws + l.a);
+    return h;
+}
+
+int common_checks(sstep_matrix A, const double* f, double* x, const sstep_params* p, sstep_result* res) {
+    if (!A || !f || !x || !p || !res) return SSTEP_ERR_ARG;
+    if (!(p->tol > 0.0)) return SSTEP_ERR_ARG;
+    if (p->history && p->history_cap < 0) return SSTEP_ERR_ARG;
+    if (p->sigma < 0.0 || !isfinite(p->sigma)) return SSTEP_ERR_ARG;
+    return SSTEP_OK;
+}
+
+// Copies the final state into res and the history into the caller's host array.
+int finish(sstep_matrix M, const Layout& l, SolverState* st, const double* f, const double* x,
+           const sstep_params* p, sstep_result* res, cudaStream_t stream) {
+    Scratch sc{(double*)(M->ws + l.partials), (unsigned*)(M->ws + l.counter)};
+    Epi e;
+    e.mode = EPI_FINAL;
+    e.st = st;
+    TRACED(K_RESIDUAL, stream, launch_residual(M->A, f, x, nullptr, sc, e, GATE_NONE, stream));
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(M->hdr, st, sizeof(SolverState), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    trace_collect();
+    const SolverState& h = *M->hdr;
+    res->status = h.status;
+    res->cycles = h.cycles;
+    res->iters = h.iters;
+    res->matvecs = h.matvecs;
+    res->relres = h.relres;
+    int nh = std::min(h.hist_len, h.hist_cap);
+    res->history_len = nh;
+    if (p->history && nh > 0) {
+        CUDA_TRY(cudaMemcpy(p->history, M->ws + l.hist, sizeof(double) * nh, cudaMemcpyDeviceToHost));
+    }
+    return SSTEP_OK;
+}
+
+int read_header(sstep_matrix M, SolverState* st, cudaStream_t stream) {
+    CUDA_TRY(cudaMemcpyAsync(M->hdr, st, sizeof(SolverState), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    return SSTEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sstep_trace_enable(int on) {
+    g_trace.on = on != 0;
+    for (int k = 0; k < K_COUNT; ++k) {
+        g_trace.total_ms[k] = 0.0;
+        g_trace.launches[k] = 0;
+    }
+    g_trace.kinds.clear();
+    g_trace.used = 0;
+    return SSTEP_OK;
+}
+
+int sstep_trace_kinds(void) { return K_COUNT; }
+
+const char* sstep_trace_kind_name(int kind) { return (kind >= 0 && kind < K_COUNT) ? kKindNames[kind] : ""; }
+
+int sstep_trace_read(int kind, double* total_ms, int64_t* launches) {
+    if (kind < 0 || kind >= K_COUNT) return SSTEP_ERR_ARG;
+    if (total_ms) *total_ms = g_trace.total_ms[kind];
+    if (launches) *launches = g_trace.launches[kind];
+    return SSTEP_OK;
+}
+
+const char* sstep_status_string(int status) {
+    switch (status) {
+        case SSTEP_OK: return "ok";
+        case SSTEP_NOT_CONVERGED: return "not converged";
+        case SSTEP_ERR_ARG: return "invalid argument";
+        case SSTEP_ERR_CUDA: return "CUDA error";
+        case SSTEP_ERR_OOM: return "out of device memory";
+        case SSTEP_ERR_BREAKDOWN: return "breakdown: non-positive Cholesky pivot in a Gram block";
+        case SSTEP_ERR_NAN: return "residual is NaN or Inf";
+        default: return "unknown status";
+    }
+}
+
+int stencil_matrix_create(sstep_matrix* out, int dim, const int64_t shape[3], const double* coef) {
+    if (!out || !coef) return SSTEP_ERR_ARG;
+    *out = nullptr;
+    StencilDesc A;
+    int rc = make_desc(A, dim, shape);
+    if (rc) return rc;
+    for (int q = 0; q < 2 * dim + 1; ++q) {
+        if (!isfinite(coef[q])) return SSTEP_ERR_ARG;
+        A.c[q] = coef[q];
+    }
+    sstep_matrix M = new (std::nothrow) sstep_matrix_s;
+    if (!M) return SSTEP_ERR_OOM;
+    M->A = A;
+    M->norm_inf = row_norm_inf_const(A);
+    *out = M;
+    return SSTEP_OK;
+}
+
+int stencil_matrix_create_convdiff(sstep_matrix* out, int dim, const int64_t shape[3], const double* beta) {
+    if (!out || !beta || !shape) return SSTEP_ERR_ARG;
+    if (dim != 2 && dim != 3) return SSTEP_ERR_ARG;
+    for (int d = 1; d < dim; ++d)
+        if (shape[d] != shape[0]) return SSTEP_ERR_ARG;
+    const double h = 1.0 / (double)(shape[0] + 1);
+    double coef[7];
+    coef[0] = 2.0 * dim;
+    for (int d = 0; d < dim; ++d) {
+        const double c = beta[d] * h / 2.0;
+        coef[1 + 2 * d] = -1.0 - c;
+        coef[2 + 2 * d] = -1.0 + c;
+    }
+    return stencil_matrix_create(out, dim, shape, coef);
+}
+
+int stencil_matrix_create_fields(sstep_matrix* out, int dim, const int64_t shape[3], const double* const* fields,
+                                 void* stream) {
+    if (!out || !fields) return SSTEP_ERR_ARG;
+    *out = nullptr;
+    StencilDesc A;
+    int rc = make_desc(A, dim, shape);
+    if (rc) return rc;
+    const int nq = 2 * dim + 1;
+    for (int q = 0; q < nq; ++q)
+        if (!fields[q]) return SSTEP_ERR_ARG;
+    sstep_matrix M = new (std::nothrow) sstep_matrix_s;
+    if (!M) return SSTEP_ERR_OOM;
+    if (cudaMalloc((void**)&M->fields, sizeof(double) * A.n * nq) != cudaSuccess) {
+        cudaGetLastError();
+        delete M;
+        return SSTEP_ERR_OOM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int q = 0; q < nq; ++q) {
+        if (cudaMemcpyAsync(M->fields + q * A.n, fields[q], sizeof(double) * A.n, cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess) {
+            cudaFree(M->fields);
+            delete M;
+            return SSTEP_ERR_CUDA;
+        }
+        A.f[q] = M->fields + q * A.n;
+    }
+    A.variable = 1;
+    M->A = A;
+    // ||A||_inf: reduce on the host from a copy (creation-time only)
+    std::vector<double> host((size_t)A.n * nq);
+    if (cudaMemcpyAsync(host.data(), M->fields, sizeof(double) * A.n * nq, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaFree(M->fields);
+        delete M;
+        return SSTEP_ERR_CUDA;
+    }
+    double best = 0.0;
+    for (int64_t p = 0; p < A.n; ++p) {
+        int64_t x = p % A.nx, t = p / A.nx, y = t % A.ny, z = t / A.ny;
+        double r = fabs(host[p]);
+        if (x > 0) r += fabs(host[1 * A.n + p]);
+        if (x < A.nx - 1) r += fabs(host[2 * A.n + p]);
+        if (y > 0) r += fabs(host[3 * A.n + p]);
+        if (y < A.ny - 1) r += fabs(host[4 * A.n + p]);
+        if (dim == 3) {
+            if (z > 0) r += fabs(host[5 * A.n + p]);
+            if (z < A.nz - 1) r += fabs(host[6 * A.n + p]);
+        }
+        best = std::max(best, r);
+    }
+    M->norm_inf = best;
+    *out = M;
+    return SSTEP_OK;
+}
+
+int stencil_matrix_destroy(sstep_matrix M) {
+    if (!M) return SSTEP_ERR_ARG;
+    if (M->fields) cudaFree(M->fields);
+    if (M->ws) cudaFree(M->ws);
+    if (M->hdr) cudaFreeHost(M->hdr);
+    delete M;
+    return SSTEP_OK;
+}
+
+int stencil_matrix_info(sstep_matrix M, int64_t* n, double* norm_inf) {
+    if (!M) return SSTEP_ERR_ARG;
+    if (n) *n = M->A.n;
+    if (norm_inf) *norm_inf = M->norm_inf;
+    return SSTEP_OK;
+}
+
+int stencil_matrix_apply(sstep_matrix M, const double* x, double* y, void* stream) {
+    if (!M || !x || !y) return SSTEP_ERR_ARG;
+    launch_stencil(M->A, x, 1.0, y, 0.0, nullptr, nullptr, nullptr, GATE_NONE, (cudaStream_t)stream);
+    return check_launch();
+}
+
+int sstep_matrix_powers(sstep_matrix M, const double* v, double scale, double sigma, int s, double* Y, int64_t ldy,
+                        void* stream) {
+    if (!M || !v || !Y || s < 1 || s > SSTEP_MAX_S || ldy < M->A.n) return SSTEP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_stencil(M->A, v, sigma * scale, Y + ldy, scale, Y, nullptr, nullptr, GATE_NONE, st);
+    for (int j = 2; j <= s; ++j)
+        launch_stencil(M->A, Y + (j - 1) * ldy, sigma, Y + j * ldy, 0.0, nullptr, nullptr, nullptr, GATE_NONE, st);
+    return check_launch();
+}
+
+int sstep_gram_workspace_size(int64_t n, int ka, int kb, size_t* bytes) {
+    if (!bytes || n < 0 || ka < 1 || ka > SSTEP_MAX_COLS || kb < 1 || kb > SSTEP_MAX_S + 1) return SSTEP_ERR_ARG;
+    *bytes = kAlign + sizeof(double) * (size_t)max_partials_doubles();
+    return SSTEP_OK;
+}
+
+int sstep_gram(int64_t n, const double* V, int64_t ldv, int ka, const double* Y, int64_t ldy, int kb, double* C,
+               int ldc, void* work, size_t work_bytes, void* stream) {
+    size_t need = 0;
+    if (sstep_gram_workspace_size(n, ka, kb, &need)) return SSTEP_ERR_ARG;
+    if (!V || !Y || !C || !work || work_bytes < need || ldv < n || ldy < n || ldc < ka) return SSTEP_ERR_ARG;
+    if (((uintptr_t)work) % kAlign) return SSTEP_ERR_ARG;
+    if (n == 0) return cudaMemsetAsync(C, 0, sizeof(double) * ldc * kb, (cudaStream_t)stream) == cudaSuccess
+                           ? SSTEP_OK
+                           : SSTEP_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc{(double*)((char*)work + kAlign), (unsigned*)work};
+    CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned), st));
+    Epi e;
+    e.mode = EPI_NONE;
+    e.out = C;
+    e.ldo = ldc;
+    launch_gram(n, V, ldv, ka, Y, ldy, kb, 0, sc, e, GATE_NONE, st);
+    return check_launch();
+}
+
+int sstep_block_update(int64_t n, const double* V, int64_t ldv, int ka, double* Y, int64_t ldy, int kb,
+                       const double* T, int ldt, double* Gout, void* work, size_t work_bytes, void* stream) {
+    size_t need = 0;
+    if (sstep_gram_workspace_size(n, 1, kb, &need)) return SSTEP_ERR_ARG;
+    if (ka < 0 || ka > SSTEP_MAX_COLS || !Y || !Gout || !work || work_bytes < need || ldy < n) return SSTEP_ERR_ARG;
+    if (ka > 0 && (!V || !T || ldv < n || ldt < ka)) return SSTEP_ERR_ARG;
+    if (((uintptr_t)work) % kAlign) return SSTEP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) return cudaMemsetAsync(Gout, 0, sizeof(double) * kb * kb, st) == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA;
+    Scratch sc{(double*)((char*)work + kAlign), (unsigned*)work};
+    CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned), st));
+    Epi e;
+    e.mode = EPI_NONE;
+    e.out = Gout;
+    e.ldo = kb;
+    launch_update(n, V, ldv, ka, Y, ldy, Y, ldy, kb, 0, T, ldt, -1.0, true, sc, e, GATE_NONE, st);
+    return check_launch();
+}
+
+// ------------------------------------------------------------------ s-step GMRES (Alg. 4.1 / 4.2)
+int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_params* p, sstep_result* res,
+                      void* stream) {
+    int rc = common_checks(M, f, x, p, res);
+    if (rc) return rc;
+    const int s = p->s, m = p->m;
+    if (s < 1 || s > SSTEP_MAX_S || m < s || m > SSTEP_MAX_M || m % s != 0 || p->max_cycles < 0) return SSTEP_ERR_ARG;
+    cudaStream_t stream_ = (cudaStream_t)stream;
+    const int64_t n = M->A.n, ld = col_ld(n);
+    // columns: U (m+1) and the raw start vector
+    Layout l = plan(n, m + 2, m, p->history ? p->history_cap : 0);
+    if ((rc = ensure_workspace(M, l.total))) return rc;
+    SolverState h = init_state(l, M->ws, p, s, m, 0);
+    h.sigma = p->sigma > 0.0 ? p->sigma : 1.0 / M->norm_inf;
+    SolverState* st = (SolverState*)(M->ws + l.state);
+    double* U = (double*)(M->ws + l.cols);
+    double* uraw = U + (int64_t)(m + 1) * ld;
+    Scratch sc{(double*)(M->ws + l.partials), (unsigned*)(M->ws + l.counter)};
+    CUDA_TRY(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
+    CUDA_TRY(cudaMemsetAsync(M->ws + l.counter, 0, kAlign, stream_));
+    CUDA_TRY(cudaMemsetAsync(M->ws + l.G, 0, sizeof(double) * (m + 1) * m, stream_));
+    Epi e;
+    e.st = st;
+    e.mode = EPI_NF;
+    TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, nullptr, nullptr, sc, e, GATE_NONE, stream_));
+    const double sigma = h.sigma;
+    const int nb = m / s;
+    for (;;) {
+        e = Epi();
+        e.st = st;
+        e.mode = EPI_RESTART;
+        TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, x, uraw, sc, e, GATE_ACTIVE, stream_));
+        for (int k = 0; k < nb; ++k) {
+            const int o = k * s;
+            // Alg. 4.1 step 3: v_k^1 = u / ||u|| and its s scaled powers
+            TRACED(K_STENCIL, stream_, launch_stencil(M->A, uraw, sigma, U + (o + 1) * ld, 1.0, U + o * ld, &st->vscale, st, GATE_BUILDING,
+                           stream_));
+            for (int j = 2; j <= s; ++j)
+                TRACED(K_STENCIL, stream_, launch_stencil(M->A, U + (o + j - 1) * ld, sigma, U + (o + j) * ld, 0.0, nullptr, nullptr, st,
+                               GATE_BUILDING, stream_));
+            if (k > 0) {   // steps 4-5 and Scalar2: inner products with the earlier blocks
+                e = Epi();
+                e.st = st;
+                e.mode = EPI_GM_T;
+                e.o = o;
+                TRACED(K_GRAM, stream_, launch_gram(n, U, ld, o, U + (o + 1) * ld, ld, s, 0, sc, e, GATE_BUILDING, stream_));
+            }
+            // step 7 and Scalar1: project, then Gram of the projected block
+            e = Epi();
+            e.st = st;
+            e.mode = EPI_GM_W;
+            e.o = o;
+            TRACED(K_UPDATE, stream_, launch_update(n, U, ld, o, U + o * ld, ld, U + o * ld, ld, s + 1, 1, h.T, m, -1.0, true, sc, e,
+                          GATE_BUILDING, stream_));
+            // step 2: the next start vector u = z - V_k S and its norm; G, Givens
+            e = Epi();
+            e.st = st;
+            e.mode = EPI_GM_NU;
+            e.o = o;
+            e.lastblock = (k == nb - 1);
+            TRACED(K_NEXT, stream_, launch_update(n, U + o * ld, ld, s, U + (o + s) * ld, ld, uraw, ld, 1, 0, h.S, s, -1.0, true, sc, e,
+                          GATE_BUILDING, stream_));
+        }
+        // Alg. 4.2 step 3: x = x0 + V y
+        TRACED(K_LSQ, stream_, launch_lsq_solve(st, GATE_ACTIVE, stream_));
+        e = Epi();
+        e.st = st;
+        TRACED(K_AXPY, stream_, launch_update(n, U, ld, -1, x, n, x, n, 1, 0, nullptr, 0, 1.0, false, sc, e, GATE_ACTIVE, stream_));
+        CUDA_TRY(cudaGetLastError());
+        if ((rc = read_header(M, st, stream_))) return rc;
+        if (!M->hdr->active) break;
+    }
+    return finish(M, l, st, f, x, p, res, stream_);
+}
+
+// ------------------------------------------------------------------ GMRES(m), Alg. 2.2
+int gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_params* p, sstep_result* res, void* stream) {
+    int rc = common_checks(M, f, x, p, res);
+    if (rc) return rc;
+    const int m = p->m;
+    if (m < 1 || m > SSTEP_MAX_M || p->max_cycles < 0) return SSTEP_ERR_ARG;
+    cudaStream_t stream_ = (cudaStream_t)stream;
+    const int64_t n = M->A.n, ld = col_ld(n);
+    Layout l = plan(n, m + 3, m, p->history ? p->history_cap : 0);
+    if ((rc = ensure_workspace(M, l.total))) return rc;
+    SolverState h = init_state(l, M->ws, p, 1, m, 0);
+    h.sigma = 1.0;
+    SolverState* st = (SolverState*)(M->ws + l.state);
+    double* U = (double*)(M->ws + l.cols);
+    double* wraw = U + (int64_t)(m + 1) * ld;
+    double* ybuf = wraw + ld;
+    Scratch sc{(double*)(M->ws + l.partials), (unsigned*)(M->ws + l.counter)};
+    CUDA_TRY(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
+    CUDA_TRY(cudaMemsetAsync(M->ws + l.counter, 0, kAlign, stream_));
+    CUDA_TRY(cudaMemsetAsync(M->ws + l.G, 0, sizeof(double) * (m + 1) * m, stream_));
+    Epi e;
+    e.st = st;
+    e.mode = EPI_NF;
+    TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, nullptr, nullptr, sc, e, GATE_NONE, stream_));
+    for (;;) {
+        e = Epi();
+        e.st = st;
+        e.mode = EPI_RESTART;
+        TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, x, wraw, sc, e, GATE_ACTIVE, stream_));
+        for (int j = 0; j < m; ++j) {
+            // step 4 of the previous step (q_j = q^_j / h) fused with A q_j
+            TRACED(K_STENCIL, stream_, launch_stencil(M->A, wraw, 1.0, ybuf, 1.0, U + j * ld, &st->vscale, st, GATE_BUILDING, stream_));
+            e = Epi();
+            e.st = st;
+            e.mode = EPI_ST_H;
+            e.o = j;
+            TRACED(K_GRAM, stream_, launch_gram(n, U, ld, j + 1, ybuf, ld, 1, 0, sc, e, GATE_BUILDING, stream_));   // step 1
+            e = Epi();
+            e.st = st;
+            e.mode = EPI_ST_NORM;
+            e.o = j;
+            e.lastblock = (j == m - 1);
+            TRACED(K_UPDATE, stream_, launch_update(n, U, ld, j + 1, ybuf, ld, wraw, ld, 1, 0, h.G + (int64_t)j * (m + 1), m + 1, -1.0, true,
+                          sc, e, GATE_BUILDING, stream_));   // steps 2-3
+        }
+        TRACED(K_LSQ, stream_, launch_lsq_solve(st, GATE_ACTIVE, stream_));
+        e = Epi();
+        e.st = st;
+        TRACED(K_AXPY, stream_, launch_update(n, U, ld, -1, x, n, x, n, 1, 0, nullptr, 0, 1.0, false, sc, e, GATE_ACTIVE, stream_));
+        CUDA_TRY(cudaGetLastError());
+        if ((rc = read_header(M, st, stream_))) return rc;
+        if (!M->hdr->active) break;
+    }
+    return finish(M, l, st, f, x, p, res, stream_);
+}
+
+// ------------------------------------------------------------------ s-step Orthomin(k), Alg. 3.1
+int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_params* p, sstep_result* res,
+                     void* stream) {
+    int rc = common_checks(M, f, x, p, res);
+    if (rc) return rc;
+    const int s = p->s, k = p->k;
+    if (s < 1 || s > SSTEP_MAX_S || k < 0 || (int64_t)k * s > SSTEP_MAX_COLS || p->max_iters < 0) return SSTEP_ERR_ARG;
+    cudaStream_t stream_ = (cudaStream_t)stream;
+    const int64_t n = M->A.n, ld = col_ld(n);
+    const int keep = std::max(k, 1);
+    const int nslots = keep + 1;
+    // columns: P and AP panels (nslots*s each), AR (s), r (1)
+    Layout l = plan(n, 2 * nslots * s + s + 1, 1, p->history ? p->history_cap : 0);
+    if ((rc = ensure_workspace(M, l.total))) return rc;
+    SolverState h = init_state(l, M->ws, p, s, 1, k);
+    h.sigma = p->sigma > 0.0 ? p->sigma : 1.0 / M->norm_inf;
+    SolverState* st = (SolverState*)(M->ws + l.state);
+    double* Ppanel = (double*)(M->ws + l.cols);
+    double* APpanel = Ppanel + (int64_t)nslots * s * ld;
+    double* AR = APpanel + (int64_t)nslots * s * ld;
+    double* r = AR + (int64_t)s * ld;
+    Scratch sc{(double*)(M->ws + l.partials), (unsigned*)(M->ws + l.counter)};
+    CUDA_TRY(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
+    CUDA_TRY(cudaMemsetAsync(M->ws + l.counter, 0, kAlign, stream_));
+    Epi e;
+    e.st = st;
+    e.mode = EPI_NF;
+    TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, nullptr, nullptr, sc, e, GATE_NONE, stream_));
+    const double sigma = h.sigma;
+    auto powers = [&]() {   // A R_{i+1}: A r, then A (sigma A R_j)
+        TRACED(K_STENCIL, stream_, launch_stencil(M->A, r, 1.0, AR, 0.0, nullptr, nullptr, st, GATE_BUILDING, stream_));
+        for (int j = 1; j < s; ++j)
+            TRACED(K_STENCIL, stream_, launch_stencil(M->A, AR + (j - 1) * ld, sigma, AR + j * ld, 0.0, nullptr, nullptr, st, GATE_BUILDING,
+                           stream_));
+    };
+    std::vector<int> ring;
+    bool restart = true;
+    const int batch = 8;
+    for (;;) {
+        if (restart) {
+            e = Epi();
+            e.st = st;
+            e.mode = EPI_OM_RESTART;
+            TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, x, r, sc, e, GATE_ACTIVE, stream_));
+            powers();   // R_0, A R_0; P_0 = R_0
+            e = Epi();
+            e.st = st;
+            e.mode = EPI_OM_W;
+            e.slot = 0;
+            e.nwin = 0;
+            TRACED(K_OMIN_PUPDATE, stream_, launch_omin_pupdate(n, r, AR, Ppanel, APpanel, ld, s, sigma, sc, e, GATE_BUILDING, stream_));
+            ring.assign(1, 0);
+            restart = false;
+        }
+        for (int b = 0; b < batch; ++b) {
+            const int cur = ring.back();
+            e = Epi();
+            e.st = st;
+            e.mode = EPI_OM_R;
+            TRACED(K_OMIN_XR, stream_, launch_omin_xr(n, Ppanel + (int64_t)cur * s * ld, APpanel + (int64_t)cur * s * ld, ld, s, x, r, sc, e,
+                           GATE_BUILDING, stream_));   // steps 3-4
+            powers();                                 // step 5
+            const int nwin = std::min<int>(k, (int)ring.size());
+            Epi w;
+            w.st = st;
+            w.nwin = nwin;
+            for (int i = 0; i < nwin; ++i) w.win[i] = ring[ring.size() - nwin + i];
+            if (nwin > 0) {   // steps 6-7
+                w.mode = EPI_OM_B;
+                TRACED(K_GRAM, stream_, launch_gram(n, APpanel, ld, nwin * s, AR, ld, s, s, sc, w, GATE_BUILDING, stream_));
+            }
+            int nslot = 0;
+            while (std::find(ring.begin(), ring.end(), nslot) != ring.end()) ++nslot;
+            w.mode = EPI_OM_W;   // steps 8-9 and the next step's 1-2
+            w.slot = nslot;
+            TRACED(K_OMIN_PUPDATE, stream_, launch_omin_pupdate(n, r, AR, Ppanel, APpanel, ld, s, sigma, sc, w, GATE_BUILDING, stream_));
+            ring.push_back(nslot);
+            if ((int)ring.size() > keep) ring.erase(ring.begin());
+        }
+        CUDA_TRY(cudaGetLastError());
+        if ((rc = read_header(M, st, stream_))) return rc;
+        if (!M->hdr->active) break;
+        if (M->hdr->confirm) restart = true;
+    }
+    return finish(M, l, st, f, x, p, res, stream_);
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// Kernel declarations and launch-argument structs of the FP64 path.
+#pragma once
+
+#include "common.cuh"
+
+namespace sstep {
+
+// What the last CTA of a reduction does with the reduced values.
+enum EpiMode : int {
+    EPI_NONE = 0,       // write the reduced matrix to `out` only
+    EPI_NF,             // ||f||^2 -> st->nf
+    EPI_FINAL,          // ||f - A x||^2 -> st->relres (no decisions)
+    EPI_RESTART,        // GMRES restart (Alg. 4.2 step 5 / Alg. 2.2 start)
+    EPI_GM_T,           // s-step GMRES Scalar2: T_i = W_i^{-1} C_i
+    EPI_GM_W,           // s-step GMRES Scalar1: W_k = L^T L, S = W_k^{-1} V_k^T z
+    EPI_GM_NU,          // s-step GMRES: nu, columns of G (eq. 4-5), Givens on L G (eq. 9)
+    EPI_ST_H,           // GMRES: h_{i,j} (Alg. 2.2 step 1)
+    EPI_ST_NORM,        // GMRES: h_{j+1,j} (step 3), Givens (eq. 2)
+    EPI_OM_RESTART,     // Orthomin: explicit residual at a (re)start
+    EPI_OM_R,           // Orthomin: updated residual after step 4
+    EPI_OM_B,           // Orthomin Scalar2: B_j = -W_j^{-1} C_j
+    EPI_OM_W            // Orthomin Scalar1: W_{i+1} = L^T L, a = W^{-1} m
+};
+
+// Kernels run only while a flag of the solver state is set.
+enum Gate : int { GATE_NONE = 0, GATE_ACTIVE = 1, GATE_BUILDING = 2 };
+
+struct Epi {
+    int mode = EPI_NONE;
+    SolverState* st = nullptr;
+    double* out = nullptr;   // EPI_NONE: reduced result (column-major, ld = ldo)
+    int ldo = 0;
+    int o = 0;               // GMRES: first column of the block / step index j
+    int lastblock = 0;       // GMRES: this block or step ends the cycle
+    int slot = 0;            // Orthomin: slot of the new direction block
+    int nwin = 0;            // Orthomin: blocks in the window
+    int win[kMaxCols];       // Orthomin: window slots, oldest first
+};
+
+struct Scratch {
+    double* partials;        // per-CTA partial results
+    unsigned* counter;       // arrival counter (zero between launches)
+};
+
+__device__ __forceinline__ bool gate_open(const SolverState* st, int gate) {
+    if (gate == GATE_NONE) return true;
+    if (gate == GATE_ACTIVE) return ((volatile const int*)st)[0] != 0;
+    return ((volatile const int*)st)[1] != 0;
+}
+
+// ------------------------------------------------------------------ launchers (kernels.cu)
+// y = fy * (A v), w = fw * v (if w); fy and fw are multiplied by *dscale when dscale is set.
+void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y, double fw, double* w,
+                    const double* dscale, const SolverState* st, int gate, cudaStream_t stream);
+
+// r = f - A x (x may be null: r = f); out (may be null) receives r; reduces ||r||^2.
+void launch_residual(const StencilDesc& A, const double* f, const double* x, double* out, Scratch sc,
+                     const Epi& epi, int gate, cudaStream_t stream);
+
+// C = V^T Y (ka x kb), V columns at V + i*ldv (win_s > 0: blocks of win_s columns at
+// the panel slots epi.win[]), Y columns at Y + j*ldy.
+void launch_gram(int64_t n, const double* V, int64_t ldv, int ka, const double* Y, int64_t ldy, int kb,
+                 int win_s, Scratch sc, const Epi& epi, int gate, cudaStream_t stream);
+
+// Yout[:, j] = Yin[:, j] + sgn * V T[:, j] for j >= j0 (columns j < j0 copied as is only
+// when Yout != Yin); with gram, reduces Yout^T Yout (kb x kb). ka < 0: ka = st->K and
+// T = st->y (the least-squares solution).
+void launch_update(int64_t n, const double* V, int64_t ldv, int ka, const double* Yin, int64_t ldy,
+                   double* Yout, int64_t ldo, int kb, int j0, const double* T, int ldt, double sgn,
+                   bool gram, Scratch sc, const Epi& epi, int gate, cudaStream_t stream);
+
+// Orthomin: x += P a, r -= AP a (a = st->a), reduces ||r||^2.
+void launch_omin_xr(int64_t n, const double* P, const double* AP, int64_t ld, int s, double* x, double* r,
+                    Scratch sc, const Epi& epi, int gate, cudaStream_t stream);
+
+// Orthomin: P_new = R + sum_w P_w B_w, AP_new = AR + sum_w AP_w B_w with R = [r, sigma AR_1..];
+// reduces W = AP_new^T AP_new and m = AP_new^T r.
+void launch_omin_pupdate(int64_t n, const double* r, const double* AR, const double* Ppanel,
+                         const double* APpanel, int64_t ld, int s, double sigma, Scratch sc, const Epi& epi,
+                         int gate, cudaStream_t stream);
+
+// One CTA: y = R^{-1} g over the first st->K columns (back substitution).
+void launch_lsq_solve(SolverState* st, int gate, cudaStream_t stream);
+
+int max_partials_doubles();
+
+}  // namespace sstep

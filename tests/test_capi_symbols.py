@@ -1,0 +1,53 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared entry point."""
+import os
+import re
+
+import pytest
+
+import __graft_entry__ as entry
+import paper_2001_04886_gb300 as pkg
+from paper_2001_04886_gb300 import _binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "sstep.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_parses():
+    names = declared_functions()
+    assert "sstep_gmres_solve" in names and "stencil_matrix_create" in names and len(names) >= 13
+
+
+def test_library_exports_every_declared_symbol():
+    entry.build()
+    L = pkg.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+        assert name in _binding.SIGNATURES, name
+
+
+def test_status_strings_and_argument_errors_without_gpu():
+    L = pkg.lib()
+    assert L.sstep_status_string(-4).decode().startswith("breakdown")
+    # argument validation happens before any CUDA call
+    import ctypes
+
+    h = ctypes.c_void_p()
+    shp = (ctypes.c_int64 * 3)(8, 8, 1)
+    assert L.stencil_matrix_create(ctypes.byref(h), 4, shp, (ctypes.c_double * 7)()) == -1
+    b = ctypes.c_size_t()
+    assert L.sstep_gram_workspace_size(100, 0, 1, ctypes.byref(b)) == -1
+    assert L.sstep_gram_workspace_size(100, 4, 5, ctypes.byref(b)) == 0 and b.value > 0
+
+
+def test_params_struct_layout_matches_header():
+    # sstep_params: int s, m, k; double tol; int max_cycles, max_iters; double sigma; double* history; int cap
+    import ctypes
+
+    P = _binding.SStepParams
+    assert P.tol.offset == 16 and P.sigma.offset == 32 and P.history.offset == 40
+    assert ctypes.sizeof(_binding.SStepResult) == 32
