@@ -96,6 +96,23 @@ int sstep_gram_workspace_size(int64_t n, int ka, int kb, size_t* bytes);
 int sstep_gram(int64_t n, const double* V, int64_t ldv, int ka, const double* Y, int64_t ldy, int kb,
                double* C, int ldc, void* work, size_t work_bytes, void* stream);
 
+/* The same Gram pass as sstep_gram, for callers that cannot allocate device
+ * memory when they call it: code running while a stream is captured into a CUDA
+ * graph, applications that fix their device-memory budget at start-up, or plug-in
+ * hosts whose allocator owns all device memory. The paper has no counterpart; this
+ * is a property of the library's interface, not of the method.
+ *   - Allocates nothing: the scratch is a fixed 700,672-byte array in the library's
+ *     device image, present on every GPU that loads the library until the process
+ *     exits. ka <= SSTEP_MAX_COLS and kb <= SSTEP_MAX_S + 1, else SSTEP_ERR_ARG.
+ *   - The first call on each device looks up the array's device address (with that
+ *     device current); make that first call before any stream capture begins.
+ *   - Every call shares the one array per device, and its contents persist between
+ *     calls: calls whose executions overlap on the GPU (other streams, other host
+ *     threads) race and give wrong results. Serialise them on one stream.
+ * Arguments and results as for sstep_gram. */
+int sstep_gram_noalloc(int64_t n, const double* V, int64_t ldv, int ka, const double* Y, int64_t ldy, int kb,
+                       double* C, int ldc, void* stream);
+
 /* Block update (Alg. 4.1 step 7 with Scalar1's Gram; Alg. 3.1 steps 8-9 shape):
  *   Y <- Y - V T  (in place; V: n x ka, T: ka x kb column-major device, ldt >= ka),
  *   then Gout = Y^T Y (kb x kb, column-major, device) over the updated Y.

@@ -40,6 +40,8 @@ SIGNATURES = {
     "sstep_gram_workspace_size": (c_int, [c_int64, c_int, c_int, P(c_size_t)]),
     "sstep_gram": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
                            c_void_p, c_size_t, c_void_p]),
+    "sstep_gram_noalloc": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
+                                   c_void_p]),
     "sstep_block_update": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
                                    c_void_p, c_void_p, c_size_t, c_void_p]),
     "sstep_gmres_solve": (c_int, [c_void_p, c_void_p, c_void_p, P(SStepParams), P(SStepResult), c_void_p]),
