@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--s", type=int, default=8, help="block size of the headline s-step GMRES")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32"],
+                    help="basis precision of the headline solve")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -246,10 +248,12 @@ def main():
     s = args.s
 
     def solve(xv, method="sstep", **kw):
+        prec = kw.get("precision", "fp64")
         if method == "sstep":
-            return pkg.sstep_gmres_solve(A, f, xv, kw.get("s", s), M, TOL, max_cycles=200, history_cap=8192)
+            return pkg.sstep_gmres_solve(A, f, xv, kw.get("s", s), M, TOL, max_cycles=200, history_cap=8192,
+                                         precision=kw.get("precision", args.precision))
         if method == "gmres":
-            return pkg.gmres_solve(A, f, xv, M, TOL, max_cycles=200, history_cap=8192)
+            return pkg.gmres_solve(A, f, xv, M, TOL, max_cycles=200, history_cap=8192, precision=prec)
         return pkg.sstep_omin_solve(A, f, xv, kw["s"], kw["k"], TOL, max_iters=20000, history_cap=8192)
 
     for _ in range(max(args.warmup, 3)):
@@ -310,7 +314,7 @@ def main():
     for _ in range(args.steps):
         f_d.copy_(f_h, non_blocking=True)
         x.copy_(x_h, non_blocking=True)
-        r2 = pkg.sstep_gmres_solve(A, f_d, x, s, M, TOL, max_cycles=200, history_cap=0)
+        r2 = pkg.sstep_gmres_solve(A, f_d, x, s, M, TOL, max_cycles=200, history_cap=0, precision=args.precision)
         out_h.copy_(x, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -322,7 +326,11 @@ def main():
         for name, kw in [("sstep_gmres_s2", dict(method="sstep", s=2)), ("sstep_gmres_s4", dict(method="sstep", s=4)),
                          ("sstep_gmres_s8", dict(method="sstep", s=8)), ("gmres", dict(method="gmres")),
                          ("sstep_omin_s4_k1", dict(method="omin", s=4, k=1)),
-                         ("omin_k1", dict(method="omin", s=1, k=1)), ("omin_k7", dict(method="omin", s=1, k=7))]:
+                         ("omin_k1", dict(method="omin", s=1, k=1)), ("omin_k7", dict(method="omin", s=1, k=7)),
+                         ("df64_sstep_gmres_s4", dict(method="sstep", s=4, precision="df64")),
+                         ("df64_sstep_gmres_s8", dict(method="sstep", s=8, precision="df64")),
+                         ("df64_gmres", dict(method="gmres", precision="df64")),
+                         ("fp32ir_sstep_gmres_s8", dict(method="sstep", s=8, precision="fp32"))]:
             x.zero_()
             solve(x, **kw)                                  # warm the workspace
             torch.cuda.synchronize()
@@ -335,6 +343,30 @@ def main():
             torch.cuda.synchronize()
             variants[name] = {"ms": e0.elapsed_time(e1) / reps, "status": rv["status"], "cycles": rv["cycles"],
                               "iters": rv["iters"], "matvecs": rv["matvecs"], "relres": rv["relres"]}
+
+    if not args.no_variants:
+        # the precision form: 3-D 256^3, beta = (50, 0, 0), s = 8, m = 32, to 1e-10; FP32
+        # iterative refinement against the all-FP64 s-step solve
+        A3 = pkg.StencilMatrix(3, (256, 256, 256), beta=(50.0, 0.0, 0.0))
+        xt3 = torch.tensor(inputs.x_true(rank, A3.n), dtype=torch.float64, device=dev)
+        f3 = torch.empty_like(xt3)
+        A3.apply(xt3, f3)
+        x3 = torch.zeros_like(f3)
+        form = {}
+        for prec in ("fp32", "df64", "fp64"):
+            x3.zero_()
+            pkg.sstep_gmres_solve(A3, f3, x3, 8, 32, 1e-10, max_cycles=400, history_cap=0, precision=prec)
+            x3.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            r3 = pkg.sstep_gmres_solve(A3, f3, x3, 8, 32, 1e-10, max_cycles=400, history_cap=0, precision=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            form[prec] = {"ms": e0.elapsed_time(e1), "status": r3["status"], "cycles": r3["cycles"],
+                          "matvecs": r3["matvecs"], "relres": r3["relres"],
+                          "x_err_vs_x_true": float((x3 - xt3).norm() / xt3.norm())}
+        variants["precision_form_256cube_s8_m32_tol1e-10"] = form
+        del A3, xt3, f3, x3
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

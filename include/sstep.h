@@ -135,7 +135,17 @@ typedef struct {
     double sigma;       /* basis scale of the monomial powers; 0 => 1 / ||A||_inf */
     double* history;    /* HOST array receiving the residual history, or NULL */
     int history_cap;    /* capacity of history */
+    int precision;      /* storage/arithmetic of the Krylov basis (GMRES solvers; Orthomin: FP64 only):
+                           SSTEP_PREC_FP64: FP64;
+                           SSTEP_PREC_DF64: double-float pairs (48-bit significand) on the FP32 pipe;
+                           SSTEP_PREC_FP32: FP32 basis and powers, inner products accumulated in
+                           double-float; with the FP64 restart residual this is FP32 iterative
+                           refinement. f, x, residuals and all scalar work are FP64 in every mode. */
 } sstep_params;
+
+#define SSTEP_PREC_FP64 0
+#define SSTEP_PREC_DF64 1
+#define SSTEP_PREC_FP32 2
 
 typedef struct {
     int status;         /* sstep_status of the solve */

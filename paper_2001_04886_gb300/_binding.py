@@ -20,7 +20,11 @@ P = ctypes.POINTER
 
 class SStepParams(ctypes.Structure):
     _fields_ = [("s", c_int), ("m", c_int), ("k", c_int), ("tol", c_double), ("max_cycles", c_int),
-                ("max_iters", c_int), ("sigma", c_double), ("history", P(c_double)), ("history_cap", c_int)]
+                ("max_iters", c_int), ("sigma", c_double), ("history", P(c_double)), ("history_cap", c_int),
+                ("precision", c_int)]
+
+
+PRECISIONS = {"fp64": 0, "df64": 1, "fp32": 2}
 
 
 class SStepResult(ctypes.Structure):
@@ -232,13 +236,13 @@ def sstep_block_update(V, Y, T, work=None, stream=None):
 
 
 def _solve(name, A, f, x, s=1, m=20, k=1, tol=1e-8, max_cycles=1000, max_iters=100000, sigma=0.0,
-           history_cap=4096, stream=None):
+           history_cap=4096, stream=None, precision="fp64"):
     import numpy as np
 
     hist = np.zeros(max(history_cap, 1), dtype=np.float64)
     p = SStepParams(s=s, m=m, k=k, tol=tol, max_cycles=max_cycles, max_iters=max_iters, sigma=sigma,
                     history=hist.ctypes.data_as(P(c_double)) if history_cap > 0 else None,
-                    history_cap=history_cap)
+                    history_cap=history_cap, precision=PRECISIONS[precision])
     r = SStepResult()
     rc = getattr(lib(), name)(A.handle, _ptr(f), _ptr(x), ctypes.byref(p), ctypes.byref(r), _stream(stream))
     _check(name, rc)
@@ -246,16 +250,20 @@ def _solve(name, A, f, x, s=1, m=20, k=1, tol=1e-8, max_cycles=1000, max_iters=1
                 history=hist[: r.history_len].tolist())
 
 
-def sstep_gmres_solve(A, f, x, s, m, tol, max_cycles=1000, sigma=0.0, history_cap=4096, stream=None):
-    """s-step GMRES (Alg. 4.1/4.2); x is updated in place. Returns the result as a dict."""
+def sstep_gmres_solve(A, f, x, s, m, tol, max_cycles=1000, sigma=0.0, history_cap=4096, stream=None,
+                      precision="fp64"):
+    """s-step GMRES (Alg. 4.1/4.2); x is updated in place. Returns the result as a dict.
+
+    precision: "fp64", "df64" (double-float basis) or "fp32" (FP32 basis, FP32 iterative refinement).
+    """
     return _solve("sstep_gmres_solve", A, f, x, s=s, m=m, tol=tol, max_cycles=max_cycles, sigma=sigma,
-                  history_cap=history_cap, stream=stream)
+                  history_cap=history_cap, stream=stream, precision=precision)
 
 
-def gmres_solve(A, f, x, m, tol, max_cycles=1000, history_cap=4096, stream=None):
+def gmres_solve(A, f, x, m, tol, max_cycles=1000, history_cap=4096, stream=None, precision="fp64"):
     """Standard GMRES(m) with classical Gram-Schmidt (Alg. 2.2)."""
     return _solve("gmres_solve", A, f, x, m=m, tol=tol, max_cycles=max_cycles, history_cap=history_cap,
-                  stream=stream)
+                  stream=stream, precision=precision)
 
 
 def sstep_omin_solve(A, f, x, s, k, tol, max_iters=100000, sigma=0.0, history_cap=4096, stream=None):

@@ -20,6 +20,7 @@ struct sstep_matrix_s {
     StencilDesc A;
     double norm_inf = 0.0;
     double* fields = nullptr;        // owned copies of variable coefficients (7 x n)
+    float2* fields_df = nullptr;     // the same as float pairs (mixed-precision kernels)
     // solver workspace, grown on demand
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -110,6 +111,14 @@ double row_norm_inf_const(const StencilDesc& A) {
     return t;
 }
 
+// hi = c rounded to float, lo = the rest rounded to float: c = hi + lo to ~48 bits
+void split_coefficients(StencilDesc& A) {
+    for (int q = 0; q < 7; ++q) {
+        A.ch[q] = (float)A.c[q];
+        A.cl[q] = (float)(A.c[q] - (double)A.ch[q]);
+    }
+}
+
 int make_desc(StencilDesc& A, int dim, const int64_t shape[3]) {
     if (dim != 2 && dim != 3) return SSTEP_ERR_ARG;
     if (!shape) return SSTEP_ERR_ARG;
@@ -132,7 +141,7 @@ struct Layout {
     size_t total;
 };
 
-Layout plan(int64_t n, int ncols, int m, int hist_cap) {
+Layout plan(int64_t n, int ncols, int m, int hist_cap, size_t elem_bytes = sizeof(double)) {
     Layout l;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -156,7 +165,7 @@ Layout plan(int64_t n, int ncols, int m, int hist_cap) {
     l.a = take(sizeof(double) * kMaxCols);
     l.counter = take(kAlign);
     l.partials = take(sizeof(double) * (size_t)max_partials_doubles());
-    l.cols = take(sizeof(double) * (size_t)col_ld(n) * ncols);
+    l.cols = take(elem_bytes * (size_t)col_ld(n) * ncols);
     l.total = off;
     return l;
 }
@@ -250,6 +259,137 @@ int read_header(sstep_matrix M, SolverState* st, cudaStream_t stream) {
     return SSTEP_OK;
 }
 
+
+// ------------------------------------------------------------------ mixed-precision basis drivers
+// The same kernel sequences as the FP64 drivers below, with the basis columns in
+// the storage type of P (double-float pairs or FP32); f, x and all scalar work FP64.
+template <int P>
+int sstep_gmres_mp(sstep_matrix M, const double* f, double* x, const sstep_params* p, sstep_result* res,
+                   cudaStream_t stream_) {
+    int rc;
+    const int s = p->s, m = p->m;
+    const int64_t n = M->A.n, ld = col_ld(n);
+    const size_t eb = prec_bytes(P);
+    Layout l = plan(n, m + 2, m, p->history ? p->history_cap : 0, eb);
+    if ((rc = ensure_workspace(M, l.total))) return rc;
+    SolverState h = init_state(l, M->ws, p, s, m, 0);
+    h.sigma = p->sigma > 0.0 ? p->sigma : 1.0 / M->norm_inf;
+    SolverState* st = (SolverState*)(M->ws + l.state);
+    char* U = M->ws + l.cols;
+    auto col = [&](int j) { return (void*)(U + (size_t)j * ld * eb); };
+    void* uraw = col(m + 1);
+    Scratch sc{(double*)(M->ws + l.partials), (unsigned*)(M->ws + l.counter)};
+    CUDA_TRY(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
+    CUDA_TRY(cudaMemsetAsync(M->ws + l.counter, 0, kAlign, stream_));
+    CUDA_TRY(cudaMemsetAsync(M->ws + l.G, 0, sizeof(double) * (m + 1) * m, stream_));
+    Epi e;
+    e.st = st;
+    e.mode = EPI_NF;
+    TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, nullptr, nullptr, sc, e, GATE_NONE, stream_));
+    const double sigma = h.sigma;
+    const int nb = m / s;
+    for (;;) {
+        e = Epi();
+        e.st = st;
+        e.mode = EPI_RESTART;
+        TRACED(K_RESIDUAL, stream_, mp_launch_residual<P>(M->A, f, x, uraw, sc, e, GATE_ACTIVE, stream_));
+        for (int k = 0; k < nb; ++k) {
+            const int o = k * s;
+            TRACED(K_STENCIL, stream_, mp_launch_stencil<P>(M->A, uraw, sigma, col(o + 1), 1.0, col(o), &st->vscale,
+                                                            st, GATE_BUILDING, stream_));
+            for (int j = 2; j <= s; ++j)
+                TRACED(K_STENCIL, stream_, mp_launch_stencil<P>(M->A, col(o + j - 1), sigma, col(o + j), 0.0, nullptr,
+                                                                nullptr, st, GATE_BUILDING, stream_));
+            if (k > 0) {
+                e = Epi();
+                e.st = st;
+                e.mode = EPI_GM_T;
+                e.o = o;
+                TRACED(K_GRAM, stream_, mp_launch_gram<P>(n, col(0), ld, o, col(o + 1), ld, s, sc, e, GATE_BUILDING,
+                                                          stream_));
+            }
+            e = Epi();
+            e.st = st;
+            e.mode = EPI_GM_W;
+            e.o = o;
+            TRACED(K_UPDATE, stream_, mp_launch_update<P>(n, col(0), ld, o, col(o), ld, col(o), ld, s + 1, 1, h.T, m,
+                                                          -1.0, true, sc, e, GATE_BUILDING, stream_));
+            e = Epi();
+            e.st = st;
+            e.mode = EPI_GM_NU;
+            e.o = o;
+            e.lastblock = (k == nb - 1);
+            TRACED(K_NEXT, stream_, mp_launch_update<P>(n, col(o), ld, s, col(o + s), ld, uraw, ld, 1, 0, h.S, s, -1.0,
+                                                        true, sc, e, GATE_BUILDING, stream_));
+        }
+        TRACED(K_LSQ, stream_, launch_lsq_solve(st, GATE_ACTIVE, stream_));
+        e = Epi();
+        e.st = st;
+        TRACED(K_AXPY, stream_, mp_launch_axpy<P>(n, col(0), ld, x, e, GATE_ACTIVE, stream_));
+        CUDA_TRY(cudaGetLastError());
+        if ((rc = read_header(M, st, stream_))) return rc;
+        if (!M->hdr->active) break;
+    }
+    return finish(M, l, st, f, x, p, res, stream_);
+}
+
+template <int P>
+int gmres_mp(sstep_matrix M, const double* f, double* x, const sstep_params* p, sstep_result* res,
+             cudaStream_t stream_) {
+    int rc;
+    const int m = p->m;
+    const int64_t n = M->A.n, ld = col_ld(n);
+    const size_t eb = prec_bytes(P);
+    Layout l = plan(n, m + 3, m, p->history ? p->history_cap : 0, eb);
+    if ((rc = ensure_workspace(M, l.total))) return rc;
+    SolverState h = init_state(l, M->ws, p, 1, m, 0);
+    h.sigma = 1.0;
+    SolverState* st = (SolverState*)(M->ws + l.state);
+    char* U = M->ws + l.cols;
+    auto col = [&](int j) { return (void*)(U + (size_t)j * ld * eb); };
+    void* wraw = col(m + 1);
+    void* ybuf = col(m + 2);
+    Scratch sc{(double*)(M->ws + l.partials), (unsigned*)(M->ws + l.counter)};
+    CUDA_TRY(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
+    CUDA_TRY(cudaMemsetAsync(M->ws + l.counter, 0, kAlign, stream_));
+    CUDA_TRY(cudaMemsetAsync(M->ws + l.G, 0, sizeof(double) * (m + 1) * m, stream_));
+    Epi e;
+    e.st = st;
+    e.mode = EPI_NF;
+    TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, nullptr, nullptr, sc, e, GATE_NONE, stream_));
+    for (;;) {
+        e = Epi();
+        e.st = st;
+        e.mode = EPI_RESTART;
+        TRACED(K_RESIDUAL, stream_, mp_launch_residual<P>(M->A, f, x, wraw, sc, e, GATE_ACTIVE, stream_));
+        for (int j = 0; j < m; ++j) {
+            TRACED(K_STENCIL, stream_, mp_launch_stencil<P>(M->A, wraw, 1.0, ybuf, 1.0, col(j), &st->vscale, st,
+                                                            GATE_BUILDING, stream_));
+            e = Epi();
+            e.st = st;
+            e.mode = EPI_ST_H;
+            e.o = j;
+            TRACED(K_GRAM, stream_, mp_launch_gram<P>(n, col(0), ld, j + 1, ybuf, ld, 1, sc, e, GATE_BUILDING, stream_));
+            e = Epi();
+            e.st = st;
+            e.mode = EPI_ST_NORM;
+            e.o = j;
+            e.lastblock = (j == m - 1);
+            TRACED(K_UPDATE, stream_, mp_launch_update<P>(n, col(0), ld, j + 1, ybuf, ld, wraw, ld, 1, 0,
+                                                          h.G + (int64_t)j * (m + 1), m + 1, -1.0, true, sc, e,
+                                                          GATE_BUILDING, stream_));
+        }
+        TRACED(K_LSQ, stream_, launch_lsq_solve(st, GATE_ACTIVE, stream_));
+        e = Epi();
+        e.st = st;
+        TRACED(K_AXPY, stream_, mp_launch_axpy<P>(n, col(0), ld, x, e, GATE_ACTIVE, stream_));
+        CUDA_TRY(cudaGetLastError());
+        if ((rc = read_header(M, st, stream_))) return rc;
+        if (!M->hdr->active) break;
+    }
+    return finish(M, l, st, f, x, p, res, stream_);
+}
+
 }  // namespace
 
 extern "C" {
@@ -299,6 +439,7 @@ int stencil_matrix_create(sstep_matrix* out, int dim, const int64_t shape[3], co
         if (!isfinite(coef[q])) return SSTEP_ERR_ARG;
         A.c[q] = coef[q];
     }
+    split_coefficients(A);
     sstep_matrix M = new (std::nothrow) sstep_matrix_s;
     if (!M) return SSTEP_ERR_OOM;
     M->A = A;
@@ -351,6 +492,17 @@ int stencil_matrix_create_fields(sstep_matrix* out, int dim, const int64_t shape
         A.f[q] = M->fields + q * A.n;
     }
     A.variable = 1;
+    if (cudaMalloc((void**)&M->fields_df, sizeof(float2) * A.n * nq) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(M->fields);
+        delete M;
+        return SSTEP_ERR_OOM;
+    }
+    for (int q = 0; q < nq; ++q) {
+        launch_split_fields(A.f[q], M->fields_df + q * A.n, A.n, s);
+        A.fdf[q] = M->fields_df + q * A.n;
+    }
+    split_coefficients(A);
     M->A = A;
     // ||A||_inf: reduce on the host from a copy (creation-time only)
     std::vector<double> host((size_t)A.n * nq);
@@ -383,6 +535,7 @@ int stencil_matrix_create_fields(sstep_matrix* out, int dim, const int64_t shape
 int stencil_matrix_destroy(sstep_matrix M) {
     if (!M) return SSTEP_ERR_ARG;
     if (M->fields) cudaFree(M->fields);
+    if (M->fields_df) cudaFree(M->fields_df);
     if (M->ws) cudaFree(M->ws);
     if (M->hdr) cudaFreeHost(M->hdr);
     delete M;
@@ -465,6 +618,9 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     const int s = p->s, m = p->m;
     if (s < 1 || s > SSTEP_MAX_S || m < s || m > SSTEP_MAX_M || m % s != 0 || p->max_cycles < 0) return SSTEP_ERR_ARG;
     cudaStream_t stream_ = (cudaStream_t)stream;
+    if (p->precision == SSTEP_PREC_DF64) return sstep_gmres_mp<PREC_DF64>(M, f, x, p, res, stream_);
+    if (p->precision == SSTEP_PREC_FP32) return sstep_gmres_mp<PREC_FP32>(M, f, x, p, res, stream_);
+    if (p->precision != SSTEP_PREC_FP64) return SSTEP_ERR_ARG;
     const int64_t n = M->A.n, ld = col_ld(n);
     // columns: U (m+1) and the raw start vector
     Layout l = plan(n, m + 2, m, p->history ? p->history_cap : 0);
@@ -539,6 +695,9 @@ int gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_params* 
     const int m = p->m;
     if (m < 1 || m > SSTEP_MAX_M || p->max_cycles < 0) return SSTEP_ERR_ARG;
     cudaStream_t stream_ = (cudaStream_t)stream;
+    if (p->precision == SSTEP_PREC_DF64) return gmres_mp<PREC_DF64>(M, f, x, p, res, stream_);
+    if (p->precision == SSTEP_PREC_FP32) return gmres_mp<PREC_FP32>(M, f, x, p, res, stream_);
+    if (p->precision != SSTEP_PREC_FP64) return SSTEP_ERR_ARG;
     const int64_t n = M->A.n, ld = col_ld(n);
     Layout l = plan(n, m + 3, m, p->history ? p->history_cap : 0);
     if ((rc = ensure_workspace(M, l.total))) return rc;
@@ -595,6 +754,7 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
     if (rc) return rc;
     const int s = p->s, k = p->k;
     if (s < 1 || s > SSTEP_MAX_S || k < 0 || (int64_t)k * s > SSTEP_MAX_COLS || p->max_iters < 0) return SSTEP_ERR_ARG;
+    if (p->precision != SSTEP_PREC_FP64) return SSTEP_ERR_ARG;
     cudaStream_t stream_ = (cudaStream_t)stream;
     const int64_t n = M->A.n, ld = col_ld(n);
     const int keep = std::max(k, 1);

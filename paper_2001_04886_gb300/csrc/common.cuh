@@ -28,6 +28,10 @@ struct StencilDesc {
     int variable;            // 0: constant coefficients in c[], 1: per-point fields in f[]
     double c[7];             // a0, am_x, ap_x, am_y, ap_y, am_z, ap_z
     const double* f[7];      // same order, device arrays of n (variable == 1)
+    // the same coefficients split into float pairs (hi + lo = c to 48 bits) for the
+    // mixed-precision kernels, so no kernel converts FP64 constants on the slow pipe
+    float ch[7], cl[7];
+    const float2* fdf[7];    // variable coefficients as float pairs (variable == 1)
 };
 
 __device__ __forceinline__ double coef(const StencilDesc& A, int q, int64_t p) {

@@ -85,3 +85,37 @@ void launch_lsq_solve(SolverState* st, int gate, cudaStream_t stream);
 int max_partials_doubles();
 
 }  // namespace sstep
+
+namespace sstep {
+
+// ------------------------------------------------------------------ mixed-precision basis (kernels_mp.cu)
+// PREC_DF64: basis stored as float pairs (hi, lo) and processed in double-float
+// arithmetic on the FP32 pipe. PREC_FP32: basis stored and processed in FP32,
+// with every inner product accumulated in double-float. Right-hand side,
+// iterate and explicit residuals stay FP64; so does all scalar work.
+enum Prec : int { PREC_FP64 = 0, PREC_DF64 = 1, PREC_FP32 = 2 };
+
+inline size_t prec_bytes(int prec) { return prec == PREC_FP32 ? 4 : 8; }
+
+template <int P>
+void mp_launch_stencil(const StencilDesc& A, const void* v, double fy, void* y, double fw, void* w,
+                       const double* dscale, const SolverState* st, int gate, cudaStream_t stream);
+template <int P>
+void mp_launch_residual(const StencilDesc& A, const double* f, const double* x, void* out, Scratch sc,
+                        const Epi& epi, int gate, cudaStream_t stream);
+template <int P>
+void mp_launch_gram(int64_t n, const void* V, int64_t ldv, int ka, const void* Y, int64_t ldy, int kb,
+                    Scratch sc, const Epi& epi, int gate, cudaStream_t stream);
+template <int P>
+void mp_launch_update(int64_t n, const void* V, int64_t ldv, int ka, const void* Yin, int64_t ldy, void* Yout,
+                      int64_t ldo, int kb, int j0, const double* T, int ldt, double sgn, bool gram, Scratch sc,
+                      const Epi& epi, int gate, cudaStream_t stream);
+// dst[p] = src[p] split into a float pair (variable coefficients for the mixed-precision kernels)
+void launch_split_fields(const double* src, float2* dst, int64_t n, cudaStream_t stream);
+
+// x += V y over the current cycle's st->K columns (y = st->y)
+template <int P>
+void mp_launch_axpy(int64_t n, const void* V, int64_t ldv, double* x, const Epi& epi, int gate,
+                    cudaStream_t stream);
+
+}  // namespace sstep

@@ -1,0 +1,94 @@
+"""The mixed-precision basis modes against the FP64 oracle.
+
+df64: the basis in double-float pairs (48-bit significand, u = 2^-48). Same
+algorithm as the oracle, so the same parity bars with u = 2^-48 in place of
+2^-53: first s-steps of the history to max(1e-10, u cond(W_1)), x to 1e-8.
+
+fp32 (FP32 iterative refinement, the precision form): the basis and the powers
+in FP32, inner products accumulated in double-float, FP64 restart residual and
+iterate. It solves to 1e-10 measured by the oracle's own FP64 residual.
+"""
+import numpy as np
+import pytest
+
+from oracle import sstep as osstep
+from oracle import krylov as okrylov
+from oracle import stencil as ostencil
+from paper_2001_04886_gb300 import inputs
+from tests.gpu_util import dev, to_dev, torch
+
+import paper_2001_04886_gb300 as pkg
+
+pytestmark = pytest.mark.gpu
+U48 = 2.0 ** -48
+
+
+def system(shape, beta, seed=0):
+    d = dev()
+    Ao = ostencil.convdiff(shape, beta)
+    f = Ao.apply(inputs.x_true(seed, Ao.n))
+    return d, Ao, pkg.StencilMatrix(len(shape), shape, beta=beta), f
+
+
+@pytest.mark.parametrize("shape,beta,s,m", [((64, 64), (20.0, 20.0), 4, 20), ((20, 20, 20), (30.0, 20.0, 10.0), 2, 40),
+                                            ((20, 20, 20), (30.0, 20.0, 10.0), 4, 40),
+                                            ((20, 20, 20), (30.0, 20.0, 10.0), 8, 40), ((13, 13), (20.0, 20.0), 3, 9)])
+def test_df64_sstep_gmres_parity(shape, beta, s, m):
+    d, Ao, A, f = system(shape, beta)
+    sigma = 1.0 / Ao.norm_inf()
+    tr = {}
+    osstep.sstep_gmres(Ao, f, np.zeros(Ao.n), s, m, 1e-30, sigma, 1, trace=tr)
+    hist_tol = max(1e-10, U48 * np.linalg.cond(tr["W"][0]))
+    ref = osstep.sstep_gmres(Ao, f, np.zeros(Ao.n), s, m, 1e-8, sigma, 500)
+    xd = torch.zeros(Ao.n, dtype=torch.float64, device=d)
+    res = pkg.sstep_gmres_solve(A, to_dev(f, d), xd, s, m, 1e-8, max_cycles=500, sigma=sigma, precision="df64")
+    assert res["status"] == 0 and res["cycles"] == ref["cycles"]
+    h, hr = np.array(res["history"]), np.array(ref["history"])
+    assert np.max(np.abs(h[: s + 1] - hr[: s + 1]) / hr[: s + 1]) <= hist_tol
+    x = xd.cpu().numpy()
+    assert np.linalg.norm(x - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+    rel = np.linalg.norm(f - Ao.apply(x)) / np.linalg.norm(f)
+    assert rel <= 1e-8 and abs(rel - res["relres"]) <= 1e-6 * rel
+
+
+@pytest.mark.parametrize("shape,beta,m", [((64, 64), (20.0, 20.0), 20), ((20, 20, 20), (30.0, 20.0, 10.0), 40)])
+def test_df64_gmres_parity(shape, beta, m):
+    d, Ao, A, f = system(shape, beta)
+    ref = okrylov.gmres(Ao, f, np.zeros(Ao.n), m, 1e-8, 500)
+    xd = torch.zeros(Ao.n, dtype=torch.float64, device=d)
+    res = pkg.gmres_solve(A, to_dev(f, d), xd, m, 1e-8, max_cycles=500, precision="df64")
+    assert res["status"] == 0 and res["cycles"] == ref["cycles"]
+    h, hr = np.array(res["history"]), np.array(ref["history"])
+    assert np.max(np.abs(h[:5] - hr[:5]) / hr[:5]) <= 1e-10
+    x = xd.cpu().numpy()
+    assert np.linalg.norm(x - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+
+
+@pytest.mark.parametrize("shape,beta,s,m", [((32, 32, 32), (50.0, 0.0, 0.0), 8, 32), ((64, 64), (20.0, 20.0), 4, 20),
+                                            ((24, 24, 24), (30.0, 20.0, 10.0), 4, 40)])
+def test_fp32_refinement_reaches_1e10(shape, beta, s, m):
+    d, Ao, A, f = system(shape, beta)
+    sigma = 1.0 / Ao.norm_inf()
+    xd = torch.zeros(Ao.n, dtype=torch.float64, device=d)
+    res = pkg.sstep_gmres_solve(A, to_dev(f, d), xd, s, m, 1e-10, max_cycles=500, sigma=sigma, precision="fp32")
+    assert res["status"] == 0
+    x = xd.cpu().numpy()
+    rel = np.linalg.norm(f - Ao.apply(x)) / np.linalg.norm(f)
+    assert rel <= 1e-10 and abs(rel - res["relres"]) <= 1e-4 * rel
+    # against the all-FP64 s-step solve of the oracle to the same tolerance
+    ref = osstep.sstep_gmres(Ao, f, np.zeros(Ao.n), s, m, 1e-10, sigma, 500)
+    err = np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"])
+    assert err <= 1e-7
+    # the FP32 basis costs at most a few extra cycles
+    assert res["cycles"] <= ref["cycles"] + 3
+
+
+def test_fp32_refinement_256cube():
+    """The precision form's own workload: 256^3, beta = (50, 0, 0), s = 8, m = 32, tol 1e-10."""
+    d, Ao, A, f = system((256, 256, 256), (50.0, 0.0, 0.0))
+    xd = torch.zeros(Ao.n, dtype=torch.float64, device=d)
+    res = pkg.sstep_gmres_solve(A, to_dev(f, d), xd, 8, 32, 1e-10, max_cycles=200, precision="fp32")
+    assert res["status"] == 0
+    x = xd.cpu().numpy()
+    rel = np.linalg.norm(f - Ao.apply(x)) / np.linalg.norm(f)
+    assert rel <= 1e-10
