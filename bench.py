@@ -368,6 +368,38 @@ def main():
         variants["precision_form_256cube_s8_m32_tol1e-10"] = form
         del A3, xt3, f3, x3
 
+    if not args.no_variants:
+        # the batched form: 512 systems, sides L ~ U{32..256}, beta ~ U[0, 50], s = 4, m = 20, tol 1e-8
+        systems = inputs.batched_systems(rank, 512)
+        mats, fs, xs, xts = [], [], [], []
+        for sy in systems:
+            Ab = pkg.StencilMatrix(2, (sy["L"], sy["L"]), beta=(sy["beta"], sy["beta"]))
+            xb = torch.tensor(inputs.x_true(sy["xseed"], Ab.n), dtype=torch.float64, device=dev)
+            fb = torch.empty_like(xb)
+            Ab.apply(xb, fb)
+            mats.append(Ab)
+            fs.append(fb)
+            xs.append(torch.zeros_like(fb))
+        Bs = pkg.BatchSolver(mats, 4, 20, TOL, max_cycles=2000)
+        t0 = time.perf_counter()
+        cfg = Bs.tune(fs, xs)
+        tune_s = time.perf_counter() - t0
+        out = {"systems": 512, "unknowns": int(sum(A_.n for A_ in mats)), "tuned": cfg, "tune_s": tune_s}
+        for mode, name in ((Bs.PERSISTENT, "persistent_graph"), (Bs.PER_SYSTEM, "per_system_launches")):
+            for x_ in xs:
+                x_.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            rb = Bs.solve(fs, xs, mode=mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[name] = {"ms": e0.elapsed_time(e1), "all_converged": all(r["status"] == 0 for r in rb),
+                         "cycles_total": int(sum(r["cycles"] for r in rb)),
+                         "max_relres": float(max(r["relres"] for r in rb))}
+        variants["batched_512_s4_m20"] = out
+        Bs.close()
+        del mats, fs, xs
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:

@@ -177,6 +177,33 @@ int gmres_solve(sstep_matrix A, const double* f, double* x, const sstep_params* 
 int sstep_omin_solve(sstep_matrix A, const double* f, double* x, const sstep_params* p,
                      sstep_result* res, void* stream);
 
+/* ------------------------------------------------------------------ batched solves
+ * Many independent systems solved by s-step GMRES (Alg. 4.1/4.2) together. A batch
+ * handle plans the work once (workspace for every system, launch configuration)
+ * and then solves any number of right-hand sides. Mode SSTEP_BATCH_PERSISTENT runs
+ * the whole batch as one persistent kernel, replayed from a captured CUDA graph:
+ * each CTA takes the next system from a work queue (largest first unless tuned
+ * otherwise) and runs its entire solve with CTA-wide reductions. Mode
+ * SSTEP_BATCH_PER_SYSTEM calls sstep_gmres_solve once per system (the comparison).
+ * The handle keeps references to the matrices, which must outlive it.
+ * p: s in {1, 2, 4, 8}, m <= 40 and a multiple of s, FP64 only; p->history is
+ * ignored. */
+#define SSTEP_BATCH_PERSISTENT 0
+#define SSTEP_BATCH_PER_SYSTEM 1
+typedef struct sstep_batch_s* sstep_batch;
+int sstep_batch_create(sstep_batch* out, int nsys, const sstep_matrix* A, const sstep_params* p);
+/* f, x: HOST arrays of nsys DEVICE pointers (x: initial guesses in, solutions out);
+ * res: HOST array of nsys results. Synchronises `stream`. */
+int sstep_batch_solve(sstep_batch B, const double* const* f, double* const* x, sstep_result* res, int mode,
+                      void* stream);
+/* Autotuner: times the persistent solve of the given batch under each candidate
+ * launch configuration (threads per CTA, CTAs per SM, queue order), keeps the
+ * fastest in the handle and reports it (host outputs, may be NULL). x is restored
+ * to its initial content after every trial. */
+int sstep_batch_tune(sstep_batch B, const double* const* f, double* const* x, int* threads, int* ctas_per_sm,
+                     int* largest_first, void* stream);
+int sstep_batch_destroy(sstep_batch B);
+
 const char* sstep_status_string(int status);
 
 /* ------------------------------------------------------------------ launch tracing

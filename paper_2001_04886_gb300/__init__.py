@@ -11,6 +11,7 @@ used without a GPU.
 from __future__ import annotations
 
 from ._binding import (  # noqa: F401
+    BatchSolver,
     SSTEP_MAX_COLS,
     SSTEP_MAX_M,
     SSTEP_MAX_S,
@@ -30,6 +31,7 @@ from ._binding import (  # noqa: F401
 )
 
 __all__ = [
+    "BatchSolver",
     "StencilMatrix",
     "stencil_matrix_apply",
     "sstep_matrix_powers",

@@ -52,6 +52,10 @@ SIGNATURES = {
     "gmres_solve": (c_int, [c_void_p, c_void_p, c_void_p, P(SStepParams), P(SStepResult), c_void_p]),
     "sstep_omin_solve": (c_int, [c_void_p, c_void_p, c_void_p, P(SStepParams), P(SStepResult), c_void_p]),
     "sstep_status_string": (ctypes.c_char_p, [c_int]),
+    "sstep_batch_create": (c_int, [P(c_void_p), c_int, P(c_void_p), P(SStepParams)]),
+    "sstep_batch_solve": (c_int, [c_void_p, P(c_void_p), P(c_void_p), P(SStepResult), c_int, c_void_p]),
+    "sstep_batch_tune": (c_int, [c_void_p, P(c_void_p), P(c_void_p), P(c_int), P(c_int), P(c_int), c_void_p]),
+    "sstep_batch_destroy": (c_int, [c_void_p]),
     "sstep_trace_enable": (c_int, [c_int]),
     "sstep_trace_kinds": (c_int, []),
     "sstep_trace_kind_name": (ctypes.c_char_p, [c_int]),
@@ -287,3 +291,50 @@ def trace_read():
         _check("sstep_trace_read", L.sstep_trace_read(k, ctypes.byref(ms), ctypes.byref(nl)))
         out[L.sstep_trace_kind_name(k).decode()] = (ms.value, nl.value)
     return out
+
+
+class BatchSolver:
+    """Batched s-step GMRES over many systems (include/sstep.h, batched solves).
+
+    mats: list of StencilMatrix (kept alive by this object). solve() takes lists of
+    float64 CUDA tensors f and x (x in/out) and returns one result dict per system.
+    """
+
+    PERSISTENT = 0
+    PER_SYSTEM = 1
+
+    def __init__(self, mats, s, m, tol, max_cycles=1000, sigma=0.0):
+        self.mats = list(mats)
+        self.n = len(self.mats)
+        h = c_void_p()
+        arr = (c_void_p * self.n)(*[A.handle.value for A in self.mats])
+        p = SStepParams(s=s, m=m, k=0, tol=tol, max_cycles=max_cycles, max_iters=0, sigma=sigma, history=None,
+                        history_cap=0, precision=0)
+        _check("sstep_batch_create", lib().sstep_batch_create(ctypes.byref(h), self.n, arr, ctypes.byref(p)))
+        self.handle = h
+
+    def _ptrs(self, ts):
+        return (c_void_p * self.n)(*[_ptr(t).value for t in ts])
+
+    def solve(self, f, x, mode=0, stream=None):
+        res = (SStepResult * self.n)()
+        _check("sstep_batch_solve", lib().sstep_batch_solve(self.handle, self._ptrs(f), self._ptrs(x), res, mode,
+                                                            _stream(stream)))
+        return [dict(status=r.status, cycles=r.cycles, iters=r.iters, matvecs=r.matvecs, relres=r.relres) for r in res]
+
+    def tune(self, f, x, stream=None):
+        t, c, o = c_int(), c_int(), c_int()
+        _check("sstep_batch_tune", lib().sstep_batch_tune(self.handle, self._ptrs(f), self._ptrs(x), ctypes.byref(t),
+                                                          ctypes.byref(c), ctypes.byref(o), _stream(stream)))
+        return dict(threads=t.value, ctas_per_sm=c.value, largest_first=o.value)
+
+    def close(self):
+        if self.handle:
+            lib().sstep_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

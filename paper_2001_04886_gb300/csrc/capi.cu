@@ -12,6 +12,8 @@
 #include <new>
 #include <vector>
 
+#include <chrono>
+
 #include "kernels.cuh"
 
 using namespace sstep;
@@ -388,6 +390,98 @@ int gmres_mp(sstep_matrix M, const double* f, double* x, const sstep_params* p, 
         if (!M->hdr->active) break;
     }
     return finish(M, l, st, f, x, p, res, stream_);
+}
+
+
+}  // namespace
+
+// ------------------------------------------------------------------ batched solves
+struct sstep_batch_s {
+    int nsys = 0, s = 0, m = 0;
+    sstep_params p{};
+    std::vector<sstep_matrix> mats;
+    std::vector<int> order_largest;      // system indices, largest n first
+    char* ws = nullptr;                  // states, small arrays, basis panels
+    size_t ws_bytes = 0;
+    BatchSys* d_sys = nullptr;           // device descriptors
+    int* d_order = nullptr;              // device copy of the queue order (largest first)
+    unsigned* d_queue = nullptr;
+    std::vector<BatchSys> h_sys;
+    std::vector<SolverState> h_init;     // initial states
+    SolverState* h_states = nullptr;     // pinned copy back
+    std::vector<size_t> state_off;
+    // launch configuration (autotuned)
+    int threads = 256, ctas_per_sm = 2, largest_first = 1;
+    cudaGraphExec_t graph = nullptr;
+    int graph_cfg[3] = {0, 0, 0};
+};
+
+namespace {
+
+constexpr int kBatchMaxM = 40;
+
+// Per-system state plus small arrays, laid out like plan() of one solve.
+size_t batch_state_bytes(int m) {
+    Layout l = plan(0, 0, m, 0);
+    return align_up(l.partials);   // state .. counter (no partials, no columns)
+}
+
+SolverState batch_state(char* base, int m, int s, const sstep_params* p, double sigma) {
+    Layout l = plan(0, 0, m, 0);
+    sstep_params q = *p;
+    q.history = nullptr;
+    q.history_cap = 0;
+    SolverState h = init_state(l, base, &q, s, m, 0);
+    h.sigma = sigma;
+    return h;
+}
+
+int batch_graph(sstep_batch B, cudaStream_t stream) {
+    const int cfg[3] = {B->threads, B->ctas_per_sm, B->largest_first};
+    if (B->graph && memcmp(cfg, B->graph_cfg, sizeof(cfg)) == 0) return SSTEP_OK;
+    if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
+    int dev = 0, sms = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t cap;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    int rc = SSTEP_OK;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = SSTEP_ERR_CUDA;
+    if (!rc) {
+        cudaMemsetAsync(B->d_queue, 0, sizeof(unsigned), cap);
+        if (launch_batched(B->d_sys, B->largest_first ? B->d_order : nullptr, B->nsys, B->d_queue, B->s, B->threads,
+                           sms * B->ctas_per_sm, cap))
+            rc = SSTEP_ERR_ARG;
+        if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = SSTEP_ERR_CUDA;
+    }
+    if (!rc) {
+        if (cudaGraphInstantiate(&B->graph, g, 0) != cudaSuccess) rc = SSTEP_ERR_CUDA;
+        cudaGraphDestroy(g);
+    }
+    cudaStreamDestroy(cap);
+    cudaGetLastError();
+    if (!rc) memcpy(B->graph_cfg, cfg, sizeof(cfg));
+    (void)stream;
+    return rc;
+}
+
+int batch_run_persistent(sstep_batch B, const double* const* f, double* const* x, cudaStream_t stream) {
+    for (int i = 0; i < B->nsys; ++i) {
+        B->h_sys[i].f = f[i];
+        B->h_sys[i].x = x[i];
+    }
+    CUDA_TRY(cudaMemcpyAsync(B->d_sys, B->h_sys.data(), sizeof(BatchSys) * B->nsys, cudaMemcpyHostToDevice, stream));
+    for (int i = 0; i < B->nsys; ++i)
+        CUDA_TRY(cudaMemcpyAsync(B->ws + B->state_off[i], &B->h_init[i], sizeof(SolverState), cudaMemcpyHostToDevice,
+                                 stream));
+    int rc = batch_graph(B, stream);
+    if (rc) return rc;
+    CUDA_TRY(cudaGraphLaunch(B->graph, stream));
+    return SSTEP_OK;
 }
 
 }  // namespace
@@ -833,6 +927,184 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
         if (M->hdr->confirm) restart = true;
     }
     return finish(M, l, st, f, x, p, res, stream_);
+}
+
+
+int sstep_batch_create(sstep_batch* out, int nsys, const sstep_matrix* A, const sstep_params* p) {
+    if (!out || nsys < 1 || !A || !p) return SSTEP_ERR_ARG;
+    *out = nullptr;
+    const int s = p->s, m = p->m;
+    if (!(s == 1 || s == 2 || s == 4 || s == 8) || m < s || m > kBatchMaxM || m % s || p->max_cycles < 0 ||
+        !(p->tol > 0.0) || p->sigma < 0.0 || p->precision != SSTEP_PREC_FP64)
+        return SSTEP_ERR_ARG;
+    for (int i = 0; i < nsys; ++i)
+        if (!A[i]) return SSTEP_ERR_ARG;
+    sstep_batch B = new (std::nothrow) sstep_batch_s;
+    if (!B) return SSTEP_ERR_OOM;
+    B->nsys = nsys;
+    B->s = s;
+    B->m = m;
+    B->p = *p;
+    B->mats.assign(A, A + nsys);
+    // workspace: per system a state block and an (m+2)-column panel
+    const size_t sb = batch_state_bytes(m);
+    size_t total = 0;
+    B->state_off.resize(nsys);
+    std::vector<size_t> col_off(nsys);
+    for (int i = 0; i < nsys; ++i) {
+        B->state_off[i] = total;
+        total += sb;
+    }
+    for (int i = 0; i < nsys; ++i) {
+        col_off[i] = total;
+        total += align_up(sizeof(double) * (size_t)col_ld(A[i]->A.n) * (m + 2));
+    }
+    int rc = SSTEP_OK;
+    if (cudaMalloc((void**)&B->ws, total) != cudaSuccess || cudaMalloc((void**)&B->d_sys, sizeof(BatchSys) * nsys) !=
+            cudaSuccess || cudaMalloc((void**)&B->d_order, sizeof(int) * nsys) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_queue, sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost((void**)&B->h_states, sizeof(SolverState) * nsys) != cudaSuccess) {
+        cudaGetLastError();
+        rc = SSTEP_ERR_OOM;
+    }
+    if (rc) {
+        sstep_batch_destroy(B);
+        return rc;
+    }
+    B->ws_bytes = total;
+    B->h_sys.resize(nsys);
+    B->h_init.resize(nsys);
+    for (int i = 0; i < nsys; ++i) {
+        const double sigma = p->sigma > 0.0 ? p->sigma : 1.0 / A[i]->norm_inf;
+        B->h_init[i] = batch_state(B->ws + B->state_off[i], m, s, p, sigma);
+        BatchSys& b = B->h_sys[i];
+        b.A = A[i]->A;
+        b.U = (double*)(B->ws + col_off[i]);
+        b.st = (SolverState*)(B->ws + B->state_off[i]);
+        b.ld = col_ld(A[i]->A.n);
+        b.f = nullptr;
+        b.x = nullptr;
+    }
+    B->order_largest.resize(nsys);
+    for (int i = 0; i < nsys; ++i) B->order_largest[i] = i;
+    std::stable_sort(B->order_largest.begin(), B->order_largest.end(),
+                     [&](int a, int b) { return A[a]->A.n > A[b]->A.n; });
+    if (cudaMemcpy(B->d_order, B->order_largest.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(B->ws, 0, total) != cudaSuccess) {
+        sstep_batch_destroy(B);
+        return SSTEP_ERR_CUDA;
+    }
+    *out = B;
+    return SSTEP_OK;
+}
+
+int sstep_batch_solve(sstep_batch B, const double* const* f, double* const* x, sstep_result* res, int mode,
+                      void* stream) {
+    if (!B || !f || !x || !res) return SSTEP_ERR_ARG;
+    for (int i = 0; i < B->nsys; ++i)
+        if (!f[i] || !x[i]) return SSTEP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mode == SSTEP_BATCH_PER_SYSTEM) {
+        for (int i = 0; i < B->nsys; ++i) {
+            sstep_params q = B->p;
+            q.history = nullptr;
+            q.history_cap = 0;
+            int rc = sstep_gmres_solve(B->mats[i], f[i], x[i], &q, &res[i], stream);
+            if (rc < 0) return rc;
+        }
+        return SSTEP_OK;
+    }
+    if (mode != SSTEP_BATCH_PERSISTENT) return SSTEP_ERR_ARG;
+    int rc = batch_run_persistent(B, f, x, st);
+    if (rc) return rc;
+    for (int i = 0; i < B->nsys; ++i)
+        CUDA_TRY(cudaMemcpyAsync(&B->h_states[i], B->ws + B->state_off[i], sizeof(SolverState), cudaMemcpyDeviceToHost,
+                                 st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < B->nsys; ++i) {
+        const SolverState& h = B->h_states[i];
+        res[i].status = h.status;
+        res[i].cycles = h.cycles;
+        res[i].iters = h.iters;
+        res[i].matvecs = h.matvecs;
+        res[i].relres = h.relres;
+        res[i].history_len = 0;
+    }
+    return SSTEP_OK;
+}
+
+int sstep_batch_tune(sstep_batch B, const double* const* f, double* const* x, int* threads, int* ctas_per_sm,
+                     int* largest_first, void* stream) {
+    if (!B || !f || !x) return SSTEP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // keep the initial guesses to restore them after every trial
+    std::vector<double*> saved(B->nsys, nullptr);
+    int rc = SSTEP_OK;
+    for (int i = 0; i < B->nsys && !rc; ++i) {
+        const size_t bytes = sizeof(double) * B->mats[i]->A.n;
+        if (cudaMalloc((void**)&saved[i], bytes) != cudaSuccess) rc = SSTEP_ERR_OOM;
+        else if (cudaMemcpyAsync(saved[i], x[i], bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) rc = SSTEP_ERR_CUDA;
+    }
+    const int cand_threads[2] = {128, 256};
+    const int cand_ctas[3] = {1, 2, 4};
+    const int cand_order[2] = {1, 0};
+    double best = 1e300;
+    int bt = B->threads, bc = B->ctas_per_sm, bo = B->largest_first;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int t : cand_threads)
+        for (int c : cand_ctas)
+            for (int o : cand_order) {
+                if (rc) break;
+                if (t == 256 && c == 4) continue;   // more threads than the register file holds
+                B->threads = t;
+                B->ctas_per_sm = c;
+                B->largest_first = o;
+                for (int i = 0; i < B->nsys; ++i)
+                    cudaMemcpyAsync(x[i], saved[i], sizeof(double) * B->mats[i]->A.n, cudaMemcpyDeviceToDevice, st);
+                cudaEventRecord(e0, st);
+                rc = batch_run_persistent(B, f, x, st);
+                cudaEventRecord(e1, st);
+                if (cudaStreamSynchronize(st) != cudaSuccess) rc = SSTEP_ERR_CUDA;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (!rc && ms < best) {
+                    best = ms;
+                    bt = t;
+                    bc = c;
+                    bo = o;
+                }
+            }
+    for (int i = 0; i < B->nsys; ++i) {
+        if (saved[i]) {
+            cudaMemcpyAsync(x[i], saved[i], sizeof(double) * B->mats[i]->A.n, cudaMemcpyDeviceToDevice, st);
+        }
+    }
+    cudaStreamSynchronize(st);
+    for (double* q : saved)
+        if (q) cudaFree(q);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B->threads = bt;
+    B->ctas_per_sm = bc;
+    B->largest_first = bo;
+    if (threads) *threads = bt;
+    if (ctas_per_sm) *ctas_per_sm = bc;
+    if (largest_first) *largest_first = bo;
+    return rc;
+}
+
+int sstep_batch_destroy(sstep_batch B) {
+    if (!B) return SSTEP_ERR_ARG;
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->ws) cudaFree(B->ws);
+    if (B->d_sys) cudaFree(B->d_sys);
+    if (B->d_order) cudaFree(B->d_order);
+    if (B->d_queue) cudaFree(B->d_queue);
+    if (B->h_states) cudaFreeHost(B->h_states);
+    delete B;
+    return SSTEP_OK;
 }
 
 }  // extern "C"

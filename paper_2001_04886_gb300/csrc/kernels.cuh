@@ -119,3 +119,19 @@ void mp_launch_axpy(int64_t n, const void* V, int64_t ldv, double* x, const Epi&
                     cudaStream_t stream);
 
 }  // namespace sstep
+
+namespace sstep {
+// ------------------------------------------------------------------ batched persistent solver (batched.cu)
+// one system of a batch: its operator, right-hand side, iterate, basis panel and state
+struct BatchSys {
+    StencilDesc A;
+    const double* f;
+    double* x;
+    double* U;           // m+2 columns of ld doubles: basis, raw start vector
+    SolverState* st;
+    int64_t ld;
+};
+size_t batched_scratch_bytes(int threads);
+int launch_batched(const BatchSys* sys, const int* order, int nsys, unsigned* queue, int s, int threads, int ctas,
+                   cudaStream_t stream);
+}  // namespace sstep

@@ -40,6 +40,18 @@ struct Mode<PREC_DF64> {
         return df64{t.x, t.y};
     }
     static __device__ __forceinline__ void store(T* p, V v) { *p = make_float2(v.hi, v.lo); }
+    // rows 2q and 2q+1 with one 16-byte access (columns are 256-byte aligned, ld even)
+    static __device__ __forceinline__ void load2(const T* p, V& a, V& b) {
+        const float4 t = __ldg((const float4*)p);
+        a = df64{t.x, t.y};
+        b = df64{t.z, t.w};
+    }
+    static __device__ __forceinline__ void load2_rw(const T* p, V& a, V& b) {
+        const float4 t = *(const float4*)p;
+        a = df64{t.x, t.y};
+        b = df64{t.z, t.w};
+    }
+    static __device__ __forceinline__ void store2(T* p, V a, V b) { *(float4*)p = make_float4(a.hi, a.lo, b.hi, b.lo); }
     static __device__ __forceinline__ df64 wide(V v) { return v; }
     static __device__ __forceinline__ V narrow(df64 v) { return v; }
     static __device__ __forceinline__ V zero() { return df64{0.f, 0.f}; }
@@ -52,6 +64,17 @@ struct Mode<PREC_FP32> {
     static __device__ __forceinline__ V load(const T* p) { return __ldg(p); }
     static __device__ __forceinline__ V load_rw(const T* p) { return *p; }
     static __device__ __forceinline__ void store(T* p, V v) { *p = v; }
+    static __device__ __forceinline__ void load2(const T* p, V& a, V& b) {
+        const float2 t = __ldg((const float2*)p);
+        a = t.x;
+        b = t.y;
+    }
+    static __device__ __forceinline__ void load2_rw(const T* p, V& a, V& b) {
+        const float2 t = *(const float2*)p;
+        a = t.x;
+        b = t.y;
+    }
+    static __device__ __forceinline__ void store2(T* p, V a, V b) { *(float2*)p = make_float2(a, b); }
     static __device__ __forceinline__ df64 wide(V v) { return df64{v, 0.f}; }
     static __device__ __forceinline__ V narrow(df64 v) { return __fadd_rn(v.hi, v.lo); }
     static __device__ __forceinline__ V zero() { return 0.f; }
@@ -122,80 +145,56 @@ __device__ __forceinline__ df64 mp_coef(const StencilDesc& A, int q, int64_t p) 
     return df64{A.ch[q], P == PREC_DF64 ? A.cl[q] : 0.f};
 }
 
-template <int P>
-__device__ __forceinline__ typename Mode<P>::V mp_row(const StencilDesc& A, const typename Mode<P>::T* v,
-                                                      int64_t p) {
-    using M = Mode<P>;
-    const unsigned up = (unsigned)p;
-    const unsigned t = up / (unsigned)A.nx;
-    const int x = (int)(up - t * (unsigned)A.nx);
-    const unsigned zz = t / (unsigned)A.ny;
-    const int y = (int)(t - zz * (unsigned)A.ny), z = (int)zz;
-    const int64_t pl = (int64_t)A.nx * A.ny;
-    // gather the neighbours first (independent loads), then combine
-    typename M::V nb[7];
-    nb[0] = M::load(v + p);
-    nb[1] = x > 0 ? M::load(v + p - 1) : M::zero();
-    nb[2] = x < A.nx - 1 ? M::load(v + p + 1) : M::zero();
-    nb[3] = y > 0 ? M::load(v + p - A.nx) : M::zero();
-    nb[4] = y < A.ny - 1 ? M::load(v + p + A.nx) : M::zero();
-    nb[5] = (A.dim == 3 && z > 0) ? M::load(v + p - pl) : M::zero();
-    nb[6] = (A.dim == 3 && z < A.nz - 1) ? M::load(v + p + pl) : M::zero();
-    if constexpr (P == PREC_DF64) {
-        df64 acc = df_mul(mp_coef<P>(A, 0, p), nb[0]);
-#pragma unroll
-        for (int q = 1; q < 7; ++q)
-            if (q < 2 * A.dim + 1) acc = df_fma(mp_coef<P>(A, q, p), nb[q], acc);
-        return acc;
-    } else {
-        float acc = __fmul_rn(mp_coef<P>(A, 0, p).hi, nb[0]);
-#pragma unroll
-        for (int q = 1; q < 7; ++q)
-            if (q < 2 * A.dim + 1) acc = __fmaf_rn(mp_coef<P>(A, q, p).hi, nb[q], acc);
-        return acc;
-    }
-}
-
+// One point per thread on a (32 x 8) tile of x-y rows, one z plane per grid.z step:
+// the grid coordinates come from the launch shape, with no per-point division.
 template <int P>
 __global__ void __launch_bounds__(kThreads) mp_stencil_kernel(StencilDesc A, const typename Mode<P>::T* __restrict__ v,
                                                               double fy, typename Mode<P>::T* __restrict__ y, double fw,
                                                               typename Mode<P>::T* __restrict__ w,
                                                               const double* dscale, const SolverState* st, int gate) {
     using M = Mode<P>;
+    using Vt = typename M::V;
     __shared__ df64 fac[2];
     if (!gate_open(st, gate)) return;
     broadcast_factors(fy, fw, dscale, fac);
     const df64 vfy = fac[0], vfw = fac[1];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // two rows per iteration: their neighbour loads are all in flight together
-    for (; p + stride < A.n; p += 2 * stride) {
-        const auto r0 = mp_row<P>(A, v, p);
-        const auto r1 = mp_row<P>(A, v, p + stride);
+    const int64_t pl = (int64_t)A.nx * A.ny;
+    // one wave of CTAs, each walking (32 x 8)-point tiles: the prologue above is paid once
+    const int tx = (A.nx + 31) / 32, ty = (A.ny + 7) / 8;
+    const int64_t ntiles = (int64_t)tx * ty * A.nz;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int bx = (int)(tile % tx);
+        const int64_t rest = tile / tx;
+        const int by = (int)(rest % ty);
+        const int z = (int)(rest / ty);
+        const int x = bx * 32 + threadIdx.x;
+        const int yy = by * 8 + threadIdx.y;
+        if (x >= A.nx || yy >= A.ny) continue;
+        const int64_t p = (int64_t)z * pl + (int64_t)yy * A.nx + x;
+        Vt nb[7];
+        nb[0] = M::load(v + p);
+        nb[1] = x > 0 ? M::load(v + p - 1) : M::zero();
+        nb[2] = x < A.nx - 1 ? M::load(v + p + 1) : M::zero();
+        nb[3] = yy > 0 ? M::load(v + p - A.nx) : M::zero();
+        nb[4] = yy < A.ny - 1 ? M::load(v + p + A.nx) : M::zero();
+        nb[5] = (A.dim == 3 && z > 0) ? M::load(v + p - pl) : M::zero();
+        nb[6] = (A.dim == 3 && z < A.nz - 1) ? M::load(v + p + pl) : M::zero();
         if constexpr (P == PREC_DF64) {
-            M::store(y + p, df_mul(vfy, r0));
-            M::store(y + p + stride, df_mul(vfy, r1));
-            if (w) {
-                M::store(w + p, df_mul(vfw, M::load(v + p)));
-                M::store(w + p + stride, df_mul(vfw, M::load(v + p + stride)));
-            }
+            // centre, then the neighbours: exact products summed in double-float
+            DfAcc acc;
+#pragma unroll
+            for (int q = 0; q < 7; ++q)
+                if (q < 2 * A.dim + 1) acc.add_prod(mp_coef<P>(A, q, p), nb[q]);
+            acc.normalize();
+            M::store(y + p, df_mul(vfy, df64{acc.hi, acc.lo}));
+            if (w) M::store(w + p, df_mul(vfw, nb[0]));
         } else {
-            M::store(y + p, __fmul_rn(vfy.hi, r0));
-            M::store(y + p + stride, __fmul_rn(vfy.hi, r1));
-            if (w) {
-                M::store(w + p, __fmul_rn(vfw.hi, M::load(v + p)));
-                M::store(w + p + stride, __fmul_rn(vfw.hi, M::load(v + p + stride)));
-            }
-        }
-    }
-    if (p < A.n) {
-        const auto r0 = mp_row<P>(A, v, p);
-        if constexpr (P == PREC_DF64) {
-            M::store(y + p, df_mul(vfy, r0));
-            if (w) M::store(w + p, df_mul(vfw, M::load(v + p)));
-        } else {
-            M::store(y + p, __fmul_rn(vfy.hi, r0));
-            if (w) M::store(w + p, __fmul_rn(vfw.hi, M::load(v + p)));
+            float acc = __fmul_rn(mp_coef<P>(A, 0, p).hi, nb[0]);
+#pragma unroll
+            for (int q = 1; q < 7; ++q)
+                if (q < 2 * A.dim + 1) acc = __fmaf_rn(mp_coef<P>(A, q, p).hi, nb[q], acc);
+            M::store(y + p, __fmul_rn(vfy.hi, acc));
+            if (w) M::store(w + p, __fmul_rn(vfw.hi, nb[0]));
         }
     }
 }
@@ -204,8 +203,10 @@ template <int P>
 void mp_launch_stencil(const StencilDesc& A, const void* v, double fy, void* y, double fw, void* w,
                        const double* dscale, const SolverState* st, int gate, cudaStream_t stream) {
     using T = typename Mode<P>::T;
-    int grid = grid_for(A.n, 152 * 8);
-    mp_stencil_kernel<P><<<grid, kThreads, 0, stream>>>(A, (const T*)v, fy, (T*)y, fw, (T*)w, dscale, st, gate);
+    dim3 block(32, 8);
+    const int64_t ntiles = (int64_t)((A.nx + 31) / 32) * ((A.ny + 7) / 8) * A.nz;
+    const int grid = (int)(ntiles < 152 * 8 ? ntiles : 152 * 8);
+    mp_stencil_kernel<P><<<grid, block, 0, stream>>>(A, (const T*)v, fy, (T*)y, fw, (T*)w, dscale, st, gate);
 }
 
 // ================================================================== residual (FP64) into the basis type
@@ -248,8 +249,10 @@ void mp_launch_residual(const StencilDesc& A, const double* f, const double* x, 
 }
 
 // ================================================================== Gram pass, double-float accumulation
-// C[by*KA + i, j] = sum_rows V[row, by*KA + i] Y[row, j]; the next row's operands are
-// loaded before the current row is accumulated.
+// C[by*KA + i, j] = sum_rows V[row, by*KA + i] Y[row, j]. Each thread takes two
+// consecutive rows per step (16-byte loads; the row past n in the last pair lies in
+// the column padding and is masked out), and loads the next pair before it
+// accumulates the current one.
 template <int P, int KA, int KB>
 __global__ void __launch_bounds__(kThreads) mp_gram_kernel(int64_t n, const typename Mode<P>::T* __restrict__ V,
                                                            int64_t ldv, int ka, const typename Mode<P>::T* __restrict__ Y,
@@ -266,37 +269,35 @@ __global__ void __launch_bounds__(kThreads) mp_gram_kernel(int64_t n, const type
 #pragma unroll
     for (int i = 0; i < KA; ++i) voff[i] = (int64_t)min(a0 + i, ka - 1) * ldv;
     DfAcc acc[NV];
+    const int64_t npairs = (n + 1) / 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    Vt ya[KB], va[KA];
-    auto load_row = [&](int64_t q, Vt (&yy)[KB], Vt (&vv)[KA]) {
-#pragma unroll
-        for (int j = 0; j < KB; ++j) yy[j] = M::load(Y + q + j * ldy);
-#pragma unroll
-        for (int i = 0; i < KA; ++i) vv[i] = M::load(V + q + voff[i]);
-    };
-    if (p < n) load_row(p, ya, va);
     int cnt = 0;
-    while (p < n) {
-        const int64_t pn = p + stride;
-        Vt yb[KB], vb[KA];
-        if (pn < n) load_row(pn, yb, vb);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += stride) {
+        const int64_t p = 2 * q;
+        const bool second = p + 1 < n;
+        Vt y0[KB], y1[KB], v0[KA], v1[KA];
+#pragma unroll
+        for (int j = 0; j < KB; ++j) M::load2(Y + p + j * ldy, y0[j], y1[j]);
+#pragma unroll
+        for (int i = 0; i < KA; ++i) M::load2(V + p + voff[i], v0[i], v1[i]);
+        if (!second) {
+#pragma unroll
+            for (int i = 0; i < KA; ++i) v1[i] = M::zero();
+        }
 #pragma unroll
         for (int i = 0; i < KA; ++i)
             if (i < na) {
 #pragma unroll
-                for (int j = 0; j < KB; ++j) acc_add(acc[i * KB + j], va[i], M::wide(ya[j]));
+                for (int j = 0; j < KB; ++j) {
+                    acc_add(acc[i * KB + j], v0[i], M::wide(y0[j]));
+                    acc_add(acc[i * KB + j], v1[i], M::wide(y1[j]));
+                }
             }
-        if (++cnt == kRenorm) {
+        if (++cnt == kRenorm / 2) {
             cnt = 0;
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc[v].normalize();
         }
-#pragma unroll
-        for (int j = 0; j < KB; ++j) ya[j] = yb[j];
-#pragma unroll
-        for (int i = 0; i < KA; ++i) va[i] = vb[i];
-        p = pn;
     }
     block_reduce_df<NV>(acc, red);
     if (!publish_partial(red + kWarps * NV, NV, sc.partials, sc.counter)) return;
@@ -318,7 +319,7 @@ void mp_launch_gram(int64_t n, const void* V, int64_t ldv, int ka, const void* Y
     using T = typename Mode<P>::T;
     const int KAc = kb <= 4 ? 8 : 4;   // V columns per CTA, keeping the accumulators in registers
     const int gy = (ka + KAc - 1) / KAc;
-    int gx = grid_for(n, kMpRedCtas * 2 / gy > 0 ? kMpRedCtas * 2 / gy : 1);
+    int gx = grid_for((n + 1) / 2, kMpRedCtas * 2 / gy > 0 ? kMpRedCtas * 2 / gy : 1);
     dim3 grid(gx, gy);
     const T* Vp = (const T*)V;
     const T* Yp = (const T*)Y;
@@ -439,55 +440,162 @@ __global__ void __launch_bounds__(kThreads) mp_update_kernel(int64_t n, const ty
     run_epilogue(epi, res, KB, KB);
 }
 
-// ================================================================== Gram of one block (symmetric)
-// G = Y^T Y for kb columns, upper triangle accumulated in double-float; the next
-// row is loaded before the current one is accumulated.
+// ================================================================== projection on row pairs
+// Yout[:, j] = Yin[:, j] + V (sgn T)[:, j] for j >= j0, summed in double-float and
+// rounded once. Two consecutive rows per thread: every coefficient read from shared
+// memory serves two products, and the basis columns come in 16-byte loads, the next
+// group of kChunk columns issued before the current group is accumulated.
 template <int P, int KB>
-__global__ void __launch_bounds__(kThreads) mp_symgram_kernel(int64_t n, const typename Mode<P>::T* __restrict__ Y,
-                                                              int64_t ldy, Scratch sc, Epi epi, int gate) {
+__global__ void __launch_bounds__(kThreads) mp_project_kernel(int64_t n, const typename Mode<P>::T* __restrict__ V,
+                                                              int64_t ldv, int ka, const typename Mode<P>::T* Yin,
+                                                              int64_t ldy, typename Mode<P>::T* Yout, int64_t ldo,
+                                                              int j0, const double* __restrict__ T, int ldt, double sgn,
+                                                              Epi epi, int gate) {
     using M = Mode<P>;
     using Vt = typename M::V;
-    constexpr int NV = KB * (KB + 1) / 2;
-    __shared__ double red[(kWarps + 1) * NV];
-    __shared__ double res[(kMaxS + 1) * (kMaxS + 1)];
+    __shared__ df64 Ts[kMaxCols * KB];
     if (!gate_open(epi.st, gate)) return;
-    DfAcc acc[NV];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    Vt ya[KB];
-    if (p < n) {
-#pragma unroll
-        for (int j = 0; j < KB; ++j) ya[j] = M::load(Y + p + j * ldy);
+    for (int t = threadIdx.x; t < ka * KB; t += blockDim.x) {
+        const int i = t % ka, j = t / ka;
+        Ts[i * KB + j] = df_from_double(sgn * T[i + (int64_t)j * ldt]);
     }
-    int cnt = 0;
-    while (p < n) {
-        const int64_t pn = p + stride;
-        Vt yb[KB];
-        if (pn < n) {
+    __syncthreads();
+    const bool inplace = (Yin == Yout) && (ldy == ldo);
+    const int64_t npairs = (n + 1) / 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int nch = (ka + kChunk - 1) / kChunk;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += stride) {
+        const int64_t p = 2 * q;
+        Vt c0[kChunk], c1[kChunk];
 #pragma unroll
-            for (int j = 0; j < KB; ++j) yb[j] = M::load(Y + pn + j * ldy);
+        for (int c = 0; c < kChunk; ++c) {
+            if (c < ka) M::load2(V + p + (int64_t)c * ldv, c0[c], c1[c]);
+            else c0[c] = c1[c] = M::zero();
+        }
+        Vt y0[KB], y1[KB];
+#pragma unroll
+        for (int j = 0; j < KB; ++j) M::load2_rw(Yin + p + j * ldy, y0[j], y1[j]);
+        DfAcc s0[KB], s1[KB];
+        for (int ch = 0; ch < nch; ++ch) {
+            const int base = ch * kChunk, nb = base + kChunk;
+            Vt n0[kChunk], n1[kChunk];
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) {
+                if (nb + c < ka) M::load2(V + p + (int64_t)(nb + c) * ldv, n0[c], n1[c]);
+                else n0[c] = n1[c] = M::zero();
+            }
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) {
+                if (base + c < ka) {
+#pragma unroll
+                    for (int j = 0; j < KB; ++j)
+                        if (j >= j0) {
+                            const df64 t = Ts[(base + c) * KB + j];
+                            acc_add(s0[j], c0[c], t);
+                            acc_add(s1[j], c1[c], t);
+                        }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) {
+                c0[c] = n0[c];
+                c1[c] = n1[c];
+            }
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                s0[j].normalize();
+                s1[j].normalize();
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < KB; ++j) {
+            if (j >= j0 && ka > 0) {
+                y0[j] = M::narrow(df_add(M::wide(y0[j]), df64{s0[j].hi, s0[j].lo}));
+                y1[j] = M::narrow(df_add(M::wide(y1[j]), df64{s1[j].hi, s1[j].lo}));
+            }
+            if (!inplace || (j >= j0 && ka > 0)) M::store2(Yout + p + j * ldo, y0[j], y1[j]);
+        }
+    }
+}
+
+// ================================================================== Gram of one block (symmetric)
+// G = Y^T Y for kb columns; the packed upper triangle (entry (p, q), p <= q, at
+// q(q+1)/2 + p) is split between two CTA groups by column q (q < QS and q >= QS,
+// QS chosen to balance the entry counts) so neither group runs out of registers.
+// Two rows per thread with 16-byte loads; double-float accumulation.
+__host__ __device__ constexpr int tri(int q) { return q * (q + 1) / 2; }
+__host__ __device__ constexpr int sym_split(int kb) {
+    int best = 1, bestv = 1 << 30;
+    for (int q = 1; q < kb; ++q) {
+        const int a = tri(q), b = tri(kb) - tri(q);
+        const int v = a > b ? a : b;
+        if (v < bestv) {
+            bestv = v;
+            best = q;
+        }
+    }
+    return best;
+}
+
+template <int P, int KB, int Q0, int Q1>
+__device__ __forceinline__ void symgram_rows(int64_t n, const typename Mode<P>::T* __restrict__ Y, int64_t ldy,
+                                             DfAcc* acc) {
+    using M = Mode<P>;
+    using Vt = typename M::V;
+    constexpr int NV = tri(Q1) - tri(Q0);
+    const int64_t npairs = (n + 1) / 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int cnt = 0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += stride) {
+        const int64_t p = 2 * q;
+        Vt y0[Q1], y1[Q1];
+#pragma unroll
+        for (int j = 0; j < Q1; ++j) M::load2(Y + p + j * ldy, y0[j], y1[j]);
+        if (p + 1 >= n) {
+#pragma unroll
+            for (int j = 0; j < Q1; ++j) y1[j] = M::zero();
         }
         int idx = 0;
 #pragma unroll
-        for (int q = 0; q < KB; ++q)
+        for (int c = Q0; c < Q1; ++c)
 #pragma unroll
-            for (int pp = 0; pp <= q; ++pp) {
-                acc_add(acc[idx], ya[pp], M::wide(ya[q]));
+            for (int r = 0; r <= c; ++r) {
+                acc_add(acc[idx], y0[r], M::wide(y0[c]));
+                acc_add(acc[idx], y1[r], M::wide(y1[c]));
                 ++idx;
             }
-        if (++cnt == kRenorm) {
+        if (++cnt == kRenorm / 2) {
             cnt = 0;
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc[v].normalize();
         }
-#pragma unroll
-        for (int j = 0; j < KB; ++j) ya[j] = yb[j];
-        p = pn;
     }
-    block_reduce_df<NV>(acc, red);
-    if (!publish_partial(red + kWarps * NV, NV, sc.partials, sc.counter)) return;
-    __shared__ double packed[NV];
-    finish_reduction(packed, NV, gridDim.x * gridDim.y, sc);
+}
+
+template <int P, int KB>
+__global__ void __launch_bounds__(kThreads) mp_symgram_kernel(int64_t n, const typename Mode<P>::T* __restrict__ Y,
+                                                              int64_t ldy, Scratch sc, Epi epi, int gate) {
+    constexpr int QS = sym_split(KB);
+    constexpr int NV0 = tri(QS), NV1 = tri(KB) - tri(QS);
+    constexpr int NVM = NV0 > NV1 ? NV0 : NV1;
+    __shared__ double red[(kWarps + 1) * NVM];
+    __shared__ double res[(kMaxS + 1) * (kMaxS + 1)];
+    __shared__ double packed[tri(KB)];
+    if (!gate_open(epi.st, gate)) return;
+    DfAcc acc[NVM];
+    if (blockIdx.y == 0) symgram_rows<P, KB, 0, QS>(n, Y, ldy, acc);
+    else symgram_rows<P, KB, QS, KB>(n, Y, ldy, acc);
+    block_reduce_df<NVM>(acc, red);
+    if (!publish_partial(red + kWarps * NVM, NVM, sc.partials, sc.counter)) return;
+    const int gx = gridDim.x;
+    for (int e = threadIdx.x; e < tri(KB); e += blockDim.x) {
+        const int g = e < NV0 ? 0 : 1, le = g == 0 ? e : e - NV0;
+        double t = 0.0;
+        for (int bx = 0; bx < gx; ++bx) t += ld_cg(sc.partials + (int64_t)(g * gx + bx) * NVM + le);
+        packed[e] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *sc.counter = 0u;
     for (int t = threadIdx.x; t < KB * KB; t += blockDim.x) {
         int pp = t % KB, q = t / KB;
         if (pp > q) {
@@ -495,7 +603,7 @@ __global__ void __launch_bounds__(kThreads) mp_symgram_kernel(int64_t n, const t
             pp = q;
             q = tmp;
         }
-        res[t] = packed[q * (q + 1) / 2 + pp];
+        res[t] = packed[tri(q) + pp];
     }
     __syncthreads();
     run_epilogue(epi, res, KB, KB);
@@ -509,12 +617,32 @@ void mp_launch_update(int64_t n, const void* V, int64_t ldv, int ka, const void*
     const Tt* Vp = (const Tt*)V;
     const Tt* Yi = (const Tt*)Yin;
     Tt* Yo = (Tt*)Yout;
-    if (gram && kb > 2) {
+    if (!gram) {
+        int grid = grid_for((n + 1) / 2, kMpCtas);
+        switch (kb) {
+#define SSTEP_MPP(KB)                                                                                             \
+    case KB:                                                                                                      \
+        mp_project_kernel<P, KB><<<grid, kThreads, 0, stream>>>(n, Vp, ldv, ka, Yi, ldy, Yo, ldo, j0, T, ldt, sgn, \
+                                                                epi, gate);                                      \
+        break;
+            SSTEP_MPP(1)
+            SSTEP_MPP(2)
+            SSTEP_MPP(3)
+            SSTEP_MPP(4)
+            SSTEP_MPP(5)
+            SSTEP_MPP(6)
+            SSTEP_MPP(7)
+            SSTEP_MPP(8)
+            SSTEP_MPP(9)
+#undef SSTEP_MPP
+            default: break;
+        }
+        return;
+    }
+    if (kb > 2) {
         // wide blocks: the projection alone (light, many CTAs), then the block's Gram
-        Epi none = epi;
-        none.mode = EPI_NONE;
-        mp_launch_update<P>(n, V, ldv, ka, Yin, ldy, Yout, ldo, kb, j0, T, ldt, sgn, false, sc, none, gate, stream);
-        int grid = grid_for(n, kMpRedCtas);
+        mp_launch_update<P>(n, V, ldv, ka, Yin, ldy, Yout, ldo, kb, j0, T, ldt, sgn, false, sc, epi, gate, stream);
+        dim3 grid(grid_for((n + 1) / 2, kMpRedCtas), 2);
         switch (kb) {
 #define SSTEP_MPS(KB) \
     case KB: mp_symgram_kernel<P, KB><<<grid, kThreads, 0, stream>>>(n, Yo, ldo, sc, epi, gate); break;
@@ -530,27 +658,12 @@ void mp_launch_update(int64_t n, const void* V, int64_t ldv, int ka, const void*
         }
         return;
     }
-    int grid = grid_for(n, gram ? kMpRedCtas * 2 : kMpCtas);
+    int grid = grid_for(n, kMpRedCtas * 2);
     switch (kb) {
-#define SSTEP_MPU(KB)                                                                                         \
-    case KB:                                                                                                  \
-        if (gram)                                                                                             \
-            mp_update_kernel<P, KB, true><<<grid, kThreads, 0, stream>>>(n, Vp, ldv, ka, Yi, ldy, Yo, ldo, j0, \
-                                                                         T, ldt, sgn, sc, epi, gate);        \
-        else                                                                                                  \
-            mp_update_kernel<P, KB, false><<<grid, kThreads, 0, stream>>>(n, Vp, ldv, ka, Yi, ldy, Yo, ldo,    \
-                                                                          j0, T, ldt, sgn, sc, epi, gate);   \
-        break;
-        SSTEP_MPU(1)
-        SSTEP_MPU(2)
-        SSTEP_MPU(3)
-        SSTEP_MPU(4)
-        SSTEP_MPU(5)
-        SSTEP_MPU(6)
-        SSTEP_MPU(7)
-        SSTEP_MPU(8)
-        SSTEP_MPU(9)
-#undef SSTEP_MPU
+        case 1: mp_update_kernel<P, 1, true><<<grid, kThreads, 0, stream>>>(n, Vp, ldv, ka, Yi, ldy, Yo, ldo, j0, T, ldt,
+                                                                            sgn, sc, epi, gate); break;
+        case 2: mp_update_kernel<P, 2, true><<<grid, kThreads, 0, stream>>>(n, Vp, ldv, ka, Yi, ldy, Yo, ldo, j0, T, ldt,
+                                                                            sgn, sc, epi, gate); break;
         default: break;
     }
 }
