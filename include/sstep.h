@@ -64,6 +64,12 @@ int stencil_matrix_create_fields(sstep_matrix* out, int dim, const int64_t shape
  * ap_d = -1 + c_d. beta (host) holds dim values. */
 int stencil_matrix_create_convdiff(sstep_matrix* out, int dim, const int64_t shape[3], const double* beta);
 
+/* The 2-D operator of -Lap u + beta(x, y) (u_x + u_y) on an N x N interior grid
+ * (non-conservative form): row p has a0 = 4 and am_d = -1 - c_p, ap_d = -1 + c_p with
+ * c_p = beta_p h / 2, h = 1/(N+1). beta_field: DEVICE array of N*N values (copied;
+ * the coefficient fields are computed on the device). */
+int stencil_matrix_create_convdiff_variable(sstep_matrix* out, int64_t N, const double* beta_field, void* stream);
+
 int stencil_matrix_destroy(sstep_matrix A);
 
 /* n (number of unknowns) and ||A||_inf (max absolute row sum). Host outputs. */
@@ -141,6 +147,8 @@ typedef struct {
                            SSTEP_PREC_FP32: FP32 basis and powers, inner products accumulated in
                            double-float; with the FP64 restart residual this is FP32 iterative
                            refinement. f, x, residuals and all scalar work are FP64 in every mode. */
+    int x0_guard;       /* 1: if ||f - A x0|| > ||f|| on entry, start from x0 = 0 instead (for
+                           predicted initial guesses); 0: use x0 as given */
 } sstep_params;
 
 #define SSTEP_PREC_FP64 0
@@ -205,6 +213,42 @@ int sstep_batch_tune(sstep_batch B, const double* const* f, double* const* x, in
 int sstep_batch_destroy(sstep_batch B);
 
 const char* sstep_status_string(int status);
+
+/* ------------------------------------------------------------------ learned initial guess
+ * A 4-level convolutional U-Net mapping the channels (f, beta) of an H x W grid
+ * (H, W multiples of 8) to an initial guess x0 for the solvers above. The paper has
+ * no such component: it is a predictor whose output only enters as x0, and the
+ * solver's own stopping test decides convergence. Weights are BF16 with an FP32
+ * master copy (bf16_weights = 0 keeps FP32 weights, for gradient checks); every
+ * product accumulates in FP32; activations are FP32, NCHW.
+ * Layers (3x3, padding 1, ReLU): 2->16->16 | pool | 16->32->32 | pool | 32->64->64 |
+ * pool | 64->64->64 | up, concat | 128->64->64 | up, concat | 96->32->32 | up,
+ * concat | 48->16->16 | 1x1 16->1, then smooth_passes passes of the fixed filter
+ * [1 2 1]/4 x [1 2 1]/4 (zero outside the grid). Pooling: 2x2 mean; upsampling: nearest.
+ * Parameters: one flat FP32 vector, per layer W[co][ci][kh][kw] then b[co].
+ * input: DEVICE (batch, 2, H, W) float32; output/target: DEVICE (batch, 1, H, W). */
+typedef struct x0net_s* x0net;
+int x0net_create(x0net* out, int H, int W, int batch_max, int bf16_weights, int smooth_passes);
+int x0net_destroy(x0net X);
+int x0net_num_params(x0net X, int64_t* n);
+/* Adds w * mean((kappa A out - f_hat)^2) to the loss (w = 0: mean-squared error only), for
+ * the operator the features encode: channel 0 = f_hat = f / s_f, channel 1 = beta / 20, A the
+ * h^2-scaled operator of -Lap u + beta (u_x + u_y) on the H x W interior grid, h = 1/(H+1),
+ * and out the solution divided by kappa s_f. The residual term penalises the rough error
+ * components that A amplifies in ||f - A x0||. */
+int x0net_set_residual_weight(x0net X, float w, float kappa);
+/* params: host or device float32 array of x0net_num_params values; resets Adam */
+int x0net_set_params(x0net X, const float* params, void* stream);
+int x0net_get_params(x0net X, float* params, void* stream);
+int x0net_forward(x0net X, const float* input, float* output, int batch, void* stream);
+/* loss = mean over batch*H*W of (out - target)^2 and its gradient with respect to
+ * every parameter (host or device outputs; either may be NULL). Synchronises. */
+int x0net_gradient(x0net X, const float* input, const float* target, int batch, float* loss, float* grads,
+                   void* stream);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean-squared loss;
+ * loss_dev (DEVICE, may be NULL) receives the loss before the step. */
+int x0net_train_step(x0net X, const float* input, const float* target, int batch, float lr, float* loss_dev,
+                     void* stream);
 
 /* ------------------------------------------------------------------ launch tracing
  * The library counts every kernel launch of the solvers per kernel kind. With

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 from ._binding import (  # noqa: F401
     BatchSolver,
+    X0Net,
     SSTEP_MAX_COLS,
     SSTEP_MAX_M,
     SSTEP_MAX_S,
@@ -32,6 +33,7 @@ from ._binding import (  # noqa: F401
 
 __all__ = [
     "BatchSolver",
+    "X0Net",
     "StencilMatrix",
     "stencil_matrix_apply",
     "sstep_matrix_powers",

@@ -21,7 +21,7 @@ P = ctypes.POINTER
 class SStepParams(ctypes.Structure):
     _fields_ = [("s", c_int), ("m", c_int), ("k", c_int), ("tol", c_double), ("max_cycles", c_int),
                 ("max_iters", c_int), ("sigma", c_double), ("history", P(c_double)), ("history_cap", c_int),
-                ("precision", c_int)]
+                ("precision", c_int), ("x0_guard", c_int)]
 
 
 PRECISIONS = {"fp64": 0, "df64": 1, "fp32": 2}
@@ -37,6 +37,7 @@ SIGNATURES = {
     "stencil_matrix_create": (c_int, [P(c_void_p), c_int, P(c_int64), P(c_double)]),
     "stencil_matrix_create_fields": (c_int, [P(c_void_p), c_int, P(c_int64), P(c_void_p), c_void_p]),
     "stencil_matrix_create_convdiff": (c_int, [P(c_void_p), c_int, P(c_int64), P(c_double)]),
+    "stencil_matrix_create_convdiff_variable": (c_int, [P(c_void_p), c_int64, c_void_p, c_void_p]),
     "stencil_matrix_destroy": (c_int, [c_void_p]),
     "stencil_matrix_info": (c_int, [c_void_p, P(c_int64), P(c_double)]),
     "stencil_matrix_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -56,6 +57,15 @@ SIGNATURES = {
     "sstep_batch_solve": (c_int, [c_void_p, P(c_void_p), P(c_void_p), P(SStepResult), c_int, c_void_p]),
     "sstep_batch_tune": (c_int, [c_void_p, P(c_void_p), P(c_void_p), P(c_int), P(c_int), P(c_int), c_void_p]),
     "sstep_batch_destroy": (c_int, [c_void_p]),
+    "x0net_create": (c_int, [P(c_void_p), c_int, c_int, c_int, c_int, c_int]),
+    "x0net_destroy": (c_int, [c_void_p]),
+    "x0net_num_params": (c_int, [c_void_p, P(c_int64)]),
+    "x0net_set_residual_weight": (c_int, [c_void_p, ctypes.c_float, ctypes.c_float]),
+    "x0net_set_params": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "x0net_get_params": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "x0net_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "x0net_gradient": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "x0net_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p, c_void_p]),
     "sstep_trace_enable": (c_int, [c_int]),
     "sstep_trace_kinds": (c_int, []),
     "sstep_trace_kind_name": (ctypes.c_char_p, [c_int]),
@@ -128,11 +138,15 @@ def _col_major(t, name):
 class StencilMatrix:
     """Handle of a (2d+1)-point stencil operator (include/sstep.h, operator section)."""
 
-    def __init__(self, dim, shape, coef=None, beta=None, fields=None, stream=None):
+    def __init__(self, dim, shape, coef=None, beta=None, fields=None, beta_field=None, stream=None):
         L = lib()
         h = c_void_p()
         shp = (c_int64 * 3)(*(list(shape) + [1] * (3 - len(shape))))
-        if beta is not None:
+        if beta_field is not None:
+            _check("stencil_matrix_create_convdiff_variable",
+                   L.stencil_matrix_create_convdiff_variable(ctypes.byref(h), shape[0], _ptr(beta_field),
+                                                             _stream(stream)))
+        elif beta is not None:
             b = (c_double * 3)(*list(beta))
             _check("stencil_matrix_create_convdiff", L.stencil_matrix_create_convdiff(ctypes.byref(h), dim, shp, b))
         elif coef is not None:
@@ -240,13 +254,13 @@ def sstep_block_update(V, Y, T, work=None, stream=None):
 
 
 def _solve(name, A, f, x, s=1, m=20, k=1, tol=1e-8, max_cycles=1000, max_iters=100000, sigma=0.0,
-           history_cap=4096, stream=None, precision="fp64"):
+           history_cap=4096, stream=None, precision="fp64", x0_guard=False):
     import numpy as np
 
     hist = np.zeros(max(history_cap, 1), dtype=np.float64)
     p = SStepParams(s=s, m=m, k=k, tol=tol, max_cycles=max_cycles, max_iters=max_iters, sigma=sigma,
                     history=hist.ctypes.data_as(P(c_double)) if history_cap > 0 else None,
-                    history_cap=history_cap, precision=PRECISIONS[precision])
+                    history_cap=history_cap, precision=PRECISIONS[precision], x0_guard=1 if x0_guard else 0)
     r = SStepResult()
     rc = getattr(lib(), name)(A.handle, _ptr(f), _ptr(x), ctypes.byref(p), ctypes.byref(r), _stream(stream))
     _check(name, rc)
@@ -255,13 +269,13 @@ def _solve(name, A, f, x, s=1, m=20, k=1, tol=1e-8, max_cycles=1000, max_iters=1
 
 
 def sstep_gmres_solve(A, f, x, s, m, tol, max_cycles=1000, sigma=0.0, history_cap=4096, stream=None,
-                      precision="fp64"):
+                      precision="fp64", x0_guard=False):
     """s-step GMRES (Alg. 4.1/4.2); x is updated in place. Returns the result as a dict.
 
     precision: "fp64", "df64" (double-float basis) or "fp32" (FP32 basis, FP32 iterative refinement).
     """
     return _solve("sstep_gmres_solve", A, f, x, s=s, m=m, tol=tol, max_cycles=max_cycles, sigma=sigma,
-                  history_cap=history_cap, stream=stream, precision=precision)
+                  history_cap=history_cap, stream=stream, precision=precision, x0_guard=x0_guard)
 
 
 def gmres_solve(A, f, x, m, tol, max_cycles=1000, history_cap=4096, stream=None, precision="fp64"):
@@ -303,13 +317,13 @@ class BatchSolver:
     PERSISTENT = 0
     PER_SYSTEM = 1
 
-    def __init__(self, mats, s, m, tol, max_cycles=1000, sigma=0.0):
+    def __init__(self, mats, s, m, tol, max_cycles=1000, sigma=0.0, x0_guard=False):
         self.mats = list(mats)
         self.n = len(self.mats)
         h = c_void_p()
         arr = (c_void_p * self.n)(*[A.handle.value for A in self.mats])
         p = SStepParams(s=s, m=m, k=0, tol=tol, max_cycles=max_cycles, max_iters=0, sigma=sigma, history=None,
-                        history_cap=0, precision=0)
+                        history_cap=0, precision=0, x0_guard=1 if x0_guard else 0)
         _check("sstep_batch_create", lib().sstep_batch_create(ctypes.byref(h), self.n, arr, ctypes.byref(p)))
         self.handle = h
 
@@ -331,6 +345,77 @@ class BatchSolver:
     def close(self):
         if self.handle:
             lib().sstep_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class X0Net:
+    """The learned-initial-guess U-Net (include/sstep.h, learned initial guess).
+
+    Tensors are float32 CUDA tensors: input (B, 2, H, W), output/target (B, 1, H, W).
+    """
+
+    def __init__(self, H, W, batch_max, bf16=True, smooth=4, residual_weight=0.0, kappa=1.0):
+        h = c_void_p()
+        _check("x0net_create", lib().x0net_create(ctypes.byref(h), H, W, batch_max, 1 if bf16 else 0, smooth))
+        _check("x0net_set_residual_weight", lib().x0net_set_residual_weight(h, residual_weight, kappa))
+        self.handle = h
+        n = c_int64()
+        _check("x0net_num_params", lib().x0net_num_params(h, ctypes.byref(n)))
+        self.num_params = n.value
+        self.H, self.W = H, W
+
+    @staticmethod
+    def _f32(t):
+        import torch
+
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError("expected a contiguous float32 CUDA tensor")
+        return c_void_p(t.data_ptr())
+
+    def set_params(self, theta, stream=None):
+        import torch
+
+        t = torch.as_tensor(theta, dtype=torch.float32).contiguous()
+        if not t.is_cuda:
+            t = t.cuda()
+        _check("x0net_set_params", lib().x0net_set_params(self.handle, c_void_p(t.data_ptr()), _stream(stream)))
+        torch.cuda.current_stream().synchronize()
+
+    def get_params(self, stream=None):
+        import numpy as np
+
+        out = np.zeros(self.num_params, dtype=np.float32)
+        _check("x0net_get_params", lib().x0net_get_params(self.handle, c_void_p(out.ctypes.data), _stream(stream)))
+        return out
+
+    def forward(self, inp, out, stream=None):
+        _check("x0net_forward", lib().x0net_forward(self.handle, self._f32(inp), self._f32(out), inp.shape[0],
+                                                    _stream(stream)))
+
+    def gradient(self, inp, target, stream=None):
+        import numpy as np
+
+        g = np.zeros(self.num_params, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        _check("x0net_gradient", lib().x0net_gradient(self.handle, self._f32(inp), self._f32(target), inp.shape[0],
+                                                      c_void_p(loss.ctypes.data), c_void_p(g.ctypes.data),
+                                                      _stream(stream)))
+        return float(loss[0]), g
+
+    def train_step(self, inp, target, lr, loss_out=None, stream=None):
+        lp = self._f32(loss_out) if loss_out is not None else c_void_p(0)
+        _check("x0net_train_step", lib().x0net_train_step(self.handle, self._f32(inp), self._f32(target), inp.shape[0],
+                                                          lr, lp, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            lib().x0net_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -191,6 +191,14 @@ __device__ void cta_solve(const BatchSys& b, double* scratch) {
     e.mode = EPI_NF;
     run_epilogue(e, res, 1, 1);
     __syncthreads();
+    if (st->pad_) {   // x0 guard: restart from zero when ||f - A x0|| > ||f||
+        cta_residual(A, b.f, b.x, nullptr, scratch, res);
+        const bool bad = !(res[0] <= st->nf * st->nf);
+        __syncthreads();
+        if (bad)
+            for (int64_t p = threadIdx.x; p < n; p += blockDim.x) b.x[p] = 0.0;
+        __syncthreads();
+    }
     for (;;) {
         cta_residual(A, b.f, b.x, uraw, scratch, res);
         e.mode = EPI_RESTART;

@@ -261,6 +261,21 @@ int read_header(sstep_matrix M, SolverState* st, cudaStream_t stream) {
     return SSTEP_OK;
 }
 
+// x0_guard: when ||f - A x0|| > ||f|| (st->nf already set), start from x0 = 0
+int apply_x0_guard(sstep_matrix M, const Layout& l, SolverState* st, const double* f, double* x,
+                   cudaStream_t stream) {
+    Scratch sc{(double*)(M->ws + l.partials), (unsigned*)(M->ws + l.counter)};
+    Epi e;
+    e.mode = EPI_FINAL;
+    e.st = st;
+    launch_residual(M->A, f, x, nullptr, sc, e, GATE_NONE, stream);
+    CUDA_TRY(cudaGetLastError());
+    int rc = read_header(M, st, stream);
+    if (rc) return rc;
+    if (!(M->hdr->relres <= 1.0)) CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * M->A.n, stream));
+    return SSTEP_OK;
+}
+
 
 // ------------------------------------------------------------------ mixed-precision basis drivers
 // The same kernel sequences as the FP64 drivers below, with the basis columns in
@@ -288,6 +303,7 @@ int sstep_gmres_mp(sstep_matrix M, const double* f, double* x, const sstep_param
     e.st = st;
     e.mode = EPI_NF;
     TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, nullptr, nullptr, sc, e, GATE_NONE, stream_));
+    if (p->x0_guard && (rc = apply_x0_guard(M, l, st, f, x, stream_))) return rc;
     const double sigma = h.sigma;
     const int nb = m / s;
     for (;;) {
@@ -359,6 +375,7 @@ int gmres_mp(sstep_matrix M, const double* f, double* x, const sstep_params* p, 
     e.st = st;
     e.mode = EPI_NF;
     TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, nullptr, nullptr, sc, e, GATE_NONE, stream_));
+    if (p->x0_guard && (rc = apply_x0_guard(M, l, st, f, x, stream_))) return rc;
     for (;;) {
         e = Epi();
         e.st = st;
@@ -433,6 +450,7 @@ SolverState batch_state(char* base, int m, int s, const sstep_params* p, double 
     q.history_cap = 0;
     SolverState h = init_state(l, base, &q, s, m, 0);
     h.sigma = sigma;
+    h.pad_ = p->x0_guard ? 1 : 0;   // the batched kernel reads the x0 guard here
     return h;
 }
 
@@ -626,6 +644,25 @@ int stencil_matrix_create_fields(sstep_matrix* out, int dim, const int64_t shape
     return SSTEP_OK;
 }
 
+int stencil_matrix_create_convdiff_variable(sstep_matrix* out, int64_t N, const double* beta_field, void* stream) {
+    if (!out || !beta_field || N < 1 || N > 46340) return SSTEP_ERR_ARG;
+    *out = nullptr;
+    const int64_t n = N * N;
+    double* tmp = nullptr;
+    if (cudaMalloc((void**)&tmp, sizeof(double) * n * 5) != cudaSuccess) {
+        cudaGetLastError();
+        return SSTEP_ERR_OOM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_convdiff_fields(beta_field, 1.0 / (double)(N + 1), n, tmp, s);
+    const double* f[5] = {tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, tmp + 4 * n};
+    const int64_t shape[3] = {N, N, 1};
+    int rc = stencil_matrix_create_fields(out, 2, shape, f, stream);
+    cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    return rc;
+}
+
 int stencil_matrix_destroy(sstep_matrix M) {
     if (!M) return SSTEP_ERR_ARG;
     if (M->fields) cudaFree(M->fields);
@@ -732,6 +769,7 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     e.st = st;
     e.mode = EPI_NF;
     TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, nullptr, nullptr, sc, e, GATE_NONE, stream_));
+    if (p->x0_guard && (rc = apply_x0_guard(M, l, st, f, x, stream_))) return rc;
     const double sigma = h.sigma;
     const int nb = m / s;
     for (;;) {
@@ -809,6 +847,7 @@ int gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_params* 
     e.st = st;
     e.mode = EPI_NF;
     TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, nullptr, nullptr, sc, e, GATE_NONE, stream_));
+    if (p->x0_guard && (rc = apply_x0_guard(M, l, st, f, x, stream_))) return rc;
     for (;;) {
         e = Epi();
         e.st = st;
@@ -870,6 +909,7 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
     e.st = st;
     e.mode = EPI_NF;
     TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, nullptr, nullptr, sc, e, GATE_NONE, stream_));
+    if (p->x0_guard && (rc = apply_x0_guard(M, l, st, f, x, stream_))) return rc;
     const double sigma = h.sigma;
     auto powers = [&]() {   // A R_{i+1}: A r, then A (sigma A R_j)
         TRACED(K_STENCIL, stream_, launch_stencil(M->A, r, 1.0, AR, 0.0, nullptr, nullptr, st, GATE_BUILDING, stream_));

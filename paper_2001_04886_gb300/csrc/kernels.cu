@@ -406,6 +406,23 @@ void launch_omin_pupdate(int64_t n, const double* r, const double* AR, const dou
     }
 }
 
+// ================================================================== variable-coefficient operator fields
+__global__ void convdiff_fields_kernel(const double* __restrict__ beta, double h, int64_t n, double* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        const double c = beta[p] * h / 2.0;
+        out[p] = 4.0;
+        out[n + p] = -1.0 - c;
+        out[2 * n + p] = -1.0 + c;
+        out[3 * n + p] = -1.0 - c;
+        out[4 * n + p] = -1.0 + c;
+    }
+}
+
+void launch_convdiff_fields(const double* beta, double h, int64_t n, double* out, cudaStream_t stream) {
+    convdiff_fields_kernel<<<grid_for(n, kMaxCtas), kThreads, 0, stream>>>(beta, h, n, out);
+}
+
 // ================================================================== least squares solve
 // y = R^{-1} g by back substitution: R and g are staged in shared memory and each
 // row's dot product is a warp reduction (fixed order), so the dependent chain is K

@@ -84,6 +84,10 @@ void launch_lsq_solve(SolverState* st, int gate, cudaStream_t stream);
 
 int max_partials_doubles();
 
+// out = [a0 | am_x | ap_x | am_y | ap_y] (5 arrays of n) for -Lap u + beta (u_x + u_y):
+// a0 = 4, am = -1 - beta h/2, ap = -1 + beta h/2
+void launch_convdiff_fields(const double* beta, double h, int64_t n, double* out, cudaStream_t stream);
+
 }  // namespace sstep
 
 namespace sstep {

@@ -1,0 +1,194 @@
+"""The learned-initial-guess form: a U-Net predicts x0 for the s-step GMRES solve.
+
+Systems: the 2-D operator of -Lap u + beta(x, y)(u_x + u_y) on an N x N grid, beta
+and f from 8 random Fourier modes each (inputs.fourier_fields). Training data are
+solutions computed by the library's own FP64 s-step GMRES (batched persistent
+solver); the network (X0Net) is trained with the library's own forward/backward
+and Adam kernels. Evaluation solves held-out systems from x0 = 0 and from the
+predicted x0; the solver's x0 guard falls back to x0 = 0 when the predicted
+guess's residual exceeds ||f||, so the method is never worse off in iterations
+than without the network.
+
+Scaling: the network sees f / s_f and beta / 20 (s_f = rms of f) and predicts
+x / (kappa s_f) with kappa = 1 / (2 pi^2 h^2), the inverse of the smallest
+eigenvalue scale of the h^2-scaled operator, so that targets are O(1) on every
+grid; since A x = f is linear in f for fixed beta, scaling f scales x.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import inputs
+from ._binding import BatchSolver, StencilMatrix, X0Net
+
+BETA_SCALE = 20.0
+
+
+def kappa(N):
+    h = 1.0 / (N + 1)
+    return 1.0 / (2.0 * np.pi ** 2 * h * h)
+
+
+def make_systems(seeds, N, device):
+    """Operators, right-hand sides (FP64, device), features (FP32, device) and f scales."""
+    import torch
+
+    mats, fs, feats, scales = [], [], [], []
+    for sd in seeds:
+        beta, f = inputs.fourier_fields(int(sd), N)
+        sf = float(np.sqrt(np.mean(f * f)))
+        mats.append(StencilMatrix(2, (N, N), beta_field=torch.tensor(beta, dtype=torch.float64, device=device)))
+        fs.append(torch.tensor(f, dtype=torch.float64, device=device))
+        feat = np.stack([f / sf, beta / BETA_SCALE]).astype(np.float32).reshape(2, N, N)
+        feats.append(torch.tensor(feat, device=device))
+        scales.append(sf)
+    return mats, fs, torch.stack(feats), np.array(scales)
+
+
+def solve_batch(mats, fs, x0s, s=4, m=20, tol=1e-8, guard=False, tune=False):
+    """Batched persistent s-step GMRES; returns (results, milliseconds)."""
+    import torch
+
+    B = BatchSolver(mats, s, m, tol, max_cycles=5000, x0_guard=guard)
+    if tune:
+        B.tune(fs, x0s)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    res = B.solve(fs, x0s, mode=B.PERSISTENT)
+    e1.record(st)
+    torch.cuda.synchronize()
+    B.close()
+    return res, e0.elapsed_time(e1)
+
+
+def generate(seeds, N, device, chunk=1024):
+    """Training pairs: features (S, 2, N, N) and targets x / s_f (S, 1, N, N), FP32 on the device."""
+    import torch
+
+    feats, targets = [], []
+    for c0 in range(0, len(seeds), chunk):
+        mats, fs, ft, sc = make_systems(seeds[c0 : c0 + chunk], N, device)
+        xs = [torch.zeros_like(f) for f in fs]
+        res, _ = solve_batch(mats, fs, xs)
+        if not all(r["status"] == 0 for r in res):
+            raise RuntimeError("a training system did not converge")
+        k = kappa(N)
+        for x, s_ in zip(xs, sc):
+            targets.append((x / (k * s_)).to(torch.float32).reshape(1, N, N))
+        feats.append(ft)
+        del mats, fs, xs
+    return torch.cat(feats), torch.stack(targets)
+
+
+def train(net, feats, targets, epochs, batch=32, lr=1e-3, seed=0, log=None):
+    """Adam on the mean-squared error; learning rate halved for the last third of the epochs."""
+    import torch
+
+    S = feats.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    lossd = torch.zeros(1, dtype=torch.float32, device=feats.device)
+    history = []
+    for ep in range(epochs):
+        rate = lr if ep < (2 * epochs) // 3 else lr / 2
+        perm = torch.randperm(S, generator=g).to(feats.device)
+        tot, nb = 0.0, 0
+        for b0 in range(0, S - batch + 1, batch):
+            idx = perm[b0 : b0 + batch]
+            net.train_step(feats.index_select(0, idx).contiguous(), targets.index_select(0, idx).contiguous(), rate,
+                           lossd)
+            if (b0 // batch) % 16 == 0:
+                tot += float(lossd.item())
+                nb += 1
+        history.append(tot / max(nb, 1))
+        if log:
+            log(f"epoch {ep}: loss {history[-1]:.4e}")
+    return history
+
+
+def predict(net, feats, scales, batch=32):
+    """x0 = s_f * net(features), FP64 device vectors."""
+    import torch
+
+    N = feats.shape[-1]
+    assert feats.dim() == 4 and feats.shape[-2] == N, "features must be (S, 2, N, N)"
+    out = torch.empty((batch, 1, N, N), dtype=torch.float32, device=feats.device)
+    x0s = []
+    for b0 in range(0, feats.shape[0], batch):
+        chunk = feats[b0 : b0 + batch].contiguous()
+        o = out[: chunk.shape[0]]
+        net.forward(chunk, o)
+        for i in range(chunk.shape[0]):
+            x0s.append((o[i].reshape(-1).to(torch.float64) * float(kappa(N) * scales[b0 + i])).contiguous())
+    return x0s
+
+
+def evaluate(net, seeds, N, device):
+    """Cycles, Krylov steps and solve time from x0 = 0 and from the predicted x0 (with the guard)."""
+    import torch
+
+    mats, fs, ft, sc = make_systems(seeds, N, device)
+    x_zero = [torch.zeros_like(f) for f in fs]
+    r0, t0 = solve_batch(mats, fs, x_zero)
+    torch.cuda.synchronize()
+    ti = time.perf_counter()
+    x_pred = predict(net, ft, sc)
+    torch.cuda.synchronize()
+    t_inf = 1e3 * (time.perf_counter() - ti)
+    r1, t1 = solve_batch(mats, fs, x_pred, guard=True)
+    ok = all(r["status"] == 0 for r in r0 + r1)
+    return {
+        "systems": len(seeds), "all_converged": ok,
+        "zero": {"mean_cycles": float(np.mean([r["cycles"] for r in r0])),
+                 "mean_iters": float(np.mean([r["iters"] for r in r0])),
+                 "mean_matvecs": float(np.mean([r["matvecs"] for r in r0])), "solve_ms": t0},
+        "predicted": {"mean_cycles": float(np.mean([r["cycles"] for r in r1])),
+                      "mean_iters": float(np.mean([r["iters"] for r in r1])),
+                      "mean_matvecs": float(np.mean([r["matvecs"] for r in r1])), "solve_ms": t1,
+                      "inference_ms": t_inf},
+    }
+
+
+def run(N=128, train_seeds=range(20000), test_seeds=range(20000, 21000), epochs=8, batch=32, lr=1e-3, log=print,
+        smooth=4, residual_weight=1.0):
+    """The whole form: generate, train, evaluate. Returns a dict of the measurements."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = time.perf_counter()
+    feats, targets = generate(np.array(list(train_seeds)), N, dev)
+    t_gen = time.perf_counter() - t
+    net = X0Net(N, N, batch, bf16=True, smooth=smooth, residual_weight=residual_weight, kappa=kappa(N))
+    from . import inputs as _in
+
+    u = _in.uniform01(12345, net.num_params)
+    net.set_params(_init_params(u))
+    t = time.perf_counter()
+    hist = train(net, feats, targets, epochs, batch, lr, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t
+    ev = evaluate(net, np.array(list(test_seeds)), N, dev)
+    ev.update({"grid": N, "train_systems": len(list(train_seeds)), "epochs": epochs, "loss_history": hist,
+               "generate_s": t_gen, "train_s": t_train, "params": net.num_params})
+    net.close()
+    return ev
+
+
+# layer shapes (cin, cout, k) in the library's parameter order
+_LAYERS = [(2, 16, 3), (16, 16, 3), (16, 32, 3), (32, 32, 3), (32, 64, 3), (64, 64, 3), (64, 64, 3), (64, 64, 3),
+           (128, 64, 3), (64, 64, 3), (96, 32, 3), (32, 32, 3), (48, 16, 3), (16, 16, 3), (16, 1, 1)]
+
+
+def _init_params(u):
+    """Uniform He initialisation W ~ U[-a, a], a = sqrt(6 / fan_in), zero biases (u: uniforms in [0, 1))."""
+    theta = np.zeros(len(u), dtype=np.float32)
+    o = 0
+    for ci, co, k in _LAYERS:
+        nw = co * ci * k * k
+        a = np.sqrt(6.0 / (ci * k * k))
+        theta[o : o + nw] = (a * (2.0 * u[o : o + nw] - 1.0)).astype(np.float32)
+        o += nw + co
+    return theta

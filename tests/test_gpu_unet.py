@@ -1,0 +1,82 @@
+"""The learned-initial-guess network's CUDA kernels against the FP64 oracle.
+
+FP32 weights: forward and every parameter gradient agree with the oracle to the
+FP32 accumulation level. BF16 weights: the same comparison against the oracle run
+at the BF16-rounded weights (rounding to nearest even of the FP32 values), which
+is exactly what the kernels multiply by.
+"""
+import numpy as np
+import pytest
+
+from oracle import unet as ounet
+from paper_2001_04886_gb300 import inputs
+from tests.gpu_util import dev, torch
+
+import paper_2001_04886_gb300 as pkg
+
+pytestmark = pytest.mark.gpu
+KAPPA = 3.25
+
+
+def bf16_round(a):
+    """float32 values rounded to the nearest bfloat16 (ties to even), returned as float64."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def setup(B, H, seed, bf16, smooth=0, res_w=0.0):
+    d = dev()
+    theta = ounet.init_params(inputs.uniform01(seed, ounet.num_params())).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((B, 2, H, H)).astype(np.float32)
+    t = rng.standard_normal((B, 1, H, H)).astype(np.float32)
+    net = pkg.X0Net(H, H, B, bf16=bf16, smooth=smooth, residual_weight=res_w, kappa=KAPPA)
+    net.set_params(theta.astype(np.float32))
+    xd = torch.tensor(x, device=d).contiguous()
+    td = torch.tensor(t, device=d).contiguous()
+    return net, theta, x.astype(np.float64), t.astype(np.float64), xd, td
+
+
+def layer_slices():
+    o = 0
+    for ci, co, k, _ in ounet.LAYERS:
+        n = co * ci * k * k + co
+        yield slice(o, o + n)
+        o += n
+
+
+@pytest.mark.parametrize("B,H,smooth,res_w", [(2, 16, 0, 0.0), (3, 32, 0, 0.0), (2, 16, 3, 0.0), (2, 16, 3, 2.0)])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_forward_and_gradient(B, H, smooth, res_w, bf16):
+    net, theta, x, t, xd, td = setup(B, H, 7, bf16, smooth, res_w)
+    th = theta.copy()
+    if bf16:
+        # weights are rounded; biases stay FP32
+        for sl, (ci, co, k, _) in zip(layer_slices(), ounet.LAYERS):
+            nw = co * ci * k * k
+            th[sl.start : sl.start + nw] = bf16_round(theta[sl.start : sl.start + nw])
+    out = torch.empty((B, 1, H, H), dtype=torch.float32, device=xd.device)
+    net.forward(xd, out)
+    torch.cuda.synchronize()
+    ref = ounet.forward(th, x, smooth=smooth)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    loss, g = net.gradient(xd, td)
+    lref, gref = ounet.gradient(th, x, t, smooth=smooth, res_w=res_w, kappa=KAPPA)
+    assert abs(loss - lref) <= 1e-5 * lref
+    for sl in layer_slices():
+        a, b = g[sl].astype(np.float64), gref[sl]
+        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b) + 1e-12
+
+
+def test_training_reduces_loss():
+    net, theta, x, t, xd, td = setup(4, 16, 3, True)
+    loss0, _ = net.gradient(xd, td)
+    lossd = torch.zeros(1, dtype=torch.float32, device=xd.device)
+    for _ in range(60):
+        net.train_step(xd, td, 1e-3, lossd)
+    torch.cuda.synchronize()
+    loss1, _ = net.gradient(xd, td)
+    assert loss1 < 0.5 * loss0
