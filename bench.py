@@ -42,6 +42,17 @@ def env_ranks():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def reduce_max(value, dist, device=None):
+    """Maximum of a per-rank float over all ranks (the replicas' step time); identity without dist."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -52,6 +63,10 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32"],
                     help="basis precision of the headline solve")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--learned", action="store_true",
+                    help="also run the learned-initial-guess form (128^2, 20k training systems; minutes)")
+    ap.add_argument("--learned-train", type=int, default=20000)
+    ap.add_argument("--learned-epochs", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -283,10 +298,7 @@ def main():
     trace = pkg.trace_read()
     pkg.trace_enable(False)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dist, dev)
     relres = res["relres"]
     err = float((x - xt).norm() / xt.norm())
 
@@ -399,6 +411,15 @@ def main():
         variants["batched_512_s4_m20"] = out
         Bs.close()
         del mats, fs, xs
+
+    if args.learned:
+        from paper_2001_04886_gb300 import learned
+
+        t0 = time.perf_counter()
+        ev = learned.run(N=128, train_seeds=range(args.learned_train), test_seeds=range(20000, 21000),
+                         epochs=args.learned_epochs, batch=32, lr=1e-3, log=lambda m: print(m, file=sys.stderr))
+        ev["total_s"] = time.perf_counter() - t0
+        variants["learned_x0_128"] = ev
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

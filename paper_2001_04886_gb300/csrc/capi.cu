@@ -43,6 +43,18 @@ inline int64_t col_ld(int64_t n) { return (n + 31) / 32 * 32; }   // 256-byte al
 
 int check_launch() { return cudaGetLastError() == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA; }
 
+// The fused matrix-powers kernel (one launch for the s powers of a block) is off by
+// default: on GB300 the 16.8 MB columns of a 128^3 solve stay in the 129 MB L2 between
+// separate sweeps, so fusion saves only L2 reads while its tile halos recompute ~4x the
+// points (measured slower). SSTEP_FUSED_POWERS=1 turns it on.
+bool fused_powers_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("SSTEP_FUSED_POWERS");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+
 // ------------------------------------------------------------------ launch tracing
 // Every launch is counted; when tracing is on, a pair of CUDA events brackets each
 // launch on its own stream and the elapsed times are summed per kernel kind at the
@@ -313,11 +325,19 @@ int sstep_gmres_mp(sstep_matrix M, const double* f, double* x, const sstep_param
         TRACED(K_RESIDUAL, stream_, mp_launch_residual<P>(M->A, f, x, uraw, sc, e, GATE_ACTIVE, stream_));
         for (int k = 0; k < nb; ++k) {
             const int o = k * s;
-            TRACED(K_STENCIL, stream_, mp_launch_stencil<P>(M->A, uraw, sigma, col(o + 1), 1.0, col(o), &st->vscale,
-                                                            st, GATE_BUILDING, stream_));
-            for (int j = 2; j <= s; ++j)
-                TRACED(K_STENCIL, stream_, mp_launch_stencil<P>(M->A, col(o + j - 1), sigma, col(o + j), 0.0, nullptr,
-                                                                nullptr, st, GATE_BUILDING, stream_));
+            // Alg. 4.1 step 3: the s powers, in one fused launch when enabled (SSTEP_FUSED_POWERS=1)
+            bool fused = false;
+            if (fused_powers_enabled())
+                TRACED(K_STENCIL, stream_,
+                       fused = mp_launch_powers_fused<P>(M->A, uraw, col(o), ld, s, sigma, &st->vscale, st,
+                                                         GATE_BUILDING, stream_));
+            if (!fused) {
+                TRACED(K_STENCIL, stream_, mp_launch_stencil<P>(M->A, uraw, sigma, col(o + 1), 1.0, col(o),
+                                                                &st->vscale, st, GATE_BUILDING, stream_));
+                for (int j = 2; j <= s; ++j)
+                    TRACED(K_STENCIL, stream_, mp_launch_stencil<P>(M->A, col(o + j - 1), sigma, col(o + j), 0.0,
+                                                                    nullptr, nullptr, st, GATE_BUILDING, stream_));
+            }
             if (k > 0) {
                 e = Epi();
                 e.st = st;

@@ -117,6 +117,12 @@ void mp_launch_update(int64_t n, const void* V, int64_t ldv, int ka, const void*
 // dst[p] = src[p] split into a float pair (variable coefficients for the mixed-precision kernels)
 void launch_split_fields(const double* src, float2* dst, int64_t n, cudaStream_t stream);
 
+// Y[:,0] = (*dscale) u, Y[:,j] = sigma A Y[:,j-1], j = 1..s, in one launch (constant
+// coefficients, s in {2, 4, 8}); returns false (nothing launched) otherwise.
+template <int P>
+bool mp_launch_powers_fused(const StencilDesc& A, const void* u, void* Y, int64_t ldy, int s, double sigma,
+                            const double* dscale, const SolverState* st, int gate, cudaStream_t stream);
+
 // x += V y over the current cycle's st->K columns (y = st->y)
 template <int P>
 void mp_launch_axpy(int64_t n, const void* V, int64_t ldv, double* x, const Epi& epi, int gate,

@@ -209,6 +209,149 @@ void mp_launch_stencil(const StencilDesc& A, const void* v, double fy, void* y, 
     mp_stencil_kernel<P><<<grid, block, 0, stream>>>(A, (const T*)v, fy, (T*)y, fw, (T*)w, dscale, st, gate);
 }
 
+// ================================================================== fused matrix powers
+// Y[:, 0] = vscale u, Y[:, j] = sigma A Y[:, j-1] for j = 1..S in one launch (constant
+// coefficients). A CTA owns a (kTile x kTile) x-y tile and a chunk of z planes and
+// marches through z: level 0 is the scaled start vector, and level j of plane z needs
+// level j-1 on planes z-1, z, z+1, so level j trails level j-1 by one plane. Each level
+// keeps a ring of its last 3 planes in shared memory over the tile plus a halo of S-j
+// points (the halo shrinks by one per level); points outside the grid hold zero (the
+// Dirichlet boundary). The S powers cost one read of u (halos from L2) and S writes.
+constexpr int kTile = 16;
+
+template <int S>
+__host__ __device__ constexpr int lvl_w(int j) { return kTile + 2 * (S - j); }
+template <int S>
+__host__ __device__ constexpr int lvl_off(int j) {   // element offset of level j's ring
+    int o = 0;
+    for (int i = 0; i < j; ++i) o += 3 * lvl_w<S>(i) * lvl_w<S>(i);
+    return o;
+}
+
+template <int P, int S>
+__global__ void __launch_bounds__(kThreads) mp_powers_fused_kernel(StencilDesc A, const typename Mode<P>::T* __restrict__ u,
+                                                                   typename Mode<P>::T* __restrict__ Y, int64_t ldy,
+                                                                   double sigma, const double* dscale, int zchunk,
+                                                                   const SolverState* st, int gate) {
+    using M = Mode<P>;
+    using Vt = typename M::V;
+    extern __shared__ unsigned char smem_raw[];
+    Vt* ring = reinterpret_cast<Vt*>(smem_raw);
+    __shared__ df64 fac[2];
+    if (!gate_open(st, gate)) return;
+    broadcast_factors(sigma, 1.0, dscale, fac);          // fac[0] = sigma*vscale (unused), fac[1] = vscale
+    __shared__ df64 sig_s;
+    if (threadIdx.x == 0) sig_s = df_from_double(sigma);
+    __syncthreads();
+    const df64 vsc = fac[1], sg = sig_s;
+    const int tilesx = (A.nx + kTile - 1) / kTile;
+    const int x0 = (blockIdx.x % tilesx) * kTile, y0 = (blockIdx.x / tilesx) * kTile;
+    const int zb = blockIdx.y * zchunk, ze = min(A.nz, zb + zchunk);
+    const int64_t pl = (int64_t)A.nx * A.ny;
+    df64 c[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) c[q] = df64{A.ch[q], P == PREC_DF64 ? A.cl[q] : 0.f};
+    const bool three = A.dim == 3;
+    for (int zc = zb - S; zc < ze + S; ++zc) {
+        // level 0: plane zc of the scaled start vector
+        if (zc >= 0 && zc < A.nz && zc >= zb - S && zc < ze + S) {
+            constexpr int w0 = lvl_w<S>(0);
+            Vt* dst = ring + lvl_off<S>(0) + (zc % 3) * w0 * w0;
+            for (int t = threadIdx.x; t < w0 * w0; t += blockDim.x) {
+                const int gx = x0 - S + t % w0, gy = y0 - S + t / w0;
+                Vt v = M::zero();
+                if (gx >= 0 && gx < A.nx && gy >= 0 && gy < A.ny) {
+                    const int64_t gp = (int64_t)zc * pl + (int64_t)gy * A.nx + gx;
+                    if constexpr (P == PREC_DF64) v = df_mul(vsc, M::load(u + gp));
+                    else v = __fmul_rn(vsc.hi, M::load(u + gp));
+                    const int lx = gx - x0, ly = gy - y0;
+                    if (zc >= zb && zc < ze && lx >= 0 && lx < kTile && ly >= 0 && ly < kTile) M::store(Y + gp, v);
+                }
+                dst[t] = v;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 1; j <= S; ++j) {
+            const int z = zc - j;
+            const bool active = z >= 0 && z < A.nz && z >= zb - (S - j) && z < ze + (S - j);
+            if (active) {
+                constexpr int dummy = 0;
+                (void)dummy;
+                const int wp = lvl_w<S>(j - 1), wj = lvl_w<S>(j);
+                const Vt* prev = ring + lvl_off<S>(j - 1);
+                const Vt* pc = prev + (z % 3) * wp * wp;
+                const Vt* pm = (three && z - 1 >= 0) ? prev + ((z + 2) % 3) * wp * wp : nullptr;
+                const Vt* pp = (three && z + 1 < A.nz) ? prev + ((z + 1) % 3) * wp * wp : nullptr;
+                Vt* dst = j < S ? ring + lvl_off<S>(j) + (z % 3) * wj * wj : nullptr;
+                for (int t = threadIdx.x; t < wj * wj; t += blockDim.x) {
+                    const int lx = t % wj, ly = t / wj;                 // in level j's region
+                    const int gx = x0 - (S - j) + lx, gy = y0 - (S - j) + ly;
+                    Vt r = M::zero();
+                    if (gx >= 0 && gx < A.nx && gy >= 0 && gy < A.ny) {
+                        const int q = (ly + 1) * wp + (lx + 1);              // same point in level j-1's region
+                        if constexpr (P == PREC_DF64) {
+                            DfAcc acc;
+                            acc.add_prod(c[0], pc[q]);
+                            acc.add_prod(c[1], pc[q - 1]);
+                            acc.add_prod(c[2], pc[q + 1]);
+                            acc.add_prod(c[3], pc[q - wp]);
+                            acc.add_prod(c[4], pc[q + wp]);
+                            if (pm) acc.add_prod(c[5], pm[q]);
+                            if (pp) acc.add_prod(c[6], pp[q]);
+                            acc.normalize();
+                            r = df_mul(sg, df64{acc.hi, acc.lo});
+                        } else {
+                            float acc = __fmul_rn(c[0].hi, pc[q]);
+                            acc = __fmaf_rn(c[1].hi, pc[q - 1], acc);
+                            acc = __fmaf_rn(c[2].hi, pc[q + 1], acc);
+                            acc = __fmaf_rn(c[3].hi, pc[q - wp], acc);
+                            acc = __fmaf_rn(c[4].hi, pc[q + wp], acc);
+                            if (pm) acc = __fmaf_rn(c[5].hi, pm[q], acc);
+                            if (pp) acc = __fmaf_rn(c[6].hi, pp[q], acc);
+                            r = __fmul_rn(sg.hi, acc);
+                        }
+                        const int tx = gx - x0, ty = gy - y0;
+                        if (z >= zb && z < ze && tx >= 0 && tx < kTile && ty >= 0 && ty < kTile)
+                            M::store(Y + (int64_t)j * ldy + (int64_t)z * pl + (int64_t)gy * A.nx + gx, r);
+                    }
+                    if (dst) dst[t] = r;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int P>
+bool mp_launch_powers_fused(const StencilDesc& A, const void* u, void* Y, int64_t ldy, int s, double sigma,
+                            const double* dscale, const SolverState* st, int gate, cudaStream_t stream) {
+    using T = typename Mode<P>::T;
+    using Vt = typename Mode<P>::V;
+    if (A.variable || !(s == 2 || s == 4 || s == 8)) return false;
+    const int tiles = ((A.nx + kTile - 1) / kTile) * ((A.ny + kTile - 1) / kTile);
+    // z chunks: enough CTAs to fill the GPU, no thinner than S planes (the recomputed halo)
+    int zchunk = A.nz;
+    while (zchunk > s && (int64_t)tiles * ((A.nz + zchunk - 1) / zchunk) < 152 * 3) zchunk = (zchunk + 1) / 2;
+    dim3 grid(tiles, (A.nz + zchunk - 1) / zchunk);
+    switch (s) {
+#define SSTEP_PF(S)                                                                                             \
+    case S: {                                                                                                   \
+        const size_t smem = sizeof(Vt) * lvl_off<S>(S);                                                        \
+        cudaFuncSetAttribute(mp_powers_fused_kernel<P, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        mp_powers_fused_kernel<P, S><<<grid, kThreads, smem, stream>>>(A, (const T*)u, (T*)Y, ldy, sigma, dscale,  \
+                                                                       zchunk, st, gate);                      \
+        break;                                                                                                  \
+    }
+        SSTEP_PF(2)
+        SSTEP_PF(4)
+        SSTEP_PF(8)
+#undef SSTEP_PF
+        default: return false;
+    }
+    return true;
+}
+
 // ================================================================== residual (FP64) into the basis type
 template <int P>
 __global__ void __launch_bounds__(kThreads) mp_residual_kernel(StencilDesc A, const double* __restrict__ f,
@@ -734,7 +877,9 @@ void launch_split_fields(const double* src, float2* dst, int64_t n, cudaStream_t
     template void mp_launch_update<P>(int64_t, const void*, int64_t, int, const void*, int64_t, void*, int64_t,  \
                                       int, int, const double*, int, double, bool, Scratch, const Epi&, int,      \
                                       cudaStream_t);                                                             \
-    template void mp_launch_axpy<P>(int64_t, const void*, int64_t, double*, const Epi&, int, cudaStream_t);
+    template void mp_launch_axpy<P>(int64_t, const void*, int64_t, double*, const Epi&, int, cudaStream_t);      \
+    template bool mp_launch_powers_fused<P>(const StencilDesc&, const void*, void*, int64_t, int, double,         \
+                                            const double*, const SolverState*, int, cudaStream_t);
 SSTEP_MP_INST(PREC_DF64)
 SSTEP_MP_INST(PREC_FP32)
 #undef SSTEP_MP_INST

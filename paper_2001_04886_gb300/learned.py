@@ -65,22 +65,31 @@ def solve_batch(mats, fs, x0s, s=4, m=20, tol=1e-8, guard=False, tune=False):
     return res, e0.elapsed_time(e1)
 
 
-def generate(seeds, N, device, chunk=1024):
-    """Training pairs: features (S, 2, N, N) and targets x / s_f (S, 1, N, N), FP32 on the device."""
+def generate(seeds, N, device, chunk=1024, report=None):
+    """Training pairs: features (S, 2, N, N) and targets x / (kappa s_f) (S, 1, N, N), FP32 on
+    the device. Systems whose solve does not converge are left out; `report` (a dict, if
+    given) receives their seeds and statuses."""
     import torch
 
     feats, targets = [], []
+    dropped = []
     for c0 in range(0, len(seeds), chunk):
-        mats, fs, ft, sc = make_systems(seeds[c0 : c0 + chunk], N, device)
+        part = seeds[c0 : c0 + chunk]
+        mats, fs, ft, sc = make_systems(part, N, device)
         xs = [torch.zeros_like(f) for f in fs]
         res, _ = solve_batch(mats, fs, xs)
-        if not all(r["status"] == 0 for r in res):
-            raise RuntimeError("a training system did not converge")
         k = kappa(N)
-        for x, s_ in zip(xs, sc):
+        keep = []
+        for i, (x, s_, r) in enumerate(zip(xs, sc, res)):
+            if r["status"] != 0:
+                dropped.append((int(part[i]), r["status"], r["cycles"]))
+                continue
+            keep.append(i)
             targets.append((x / (k * s_)).to(torch.float32).reshape(1, N, N))
-        feats.append(ft)
+        feats.append(ft[torch.tensor(keep, device=device, dtype=torch.long)])
         del mats, fs, xs
+    if report is not None:
+        report["dropped"] = dropped
     return torch.cat(feats), torch.stack(targets)
 
 
@@ -159,7 +168,8 @@ def run(N=128, train_seeds=range(20000), test_seeds=range(20000, 21000), epochs=
 
     dev = torch.device("cuda", torch.cuda.current_device())
     t = time.perf_counter()
-    feats, targets = generate(np.array(list(train_seeds)), N, dev)
+    rep = {}
+    feats, targets = generate(np.array(list(train_seeds)), N, dev, report=rep)
     t_gen = time.perf_counter() - t
     net = X0Net(N, N, batch, bf16=True, smooth=smooth, residual_weight=residual_weight, kappa=kappa(N))
     from . import inputs as _in
@@ -171,7 +181,8 @@ def run(N=128, train_seeds=range(20000), test_seeds=range(20000, 21000), epochs=
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t
     ev = evaluate(net, np.array(list(test_seeds)), N, dev)
-    ev.update({"grid": N, "train_systems": len(list(train_seeds)), "epochs": epochs, "loss_history": hist,
+    ev.update({"grid": N, "train_systems": int(feats.shape[0]), "dropped": rep.get("dropped", []), "epochs": epochs,
+               "loss_history": hist,
                "generate_s": t_gen, "train_s": t_train, "params": net.num_params})
     net.close()
     return ev

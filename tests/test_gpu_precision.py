@@ -92,3 +92,41 @@ def test_fp32_refinement_256cube():
     x = xd.cpu().numpy()
     rel = np.linalg.norm(f - Ao.apply(x)) / np.linalg.norm(f)
     assert rel <= 1e-10
+
+
+def test_fused_powers_match_separate_sweeps():
+    """The fused matrix-powers launch (opt-in) gives the separate sweeps' solve, in a fresh process."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    dev()
+    code = r"""
+import json, sys
+import numpy as np, torch
+sys.path.insert(0, '.')
+import paper_2001_04886_gb300 as pkg
+from paper_2001_04886_gb300 import inputs
+out = {}
+for shape, beta in [((24, 24, 24), (30.0, 20.0, 10.0)), ((48, 48), (20.0, 20.0))]:
+    A = pkg.StencilMatrix(len(shape), shape, beta=beta)
+    xt = torch.tensor(inputs.x_true(0, A.n), device='cuda')
+    f = torch.empty_like(xt); A.apply(xt, f)
+    for prec in ('df64', 'fp32'):
+        x = torch.zeros_like(f)
+        r = pkg.sstep_gmres_solve(A, f, x, 4, 20, 1e-8, precision=prec)
+        out[str(shape) + prec] = [r['cycles'], r['relres'], x.cpu().numpy().tolist()[:50]]
+print(json.dumps(out))
+"""
+    res = {}
+    for flag in ("0", "1"):
+        env = dict(os.environ, SSTEP_FUSED_POWERS=flag)
+        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        assert p.returncode == 0, p.stderr[-2000:]
+        res[flag] = json.loads(p.stdout.strip().splitlines()[-1])
+    for key in res["0"]:
+        c0, r0, x0 = res["0"][key]
+        c1, r1, x1 = res["1"][key]
+        assert c0 == c1 and r0 <= 1e-8 and r1 <= 1e-8
+        assert np.linalg.norm(np.array(x0) - x1) <= 1e-6 * np.linalg.norm(x0)
