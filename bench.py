@@ -37,6 +37,34 @@ TOL = 1e-8
 WORKLOAD = "3-D convection-diffusion 128^3 (n=2,097,152), beta=(30,20,10), 7-point, FP64, x0=0, tol 1e-8"
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz, FMA = 2 flops
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
+# kernel, averaged over the launches of one solve in an ncu capture of this bench
+# (profiles/sstep_gmres_fp64_128cube_traffic.md has the command and the per-kernel table).
+# Keyed by precision mode, with a hash of the kernel sources it was taken on: once the
+# sources change, the figure no longer describes the kernel and the bench reports null.
+TRAFFIC = {
+    "fp64": {"kernel": "block_update", "bytes_per_launch": 471.4e6,
+             "sources": ("common.cuh", "kernels.cuh", "epilogue.cuh", "kernels.cu"),
+             "sha256": "6e1e34b3275455ec"},
+}
+
+
+def sources_sha(names):
+    import hashlib
+
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_2001_04886_gb300", "csrc", nm), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(precision, kernel):
+    t = TRAFFIC.get(precision)
+    if not t or t["kernel"] != kernel or sources_sha(t["sources"]) != t["sha256"]:
+        return None
+    return t["bytes_per_launch"]
+
 
 def env_ranks():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
@@ -310,8 +338,10 @@ def main():
     flops, bytes_ = work[dom]
     achieved = flops / t_dom / 1e12
     launches_timed = sum(v[1] for v in kinds.values())
+    launches_dom = kinds[dom][1] / args.steps
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": measured_traffic(args.precision, dom), "kernel": dom,
+                "launches_per_solve": launches_dom, "algorithmic_bytes_per_launch": bytes_ / launches_dom,
                 "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
                 "hbm_gbs": bytes_ / t_dom / 1e9,
                 "share_of_step": kinds[dom][0] / args.steps / ms}
