@@ -78,6 +78,15 @@ int stencil_matrix_info(sstep_matrix A, int64_t* n, double* norm_inf);
 /* y = A x (Sec. 1: one sweep over the grid). x and y must not overlap. */
 int stencil_matrix_apply(sstep_matrix A, const double* x, double* y, void* stream);
 
+/* Damped Jacobi smoothing (textbook relaxation, e.g. Saad, Iterative Methods for
+ * Sparse Linear Systems, Sec. 4.1; not part of the s-step method): `sweeps` times
+ * x <- x + omega (f - A x) / a0, a0 the diagonal of the row. Used to post-smooth a
+ * learned initial guess. f, x, work: DEVICE arrays of n doubles, caller-owned; work is
+ * scratch and must not alias x or f; x is read and overwritten. sweeps >= 0 (0: no-op),
+ * 0 < omega < 2, else SSTEP_ERR_ARG. Stream-ordered, no synchronisation. */
+int stencil_matrix_smooth(sstep_matrix A, const double* f, double* x, double* work, int sweeps, double omega,
+                          void* stream);
+
 /* ------------------------------------------------------------------ s-step block primitives
  * The three data-parallel steps of one s-step (Sec. 1, Alg. 3.1, Alg. 4.1),
  * exposed one by one. Column-major panels: column j of a panel P with leading

@@ -102,3 +102,17 @@ def convdiff_variable(N, beta_field):
     h = 1.0 / (N + 1)
     c = np.asarray(beta_field, dtype=np.float64) * (h / 2.0)
     return Stencil((N, N), 4.0, [-1.0 - c, -1.0 - c], [-1.0 + c, -1.0 + c])
+
+
+def jacobi(A, f, x, sweeps, omega):
+    """Damped Jacobi relaxation: `sweeps` times x <- x + omega D^{-1} (f - A x), D = diag(A) = a0.
+
+    A textbook smoother (Saad, Iterative Methods for Sparse Linear Systems, Sec. 4.1),
+    not one of the paper's methods: it post-smooths the learned initial guess.
+    """
+    d = np.broadcast_to(A._coef(A.a0), A.shape[::-1]).reshape(-1)
+    x = np.array(x, dtype=np.float64)
+    f = np.asarray(f, dtype=np.float64)
+    for _ in range(sweeps):
+        x = x + omega * (f - A.apply(x)) / d
+    return x

@@ -27,6 +27,7 @@ from ._binding import (  # noqa: F401
     sstep_matrix_powers,
     sstep_omin_solve,
     stencil_matrix_apply,
+    stencil_matrix_smooth,
     trace_enable,
     trace_read,
 )
@@ -36,6 +37,7 @@ __all__ = [
     "X0Net",
     "StencilMatrix",
     "stencil_matrix_apply",
+    "stencil_matrix_smooth",
     "sstep_matrix_powers",
     "sstep_gram",
     "sstep_gram_workspace_size",

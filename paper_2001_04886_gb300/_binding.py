@@ -41,6 +41,7 @@ SIGNATURES = {
     "stencil_matrix_destroy": (c_int, [c_void_p]),
     "stencil_matrix_info": (c_int, [c_void_p, P(c_int64), P(c_double)]),
     "stencil_matrix_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "stencil_matrix_smooth": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_void_p]),
     "sstep_matrix_powers": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_void_p, c_int64, c_void_p]),
     "sstep_gram_workspace_size": (c_int, [c_int64, c_int, c_int, P(c_size_t)]),
     "sstep_gram": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
@@ -181,9 +182,18 @@ class StencilMatrix:
     def apply(self, x, y, stream=None):
         return stencil_matrix_apply(self, x, y, stream)
 
+    def smooth(self, f, x, work, sweeps, omega, stream=None):
+        return stencil_matrix_smooth(self, f, x, work, sweeps, omega, stream)
+
 
 def stencil_matrix_apply(A, x, y, stream=None):
     return _check("stencil_matrix_apply", lib().stencil_matrix_apply(A.handle, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def stencil_matrix_smooth(A, f, x, work, sweeps, omega, stream=None):
+    """`sweeps` damped Jacobi sweeps on x in place (work: scratch of n doubles)."""
+    return _check("stencil_matrix_smooth", lib().stencil_matrix_smooth(A.handle, _ptr(f), _ptr(x), _ptr(work),
+                                                                       int(sweeps), float(omega), _stream(stream)))
 
 
 def sstep_matrix_powers(A, v, scale, sigma, s, Y, stream=None):

@@ -706,6 +706,26 @@ int stencil_matrix_apply(sstep_matrix M, const double* x, double* y, void* strea
     return check_launch();
 }
 
+int stencil_matrix_smooth(sstep_matrix M, const double* f, double* x, double* work, int sweeps, double omega,
+                          void* stream) {
+    if (!M || sweeps < 0 || !(omega > 0.0 && omega < 2.0)) return SSTEP_ERR_ARG;
+    if (sweeps == 0) return SSTEP_OK;
+    if (!f || !x || !work || work == x || work == f) return SSTEP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* src = x;
+    double* dst = work;
+    for (int t = 0; t < sweeps; ++t) {
+        launch_jacobi(M->A, f, src, dst, omega, st);
+        double* tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    if (src != x && cudaMemcpyAsync(x, src, sizeof(double) * (size_t)M->A.n, cudaMemcpyDeviceToDevice, st) !=
+                        cudaSuccess)
+        return SSTEP_ERR_CUDA;
+    return check_launch();
+}
+
 int sstep_matrix_powers(sstep_matrix M, const double* v, double scale, double sigma, int s, double* Y, int64_t ldy,
                         void* stream) {
     if (!M || !v || !Y || s < 1 || s > SSTEP_MAX_S || ldy < M->A.n) return SSTEP_ERR_ARG;

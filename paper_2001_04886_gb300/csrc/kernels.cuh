@@ -87,6 +87,9 @@ int max_partials_doubles();
 // out = [a0 | am_x | ap_x | am_y | ap_y] (5 arrays of n) for -Lap u + beta (u_x + u_y):
 // a0 = 4, am = -1 - beta h/2, ap = -1 + beta h/2
 void launch_convdiff_fields(const double* beta, double h, int64_t n, double* out, cudaStream_t stream);
+// damped Jacobi sweep y = x + omega (f - A x) / a0 (smooth.cu)
+void launch_jacobi(const StencilDesc& A, const double* f, const double* x, double* y, double omega,
+                   cudaStream_t stream);
 
 }  // namespace sstep
 

@@ -118,3 +118,39 @@ def test_block_update(n, ka, kb):
         assert relerr(got[:, j], Yh[:, j]) <= 1e-14
     nrm = np.linalg.norm(Yh, axis=0)
     assert np.max(np.abs(G.cpu().numpy() - Gr) / np.outer(nrm, nrm)) <= 1e-14
+
+
+@pytest.mark.parametrize("shape,beta", [SHAPES[1], SHAPES[3], SHAPES[5]])
+@pytest.mark.parametrize("sweeps", [0, 1, 2, 5])
+def test_jacobi_smoother(shape, beta, sweeps):
+    """Damped Jacobi sweeps against the oracle's; odd and even counts (the result lands in
+    x either way), ragged grids and a single unknown."""
+    d = dev()
+    Ao, A = make(shape, beta, d)
+    f = inputs.x_true(5, Ao.n)
+    x = inputs.x_true(6, Ao.n)
+    xd = to_dev(x, d)
+    work = torch.full_like(xd, float("nan"))
+    A.smooth(to_dev(f, d), xd, work, sweeps, 0.8)
+    torch.cuda.synchronize()
+    ref = ostencil.jacobi(Ao, f, x, sweeps, 0.8)
+    assert np.max(np.abs(xd.cpu().numpy() - ref)) <= 1e-14 * (1 + np.abs(ref).max())
+
+
+def test_jacobi_smoother_variable_and_arguments():
+    d = dev()
+    N = 33
+    beta, f = inputs.fourier_fields(7, N)
+    Ao = ostencil.convdiff_variable(N, beta)
+    A = pkg.StencilMatrix(2, (N, N), beta_field=to_dev(beta, d))
+    x = inputs.x_true(8, Ao.n)
+    xd, fd = to_dev(x, d), to_dev(f, d)
+    work = torch.empty_like(xd)
+    A.smooth(fd, xd, work, 3, 0.7)
+    torch.cuda.synchronize()
+    ref = ostencil.jacobi(Ao, f, x, 3, 0.7)
+    assert np.max(np.abs(xd.cpu().numpy() - ref)) <= 1e-13 * (1 + np.abs(ref).max())
+    for bad in (dict(sweeps=-1, omega=0.8, w=work), dict(sweeps=2, omega=0.0, w=work),
+                dict(sweeps=2, omega=2.0, w=work), dict(sweeps=2, omega=0.8, w=xd)):
+        with pytest.raises(pkg.SStepError):
+            A.smooth(fd, xd, bad["w"], bad["sweeps"], bad["omega"])

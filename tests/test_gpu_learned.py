@@ -64,4 +64,7 @@ def test_trained_network_reduces_krylov_steps():
                      log=None, smooth=4, residual_weight=1.0)
     print(ev)
     assert ev["all_converged"]
+    assert ev["predicted"]["accepted_by_guard"] > 0
+    # fewer Krylov steps than from x0 = 0 and than from x0 = 0 after the same smoothing sweeps
     assert ev["predicted"]["mean_iters"] < ev["zero"]["mean_iters"]
+    assert ev["predicted"]["mean_iters"] < ev["zero_smoothed"]["mean_iters"]

@@ -90,3 +90,41 @@ def test_gauss_solve_matches_library():
     M = rng.standard_normal((30, 30)) + 5 * np.eye(30)
     b = rng.standard_normal(30)
     assert np.allclose(dense.gauss_solve(M, b), np.linalg.solve(M, b), rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------------ damped Jacobi (textbook smoother)
+def test_jacobi_damps_laplacian_eigenmode_by_closed_form():
+    """beta = 0: the sine mode (p, q) has eigenvalue lam = 4 - 2cos(p pi h) - 2cos(q pi h) of the
+    h^2-scaled 2-D Laplacian; with f = 0 each sweep multiplies it by 1 - omega lam / 4."""
+    N, p, q, omega, sweeps = 9, 2, 7, 0.8, 3
+    A = stencil.convdiff((N, N), (0.0, 0.0))
+    h = 1.0 / (N + 1)
+    i = np.arange(1, N + 1)
+    mode = np.outer(np.sin(q * np.pi * h * i), np.sin(p * np.pi * h * i)).reshape(-1)   # rows y, columns x
+    lam = 4.0 - 2.0 * np.cos(p * np.pi * h) - 2.0 * np.cos(q * np.pi * h)
+    got = stencil.jacobi(A, np.zeros(A.n), mode, sweeps, omega)
+    np.testing.assert_allclose(got, (1.0 - omega * lam / 4.0) ** sweeps * mode, rtol=0, atol=1e-14)
+
+
+def test_jacobi_diagonal_operator_is_solved_in_one_sweep():
+    """With no neighbours A = a0 I, and one undamped sweep lands on f / a0 from any start."""
+    rng = np.random.default_rng(3)
+    A = stencil.Stencil((5, 4, 3), 6.0, [0.0] * 3, [0.0] * 3)
+    f, x = rng.standard_normal(A.n), rng.standard_normal(A.n)
+    np.testing.assert_allclose(stencil.jacobi(A, f, x, 1, 1.0), f / 6.0, rtol=0, atol=2e-15)
+
+
+def test_jacobi_matches_dense_iteration_and_keeps_the_solution():
+    """Against the iteration written with the dense matrix (assembled entry by entry) on a
+    variable-coefficient operator; the exact solution is a fixed point."""
+    rng = np.random.default_rng(4)
+    N = 6
+    A = stencil.convdiff_variable(N, 40.0 * rng.random(N * N))
+    D = dense.dense_matrix(A)
+    f, x = rng.standard_normal(A.n), rng.standard_normal(A.n)
+    want = x.copy()
+    for _ in range(4):
+        want = want + 0.7 * (f - D @ want) / np.diag(D)
+    np.testing.assert_allclose(stencil.jacobi(A, f, x, 4, 0.7), want, rtol=1e-13, atol=1e-13)
+    xs = np.linalg.solve(D, f)
+    np.testing.assert_allclose(stencil.jacobi(A, f, xs, 3, 0.8), xs, rtol=0, atol=1e-12)
