@@ -123,7 +123,7 @@ __device__ __forceinline__ void block_reduce_df(DfAcc (&acc)[NV], double* red) {
 // Per-CTA df64 copies of launch-time FP64 scalars: computed by one thread (the FP64
 // pipe is slow) and broadcast through shared memory.
 __device__ __forceinline__ void broadcast_factors(double fy, double fw, const double* dscale, df64* out2) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
         if (dscale) {
             const double d = *dscale;
             fy *= d;
@@ -145,40 +145,44 @@ __device__ __forceinline__ df64 mp_coef(const StencilDesc& A, int q, int64_t p) 
     return df64{A.ch[q], P == PREC_DF64 ? A.cl[q] : 0.f};
 }
 
-// One point per thread on a (32 x 8) tile of x-y rows, one z plane per grid.z step:
-// the grid coordinates come from the launch shape, with no per-point division.
+// A CTA owns a (32 x 8)-point x-y tile and a chunk of z planes and marches through z:
+// each thread keeps planes z-1, z, z+1 of its (x, y) column in registers, so a point
+// costs one new load plus the four in-plane neighbours (L1 hits, loaded by the
+// neighbouring threads), and the tile coordinates come from the launch shape with no
+// per-point division.
 template <int P>
 __global__ void __launch_bounds__(kThreads) mp_stencil_kernel(StencilDesc A, const typename Mode<P>::T* __restrict__ v,
                                                               double fy, typename Mode<P>::T* __restrict__ y, double fw,
                                                               typename Mode<P>::T* __restrict__ w,
-                                                              const double* dscale, const SolverState* st, int gate) {
+                                                              const double* dscale, const SolverState* st, int gate,
+                                                              int zchunk) {
     using M = Mode<P>;
     using Vt = typename M::V;
     __shared__ df64 fac[2];
     if (!gate_open(st, gate)) return;
     broadcast_factors(fy, fw, dscale, fac);
     const df64 vfy = fac[0], vfw = fac[1];
+    const int tx = (A.nx + 31) / 32;
+    const int x = (int)(blockIdx.x % tx) * 32 + threadIdx.x;
+    const int yy = (int)(blockIdx.x / tx) * 8 + threadIdx.y;
+    const int zb = blockIdx.y * zchunk, ze = min(A.nz, zb + zchunk);
+    if (x >= A.nx || yy >= A.ny || zb >= ze) return;      // no barrier below
+    const bool three = A.dim == 3;
     const int64_t pl = (int64_t)A.nx * A.ny;
-    // one wave of CTAs, each walking (32 x 8)-point tiles: the prologue above is paid once
-    const int tx = (A.nx + 31) / 32, ty = (A.ny + 7) / 8;
-    const int64_t ntiles = (int64_t)tx * ty * A.nz;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int bx = (int)(tile % tx);
-        const int64_t rest = tile / tx;
-        const int by = (int)(rest % ty);
-        const int z = (int)(rest / ty);
-        const int x = bx * 32 + threadIdx.x;
-        const int yy = by * 8 + threadIdx.y;
-        if (x >= A.nx || yy >= A.ny) continue;
-        const int64_t p = (int64_t)z * pl + (int64_t)yy * A.nx + x;
+    int64_t p = (int64_t)zb * pl + (int64_t)yy * A.nx + x;
+    Vt vm = (three && zb > 0) ? M::load(v + p - pl) : M::zero();
+    Vt vc = M::load(v + p);
+#pragma unroll 2
+    for (int z = zb; z < ze; ++z, p += pl) {
+        const Vt vp = (three && z + 1 < A.nz) ? M::load(v + p + pl) : M::zero();
         Vt nb[7];
-        nb[0] = M::load(v + p);
+        nb[0] = vc;
         nb[1] = x > 0 ? M::load(v + p - 1) : M::zero();
         nb[2] = x < A.nx - 1 ? M::load(v + p + 1) : M::zero();
         nb[3] = yy > 0 ? M::load(v + p - A.nx) : M::zero();
         nb[4] = yy < A.ny - 1 ? M::load(v + p + A.nx) : M::zero();
-        nb[5] = (A.dim == 3 && z > 0) ? M::load(v + p - pl) : M::zero();
-        nb[6] = (A.dim == 3 && z < A.nz - 1) ? M::load(v + p + pl) : M::zero();
+        nb[5] = vm;
+        nb[6] = vp;
         if constexpr (P == PREC_DF64) {
             // centre, then the neighbours: exact products summed in double-float
             DfAcc acc;
@@ -196,6 +200,8 @@ __global__ void __launch_bounds__(kThreads) mp_stencil_kernel(StencilDesc A, con
             M::store(y + p, __fmul_rn(vfy.hi, acc));
             if (w) M::store(w + p, __fmul_rn(vfw.hi, nb[0]));
         }
+        vm = vc;
+        vc = vp;
     }
 }
 
@@ -203,10 +209,14 @@ template <int P>
 void mp_launch_stencil(const StencilDesc& A, const void* v, double fy, void* y, double fw, void* w,
                        const double* dscale, const SolverState* st, int gate, cudaStream_t stream) {
     using T = typename Mode<P>::T;
-    dim3 block(32, 8);
-    const int64_t ntiles = (int64_t)((A.nx + 31) / 32) * ((A.ny + 7) / 8) * A.nz;
-    const int grid = (int)(ntiles < 152 * 8 ? ntiles : 152 * 8);
-    mp_stencil_kernel<P><<<grid, block, 0, stream>>>(A, (const T*)v, fy, (T*)y, fw, (T*)w, dscale, st, gate);
+    const int tiles = ((A.nx + 31) / 32) * ((A.ny + 7) / 8);
+    // z chunks: about one wave of 8 CTAs per SM, at least one plane per chunk
+    int chunks = (152 * 8) / tiles;
+    chunks = chunks < 1 ? 1 : (chunks > A.nz ? A.nz : chunks);
+    const int zchunk = (A.nz + chunks - 1) / chunks;
+    chunks = (A.nz + zchunk - 1) / zchunk;
+    mp_stencil_kernel<P><<<dim3(tiles, chunks), dim3(32, 8), 0, stream>>>(A, (const T*)v, fy, (T*)y, fw, (T*)w, dscale,
+                                                                          st, gate, zchunk);
 }
 
 // ================================================================== fused matrix powers
@@ -432,8 +442,8 @@ __global__ void __launch_bounds__(kThreads) mp_gram_kernel(int64_t n, const type
             if (i < na) {
 #pragma unroll
                 for (int j = 0; j < KB; ++j) {
-                    acc_add(acc[i * KB + j], v0[i], M::wide(y0[j]));
-                    acc_add(acc[i * KB + j], v1[i], M::wide(y1[j]));
+                    acc_add(acc[i * KB + j], v0[i], y0[j]);
+                    acc_add(acc[i * KB + j], v1[i], y1[j]);
                 }
             }
         if (++cnt == kRenorm / 2) {
@@ -555,7 +565,7 @@ __global__ void __launch_bounds__(kThreads) mp_update_kernel(int64_t n, const ty
             for (int q = 0; q < KB; ++q)
 #pragma unroll
                 for (int pp = 0; pp <= q; ++pp) {
-                    acc_add(gacc[idx], yv[pp], M::wide(yv[q]));
+                    acc_add(gacc[idx], yv[pp], yv[q]);
                     ++idx;
                 }
             if (++cnt == kRenorm) {
@@ -703,8 +713,8 @@ __device__ __forceinline__ void symgram_rows(int64_t n, const typename Mode<P>::
         for (int c = Q0; c < Q1; ++c)
 #pragma unroll
             for (int r = 0; r <= c; ++r) {
-                acc_add(acc[idx], y0[r], M::wide(y0[c]));
-                acc_add(acc[idx], y1[r], M::wide(y1[c]));
+                acc_add(acc[idx], y0[r], y0[c]);       // float x float in FP32 mode: exact product
+                acc_add(acc[idx], y1[r], y1[c]);
                 ++idx;
             }
         if (++cnt == kRenorm / 2) {
