@@ -214,11 +214,20 @@ int sstep_batch_create(sstep_batch* out, int nsys, const sstep_matrix* A, const 
 int sstep_batch_solve(sstep_batch B, const double* const* f, double* const* x, sstep_result* res, int mode,
                       void* stream);
 /* Autotuner: times the persistent solve of the given batch under each candidate
- * launch configuration (threads per CTA, CTAs per SM, queue order), keeps the
- * fastest in the handle and reports it (host outputs, may be NULL). x is restored
- * to its initial content after every trial. */
+ * launch configuration, keeps the fastest in the handle and reports it (host
+ * outputs, may be NULL): threads per CTA, CTAs per SM, queue order (largest system
+ * first or not), and the size classes: systems with n >= *coop_min_n are solved by
+ * a thread-block cluster of *cluster CTAs together (cluster 1: every system by one
+ * CTA), the rest by one CTA each. x is restored to its initial content after every
+ * trial. */
 int sstep_batch_tune(sstep_batch B, const double* const* f, double* const* x, int* threads, int* ctas_per_sm,
-                     int* largest_first, void* stream);
+                     int* largest_first, int* cluster, int64_t* coop_min_n, void* stream);
+/* Sets the launch configuration by hand (the values sstep_batch_tune chooses among):
+ * threads in {32, 64, ..., 256}, ctas_per_sm >= 1, cluster in 1..8, coop_min_n >= 0
+ * (systems with n >= coop_min_n are solved by a whole cluster when cluster > 1).
+ * Configurations the device cannot run make sstep_batch_solve return SSTEP_ERR_ARG. */
+int sstep_batch_configure(sstep_batch B, int threads, int ctas_per_sm, int largest_first, int cluster,
+                          int64_t coop_min_n);
 int sstep_batch_destroy(sstep_batch B);
 
 const char* sstep_status_string(int status);

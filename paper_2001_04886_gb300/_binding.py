@@ -56,7 +56,9 @@ SIGNATURES = {
     "sstep_status_string": (ctypes.c_char_p, [c_int]),
     "sstep_batch_create": (c_int, [P(c_void_p), c_int, P(c_void_p), P(SStepParams)]),
     "sstep_batch_solve": (c_int, [c_void_p, P(c_void_p), P(c_void_p), P(SStepResult), c_int, c_void_p]),
-    "sstep_batch_tune": (c_int, [c_void_p, P(c_void_p), P(c_void_p), P(c_int), P(c_int), P(c_int), c_void_p]),
+    "sstep_batch_tune": (c_int, [c_void_p, P(c_void_p), P(c_void_p), P(c_int), P(c_int), P(c_int), P(c_int),
+                                 P(c_int64), c_void_p]),
+    "sstep_batch_configure": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int64]),
     "sstep_batch_destroy": (c_int, [c_void_p]),
     "x0net_create": (c_int, [P(c_void_p), c_int, c_int, c_int, c_int, c_int]),
     "x0net_destroy": (c_int, [c_void_p]),
@@ -347,10 +349,17 @@ class BatchSolver:
         return [dict(status=r.status, cycles=r.cycles, iters=r.iters, matvecs=r.matvecs, relres=r.relres) for r in res]
 
     def tune(self, f, x, stream=None):
-        t, c, o = c_int(), c_int(), c_int()
+        t, c, o, g, nb = c_int(), c_int(), c_int(), c_int(), c_int64()
         _check("sstep_batch_tune", lib().sstep_batch_tune(self.handle, self._ptrs(f), self._ptrs(x), ctypes.byref(t),
-                                                          ctypes.byref(c), ctypes.byref(o), _stream(stream)))
-        return dict(threads=t.value, ctas_per_sm=c.value, largest_first=o.value)
+                                                          ctypes.byref(c), ctypes.byref(o), ctypes.byref(g),
+                                                          ctypes.byref(nb), _stream(stream)))
+        return dict(threads=t.value, ctas_per_sm=c.value, largest_first=o.value, cluster=g.value,
+                    coop_min_n=nb.value)
+
+    def configure(self, threads=256, ctas_per_sm=1, largest_first=1, cluster=1, coop_min_n=0):
+        """Set the launch configuration by hand (what tune() would choose)."""
+        _check("sstep_batch_configure", lib().sstep_batch_configure(self.handle, threads, ctas_per_sm, largest_first,
+                                                                    cluster, coop_min_n))
 
     def close(self):
         if self.handle:

@@ -444,13 +444,15 @@ struct sstep_batch_s {
     int* d_order = nullptr;              // device copy of the queue order (largest first)
     unsigned* d_queue = nullptr;
     std::vector<BatchSys> h_sys;
-    std::vector<SolverState> h_init;     // initial states
+    std::vector<SolverState> h_init;     // initial states, kBatchCopies per system
+    SolverState* d_init = nullptr;       // the same on the device
     SolverState* h_states = nullptr;     // pinned copy back
     std::vector<size_t> state_off;
     // launch configuration (autotuned)
-    int threads = 256, ctas_per_sm = 2, largest_first = 1;
+    int threads = 256, ctas_per_sm = 2, largest_first = 1, cluster = 1;
+    int64_t nbig = 0;                    // systems with n >= nbig get a whole cluster
     cudaGraphExec_t graph = nullptr;
-    int graph_cfg[3] = {0, 0, 0};
+    int64_t graph_cfg[5] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -475,7 +477,7 @@ SolverState batch_state(char* base, int m, int s, const sstep_params* p, double 
 }
 
 int batch_graph(sstep_batch B, cudaStream_t stream) {
-    const int cfg[3] = {B->threads, B->ctas_per_sm, B->largest_first};
+    const int64_t cfg[5] = {B->threads, B->ctas_per_sm, B->largest_first, B->cluster, B->nbig};
     if (B->graph && memcmp(cfg, B->graph_cfg, sizeof(cfg)) == 0) return SSTEP_OK;
     if (B->graph) {
         cudaGraphExecDestroy(B->graph);
@@ -484,6 +486,8 @@ int batch_graph(sstep_batch B, cudaStream_t stream) {
     int dev = 0, sms = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = batched_grid(B->s, B->threads, sms * B->ctas_per_sm, B->cluster);
+    if (grid < 1) return SSTEP_ERR_ARG;
     cudaStream_t cap;
     CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t g;
@@ -491,8 +495,9 @@ int batch_graph(sstep_batch B, cudaStream_t stream) {
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = SSTEP_ERR_CUDA;
     if (!rc) {
         cudaMemsetAsync(B->d_queue, 0, sizeof(unsigned), cap);
+        launch_batch_init(B->d_init, B->d_sys, B->nsys, cap);
         if (launch_batched(B->d_sys, B->largest_first ? B->d_order : nullptr, B->nsys, B->d_queue, B->s, B->threads,
-                           sms * B->ctas_per_sm, cap))
+                           grid, B->cluster, B->nbig, cap))
             rc = SSTEP_ERR_ARG;
         if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = SSTEP_ERR_CUDA;
     }
@@ -513,10 +518,7 @@ int batch_run_persistent(sstep_batch B, const double* const* f, double* const* x
         B->h_sys[i].x = x[i];
     }
     CUDA_TRY(cudaMemcpyAsync(B->d_sys, B->h_sys.data(), sizeof(BatchSys) * B->nsys, cudaMemcpyHostToDevice, stream));
-    for (int i = 0; i < B->nsys; ++i)
-        CUDA_TRY(cudaMemcpyAsync(B->ws + B->state_off[i], &B->h_init[i], sizeof(SolverState), cudaMemcpyHostToDevice,
-                                 stream));
-    int rc = batch_graph(B, stream);
+    int rc = batch_graph(B, stream);   // the graph resets the queue and every state copy, then solves
     if (rc) return rc;
     CUDA_TRY(cudaGraphLaunch(B->graph, stream));
     return SSTEP_OK;
@@ -1033,7 +1035,7 @@ int sstep_batch_create(sstep_batch* out, int nsys, const sstep_matrix* A, const 
     std::vector<size_t> col_off(nsys);
     for (int i = 0; i < nsys; ++i) {
         B->state_off[i] = total;
-        total += sb;
+        total += sb * kBatchCopies;
     }
     for (int i = 0; i < nsys; ++i) {
         col_off[i] = total;
@@ -1043,6 +1045,7 @@ int sstep_batch_create(sstep_batch* out, int nsys, const sstep_matrix* A, const 
     if (cudaMalloc((void**)&B->ws, total) != cudaSuccess || cudaMalloc((void**)&B->d_sys, sizeof(BatchSys) * nsys) !=
             cudaSuccess || cudaMalloc((void**)&B->d_order, sizeof(int) * nsys) != cudaSuccess ||
         cudaMalloc((void**)&B->d_queue, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc((void**)&B->d_init, sizeof(SolverState) * nsys * kBatchCopies) != cudaSuccess ||
         cudaMallocHost((void**)&B->h_states, sizeof(SolverState) * nsys) != cudaSuccess) {
         cudaGetLastError();
         rc = SSTEP_ERR_OOM;
@@ -1053,14 +1056,16 @@ int sstep_batch_create(sstep_batch* out, int nsys, const sstep_matrix* A, const 
     }
     B->ws_bytes = total;
     B->h_sys.resize(nsys);
-    B->h_init.resize(nsys);
+    B->h_init.resize((size_t)nsys * kBatchCopies);
     for (int i = 0; i < nsys; ++i) {
         const double sigma = p->sigma > 0.0 ? p->sigma : 1.0 / A[i]->norm_inf;
-        B->h_init[i] = batch_state(B->ws + B->state_off[i], m, s, p, sigma);
+        for (int g = 0; g < kBatchCopies; ++g)
+            B->h_init[(size_t)i * kBatchCopies + g] = batch_state(B->ws + B->state_off[i] + g * sb, m, s, p, sigma);
         BatchSys& b = B->h_sys[i];
         b.A = A[i]->A;
         b.U = (double*)(B->ws + col_off[i]);
         b.st = (SolverState*)(B->ws + B->state_off[i]);
+        b.st_stride = (int64_t)sb;
         b.ld = col_ld(A[i]->A.n);
         b.f = nullptr;
         b.x = nullptr;
@@ -1070,6 +1075,8 @@ int sstep_batch_create(sstep_batch* out, int nsys, const sstep_matrix* A, const 
     std::stable_sort(B->order_largest.begin(), B->order_largest.end(),
                      [&](int a, int b) { return A[a]->A.n > A[b]->A.n; });
     if (cudaMemcpy(B->d_order, B->order_largest.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(B->d_init, B->h_init.data(), sizeof(SolverState) * B->h_init.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
         cudaMemset(B->ws, 0, total) != cudaSuccess) {
         sstep_batch_destroy(B);
         return SSTEP_ERR_CUDA;
@@ -1114,7 +1121,7 @@ int sstep_batch_solve(sstep_batch B, const double* const* f, double* const* x, s
 }
 
 int sstep_batch_tune(sstep_batch B, const double* const* f, double* const* x, int* threads, int* ctas_per_sm,
-                     int* largest_first, void* stream) {
+                     int* largest_first, int* cluster, int64_t* coop_min_n, void* stream) {
     if (!B || !f || !x) return SSTEP_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     // keep the initial guesses to restore them after every trial
@@ -1125,37 +1132,50 @@ int sstep_batch_tune(sstep_batch B, const double* const* f, double* const* x, in
         if (cudaMalloc((void**)&saved[i], bytes) != cudaSuccess) rc = SSTEP_ERR_OOM;
         else if (cudaMemcpyAsync(saved[i], x[i], bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) rc = SSTEP_ERR_CUDA;
     }
-    const int cand_threads[2] = {128, 256};
-    const int cand_ctas[3] = {1, 2, 4};
-    const int cand_order[2] = {1, 0};
+    int64_t nmax = 1;
+    for (int i = 0; i < B->nsys; ++i) nmax = std::max<int64_t>(nmax, B->mats[i]->A.n);
+    // candidates: one CTA per system (block size, CTAs per SM, queue order), and clusters
+    // of 2, 4 or 8 CTAs for the systems with at least a quarter or a half of the largest n
+    struct Cand {
+        int t, c, o, g;
+        int64_t nb;
+    };
+    std::vector<Cand> cands;
+    for (int t : {128, 256})
+        for (int c : {1, 2, 4})
+            for (int o : {1, 0})
+                if (!(t == 256 && c == 4)) cands.push_back({t, c, o, 1, 0});
+    for (int g : {2, 4, 8})
+        for (int c : {1, 2})
+            for (int64_t nb : {std::max<int64_t>(1, nmax / 4), std::max<int64_t>(1, nmax / 2)})
+                cands.push_back({256, c, 1, g, nb});
     double best = 1e300;
-    int bt = B->threads, bc = B->ctas_per_sm, bo = B->largest_first;
+    Cand bestc{B->threads, B->ctas_per_sm, B->largest_first, B->cluster, B->nbig};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int t : cand_threads)
-        for (int c : cand_ctas)
-            for (int o : cand_order) {
-                if (rc) break;
-                if (t == 256 && c == 4) continue;   // more threads than the register file holds
-                B->threads = t;
-                B->ctas_per_sm = c;
-                B->largest_first = o;
-                for (int i = 0; i < B->nsys; ++i)
-                    cudaMemcpyAsync(x[i], saved[i], sizeof(double) * B->mats[i]->A.n, cudaMemcpyDeviceToDevice, st);
-                cudaEventRecord(e0, st);
-                rc = batch_run_persistent(B, f, x, st);
-                cudaEventRecord(e1, st);
-                if (cudaStreamSynchronize(st) != cudaSuccess) rc = SSTEP_ERR_CUDA;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (!rc && ms < best) {
-                    best = ms;
-                    bt = t;
-                    bc = c;
-                    bo = o;
-                }
-            }
+    for (const Cand& cd : cands) {
+        if (rc) break;
+        B->threads = cd.t;
+        B->ctas_per_sm = cd.c;
+        B->largest_first = cd.o;
+        B->cluster = cd.g;
+        B->nbig = cd.nb;
+        for (int i = 0; i < B->nsys; ++i)
+            cudaMemcpyAsync(x[i], saved[i], sizeof(double) * B->mats[i]->A.n, cudaMemcpyDeviceToDevice, st);
+        cudaEventRecord(e0, st);
+        const int r = batch_run_persistent(B, f, x, st);
+        cudaEventRecord(e1, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = SSTEP_ERR_CUDA;
+        if (r == SSTEP_ERR_ARG) continue;      // this configuration cannot be launched here
+        if (r) rc = r;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (!rc && ms < best) {
+            best = ms;
+            bestc = cd;
+        }
+    }
     for (int i = 0; i < B->nsys; ++i) {
         if (saved[i]) {
             cudaMemcpyAsync(x[i], saved[i], sizeof(double) * B->mats[i]->A.n, cudaMemcpyDeviceToDevice, st);
@@ -1166,13 +1186,30 @@ int sstep_batch_tune(sstep_batch B, const double* const* f, double* const* x, in
         if (q) cudaFree(q);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    B->threads = bt;
-    B->ctas_per_sm = bc;
-    B->largest_first = bo;
-    if (threads) *threads = bt;
-    if (ctas_per_sm) *ctas_per_sm = bc;
-    if (largest_first) *largest_first = bo;
+    B->threads = bestc.t;
+    B->ctas_per_sm = bestc.c;
+    B->largest_first = bestc.o;
+    B->cluster = bestc.g;
+    B->nbig = bestc.nb;
+    if (threads) *threads = bestc.t;
+    if (ctas_per_sm) *ctas_per_sm = bestc.c;
+    if (largest_first) *largest_first = bestc.o;
+    if (cluster) *cluster = bestc.g;
+    if (coop_min_n) *coop_min_n = bestc.nb;
     return rc;
+}
+
+int sstep_batch_configure(sstep_batch B, int threads, int ctas_per_sm, int largest_first, int cluster,
+                          int64_t coop_min_n) {
+    if (!B || threads < 32 || threads > 256 || threads % 32 || ctas_per_sm < 1 || ctas_per_sm > 16 || cluster < 1 ||
+        cluster > kBatchCopies || coop_min_n < 0)
+        return SSTEP_ERR_ARG;
+    B->threads = threads;
+    B->ctas_per_sm = ctas_per_sm;
+    B->largest_first = largest_first ? 1 : 0;
+    B->cluster = cluster;
+    B->nbig = coop_min_n;
+    return SSTEP_OK;
 }
 
 int sstep_batch_destroy(sstep_batch B) {
@@ -1182,6 +1219,7 @@ int sstep_batch_destroy(sstep_batch B) {
     if (B->d_sys) cudaFree(B->d_sys);
     if (B->d_order) cudaFree(B->d_order);
     if (B->d_queue) cudaFree(B->d_queue);
+    if (B->d_init) cudaFree(B->d_init);
     if (B->h_states) cudaFreeHost(B->h_states);
     delete B;
     return SSTEP_OK;

@@ -55,7 +55,7 @@ def test_persistent_equals_per_system_and_tuning():
     xs2 = [torch.zeros_like(x) for x in xs]
     B = pkg.BatchSolver(mats, 4, 20, 1e-8)
     cfg = B.tune(fs, xs)
-    assert cfg["threads"] in (128, 256) and cfg["ctas_per_sm"] in (1, 2, 4)
+    assert cfg["threads"] in (128, 256) and cfg["ctas_per_sm"] in (1, 2, 4) and cfg["cluster"] in (1, 2, 4, 8)
     assert all(float(x.abs().max()) == 0.0 for x in xs)     # tuning restores the initial guesses
     r1 = B.solve(fs, xs, mode=B.PERSISTENT)
     r2 = B.solve(fs, xs2, mode=B.PER_SYSTEM)
@@ -65,3 +65,40 @@ def test_persistent_equals_per_system_and_tuning():
         assert r1[i]["cycles"] == r2[i]["cycles"]
         a, b = xs[i].cpu().numpy(), xs2[i].cpu().numpy()
         assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("cluster,coop", [(2, "all"), (4, "all"), (8, "all"), (4, "half")])
+def test_cluster_cooperative_solves_match_oracle(cluster, coop):
+    """Systems solved by a thread-block cluster together (rows split over the CTAs,
+    reductions through distributed shared memory) reach the oracle's solution with its
+    cycle count; 'half' mixes cooperative and one-CTA systems in one launch. The sizes
+    include ragged row splits (n not a multiple of the cluster) and n below the cluster's
+    thread count."""
+    d = dev()
+    mats, ora, fs, xs = batch(5, 20, 3, 48, d)
+    nmed = int(np.median([A.n for A in mats]))
+    B = pkg.BatchSolver(mats, 4, 20, 1e-8, max_cycles=400)
+    B.configure(threads=256, ctas_per_sm=1, largest_first=1, cluster=cluster, coop_min_n=0 if coop == "all" else nmed)
+    res = B.solve(fs, xs, mode=B.PERSISTENT)
+    torch.cuda.synchronize()
+    for i, ((Ao, f), r) in enumerate(zip(ora, res)):
+        ref = osstep.sstep_gmres(Ao, f, np.zeros(Ao.n), 4, 20, 1e-8, 1.0 / Ao.norm_inf(), 400)
+        x = xs[i].cpu().numpy()
+        assert r["status"] == 0 and ref["status"] == 0, (i, r)
+        assert r["cycles"] == ref["cycles"], (i, r["cycles"], ref["cycles"])
+        assert np.linalg.norm(x - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"]), i
+        assert np.linalg.norm(f - Ao.apply(x)) <= 1e-8 * np.linalg.norm(f)
+    # a second solve with the same handle (the graph resets every state copy)
+    for x in xs:
+        x.zero_()
+    res2 = B.solve(fs, xs, mode=B.PERSISTENT)
+    assert [r["cycles"] for r in res2] == [r["cycles"] for r in res]
+
+
+def test_configure_rejects_bad_arguments():
+    d = dev()
+    mats, ora, fs, xs = batch(6, 3, 8, 12, d)
+    B = pkg.BatchSolver(mats, 4, 20, 1e-8)
+    for bad in (dict(threads=100), dict(cluster=0), dict(cluster=9), dict(ctas_per_sm=0), dict(coop_min_n=-1)):
+        with pytest.raises(pkg.SStepError):
+            B.configure(**bad)
