@@ -13,6 +13,11 @@
 // The row loops are software-pipelined: the loads of the next row (or of the
 // next group of basis columns) are issued before the current one is computed,
 // so a warp keeps loads in flight while it spends its FP32 instructions.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "df64.cuh"
 #include "epilogue.cuh"
 
@@ -21,6 +26,7 @@ namespace sstep {
 constexpr int kMpRedCtas = 152 * 2;    // reductions with many accumulators: many rows per thread
 constexpr int kMpCtas = 152 * 4;       // light kernels
 constexpr int kRenorm = 8;             // rows between accumulator renormalisations
+constexpr int kMaxCtasMp = 152 * 8;    // grid bound of the reductions (the partials buffer size)
 constexpr int kChunk = 8;              // basis columns loaded together in the projection
 
 // ------------------------------------------------------------------ storage / arithmetic traits
@@ -133,6 +139,25 @@ __device__ __forceinline__ void broadcast_factors(double fy, double fw, const do
         out2[1] = df_from_double(fw);
     }
     __syncthreads();
+}
+
+// CTAs of kThreads threads of `kernel` resident at once on the current device (cached)
+int resident_ctas(const void* kernel) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find({kernel, dev});
+    if (it != cache.end()) return it->second;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    cudaGetLastError();
+    const int r = per_sm * sms;
+    cache[{kernel, dev}] = r;
+    return r;
 }
 
 // ================================================================== stencil sweep
@@ -495,9 +520,12 @@ void mp_launch_gram(int64_t n, const void* V, int64_t ldv, int ka, const void* Y
 
 // ================================================================== projection Y - V T (+ optional Gram)
 // Yout[:, j] = Yin[:, j] + V (sgn T)[:, j] for j >= j0, summed in double-float and
-// rounded once to the storage type. The basis columns are read in groups of kChunk,
-// the next group's loads issued before the current group is accumulated. With GRAM
-// (used for narrow outputs) the kb x kb Gram of Yout is reduced in the same pass.
+// rounded once to the storage type. Two consecutive rows per thread (16-byte loads;
+// every coefficient read from shared memory serves two products); the basis columns
+// are read in groups of kChunk, the next group's loads issued before the current group
+// is accumulated. With GRAM (used for narrow outputs) the kb x kb Gram of Yout is
+// reduced in the same pass. Columns are allocated to an even length, so the row pair
+// of an odd n reads and writes one padding entry, which the Gram leaves out.
 template <int P, int KB, bool GRAM>
 __global__ void __launch_bounds__(kThreads) mp_update_kernel(int64_t n, const typename Mode<P>::T* __restrict__ V,
                                                              int64_t ldv, int ka, const typename Mode<P>::T* Yin,
@@ -519,56 +547,79 @@ __global__ void __launch_bounds__(kThreads) mp_update_kernel(int64_t n, const ty
     __syncthreads();
     DfAcc gacc[NV];
     const bool inplace = (Yin == Yout) && (ldy == ldo);
+    const int64_t npairs = (n + 1) / 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int nch = (ka + kChunk - 1) / kChunk;
     int cnt = 0;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-        Vt cur[kChunk];
-        if (ka > 0) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += stride) {
+        const int64_t p = 2 * q;
+        Vt y0[KB], y1[KB];
 #pragma unroll
-            for (int c = 0; c < kChunk; ++c) cur[c] = c < ka ? M::load(V + p + (int64_t)c * ldv) : M::zero();
-        }
-        Vt yv[KB];
-#pragma unroll
-        for (int j = 0; j < KB; ++j) yv[j] = M::load_rw(Yin + p + j * ldy);
+        for (int j = 0; j < KB; ++j) M::load2_rw(Yin + p + j * ldy, y0[j], y1[j]);
         if (ka > 0) {
-            DfAcc sum[KB];
+            Vt c0[kChunk], c1[kChunk];
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) {
+                if (c < ka) M::load2(V + p + (int64_t)c * ldv, c0[c], c1[c]);
+                else c0[c] = c1[c] = M::zero();
+            }
+            DfAcc s0[KB], s1[KB];
             for (int ch = 0; ch < nch; ++ch) {
-                const int base = ch * kChunk;
-                Vt nxt[kChunk];
-                const int nb = base + kChunk;
+                const int base = ch * kChunk, nb = base + kChunk;
+                Vt n0[kChunk], n1[kChunk];
 #pragma unroll
-                for (int c = 0; c < kChunk; ++c) nxt[c] = (nb + c < ka) ? M::load(V + p + (int64_t)(nb + c) * ldv) : M::zero();
+                for (int c = 0; c < kChunk; ++c) {
+                    if (nb + c < ka) M::load2(V + p + (int64_t)(nb + c) * ldv, n0[c], n1[c]);
+                    else n0[c] = n1[c] = M::zero();
+                }
 #pragma unroll
                 for (int c = 0; c < kChunk; ++c) {
                     if (base + c < ka) {
 #pragma unroll
                         for (int j = 0; j < KB; ++j)
-                            if (j >= j0) acc_add(sum[j], cur[c], Ts[(base + c) * KB + j]);
+                            if (j >= j0) {
+                                const df64 t = Ts[(base + c) * KB + j];
+                                acc_add(s0[j], c0[c], t);
+                                acc_add(s1[j], c1[c], t);
+                            }
                     }
                 }
 #pragma unroll
-                for (int c = 0; c < kChunk; ++c) cur[c] = nxt[c];
+                for (int c = 0; c < kChunk; ++c) {
+                    c0[c] = n0[c];
+                    c1[c] = n1[c];
+                }
 #pragma unroll
-                for (int j = 0; j < KB; ++j) sum[j].normalize();
+                for (int j = 0; j < KB; ++j) {
+                    s0[j].normalize();
+                    s1[j].normalize();
+                }
             }
 #pragma unroll
             for (int j = 0; j < KB; ++j)
-                if (j >= j0) yv[j] = M::narrow(df_add(M::wide(yv[j]), df64{sum[j].hi, sum[j].lo}));
+                if (j >= j0) {
+                    y0[j] = M::narrow(df_add(M::wide(y0[j]), df64{s0[j].hi, s0[j].lo}));
+                    y1[j] = M::narrow(df_add(M::wide(y1[j]), df64{s1[j].hi, s1[j].lo}));
+                }
         }
 #pragma unroll
         for (int j = 0; j < KB; ++j)
-            if (!inplace || (j >= j0 && ka > 0)) M::store(Yout + p + j * ldo, yv[j]);
+            if (!inplace || (j >= j0 && ka > 0)) M::store2(Yout + p + j * ldo, y0[j], y1[j]);
         if (GRAM) {
+            if (p + 1 >= n) {
+#pragma unroll
+                for (int j = 0; j < KB; ++j) y1[j] = M::zero();
+            }
             int idx = 0;
 #pragma unroll
-            for (int q = 0; q < KB; ++q)
+            for (int qq = 0; qq < KB; ++qq)
 #pragma unroll
-                for (int pp = 0; pp <= q; ++pp) {
-                    acc_add(gacc[idx], yv[pp], yv[q]);
+                for (int pp = 0; pp <= qq; ++pp) {
+                    acc_add(gacc[idx], y0[pp], y0[qq]);
+                    acc_add(gacc[idx], y1[pp], y1[qq]);
                     ++idx;
                 }
-            if (++cnt == kRenorm) {
+            if (++cnt == kRenorm / 2) {
                 cnt = 0;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) gacc[v].normalize();
@@ -793,12 +844,16 @@ void mp_launch_update(int64_t n, const void* V, int64_t ldv, int ka, const void*
         return;
     }
     if (kb > 2) {
-        // wide blocks: the projection alone (light, many CTAs), then the block's Gram
+        // wide blocks: the projection alone (light, many CTAs), then the block's Gram over
+        // one wave of CTAs (two column groups along grid.y)
         mp_launch_update<P>(n, V, ldv, ka, Yin, ldy, Yout, ldo, kb, j0, T, ldt, sgn, false, sc, epi, gate, stream);
-        dim3 grid(grid_for((n + 1) / 2, kMpRedCtas), 2);
         switch (kb) {
-#define SSTEP_MPS(KB) \
-    case KB: mp_symgram_kernel<P, KB><<<grid, kThreads, 0, stream>>>(n, Yo, ldo, sc, epi, gate); break;
+#define SSTEP_MPS(KB)                                                                                             \
+    case KB: {                                                                                                    \
+        const int wave = std::min(kMaxCtasMp, resident_ctas((const void*)mp_symgram_kernel<P, KB>));             \
+        dim3 grid(grid_for((n + 1) / 2, wave / 2 > 0 ? wave / 2 : 1), 2);                                         \
+        mp_symgram_kernel<P, KB><<<grid, kThreads, 0, stream>>>(n, Yo, ldo, sc, epi, gate);                       \
+    } break;
             SSTEP_MPS(3)
             SSTEP_MPS(4)
             SSTEP_MPS(5)
@@ -811,12 +866,18 @@ void mp_launch_update(int64_t n, const void* V, int64_t ldv, int ka, const void*
         }
         return;
     }
-    int grid = grid_for(n, kMpRedCtas * 2);
+    // one wave of CTAs (the partials buffer holds kMaxCtas x kMaxNV doubles)
     switch (kb) {
-        case 1: mp_update_kernel<P, 1, true><<<grid, kThreads, 0, stream>>>(n, Vp, ldv, ka, Yi, ldy, Yo, ldo, j0, T, ldt,
-                                                                            sgn, sc, epi, gate); break;
-        case 2: mp_update_kernel<P, 2, true><<<grid, kThreads, 0, stream>>>(n, Vp, ldv, ka, Yi, ldy, Yo, ldo, j0, T, ldt,
-                                                                            sgn, sc, epi, gate); break;
+        case 1: {
+            const int grid = grid_for((n + 1) / 2, std::min(kMaxCtasMp, resident_ctas((const void*)mp_update_kernel<P, 1, true>)));
+            mp_update_kernel<P, 1, true><<<grid, kThreads, 0, stream>>>(n, Vp, ldv, ka, Yi, ldy, Yo, ldo, j0, T, ldt, sgn,
+                                                                        sc, epi, gate);
+        } break;
+        case 2: {
+            const int grid = grid_for((n + 1) / 2, std::min(kMaxCtasMp, resident_ctas((const void*)mp_update_kernel<P, 2, true>)));
+            mp_update_kernel<P, 2, true><<<grid, kThreads, 0, stream>>>(n, Vp, ldv, ka, Yi, ldy, Yo, ldo, j0, T, ldt, sgn,
+                                                                        sc, epi, gate);
+        } break;
         default: break;
     }
 }
