@@ -90,13 +90,21 @@ def parse():
     ap.add_argument("--s", type=int, default=8, help="block size of the headline s-step GMRES")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32"],
                     help="basis precision of the headline solve")
-    ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--learned", action="store_true",
-                    help="also run the learned-initial-guess form (128^2, 20k training systems; minutes)")
+    ap.add_argument("--no-variants", action="store_true", help="the headline solve only")
+    ap.add_argument("--variants", default="solvers,precision,batched",
+                    help="comma list of the extra measurements: solvers (s = 2/4/8, GMRES, Orthomin, "
+                         "mixed-precision bases), precision (the 256^3 FP32-refinement form), batched "
+                         "(512 systems), learned (the learned initial guess; minutes)")
+    ap.add_argument("--learned", action="store_true", help="add 'learned' to --variants")
     ap.add_argument("--learned-train", type=int, default=20000)
+    ap.add_argument("--learned-test", type=int, default=1000)
     ap.add_argument("--learned-epochs", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    a.groups = set() if a.no_variants else {g.strip() for g in a.variants.split(",") if g.strip()}
+    if a.learned:
+        a.groups.add("learned")
+    return a
 
 
 # ------------------------------------------------------------------ clocks
@@ -364,7 +372,7 @@ def main():
     assert r2["status"] == 0
 
     variants = {}
-    if not args.no_variants:
+    if "solvers" in args.groups:
         for name, kw in [("sstep_gmres_s2", dict(method="sstep", s=2)), ("sstep_gmres_s4", dict(method="sstep", s=4)),
                          ("sstep_gmres_s8", dict(method="sstep", s=8)), ("gmres", dict(method="gmres")),
                          ("sstep_omin_s4_k1", dict(method="omin", s=4, k=1)),
@@ -386,7 +394,7 @@ def main():
             variants[name] = {"ms": e0.elapsed_time(e1) / reps, "status": rv["status"], "cycles": rv["cycles"],
                               "iters": rv["iters"], "matvecs": rv["matvecs"], "relres": rv["relres"]}
 
-    if not args.no_variants:
+    if "precision" in args.groups:
         # the precision form: 3-D 256^3, beta = (50, 0, 0), s = 8, m = 32, to 1e-10; FP32
         # iterative refinement against the all-FP64 s-step solve
         A3 = pkg.StencilMatrix(3, (256, 256, 256), beta=(50.0, 0.0, 0.0))
@@ -410,7 +418,7 @@ def main():
         variants["precision_form_256cube_s8_m32_tol1e-10"] = form
         del A3, xt3, f3, x3
 
-    if not args.no_variants:
+    if "batched" in args.groups:
         # the batched form: 512 systems, sides L ~ U{32..256}, beta ~ U[0, 50], s = 4, m = 20, tol 1e-8
         systems = inputs.batched_systems(rank, 512)
         mats, fs, xs, xts = [], [], [], []
@@ -442,11 +450,12 @@ def main():
         Bs.close()
         del mats, fs, xs
 
-    if args.learned:
+    if "learned" in args.groups:
         from paper_2001_04886_gb300 import learned
 
         t0 = time.perf_counter()
-        ev = learned.run(N=128, train_seeds=range(args.learned_train), test_seeds=range(20000, 21000),
+        ev = learned.run(N=128, train_seeds=range(args.learned_train),
+                         test_seeds=range(20000, 20000 + args.learned_test),
                          epochs=args.learned_epochs, batch=32, lr=1e-3, log=lambda m: print(m, file=sys.stderr))
         ev["total_s"] = time.perf_counter() - t0
         variants["learned_x0_128"] = ev
