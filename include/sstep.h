@@ -36,7 +36,8 @@ typedef enum {
     SSTEP_ERR_CUDA = -2,       /* a CUDA runtime call failed */
     SSTEP_ERR_OOM = -3,        /* device allocation failed */
     SSTEP_ERR_BREAKDOWN = -4,  /* non-positive Cholesky pivot in a Gram block W (Scalar1/Scalar2) */
-    SSTEP_ERR_NAN = -5         /* a residual norm became NaN or Inf */
+    SSTEP_ERR_NAN = -5,        /* a residual norm became NaN or Inf */
+    SSTEP_ERR_TIMEOUT = -6     /* a bounded device-side wait (tensor-core pipeline) ran out */
 } sstep_status;
 
 typedef struct sstep_matrix_s* sstep_matrix;
@@ -265,6 +266,14 @@ int x0net_gradient(x0net X, const float* input, const float* target, int batch, 
                    void* stream);
 /* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean-squared loss;
  * loss_dev (DEVICE, may be NULL) receives the loss before the step. */
+/* BF16 mode: run the 3x3 convolutions (forward and backward-data) on the tensor cores
+ * (tcgen05 implicit GEMM, FP32 activations split into three BF16 parts, FP32 accumulation;
+ * default on) or on the CUDA cores (on = 0). The FP32-weight mode always uses the CUDA
+ * cores. */
+int x0net_set_tensor_cores(x0net X, int on);
+/* Synchronises `stream` and reports SSTEP_ERR_TIMEOUT if a tensor-core kernel's bounded
+ * wait ran out since the network was created (x0net_gradient reports it as well). */
+int x0net_status(x0net X, void* stream);
 int x0net_train_step(x0net X, const float* input, const float* target, int batch, float lr, float* loss_dev,
                      void* stream);
 

@@ -68,6 +68,8 @@ SIGNATURES = {
     "x0net_get_params": (c_int, [c_void_p, c_void_p, c_void_p]),
     "x0net_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "x0net_gradient": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "x0net_set_tensor_cores": (c_int, [c_void_p, c_int]),
+    "x0net_status": (c_int, [c_void_p, c_void_p]),
     "x0net_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p, c_void_p]),
     "sstep_trace_enable": (c_int, [c_int]),
     "sstep_trace_kinds": (c_int, []),
@@ -431,6 +433,14 @@ class X0Net:
         lp = self._f32(loss_out) if loss_out is not None else c_void_p(0)
         _check("x0net_train_step", lib().x0net_train_step(self.handle, self._f32(inp), self._f32(target), inp.shape[0],
                                                           lr, lp, _stream(stream)))
+
+    def set_tensor_cores(self, on):
+        """BF16 mode: 3x3 convolutions on the tensor cores (default) or on the CUDA cores."""
+        _check("x0net_set_tensor_cores", lib().x0net_set_tensor_cores(self.handle, 1 if on else 0))
+
+    def status(self, stream=None):
+        """Synchronises and raises if a tensor-core kernel's bounded wait ran out."""
+        _check("x0net_status", lib().x0net_status(self.handle, _stream(stream)))
 
     def close(self):
         if self.handle:

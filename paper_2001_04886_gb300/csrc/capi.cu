@@ -559,6 +559,7 @@ const char* sstep_status_string(int status) {
         case SSTEP_ERR_OOM: return "out of device memory";
         case SSTEP_ERR_BREAKDOWN: return "breakdown: non-positive Cholesky pivot in a Gram block";
         case SSTEP_ERR_NAN: return "residual is NaN or Inf";
+        case SSTEP_ERR_TIMEOUT: return "a bounded device wait ran out";
         default: return "unknown status";
     }
 }

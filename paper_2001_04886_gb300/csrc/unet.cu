@@ -22,6 +22,7 @@
 #include <string.h>
 
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/sstep.h"
@@ -104,6 +105,363 @@ __global__ void __launch_bounds__(kT) conv3x3_kernel(const float* __restrict__ i
         if (relu) v = fmaxf(v, 0.f);
         float* dst = out + ((int64_t)b * Cout + co0 + c) * plane + (int64_t)y * Wd + x;
         *dst = accumulate ? *dst + v : v;
+    }
+}
+
+// ------------------------------------------------------------------ 3x3 convolution on the tensor cores
+// Implicit GEMM with tcgen05: D[pixel][n] = sum over (tap, channel) A[pixel][(tap, c)] B[n][(tap, c)]
+// for a tile of 128 consecutive pixels of one image (one CTA of 128 threads, thread m <->
+// pixel m, which is TMEM lane m of the accumulator). The K dimension runs over the 9 taps x
+// the input channels in chunks of 16. The FP32 activation of every product is split into
+// three BF16 parts (hi + mid + lo represents all 24 bits of its significand), and each
+// part is multiplied by the BF16 weight in its own MMA: the products are exact and the
+// tensor core accumulates them in FP32, so the layer computes what the CUDA-core kernel
+// computes (BF16 weights, FP32 activations, FP32 accumulation) up to the order of the sums.
+// Operands are staged by the threads in shared memory in the K-major no-swizzle layout
+// (8-row x 16-byte core matrices, 128 B between K-adjacent and 256 B between row-adjacent
+// core matrices), two stages deep: while the MMAs of chunk i run, the threads gather chunk
+// i + 1. One thread issues the MMAs and commits them to the stage's mbarrier; every wait
+// is bounded and a wait that runs out sets *err, skips the rest of the work and still
+// frees the tensor memory. TRANSPOSED: the backward-data form (weights W[co][ci] read as
+// B[n = ci][c = co] with the taps rotated by 180 degrees).
+namespace tc {
+
+constexpr int kM = 128;                 // pixels per CTA (MMA M)
+constexpr int kK = 16;                  // K per MMA (BF16)
+constexpr int kLbo = 128, kSbo = 256;   // core-matrix strides (bytes)
+constexpr long kSpin = 1L << 24;        // bounded mbarrier polls
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t kmaj(int r, int kq) {   // byte offset of row r, 8-element K group kq
+    return (uint32_t)((r >> 3) * kSbo + kq * kLbo + (r & 7) * 16);
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(kLbo >> 4) << 16) | ((uint64_t)(kSbo >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+__host__ __device__ constexpr uint32_t idesc(int n) {   // BF16 x BF16 -> FP32, K-major A and B, M = 128
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+}
+
+__host__ __device__ constexpr int tmem_cols(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : 256)); }
+
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (long it = 0; it < kSpin && !done; ++it)
+        asm volatile("{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\nselp.b32 %0, 1, 0, P;\n}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+template <int NP, bool TRANSPOSED>
+__global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const float* __restrict__ in, int Kc,
+                                                        const __nv_bfloat16* __restrict__ W,
+                                                        const float* __restrict__ bias, float* __restrict__ out,
+                                                        int N, int H, int Wd, int relu, int accumulate, int* err) {
+    constexpr int kABytes = kM * kK * 2;          // one BF16 part of the A chunk
+    constexpr int kBBytes = NP * kK * 2;
+    constexpr int kStage = 3 * kABytes + kBBytes;
+    constexpr uint32_t kCols = tmem_cols(NP);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int failed;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int b = blockIdx.y;
+    const int64_t HW = (int64_t)H * Wd;
+    const int64_t p = (int64_t)blockIdx.x * kM + tid;   // this thread's pixel (A row / TMEM lane)
+    const bool live = p < HW;
+    const int py = live ? (int)(p / Wd) : 0, px = live ? (int)(p - (int64_t)py * Wd) : 0;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        failed = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const int kgroups = (Kc + kK - 1) / kK;
+    const int nchunks = 9 * kgroups;
+    const float* inb = in + (int64_t)b * Kc * HW;
+    bool ok = true;
+    for (int i = 0; i < nchunks && ok; ++i) {
+        const int st = i & 1;
+        if (i >= 2) {   // the MMAs that read this stage (chunk i - 2) are done
+            if (!wait_bar(smem_u32(&bars[st]), (uint32_t)(((i >> 1) - 1) & 1))) {
+                failed = 1;
+            }
+            __syncthreads();
+            if (failed) {
+                ok = false;
+                break;
+            }
+        }
+        const int tap = i / kgroups, c0 = (i - tap * kgroups) * kK;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        unsigned char* stage = smem + st * kStage;
+        // A: the 16 channels of this pixel at the tap offset, split into three BF16 parts
+        {
+            const int yy = py + dy, xx = px + dx;
+            const bool in_img = live && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+            const int64_t q = (int64_t)yy * Wd + xx;
+            uint32_t w0[8], w1[8], w2[8];
+#pragma unroll
+            for (int c = 0; c < kK; c += 2) {
+                float v[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int ch = c0 + c + e;
+                    v[e] = (in_img && ch < Kc) ? __ldg(inb + (int64_t)ch * HW + q) : 0.f;
+                }
+                __nv_bfloat16 h[2], m[2], l[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    h[e] = __float2bfloat16_rn(v[e]);
+                    const float r1 = __fsub_rn(v[e], __bfloat162float(h[e]));
+                    m[e] = __float2bfloat16_rn(r1);
+                    l[e] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(m[e])));
+                }
+                w0[c / 2] = pack2(h[0], h[1]);
+                w1[c / 2] = pack2(m[0], m[1]);
+                w2[c / 2] = pack2(l[0], l[1]);
+            }
+#pragma unroll
+            for (int kq = 0; kq < 2; ++kq) {
+                const uint32_t off = kmaj(tid, kq);
+                *(uint4*)(stage + 0 * kABytes + off) = make_uint4(w0[4 * kq], w0[4 * kq + 1], w0[4 * kq + 2], w0[4 * kq + 3]);
+                *(uint4*)(stage + 1 * kABytes + off) = make_uint4(w1[4 * kq], w1[4 * kq + 1], w1[4 * kq + 2], w1[4 * kq + 3]);
+                *(uint4*)(stage + 2 * kABytes + off) = make_uint4(w2[4 * kq], w2[4 * kq + 1], w2[4 * kq + 2], w2[4 * kq + 3]);
+            }
+        }
+        // B: NP rows x 16 channels of weights for this tap (8 channels = 16 bytes per thread and pass)
+        for (int t = tid; t < NP * 2; t += kM) {
+            const int n = t >> 1, kq = t & 1;
+            uint32_t wv[4];
+#pragma unroll
+            for (int c = 0; c < 8; c += 2) {
+                __nv_bfloat16 e2[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int ch = c0 + kq * 8 + c + e;
+                    __nv_bfloat16 w = __float2bfloat16_rn(0.f);
+                    if (n < N && ch < Kc) {
+                        if (!TRANSPOSED) w = W[((int64_t)n * Kc + ch) * 9 + tap];
+                        else w = W[((int64_t)ch * N + n) * 9 + (8 - tap)];
+                    }
+                    e2[e] = w;
+                }
+                wv[c / 2] = pack2(e2[0], e2[1]);
+            }
+            *(uint4*)(stage + 3 * kABytes + kmaj(n, kq)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint64_t db = sdesc(smem_u32(stage + 3 * kABytes));
+#pragma unroll
+            for (int part = 0; part < 3; ++part) {
+                const uint64_t da = sdesc(smem_u32(stage + part * kABytes));
+                const uint32_t acc = (i > 0 || part > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                             ::"r"(tmem), "l"(da), "l"(db), "r"(idesc(NP)), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&bars[st])));
+        }
+    }
+    // the last commit covers every MMA this thread issued
+    if (ok && nchunks > 0) {   // both stages' last commits, so no arrive is pending at exit
+        const int last = nchunks - 1;
+        if (!wait_bar(smem_u32(&bars[last & 1]), (uint32_t)((last >> 1) & 1))) failed = 1;
+        if (last >= 1 && !wait_bar(smem_u32(&bars[(last - 1) & 1]), (uint32_t)(((last - 1) >> 1) & 1))) failed = 1;
+        __syncthreads();
+        ok = !failed;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        const int64_t obase = (int64_t)b * N * HW;
+#pragma unroll
+        for (int n0 = 0; n0 < NP; n0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (live) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + j;
+                    if (n < N) {
+                        float v = __uint_as_float(r[j]);
+                        if (bias) v += bias[n];
+                        if (relu) v = fmaxf(v, 0.f);
+                        float* dst = out + obase + (int64_t)n * HW + p;
+                        *dst = accumulate ? *dst + v : v;
+                    }
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+}
+
+// dynamic shared memory: two stages, padded so that no more CTAs than the tensor memory
+// holds (512 columns per SM) are resident at once
+template <int NP>
+size_t smem_bytes() {
+    constexpr size_t need = 2 * (3 * kM * kK * 2 + NP * kK * 2);
+    const size_t per_sm = 228 * 1024, ctas = 512 / tmem_cols(NP);
+    const size_t pad = per_sm / ctas + 1;
+    return need > pad ? need : pad;
+}
+
+template <int NP, bool TRANSPOSED>
+int launch_np(const float* in, int Kc, const __nv_bfloat16* W, const float* bias, float* out, int N, int B, int H,
+              int Wd, int relu, int accumulate, int* err, cudaStream_t s) {
+    const size_t smem = smem_bytes<NP>();
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(conv3x3_tc_kernel<NP, TRANSPOSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return -1;
+        attr = true;
+    }
+    const int64_t HW = (int64_t)H * Wd;
+    dim3 grid((unsigned)((HW + kM - 1) / kM), (unsigned)B);
+    conv3x3_tc_kernel<NP, TRANSPOSED><<<grid, kM, smem, s>>>(in, Kc, W, bias, out, N, H, Wd, relu, accumulate, err);
+    return 0;
+}
+
+// out (N channels) = conv3x3(in (Kc channels)); N up to 128
+template <bool TRANSPOSED>
+int conv3x3(const float* in, int Kc, const __nv_bfloat16* W, const float* bias, float* out, int N, int B, int H, int Wd,
+            int relu, int accumulate, int* err, cudaStream_t s) {
+    if (N <= 16) return launch_np<16, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
+    if (N <= 32) return launch_np<32, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
+    if (N <= 48) return launch_np<48, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
+    if (N <= 64) return launch_np<64, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
+    if (N <= 96) return launch_np<96, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
+    if (N <= 128) return launch_np<128, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
+    return -1;
+}
+
+}  // namespace tc
+
+// Weight gradient, tiled: dW[co][ci][k] = sum_{b,y,x} g[b,co,y,x] in[b,ci,y+ky-1,x+kx-1].
+// A CTA owns 16 output x 16 input channels (one thread per (co, ci) pair, 9 taps in
+// registers) and one chunk of rows of one image; bands of kWgRows rows of g and of the
+// input (with a zero halo) are staged in shared memory, the input rows padded so the 16
+// channels of a warp fall in distinct banks. Each CTA writes its 16 x 16 x 9 partial sums;
+// wgrad_reduce_kernel adds the partials of all chunks in chunk order (deterministic).
+constexpr int kWgRows = 2;
+
+struct WgradShape {
+    int rows_per_chunk, chunks_per_image;
+    int in_stride, g_stride;   // floats per staged input / gradient channel
+    size_t smem;
+};
+
+inline WgradShape wgrad_shape(int H, int Wd) {
+    WgradShape w;
+    int rows = (4096 + Wd - 1) / Wd;
+    rows = (rows + kWgRows - 1) / kWgRows * kWgRows;
+    w.rows_per_chunk = rows < H ? rows : H;
+    w.chunks_per_image = (H + w.rows_per_chunk - 1) / w.rows_per_chunk;
+    int st = (kWgRows + 2) * (Wd + 2);
+    st += ((1 - st) % 32 + 32) % 32;   // stride = 1 (mod 32): a warp's 16 input channels in 16 banks
+    w.in_stride = st;
+    w.g_stride = kWgRows * Wd + 1;     // odd: the warp's two output channels in different banks
+    w.smem = sizeof(float) * (16 * (size_t)st + 16 * (size_t)w.g_stride);
+    return w;
+}
+
+__global__ void __launch_bounds__(kT) conv3x3_wgrad_tiled_kernel(const float* __restrict__ in, int Cin,
+                                                                 const float* __restrict__ g, int Cout, int H, int Wd,
+                                                                 int rows_per_chunk, int chunks_per_image,
+                                                                 int in_stride, int g_stride,
+                                                                 float* __restrict__ partial) {
+    extern __shared__ float wsm_dyn[];
+    float* in_s = wsm_dyn;                          // [16][in_stride]
+    float* g_s = wsm_dyn + 16 * in_stride;          // [16][g_stride], kWgRows * Wd used
+    const int co0 = blockIdx.x * 16, ci0 = blockIdx.y * 16;
+    const int b = blockIdx.z / chunks_per_image, ch = blockIdx.z - b * chunks_per_image;
+    const int y0 = ch * rows_per_chunk, y1 = min(H, y0 + rows_per_chunk);
+    const int col = threadIdx.x / 16, cil = threadIdx.x % 16;
+    const int64_t plane = (int64_t)H * Wd;
+    const int W2 = Wd + 2;
+    float acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+    for (int yb = y0; yb < y1; yb += kWgRows) {
+        const int nr = min(kWgRows, y1 - yb);
+        // input rows yb-1 .. yb+kWgRows with a zero halo column on each side
+        for (int t = threadIdx.x; t < 16 * (kWgRows + 2) * W2; t += kT) {
+            const int c = t / ((kWgRows + 2) * W2), rem = t - c * (kWgRows + 2) * W2;
+            const int r = rem / W2, xx = rem - r * W2 - 1, yy = yb - 1 + r;
+            float v = 0.f;
+            if (ci0 + c < Cin && yy >= 0 && yy < H && yy <= yb + nr && xx >= 0 && xx < Wd)
+                v = in[((int64_t)b * Cin + ci0 + c) * plane + (int64_t)yy * Wd + xx];
+            in_s[c * in_stride + rem] = v;
+        }
+        for (int t = threadIdx.x; t < 16 * kWgRows * Wd; t += kT) {
+            const int c = t / (kWgRows * Wd), rem = t - c * kWgRows * Wd;
+            const int r = rem / Wd;
+            g_s[c * g_stride + rem] = (co0 + c < Cout && r < nr)
+                                          ? g[((int64_t)b * Cout + co0 + c) * plane + (int64_t)(yb + r) * Wd + (rem - r * Wd)]
+                                          : 0.f;
+        }
+        __syncthreads();
+        const float* gr = g_s + col * g_stride;
+        const float* ir = in_s + cil * in_stride;
+        for (int r = 0; r < nr; ++r)
+            for (int x = 0; x < Wd; ++x) {
+                const float gv = gr[r * Wd + x];
+                const float* base = ir + r * W2 + x;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) acc[k] = fmaf(gv, base[(k / 3) * W2 + k % 3], acc[k]);
+            }
+        __syncthreads();
+    }
+    const int co = co0 + col, ci = ci0 + cil;
+    if (co < Cout && ci < Cin) {
+        float* dst = partial + (((int64_t)blockIdx.z * Cout + co) * Cin + ci) * 9;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dst[k] = acc[k];
+    }
+}
+
+// dW[w] = sum_z partial[z][w], z in order
+__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int nz, int64_t nw, float* __restrict__ dW) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += stride) {
+        float t = 0.f;
+        for (int z = 0; z < nz; ++z) t += partial[(int64_t)z * nw + w];
+        dW[w] = t;
     }
 }
 
@@ -416,6 +774,9 @@ struct Net {
         *g_d2, *g_u1, *g_a6, *g_d1, *g_out, *g_in;
     float* partial = nullptr;
     float* loss = nullptr;
+    int tc = 1;            // BF16 mode: 3x3 convolutions on the tensor cores (tcgen05)
+    float* wpart = nullptr;   // weight-gradient partial sums (chunks x weights of a layer)
+    int* err = nullptr;    // set by a tensor-core kernel whose bounded wait ran out
 };
 
 float* alloc(Net& n, int64_t count) {
@@ -433,6 +794,9 @@ void conv(const Net& n, int layer, const float* in, float* out, int B, int H, in
     if (c.k == 1) {
         conv1x1_fwd_kernel<WT><<<blocks_for((int64_t)B * H * Wd), kT, 0, s>>>(in, c.cin, W, bias, out, B, (int64_t)H * Wd);
         return;
+    }
+    if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
+        if (n.tc && tc::conv3x3<false>(in, c.cin, W, bias, out, c.cout, B, H, Wd, c.relu, 0, n.err, s) == 0) return;
     }
     dim3 grid((Wd + 15) / 16, (H + 15) / 16, B * ((c.cout + 15) / 16));
     conv3x3_kernel<WT, false><<<grid, kT, 0, s>>>(in, c.cin, W, bias, out, c.cout, H, Wd, c.relu, 0);
@@ -453,9 +817,26 @@ void conv_back(const Net& n, int layer, const float* in, const float* g, float* 
         if (din) conv1x1_dgrad_kernel<WT><<<blocks_for(B * plane), kT, 0, s>>>(g, c.cin, W, din, B, plane);
         return;
     }
-    conv3x3_wgrad_kernel<<<dim3(c.cin, c.cout), kT, 0, s>>>(in, c.cin, g, c.cout, B, H, Wd, dW);
+    {
+        const WgradShape ws = wgrad_shape(H, Wd);
+        const int nz = B * ws.chunks_per_image;
+        dim3 grid((c.cout + 15) / 16, (c.cin + 15) / 16, nz);
+        static size_t smem_set = 48 * 1024;
+        if (ws.smem > smem_set) {
+            if (cudaFuncSetAttribute(conv3x3_wgrad_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ws.smem) == cudaSuccess)
+                smem_set = ws.smem;
+        }
+        conv3x3_wgrad_tiled_kernel<<<grid, kT, ws.smem, s>>>(in, c.cin, g, c.cout, H, Wd, ws.rows_per_chunk,
+                                                             ws.chunks_per_image, ws.in_stride, ws.g_stride, n.wpart);
+        const int64_t nw = (int64_t)c.cout * c.cin * 9;
+        wgrad_reduce_kernel<<<blocks_for(nw), kT, 0, s>>>(n.wpart, nz, nw, dW);
+    }
     bias_grad_kernel<<<c.cout, kT, 0, s>>>(g, c.cout, B, plane, db);
     if (din) {
+        if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
+            if (n.tc && tc::conv3x3<true>(g, c.cout, W, nullptr, din, c.cin, B, H, Wd, 0, 0, n.err, s) == 0) return;
+        }
         dim3 grid((Wd + 15) / 16, (H + 15) / 16, B * ((c.cin + 15) / 16));
         conv3x3_kernel<WT, true><<<grid, kT, 0, s>>>(g, c.cout, W, nullptr, din, c.cin, H, Wd, 0, 0);
     }
@@ -623,6 +1004,8 @@ int x0net_create(x0net* out, int H, int W, int batch_max, int bf16_weights, int 
     n.m = A(o);
     n.v = A(o);
     if (cudaMalloc((void**)&n.wb, sizeof(__nv_bfloat16) * o) != cudaSuccess) ok = false;
+    if (cudaMalloc((void**)&n.err, sizeof(int)) != cudaSuccess) ok = false;
+    else cudaMemset(n.err, 0, sizeof(int));
     n.a1 = A(B * 16 * P1); n.e1 = A(B * 16 * P1); n.p1 = A(B * 16 * P2);
     n.a2 = A(B * 32 * P2); n.e2 = A(B * 32 * P2); n.p2 = A(B * 32 * P4);
     n.a3 = A(B * 64 * P4); n.e3 = A(B * 64 * P4); n.p3 = A(B * 64 * P8);
@@ -638,6 +1021,17 @@ int x0net_create(x0net* out, int H, int W, int batch_max, int bf16_weights, int 
     n.g_u2 = A(B * 96 * P2); n.g_a5 = A(B * 32 * P2); n.g_d2 = A(B * 32 * P2);
     n.g_u1 = A(B * 48 * P1); n.g_a6 = A(B * 16 * P1); n.g_d1 = A(B * 16 * P1); n.g_out = A(B * P1);
     n.partial = A(256);
+    {   // the largest (chunks x weights) over the 3x3 layers at their levels
+        int64_t need = 1;
+        const int lvl[kNumLayers] = {1, 1, 2, 2, 4, 4, 8, 8, 4, 4, 2, 2, 1, 1, 1};
+        for (int l = 0; l < kNumLayers; ++l) {
+            if (kLayers[l].k != 3) continue;
+            const WgradShape ws = wgrad_shape(H / lvl[l], W / lvl[l]);
+            const int64_t v = B * ws.chunks_per_image * (int64_t)kLayers[l].cout * kLayers[l].cin * 9;
+            need = v > need ? v : need;
+        }
+        n.wpart = A(need);
+    }
     n.loss = A(2);
     n.r = A(B * P1);
     n.out_raw = A(B * P1);
@@ -663,6 +1057,7 @@ int x0net_destroy(x0net X) {
     if (!X) return SSTEP_ERR_ARG;
     for (float* p : X->n.bufs) cudaFree(p);
     if (X->n.wb) cudaFree(X->n.wb);
+    if (X->n.err) cudaFree(X->n.err);
     delete X;
     return SSTEP_OK;
 }
@@ -727,7 +1122,24 @@ int x0net_gradient(x0net X, const float* input, const float* target, int batch, 
     if (grads && cudaMemcpyAsync(grads, n.g, sizeof(float) * n.nparams, cudaMemcpyDefault, s) != cudaSuccess)
         return SSTEP_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SSTEP_ERR_CUDA;
+    int e = 0;
+    if (cudaMemcpy(&e, n.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SSTEP_ERR_CUDA;
+    return e ? SSTEP_ERR_TIMEOUT : SSTEP_OK;
+}
+
+int x0net_set_tensor_cores(x0net X, int on) {
+    if (!X) return SSTEP_ERR_ARG;
+    X->n.tc = on ? 1 : 0;
     return SSTEP_OK;
+}
+
+int x0net_status(x0net X, void* stream) {
+    if (!X) return SSTEP_ERR_ARG;
+    int e = 0;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
+        cudaMemcpy(&e, X->n.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SSTEP_ERR_CUDA;
+    return e ? SSTEP_ERR_TIMEOUT : SSTEP_OK;
 }
 
 int x0net_train_step(x0net X, const float* input, const float* target, int batch, float lr, float* loss_dev,

@@ -118,6 +118,7 @@ def train(net, feats, targets, epochs, batch=32, lr=1e-3, seed=0, log=None):
             if (b0 // batch) % 16 == 0:
                 tot += float(lossd.item())
                 nb += 1
+        net.status()   # raises if a tensor-core kernel's bounded wait ran out
         history.append(tot / max(nb, 1))
         if log:
             log(f"epoch {ep}: loss {history[-1]:.4e}")

@@ -80,3 +80,30 @@ def test_training_reduces_loss():
     torch.cuda.synchronize()
     loss1, _ = net.gradient(xd, td)
     assert loss1 < 0.5 * loss0
+
+
+@pytest.mark.parametrize("B,H,smooth,res_w", [(2, 16, 0, 0.0), (3, 40, 3, 1.0), (2, 128, 2, 0.0)])
+def test_tensor_core_convolutions_match_cuda_cores(B, H, smooth, res_w):
+    """BF16 mode: the tcgen05 convolutions (FP32 activations split into three BF16 parts)
+    give the CUDA-core result up to the FP32 accumulation inside the tensor core and the
+    order of the sums (observed 2e-5 relative on the output at 128^2 over 15 layers):
+    forward output, loss and every layer's gradient. H = 40 leaves a ragged pixel tile at
+    every level; at H = 16 the coarsest level has 4 pixels of a 128-pixel tile."""
+    net, theta, x, t, xd, td = setup(B, H, 11, True, smooth, res_w)
+    outs, grads, losses = [], [], []
+    for tc in (False, True):
+        net.set_tensor_cores(tc)
+        out = torch.empty((B, 1, H, H), dtype=torch.float32, device=xd.device)
+        net.forward(xd, out)
+        loss, g = net.gradient(xd, td)
+        net.status()
+        outs.append(out.cpu().numpy().astype(np.float64))
+        grads.append(g.astype(np.float64))
+        losses.append(loss)
+    rel = np.linalg.norm(outs[1] - outs[0]) / np.linalg.norm(outs[0])
+    print("output rel diff", rel)
+    assert rel <= 1e-4
+    assert abs(losses[1] - losses[0]) <= 1e-4 * abs(losses[0])
+    for sl in layer_slices():
+        a, b = grads[1][sl], grads[0][sl]
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b) + 1e-12
