@@ -386,9 +386,14 @@ struct WgradShape {
     size_t smem;
 };
 
-inline WgradShape wgrad_shape(int H, int Wd) {
+// other_ctas: the CTAs of the grid's channel dimensions times the batch; the row chunks
+// are chosen so the grid has about 600 CTAs (a wave at 4 CTAs per SM)
+inline WgradShape wgrad_shape(int H, int Wd, int other_ctas) {
     WgradShape w;
-    int rows = (4096 + Wd - 1) / Wd;
+    const int max_chunks = (H + kWgRows - 1) / kWgRows;
+    int chunks = (600 + other_ctas - 1) / (other_ctas > 0 ? other_ctas : 1);
+    chunks = chunks < 1 ? 1 : (chunks > max_chunks ? max_chunks : chunks);
+    int rows = (H + chunks - 1) / chunks;
     rows = (rows + kWgRows - 1) / kWgRows * kWgRows;
     w.rows_per_chunk = rows < H ? rows : H;
     w.chunks_per_image = (H + w.rows_per_chunk - 1) / w.rows_per_chunk;
@@ -505,22 +510,34 @@ __global__ void __launch_bounds__(kT) conv3x3_wgrad_kernel(const float* __restri
 }
 
 // db[c] = sum_{b,y,x} g[b,c,y,x]   (one CTA per channel)
-__global__ void __launch_bounds__(kT) bias_grad_kernel(const float* __restrict__ g, int C, int B, int64_t plane,
-                                                       float* __restrict__ db) {
-    const int c = blockIdx.x;
+// Channel sums over pixels in chunks: CTA (c, z) sums chunk z (kRedChunk pixels of one
+// image) of channel c into partial[z][c]; wgrad_reduce_kernel adds the chunks in order.
+// Bias gradient: v = g[b][c][p]. 1x1 weight gradient (one output channel): v =
+// g[b][0][p] in[b][c][p].
+constexpr int kRedChunk = 4096;
+
+__global__ void __launch_bounds__(kT) chan_sum_partial_kernel(const float* __restrict__ g, const float* __restrict__ in,
+                                                              int C, int64_t plane, int chunks,
+                                                              float* __restrict__ partial) {
+    const int c = blockIdx.x, z = blockIdx.y, b = z / chunks, piece = z - b * chunks;
+    const int64_t p0 = (int64_t)piece * kRedChunk, p1 = min(plane, p0 + kRedChunk);
     float t = 0.f;
-    for (int64_t p = threadIdx.x; p < (int64_t)B * plane; p += kT) {
-        const int b = (int)(p / plane);
-        t += g[((int64_t)b * C + c) * plane + (p - (int64_t)b * plane)];
+    if (in) {
+        const float* gp = g + (int64_t)b * plane;
+        const float* ip = in + ((int64_t)b * C + c) * plane;
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += kT) t = fmaf(gp[p], ip[p], t);
+    } else {
+        const float* gp = g + ((int64_t)b * C + c) * plane;
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += kT) t += gp[p];
     }
     __shared__ float red[kT / 32];
     for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
     __syncthreads();
     if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int w = 0; w < kT / 32; ++w) s += red[w];
-        db[c] = s;
+        float sum = 0.f;
+        for (int w = 0; w < kT / 32; ++w) sum += red[w];
+        partial[(int64_t)z * C + c] = sum;
     }
 }
 
@@ -549,24 +566,6 @@ __global__ void conv1x1_dgrad_kernel(const float* __restrict__ g, int C, const W
 }
 
 // dW[c] = sum g * in[c]   (one CTA per c)
-__global__ void conv1x1_wgrad_kernel(const float* __restrict__ g, const float* __restrict__ in, int C, int B,
-                                     int64_t plane, float* __restrict__ dW) {
-    const int c = blockIdx.x;
-    float t = 0.f;
-    for (int64_t p = threadIdx.x; p < (int64_t)B * plane; p += kT) {
-        const int b = (int)(p / plane);
-        t = fmaf(g[p], in[((int64_t)b * C + c) * plane + (p - (int64_t)b * plane)], t);
-    }
-    __shared__ float red[kT / 32];
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int w = 0; w < kT / 32; ++w) s += red[w];
-        dW[c] = s;
-    }
-}
 
 // g *= (y > 0): the ReLU of the layer that produced y
 __global__ void relu_mask_kernel(float* __restrict__ g, const float* __restrict__ y, int64_t n) {
@@ -812,15 +811,19 @@ void conv_back(const Net& n, int layer, const float* in, const float* g, float* 
     float* db = dW + (int64_t)c.cout * c.cin * c.k * c.k;
     const int64_t plane = (int64_t)H * Wd;
     if (c.k == 1) {
-        conv1x1_wgrad_kernel<<<c.cin, kT, 0, s>>>(g, in, c.cin, B, plane, dW);
-        bias_grad_kernel<<<1, kT, 0, s>>>(g, 1, B, plane, db);
+        const int chunks = (int)((plane + kRedChunk - 1) / kRedChunk), nz = B * chunks;
+        chan_sum_partial_kernel<<<dim3(c.cin, nz), kT, 0, s>>>(g, in, c.cin, plane, chunks, n.wpart);
+        wgrad_reduce_kernel<<<blocks_for(c.cin), kT, 0, s>>>(n.wpart, nz, c.cin, dW);
+        chan_sum_partial_kernel<<<dim3(1, nz), kT, 0, s>>>(g, nullptr, 1, plane, chunks, n.wpart);
+        wgrad_reduce_kernel<<<1, kT, 0, s>>>(n.wpart, nz, 1, db);
         if (din) conv1x1_dgrad_kernel<WT><<<blocks_for(B * plane), kT, 0, s>>>(g, c.cin, W, din, B, plane);
         return;
     }
     {
-        const WgradShape ws = wgrad_shape(H, Wd);
+        const int cog = (c.cout + 15) / 16, cig = (c.cin + 15) / 16;
+        const WgradShape ws = wgrad_shape(H, Wd, cog * cig * B);
         const int nz = B * ws.chunks_per_image;
-        dim3 grid((c.cout + 15) / 16, (c.cin + 15) / 16, nz);
+        dim3 grid(cog, cig, nz);
         static size_t smem_set = 48 * 1024;
         if (ws.smem > smem_set) {
             if (cudaFuncSetAttribute(conv3x3_wgrad_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -832,7 +835,11 @@ void conv_back(const Net& n, int layer, const float* in, const float* g, float* 
         const int64_t nw = (int64_t)c.cout * c.cin * 9;
         wgrad_reduce_kernel<<<blocks_for(nw), kT, 0, s>>>(n.wpart, nz, nw, dW);
     }
-    bias_grad_kernel<<<c.cout, kT, 0, s>>>(g, c.cout, B, plane, db);
+    {
+        const int chunks = (int)((plane + kRedChunk - 1) / kRedChunk), nz = B * chunks;
+        chan_sum_partial_kernel<<<dim3(c.cout, nz), kT, 0, s>>>(g, nullptr, c.cout, plane, chunks, n.wpart);
+        wgrad_reduce_kernel<<<blocks_for(c.cout), kT, 0, s>>>(n.wpart, nz, c.cout, db);
+    }
     if (din) {
         if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
             if (n.tc && tc::conv3x3<true>(g, c.cout, W, nullptr, din, c.cin, B, H, Wd, 0, 0, n.err, s) == 0) return;
@@ -1025,10 +1032,18 @@ int x0net_create(x0net* out, int H, int W, int batch_max, int bf16_weights, int 
         int64_t need = 1;
         const int lvl[kNumLayers] = {1, 1, 2, 2, 4, 4, 8, 8, 4, 4, 2, 2, 1, 1, 1};
         for (int l = 0; l < kNumLayers; ++l) {
-            if (kLayers[l].k != 3) continue;
-            const WgradShape ws = wgrad_shape(H / lvl[l], W / lvl[l]);
-            const int64_t v = B * ws.chunks_per_image * (int64_t)kLayers[l].cout * kLayers[l].cin * 9;
-            need = v > need ? v : need;
+            const int cog = (kLayers[l].cout + 15) / 16, cig = (kLayers[l].cin + 15) / 16;
+            for (int bb = 1; bb <= B; ++bb) {   // the chunking depends on the batch of the call
+                if (kLayers[l].k == 3) {
+                    const WgradShape ws = wgrad_shape(H / lvl[l], W / lvl[l], cog * cig * bb);
+                    const int64_t v = bb * ws.chunks_per_image * (int64_t)kLayers[l].cout * kLayers[l].cin * 9;
+                    need = v > need ? v : need;
+                }
+                // channel sums (bias and 1x1 gradients): chunks of kRedChunk pixels
+                const int64_t px = (int64_t)(H / lvl[l]) * (W / lvl[l]);
+                const int64_t v2 = bb * ((px + kRedChunk - 1) / kRedChunk) * (int64_t)(kLayers[l].cin + kLayers[l].cout);
+                need = v2 > need ? v2 : need;
+            }
         }
         n.wpart = A(need);
     }
