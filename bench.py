@@ -98,7 +98,7 @@ def parse():
     ap.add_argument("--learned", action="store_true", help="add 'learned' to --variants")
     ap.add_argument("--learned-train", type=int, default=20000)
     ap.add_argument("--learned-test", type=int, default=1000)
-    ap.add_argument("--learned-epochs", type=int, default=8)
+    ap.add_argument("--learned-epochs", type=int, default=24)
     ap.add_argument("--no-cpu", action="store_true")
     a = ap.parse_args()
     a.groups = set() if a.no_variants else {g.strip() for g in a.variants.split(",") if g.strip()}
