@@ -87,6 +87,11 @@ int stencil_matrix_apply(sstep_matrix A, const double* x, double* y, void* strea
  * 0 < omega < 2, else SSTEP_ERR_ARG. Stream-ordered, no synchronisation. */
 int stencil_matrix_smooth(sstep_matrix A, const double* f, double* x, double* work, int sweeps, double omega,
                           void* stream);
+/* The same for nsys (1..65535) systems in one launch per sweep: A, f, x, work are HOST
+ * arrays of nsys handles / DEVICE pointers with the per-system conventions above.
+ * Synchronises `stream` once (the descriptors are copied from the host). */
+int stencil_matrix_smooth_batched(int nsys, const sstep_matrix* A, const double* const* f, double* const* x,
+                                  double* const* work, int sweeps, double omega, void* stream);
 
 /* ------------------------------------------------------------------ s-step block primitives
  * The three data-parallel steps of one s-step (Sec. 1, Alg. 3.1, Alg. 4.1),
@@ -284,6 +289,10 @@ int x0net_train_step(x0net X, const float* input, const float* target, int batch
  * kind (each pair costs about a microsecond of stream time). Process-global and
  * not thread-safe: meant for benchmarks and profiling. enable() resets the totals. */
 int sstep_trace_enable(int on);
+/* Only the kinds whose bit is set in kind_mask (bit k = kind k) get event pairs; the
+ * others are still counted. Default: every kind. Lets a benchmark time one kernel kind
+ * inside its timed region without bracketing every launch. */
+int sstep_trace_select(unsigned kind_mask);
 int sstep_trace_kinds(void);                       /* number of kernel kinds */
 const char* sstep_trace_kind_name(int kind);       /* e.g. "gram", "block_update" */
 int sstep_trace_read(int kind, double* total_ms, int64_t* launches);  /* host outputs */

@@ -28,8 +28,10 @@ from ._binding import (  # noqa: F401
     sstep_omin_solve,
     stencil_matrix_apply,
     stencil_matrix_smooth,
+    stencil_matrix_smooth_batched,
     trace_enable,
     trace_read,
+    trace_select,
 )
 
 __all__ = [
@@ -38,6 +40,7 @@ __all__ = [
     "StencilMatrix",
     "stencil_matrix_apply",
     "stencil_matrix_smooth",
+    "stencil_matrix_smooth_batched",
     "sstep_matrix_powers",
     "sstep_gram",
     "sstep_gram_workspace_size",
@@ -48,5 +51,6 @@ __all__ = [
     "SStepError",
     "trace_enable",
     "trace_read",
+    "trace_select",
     "lib",
 ]

@@ -42,6 +42,8 @@ SIGNATURES = {
     "stencil_matrix_info": (c_int, [c_void_p, P(c_int64), P(c_double)]),
     "stencil_matrix_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "stencil_matrix_smooth": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_void_p]),
+    "stencil_matrix_smooth_batched": (c_int, [c_int, P(c_void_p), P(c_void_p), P(c_void_p), P(c_void_p), c_int,
+                                              c_double, c_void_p]),
     "sstep_matrix_powers": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_void_p, c_int64, c_void_p]),
     "sstep_gram_workspace_size": (c_int, [c_int64, c_int, c_int, P(c_size_t)]),
     "sstep_gram": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
@@ -71,6 +73,7 @@ SIGNATURES = {
     "x0net_set_tensor_cores": (c_int, [c_void_p, c_int]),
     "x0net_status": (c_int, [c_void_p, c_void_p]),
     "x0net_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p, c_void_p]),
+    "sstep_trace_select": (c_int, [ctypes.c_uint]),
     "sstep_trace_enable": (c_int, [c_int]),
     "sstep_trace_kinds": (c_int, []),
     "sstep_trace_kind_name": (ctypes.c_char_p, [c_int]),
@@ -194,6 +197,16 @@ def stencil_matrix_apply(A, x, y, stream=None):
     return _check("stencil_matrix_apply", lib().stencil_matrix_apply(A.handle, _ptr(x), _ptr(y), _stream(stream)))
 
 
+def stencil_matrix_smooth_batched(mats, fs, xs, works, sweeps, omega, stream=None):
+    """`sweeps` damped Jacobi sweeps on every x in place, all systems per launch."""
+    n = len(mats)
+    arr = lambda ts: (c_void_p * n)(*[_ptr(t).value for t in ts])
+    hs = (c_void_p * n)(*[A.handle for A in mats])
+    return _check("stencil_matrix_smooth_batched",
+                  lib().stencil_matrix_smooth_batched(n, hs, arr(fs), arr(xs), arr(works), int(sweeps), float(omega),
+                                                      _stream(stream)))
+
+
 def stencil_matrix_smooth(A, f, x, work, sweeps, omega, stream=None):
     """`sweeps` damped Jacobi sweeps on x in place (work: scratch of n doubles)."""
     return _check("stencil_matrix_smooth", lib().stencil_matrix_smooth(A.handle, _ptr(f), _ptr(x), _ptr(work),
@@ -307,6 +320,19 @@ def sstep_omin_solve(A, f, x, s, k, tol, max_iters=100000, sigma=0.0, history_ca
 def trace_enable(on=True):
     """Turn per-launch CUDA-event tracing on or off (resets the totals)."""
     _check("sstep_trace_enable", lib().sstep_trace_enable(1 if on else 0))
+
+
+def trace_select(kinds=None):
+    """Bracket only the named kernel kinds with events (None: every kind)."""
+    L = lib()
+    if kinds is None:
+        mask = 0xFFFFFFFF
+    else:
+        names = [L.sstep_trace_kind_name(k).decode() for k in range(L.sstep_trace_kinds())]
+        mask = 0
+        for nm in kinds:
+            mask |= 1 << names.index(nm)
+    _check("sstep_trace_select", L.sstep_trace_select(mask))
 
 
 def trace_read():

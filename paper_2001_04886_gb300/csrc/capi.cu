@@ -15,6 +15,7 @@
 #include <chrono>
 
 #include "kernels.cuh"
+#include "smooth.cuh"
 
 using namespace sstep;
 
@@ -64,6 +65,7 @@ const char* const kKindNames[K_COUNT] = {"stencil_powers", "residual", "gram", "
                                          "basis_axpy", "omin_xr", "omin_pupdate", "lsq_solve"};
 struct Tracer {
     bool on = false;
+    unsigned mask = ~0u;          // kinds that get event pairs
     std::vector<cudaEvent_t> events;
     std::vector<int> kinds;       // kind of each recorded pair
     size_t used = 0;              // events in use (pairs * 2)
@@ -74,7 +76,7 @@ Tracer g_trace;
 
 int trace_begin(int kind, cudaStream_t s) {
     g_trace.launches[kind] += 1;
-    if (!g_trace.on) return -1;
+    if (!g_trace.on || !((g_trace.mask >> kind) & 1u)) return -1;
     if (g_trace.used + 2 > g_trace.events.size()) {
         for (int i = 0; i < 256; ++i) {
             cudaEvent_t e;
@@ -539,6 +541,11 @@ int sstep_trace_enable(int on) {
     return SSTEP_OK;
 }
 
+int sstep_trace_select(unsigned kind_mask) {
+    g_trace.mask = kind_mask;
+    return SSTEP_OK;
+}
+
 int sstep_trace_kinds(void) { return K_COUNT; }
 
 const char* sstep_trace_kind_name(int kind) { return (kind >= 0 && kind < K_COUNT) ? kKindNames[kind] : ""; }
@@ -727,6 +734,35 @@ int stencil_matrix_smooth(sstep_matrix M, const double* f, double* x, double* wo
                         cudaSuccess)
         return SSTEP_ERR_CUDA;
     return check_launch();
+}
+
+int stencil_matrix_smooth_batched(int nsys, const sstep_matrix* A, const double* const* f, double* const* x,
+                                  double* const* work, int sweeps, double omega, void* stream) {
+    if (nsys < 1 || nsys > 65535 || !A || !f || !x || !work || sweeps < 0 || !(omega > 0.0 && omega < 2.0))
+        return SSTEP_ERR_ARG;
+    std::vector<SmoothSys> h(nsys);
+    int64_t nmax = 1;
+    for (int i = 0; i < nsys; ++i) {
+        if (!A[i] || !f[i] || !x[i] || !work[i] || work[i] == x[i] || work[i] == f[i]) return SSTEP_ERR_ARG;
+        h[i].A = A[i]->A;
+        h[i].f = f[i];
+        h[i].x = x[i];
+        h[i].work = work[i];
+        nmax = std::max<int64_t>(nmax, A[i]->A.n);
+    }
+    if (sweeps == 0) return SSTEP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    SmoothSys* d = nullptr;
+    if (cudaMallocAsync((void**)&d, sizeof(SmoothSys) * nsys, st) != cudaSuccess) return SSTEP_ERR_OOM;
+    int rc = SSTEP_OK;
+    if (cudaMemcpyAsync(d, h.data(), sizeof(SmoothSys) * nsys, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        launch_jacobi_batched(d, nsys, nmax, sweeps, omega, st) != 0)
+        rc = SSTEP_ERR_CUDA;
+    // the host array must outlive the copy: wait for it before h goes out of scope
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = SSTEP_ERR_CUDA;
+    cudaFreeAsync(d, st);
+    if (rc == SSTEP_OK) rc = check_launch();
+    return rc;
 }
 
 int sstep_matrix_powers(sstep_matrix M, const double* v, double scale, double sigma, int s, double* Y, int64_t ldy,

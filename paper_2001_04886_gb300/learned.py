@@ -25,7 +25,7 @@ import time
 import numpy as np
 
 from . import inputs
-from ._binding import BatchSolver, StencilMatrix, X0Net
+from ._binding import BatchSolver, StencilMatrix, X0Net, stencil_matrix_smooth_batched
 
 BETA_SCALE = 20.0
 SWEEPS = 32          # damped Jacobi sweeps on the predicted x0
@@ -141,16 +141,14 @@ def predict(net, feats, scales, batch=32):
 
 
 def post_smooth(mats, fs, xs, sweeps, omega=OMEGA):
-    """`sweeps` damped Jacobi sweeps on every x in place (the library's kernel)."""
+    """`sweeps` damped Jacobi sweeps on every x in place (the library's batched kernel:
+    one launch per sweep for all systems)."""
     import torch
 
     if sweeps <= 0:
         return xs
-    work = torch.empty_like(xs[0])
-    for A, f, x in zip(mats, fs, xs):
-        if work.numel() != x.numel():
-            work = torch.empty_like(x)
-        A.smooth(f, x, work, sweeps, omega)
+    works = [torch.empty_like(x) for x in xs]
+    stencil_matrix_smooth_batched(mats, fs, xs, works, sweeps, omega)
     return xs
 
 
