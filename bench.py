@@ -304,7 +304,8 @@ def main():
         prec = kw.get("precision", "fp64")
         if method == "sstep":
             return pkg.sstep_gmres_solve(A, f, xv, kw.get("s", s), M, TOL, max_cycles=200, history_cap=8192,
-                                         precision=kw.get("precision", args.precision))
+                                         precision=kw.get("precision", args.precision),
+                                         basis=kw.get("basis", "monomial"))
         if method == "gmres":
             return pkg.gmres_solve(A, f, xv, M, TOL, max_cycles=200, history_cap=8192, precision=prec)
         return pkg.sstep_omin_solve(A, f, xv, kw["s"], kw["k"], TOL, max_iters=20000, history_cap=8192)
@@ -388,13 +389,17 @@ def main():
     variants = {}
     if "solvers" in args.groups:
         for name, kw in [("sstep_gmres_s2", dict(method="sstep", s=2)), ("sstep_gmres_s4", dict(method="sstep", s=4)),
-                         ("sstep_gmres_s8", dict(method="sstep", s=8)), ("gmres", dict(method="gmres")),
+                         ("sstep_gmres_s8", dict(method="sstep", s=8)),
+                         ("sstep_gmres_s8_newton", dict(method="sstep", s=8, basis="newton")),
+                         ("gmres", dict(method="gmres")),
                          ("sstep_omin_s4_k1", dict(method="omin", s=4, k=1)),
                          ("omin_k1", dict(method="omin", s=1, k=1)), ("omin_k7", dict(method="omin", s=1, k=7)),
                          ("df64_sstep_gmres_s4", dict(method="sstep", s=4, precision="df64")),
                          ("df64_sstep_gmres_s8", dict(method="sstep", s=8, precision="df64")),
                          ("df64_gmres", dict(method="gmres", precision="df64")),
-                         ("fp32ir_sstep_gmres_s8", dict(method="sstep", s=8, precision="fp32"))]:
+                         ("fp32ir_sstep_gmres_s8", dict(method="sstep", s=8, precision="fp32")),
+                         ("fp32ir_sstep_gmres_s8_newton", dict(method="sstep", s=8, precision="fp32",
+                                                               basis="newton"))]:
             x.zero_()
             solve(x, **kw)                                  # warm the workspace
             torch.cuda.synchronize()

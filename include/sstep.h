@@ -76,6 +76,17 @@ int stencil_matrix_destroy(sstep_matrix A);
 /* n (number of unknowns) and ||A||_inf (max absolute row sum). Host outputs. */
 int stencil_matrix_info(sstep_matrix A, int64_t* n, double* norm_inf);
 
+/* The Newton-basis shifts theta_1..theta_s of the last s-step GMRES solve on A with
+ * basis = SSTEP_BASIS_NEWTON (HOST output, up to cap values). Returns their number (0
+ * when the last solve kept the monomial powers), or SSTEP_ERR_ARG. */
+int sstep_last_shifts(sstep_matrix A, double* theta, int cap);
+
+/* The shift computation on its own (host only, no GPU): theta[0..s) = the Leja-ordered
+ * real parts of the eigenvalues of the K x K upper Hessenberg matrix G (HOST,
+ * column-major, leading dimension ldg >= K), as the Newton basis uses them. Returns
+ * SSTEP_ERR_BREAKDOWN if the QR iteration does not settle. */
+int sstep_newton_shifts(const double* G, int ldg, int K, int s, double* theta);
+
 /* y = A x (Sec. 1: one sweep over the grid). x and y must not overlap. */
 int stencil_matrix_apply(sstep_matrix A, const double* x, double* y, void* stream);
 
@@ -164,7 +175,17 @@ typedef struct {
                            refinement. f, x, residuals and all scalar work are FP64 in every mode. */
     int x0_guard;       /* 1: if ||f - A x0|| > ||f|| on entry, start from x0 = 0 instead (for
                            predicted initial guesses); 0: use x0 as given */
+    int basis;          /* s-step GMRES (multi-kernel solver, every precision):
+                           SSTEP_BASIS_MONOMIAL: y^{j+1} = sigma A y^j (Alg. 4.1 as printed);
+                           SSTEP_BASIS_NEWTON: the first cycle is monomial; every later cycle uses
+                           y^{j+1} = sigma (A - theta_j I) y^j with theta_1..theta_s the real parts
+                           of the first cycle's Ritz values (eigenvalues of its Hessenberg G) in
+                           Leja order. Same Krylov spaces, better-conditioned Gram blocks (Sec. 3
+                           names such bases for large s). The batched solver is monomial only. */
 } sstep_params;
+
+#define SSTEP_BASIS_MONOMIAL 0
+#define SSTEP_BASIS_NEWTON 1
 
 #define SSTEP_PREC_FP64 0
 #define SSTEP_PREC_DF64 1

@@ -70,17 +70,60 @@ def cholesky_solve(L, B):
 
 
 # ---------------------------------------------------------------- block primitives
-def matrix_powers(A, v, s, sigma, scale=1.0):
+def matrix_powers(A, v, s, sigma, scale=1.0, shifts=None):
     """Y = [y^1, ..., y^{s+1}], y^1 = scale v, y^{j+1} = sigma A y^j (s products).
 
     The directions R_i = [r, Ar, ..., A^{s-1} r] of Sec. 3 and the raw block of
-    Algorithm 4.1 step 3 are both such power blocks.
+    Algorithm 4.1 step 3 are both such power blocks. With `shifts` (theta_1..theta_s)
+    the block is the Newton basis y^{j+1} = sigma (A - theta_j I) y^j, which spans the
+    same Krylov space (Sec. 3 points to better-conditioned bases for large s).
     """
     Y = np.zeros((v.shape[0], s + 1))
     Y[:, 0] = scale * v
     for j in range(s):
         Y[:, j + 1] = sigma * A.apply(Y[:, j])
+        if shifts is not None:
+            Y[:, j + 1] -= sigma * shifts[j] * Y[:, j]
     return Y
+
+
+def leja_order(values, count):
+    """The first `count` points of the Leja ordering of real `values`: the largest in
+    modulus first, then each next point maximises the product of its distances to the
+    points already taken (sums of logarithms; ties go to the earlier value). Points within
+    1e-10 max|value| of a taken one (the two real parts of a complex pair) are skipped;
+    when the distinct values run out, the sequence repeats from its start."""
+    vals = [float(v) for v in values]
+    if not vals:
+        return [0.0] * count
+    tiny = 1e-10 * max(abs(v) for v in vals)
+    first = max(range(len(vals)), key=lambda i: (abs(vals[i]), -i))
+    order = [first]
+    while len(order) < len(vals):
+        best, best_score = None, None
+        for i, v in enumerate(vals):
+            if i in order:
+                continue
+            d = [abs(v - vals[j]) for j in order]
+            if min(d) <= tiny:
+                continue
+            score = sum(np.log(x) for x in d)
+            if best_score is None or score > best_score:
+                best, best_score = i, score
+        if best is None:
+            break
+        order.append(best)
+    seq = [vals[i] for i in order]
+    return [seq[j % len(seq)] for j in range(count)]
+
+
+def newton_shifts(G, K, s):
+    """Shifts for the Newton basis: the real parts of the Ritz values of A on the first
+    cycle's Krylov space, i.e. the eigenvalues of the leading K x K block of G (the basis
+    U is orthogonal between blocks and its next start vector is orthogonal to V, so this
+    is the Galerkin projection), sorted ascending, then in Leja order."""
+    ev = np.linalg.eigvals(G[:K, :K])
+    return leja_order(np.sort(np.real(ev)), s)
 
 
 def inner_products(V, Y):
@@ -95,13 +138,18 @@ def block_update(Y, V, T):
 
 
 # ---------------------------------------------------------------- s-step GMRES
-def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None):
+def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None, basis="monomial", shifts=None,
+                shift_rule=None):
     """Restarted s-step GMRES, Algorithm 4.2 over the s-step Arnoldi of Algorithm 4.1.
 
-    Returns dict(x, status, cycles, iters, matvecs, history, relres); the
+    Returns dict(x, status, cycles, iters, matvecs, history, relres, shifts); the
     history holds the explicit relres at each restart and the least-squares
     estimate after each of the s steps of every block. If `trace` is a dict,
     the first cycle's basis U, Hessenberg G and Gram blocks W are stored in it.
+    basis = "newton": the first cycle uses the monomial powers; every later cycle the
+    Newton basis with the Leja-ordered real parts of the first cycle's Ritz values.
+    `shifts` (test use): Newton shifts to apply from the first cycle on. `shift_rule`
+    (test use): replaces newton_shifts(G, K, s) after the first cycle.
     """
     assert m % s == 0 and s >= 1
     n = f.shape[0]
@@ -111,6 +159,7 @@ def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None):
     hist = []
     cycles = iters = mv = 0
     status = STATUS_NOT_CONVERGED
+    shifts = None if shifts is None else list(shifts)
     while True:
         r = f - A.apply(x)                                   # step 1 / step 5 (restart)
         mv += 1
@@ -131,7 +180,7 @@ def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None):
         K = 0
         for k in range(nb):                                  # Algorithm 4.1, block k+1
             o = k * s
-            Y = matrix_powers(A, U[:, o], s, sigma)         # step 3: s products
+            Y = matrix_powers(A, U[:, o], s, sigma, shifts=shifts)   # step 3: s products
             mv += s
             T = np.zeros((o, s + 1))
             if o > 0:
@@ -162,6 +211,9 @@ def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None):
                     col[o : o + s] = S
                     col[o + s] = nu
                 col = col / sigma
+                if shifts is not None:   # A y^{j+1} = y^{j+2} / sigma + theta_j y^{j+1}
+                    col[:o] += shifts[j] * T[:, j]
+                    col[o + j] += shifts[j]
                 if o > 0:
                     col = col - G[:, :o] @ T[:, j]
                 G[:, o + j] = col
@@ -186,13 +238,16 @@ def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None):
                 break
         if trace is not None and "U" not in trace:
             trace.update(U=U[:, : K + 1].copy(), G=G[: K + 1, :K].copy(), W=[w.copy() for w in Ws], s=s)
+        if basis == "newton" and shifts is None and K > 0:
+            shifts = (shift_rule or newton_shifts)(G, K, s)
         if K > 0:
             y = lsq.solve()[:K] if lsq.j == K else lsq.solve()
             x = x + U[:, : lsq.j] @ y                        # step 3: x_m = x_0 + V y
         if status == STATUS_BREAKDOWN:
             relres = norm(f - A.apply(x)) / nf
             break
-    return dict(x=x, status=status, cycles=cycles, iters=iters, matvecs=mv, history=hist, relres=relres)
+    return dict(x=x, status=status, cycles=cycles, iters=iters, matvecs=mv, history=hist, relres=relres,
+                shifts=shifts)
 
 
 # ---------------------------------------------------------------- s-step Orthomin

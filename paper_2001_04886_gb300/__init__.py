@@ -25,6 +25,7 @@ from ._binding import (  # noqa: F401
     sstep_gram,
     sstep_gram_workspace_size,
     sstep_matrix_powers,
+    sstep_newton_shifts,
     sstep_omin_solve,
     stencil_matrix_apply,
     stencil_matrix_smooth,
@@ -48,6 +49,7 @@ __all__ = [
     "sstep_gmres_solve",
     "gmres_solve",
     "sstep_omin_solve",
+    "sstep_newton_shifts",
     "SStepError",
     "trace_enable",
     "trace_read",

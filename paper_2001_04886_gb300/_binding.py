@@ -21,7 +21,7 @@ P = ctypes.POINTER
 class SStepParams(ctypes.Structure):
     _fields_ = [("s", c_int), ("m", c_int), ("k", c_int), ("tol", c_double), ("max_cycles", c_int),
                 ("max_iters", c_int), ("sigma", c_double), ("history", P(c_double)), ("history_cap", c_int),
-                ("precision", c_int), ("x0_guard", c_int)]
+                ("precision", c_int), ("x0_guard", c_int), ("basis", c_int)]
 
 
 PRECISIONS = {"fp64": 0, "df64": 1, "fp32": 2}
@@ -41,6 +41,8 @@ SIGNATURES = {
     "stencil_matrix_destroy": (c_int, [c_void_p]),
     "stencil_matrix_info": (c_int, [c_void_p, P(c_int64), P(c_double)]),
     "stencil_matrix_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sstep_last_shifts": (c_int, [c_void_p, P(c_double), c_int]),
+    "sstep_newton_shifts": (c_int, [P(c_double), c_int, c_int, c_int, P(c_double)]),
     "stencil_matrix_smooth": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_void_p]),
     "stencil_matrix_smooth_batched": (c_int, [c_int, P(c_void_p), P(c_void_p), P(c_void_p), P(c_void_p), c_int,
                                               c_double, c_void_p]),
@@ -280,14 +282,18 @@ def sstep_block_update(V, Y, T, work=None, stream=None):
     return G.t()
 
 
+BASES = {"monomial": 0, "newton": 1}
+
+
 def _solve(name, A, f, x, s=1, m=20, k=1, tol=1e-8, max_cycles=1000, max_iters=100000, sigma=0.0,
-           history_cap=4096, stream=None, precision="fp64", x0_guard=False):
+           history_cap=4096, stream=None, precision="fp64", x0_guard=False, basis="monomial"):
     import numpy as np
 
     hist = np.zeros(max(history_cap, 1), dtype=np.float64)
     p = SStepParams(s=s, m=m, k=k, tol=tol, max_cycles=max_cycles, max_iters=max_iters, sigma=sigma,
                     history=hist.ctypes.data_as(P(c_double)) if history_cap > 0 else None,
-                    history_cap=history_cap, precision=PRECISIONS[precision], x0_guard=1 if x0_guard else 0)
+                    history_cap=history_cap, precision=PRECISIONS[precision], x0_guard=1 if x0_guard else 0,
+                    basis=BASES[basis])
     r = SStepResult()
     rc = getattr(lib(), name)(A.handle, _ptr(f), _ptr(x), ctypes.byref(p), ctypes.byref(r), _stream(stream))
     _check(name, rc)
@@ -296,13 +302,19 @@ def _solve(name, A, f, x, s=1, m=20, k=1, tol=1e-8, max_cycles=1000, max_iters=1
 
 
 def sstep_gmres_solve(A, f, x, s, m, tol, max_cycles=1000, sigma=0.0, history_cap=4096, stream=None,
-                      precision="fp64", x0_guard=False):
-    """s-step GMRES (Alg. 4.1/4.2); x is updated in place. Returns the result as a dict.
+                      precision="fp64", x0_guard=False, basis="monomial"):
+    """s-step GMRES (Alg. 4.1/4.2); x is updated in place. Returns the result as a dict
+    (with "shifts": the Newton-basis shifts used, empty for the monomial basis).
 
     precision: "fp64", "df64" (double-float basis) or "fp32" (FP32 basis, FP32 iterative refinement).
+    basis: "monomial" (as printed) or "newton" (shifts from the first cycle's Ritz values).
     """
-    return _solve("sstep_gmres_solve", A, f, x, s=s, m=m, tol=tol, max_cycles=max_cycles, sigma=sigma,
-                  history_cap=history_cap, stream=stream, precision=precision, x0_guard=x0_guard)
+    r = _solve("sstep_gmres_solve", A, f, x, s=s, m=m, tol=tol, max_cycles=max_cycles, sigma=sigma,
+               history_cap=history_cap, stream=stream, precision=precision, x0_guard=x0_guard, basis=basis)
+    buf = (c_double * SSTEP_MAX_S)()
+    cnt = _check("sstep_last_shifts", lib().sstep_last_shifts(A.handle, buf, SSTEP_MAX_S))
+    r["shifts"] = list(buf[:cnt])
+    return r
 
 
 def gmres_solve(A, f, x, m, tol, max_cycles=1000, history_cap=4096, stream=None, precision="fp64"):
@@ -315,6 +327,17 @@ def sstep_omin_solve(A, f, x, s, k, tol, max_iters=100000, sigma=0.0, history_ca
     """s-step Orthomin(k) (Alg. 3.1); s = 1 is Orthomin(k)."""
     return _solve("sstep_omin_solve", A, f, x, s=s, k=k, tol=tol, max_iters=max_iters, sigma=sigma,
                   history_cap=history_cap, stream=stream)
+
+
+def sstep_newton_shifts(G, K, s):
+    """The library's Newton-basis shifts for a host Hessenberg matrix G ((>= K) x (>= K),
+    float64): the Leja-ordered real parts of the eigenvalues of G[:K, :K] (host only)."""
+    import numpy as np
+
+    Gf = np.asfortranarray(np.asarray(G, dtype=np.float64))
+    out = (c_double * s)()
+    _check("sstep_newton_shifts", lib().sstep_newton_shifts(Gf.ctypes.data_as(P(c_double)), Gf.shape[0], K, s, out))
+    return list(out)
 
 
 def trace_enable(on=True):

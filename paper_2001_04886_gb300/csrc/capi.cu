@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <complex>
 #include <new>
 #include <vector>
 
@@ -21,6 +22,7 @@ using namespace sstep;
 
 struct sstep_matrix_s {
     StencilDesc A;
+    std::vector<double> shifts;      // Newton-basis shifts of the last s-step GMRES solve (host)
     double norm_inf = 0.0;
     double* fields = nullptr;        // owned copies of variable coefficients (7 x n)
     float2* fields_df = nullptr;     // the same as float pairs (mixed-precision kernels)
@@ -43,6 +45,147 @@ inline int64_t col_ld(int64_t n) { return (n + 31) / 32 * 32; }   // 256-byte al
     } while (0)
 
 int check_launch() { return cudaGetLastError() == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA; }
+
+// ------------------------------------------------------------------ Newton-basis shifts
+// Real parts of the eigenvalues of the K x K upper Hessenberg matrix held in G
+// (column-major, leading dimension ld): single-shift QR steps in complex arithmetic
+// (complex Givens rotations, Wilkinson shift = the eigenvalue of the trailing 2 x 2
+// nearer its last diagonal entry, so complex pairs converge like real eigenvalues) on
+// the active unreduced block, deflating where a subdiagonal entry is negligible next to
+// its diagonal neighbours; every 10th step without deflation takes an exceptional
+// shift. Returns false if the iteration does not settle within 100 K steps.
+bool hessenberg_real_parts(const double* G, int ld, int K, std::vector<double>& out) {
+    typedef std::complex<double> cplx;
+    out.clear();
+    std::vector<cplx> H((size_t)K * K, cplx(0.0, 0.0));   // row-major
+    for (int j = 0; j < K; ++j)
+        for (int i = 0; i <= std::min(j + 1, K - 1); ++i) H[(size_t)i * K + j] = G[i + (size_t)j * ld];
+    auto h = [&](int i, int j) -> cplx& { return H[(size_t)i * K + j]; };
+    const double eps = 2.220446049250313e-16;
+    std::vector<double> cs(K);
+    std::vector<cplx> sn(K);
+    int hi = K - 1, steps = 0, stall = 0;
+    while (hi >= 0) {
+        if (hi == 0) {
+            out.push_back(h(0, 0).real());
+            break;
+        }
+        int lo = hi;
+        while (lo > 0 && std::abs(h(lo, lo - 1)) > eps * (std::abs(h(lo, lo)) + std::abs(h(lo - 1, lo - 1)))) --lo;
+        if (lo > 0) h(lo, lo - 1) = 0.0;
+        if (lo == hi) {
+            out.push_back(h(hi, hi).real());
+            --hi;
+            stall = 0;
+            continue;
+        }
+        if (++steps > 100 * K) return false;
+        const cplx a = h(hi - 1, hi - 1), b = h(hi - 1, hi), c = h(hi, hi - 1), d = h(hi, hi);
+        const cplx half = 0.5 * (a - d), root = std::sqrt(half * half + b * c);
+        const cplx r1 = 0.5 * (a + d) + root, r2 = 0.5 * (a + d) - root;
+        cplx mu = std::abs(r1 - d) < std::abs(r2 - d) ? r1 : r2;
+        if (++stall % 10 == 0) mu = d + 0.75 * std::abs(c);
+        for (int i = lo; i <= hi; ++i) h(i, i) -= mu;
+        for (int k = lo; k < hi; ++k) {   // Q^H (H - mu I) = R, rotation k on rows k, k+1
+            const cplx x = h(k, k), y = h(k + 1, k);
+            const double ax = std::abs(x), r = std::sqrt(ax * ax + std::norm(y));
+            double cc = 1.0;
+            cplx ss(0.0, 0.0);
+            if (r > 0.0) {
+                if (ax == 0.0) {
+                    cc = 0.0;
+                    ss = 1.0;
+                } else {
+                    cc = ax / r;
+                    ss = (x / ax) * std::conj(y) / r;
+                }
+            }
+            cs[k] = cc;
+            sn[k] = ss;
+            for (int j = k; j <= hi; ++j) {
+                const cplx t1 = h(k, j), t2 = h(k + 1, j);
+                h(k, j) = cc * t1 + ss * t2;
+                h(k + 1, j) = -std::conj(ss) * t1 + cc * t2;
+            }
+        }
+        for (int k = lo; k < hi; ++k) {   // R Q + mu I
+            const double cc = cs[k];
+            const cplx ss = sn[k];
+            for (int i = lo; i <= std::min(k + 2, hi); ++i) {
+                const cplx t1 = h(i, k), t2 = h(i, k + 1);
+                h(i, k) = cc * t1 + std::conj(ss) * t2;
+                h(i, k + 1) = -ss * t1 + cc * t2;
+            }
+        }
+        for (int i = lo; i <= hi; ++i) h(i, i) += mu;
+    }
+    return (int)out.size() == K;
+}
+
+// The first `count` points of the Leja ordering of the (ascending) values: the largest in
+// modulus first, then each next point maximises the sum of the logarithms of its
+// distances to the points taken (ties go to the earlier value); points within
+// 1e-10 max|v| of a taken one (the real parts of a complex pair) are skipped; the
+// sequence repeats when the distinct values run out.
+std::vector<double> leja_order(std::vector<double> v, int count) {
+    std::sort(v.begin(), v.end());
+    std::vector<double> seq;
+    if (v.empty()) return std::vector<double>(count, 0.0);
+    double vmax = 0.0;
+    for (double t : v) vmax = std::max(vmax, fabs(t));
+    const double tiny = 1e-10 * vmax;
+    std::vector<char> used(v.size(), 0);
+    size_t first = 0;
+    for (size_t i = 1; i < v.size(); ++i)
+        if (fabs(v[i]) > fabs(v[first])) first = i;
+    used[first] = 1;
+    seq.push_back(v[first]);
+    for (;;) {
+        int best = -1;
+        double best_score = 0.0;
+        for (size_t i = 0; i < v.size(); ++i) {
+            if (used[i]) continue;
+            double score = 0.0;
+            bool zero = false;
+            for (double t : seq) {
+                const double dd = fabs(v[i] - t);
+                if (dd <= tiny) {
+                    zero = true;
+                    break;
+                }
+                score += log(dd);
+            }
+            if (zero) continue;
+            if (best < 0 || score > best_score) {
+                best = (int)i;
+                best_score = score;
+            }
+        }
+        if (best < 0) break;
+        used[best] = 1;
+        seq.push_back(v[best]);
+    }
+    std::vector<double> out(count);
+    for (int j = 0; j < count; ++j) out[j] = seq[j % seq.size()];
+    return out;
+}
+
+// After the first cycle: the shifts from its Hessenberg G (device), written to the
+// device state (st->theta) and returned; empty (monomial kept) if the QR does not settle.
+std::vector<double> newton_shifts_from_device(const double* G_dev, int m, int K, int s, double* theta_dev,
+                                              cudaStream_t stream) {
+    std::vector<double> G((size_t)(m + 1) * m);
+    if (K < 1 || cudaMemcpyAsync(G.data(), G_dev, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, stream) !=
+                     cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return {};
+    std::vector<double> ev;
+    if (!hessenberg_real_parts(G.data(), m + 1, K, ev)) return {};
+    std::vector<double> th = leja_order(ev, s);
+    if (cudaMemcpyAsync(theta_dev, th.data(), sizeof(double) * s, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return {};
+    return th;
+}
 
 // The fused matrix-powers kernel (one launch for the s powers of a block) is off by
 // default: on GB300 the 16.8 MB columns of a 128^3 solve stay in the 129 MB L2 between
@@ -153,7 +296,7 @@ int make_desc(StencilDesc& A, int dim, const int64_t shape[3]) {
 
 // Device workspace of one solve. Small arrays first, then the columns.
 struct Layout {
-    size_t state, L, T, S, G, R, gc, gs, g, y, hist, C, a, counter, partials, cols;
+    size_t state, L, T, S, G, R, gc, gs, g, y, hist, C, a, theta, counter, partials, cols;
     size_t total;
 };
 
@@ -179,6 +322,7 @@ Layout plan(int64_t n, int ncols, int m, int hist_cap, size_t elem_bytes = sizeo
     l.hist = take(sizeof(double) * std::max(hist_cap, 1));
     l.C = take(sizeof(double) * kMaxCols * (kMaxS + 1));
     l.a = take(sizeof(double) * kMaxCols);
+    l.theta = take(sizeof(double) * kMaxS);
     l.counter = take(kAlign);
     l.partials = take(sizeof(double) * (size_t)max_partials_doubles());
     l.cols = take(elem_bytes * (size_t)col_ld(n) * ncols);
@@ -232,6 +376,7 @@ SolverState init_state(const Layout& l, char* ws, const sstep_params* p, int s, 
     h.hist = (double*)(ws + l.hist);
     h.C = (double*)(ws + l.C);
     h.a = (double*)(ws + l.a);
+    h.theta = (double*)(ws + l.theta);
     return h;
 }
 
@@ -313,6 +458,7 @@ int sstep_gmres_mp(sstep_matrix M, const double* f, double* x, const sstep_param
     CUDA_TRY(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
     CUDA_TRY(cudaMemsetAsync(M->ws + l.counter, 0, kAlign, stream_));
     CUDA_TRY(cudaMemsetAsync(M->ws + l.G, 0, sizeof(double) * (m + 1) * m, stream_));
+    CUDA_TRY(cudaMemsetAsync(M->ws + l.theta, 0, sizeof(double) * kMaxS, stream_));
     Epi e;
     e.st = st;
     e.mode = EPI_NF;
@@ -320,6 +466,9 @@ int sstep_gmres_mp(sstep_matrix M, const double* f, double* x, const sstep_param
     if (p->x0_guard && (rc = apply_x0_guard(M, l, st, f, x, stream_))) return rc;
     const double sigma = h.sigma;
     const int nb = m / s;
+    std::vector<double> theta(s, 0.0);   // Newton shifts (zero: monomial powers)
+    bool shifted = false;
+    M->shifts.clear();
     for (;;) {
         e = Epi();
         e.st = st;
@@ -329,16 +478,17 @@ int sstep_gmres_mp(sstep_matrix M, const double* f, double* x, const sstep_param
             const int o = k * s;
             // Alg. 4.1 step 3: the s powers, in one fused launch when enabled (SSTEP_FUSED_POWERS=1)
             bool fused = false;
-            if (fused_powers_enabled())
+            if (fused_powers_enabled() && !shifted)
                 TRACED(K_STENCIL, stream_,
                        fused = mp_launch_powers_fused<P>(M->A, uraw, col(o), ld, s, sigma, &st->vscale, st,
                                                          GATE_BUILDING, stream_));
             if (!fused) {
                 TRACED(K_STENCIL, stream_, mp_launch_stencil<P>(M->A, uraw, sigma, col(o + 1), 1.0, col(o),
-                                                                &st->vscale, st, GATE_BUILDING, stream_));
+                                                                &st->vscale, st, GATE_BUILDING, stream_, theta[0]));
                 for (int j = 2; j <= s; ++j)
                     TRACED(K_STENCIL, stream_, mp_launch_stencil<P>(M->A, col(o + j - 1), sigma, col(o + j), 0.0,
-                                                                    nullptr, nullptr, st, GATE_BUILDING, stream_));
+                                                                    nullptr, nullptr, st, GATE_BUILDING, stream_,
+                                                                    theta[j - 1]));
             }
             if (k > 0) {
                 e = Epi();
@@ -369,6 +519,14 @@ int sstep_gmres_mp(sstep_matrix M, const double* f, double* x, const sstep_param
         CUDA_TRY(cudaGetLastError());
         if ((rc = read_header(M, st, stream_))) return rc;
         if (!M->hdr->active) break;
+        if (p->basis == SSTEP_BASIS_NEWTON && !shifted) {   // shifts from the first cycle's Ritz values
+            std::vector<double> th = newton_shifts_from_device(h.G, m, M->hdr->K, s, h.theta, stream_);
+            if (!th.empty()) {
+                theta = th;
+                M->shifts = th;
+            }
+            shifted = true;
+        }
     }
     return finish(M, l, st, f, x, p, res, stream_);
 }
@@ -765,6 +923,22 @@ int stencil_matrix_smooth_batched(int nsys, const sstep_matrix* A, const double*
     return rc;
 }
 
+int sstep_newton_shifts(const double* G, int ldg, int K, int s, double* theta) {
+    if (!G || !theta || K < 1 || ldg < K || s < 1 || s > SSTEP_MAX_S) return SSTEP_ERR_ARG;
+    std::vector<double> ev;
+    if (!hessenberg_real_parts(G, ldg, K, ev)) return SSTEP_ERR_BREAKDOWN;
+    const std::vector<double> th = leja_order(ev, s);
+    for (int i = 0; i < s; ++i) theta[i] = th[i];
+    return SSTEP_OK;
+}
+
+int sstep_last_shifts(sstep_matrix M, double* theta, int cap) {
+    if (!M || cap < 0 || (cap > 0 && !theta)) return SSTEP_ERR_ARG;
+    const int n = (int)M->shifts.size();
+    for (int i = 0; i < n && i < cap; ++i) theta[i] = M->shifts[i];
+    return n;
+}
+
 int sstep_matrix_powers(sstep_matrix M, const double* v, double scale, double sigma, int s, double* Y, int64_t ldy,
                         void* stream) {
     if (!M || !v || !Y || s < 1 || s > SSTEP_MAX_S || ldy < M->A.n) return SSTEP_ERR_ARG;
@@ -827,6 +1001,7 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     if (rc) return rc;
     const int s = p->s, m = p->m;
     if (s < 1 || s > SSTEP_MAX_S || m < s || m > SSTEP_MAX_M || m % s != 0 || p->max_cycles < 0) return SSTEP_ERR_ARG;
+    if (p->basis != SSTEP_BASIS_MONOMIAL && p->basis != SSTEP_BASIS_NEWTON) return SSTEP_ERR_ARG;
     cudaStream_t stream_ = (cudaStream_t)stream;
     if (p->precision == SSTEP_PREC_DF64) return sstep_gmres_mp<PREC_DF64>(M, f, x, p, res, stream_);
     if (p->precision == SSTEP_PREC_FP32) return sstep_gmres_mp<PREC_FP32>(M, f, x, p, res, stream_);
@@ -844,6 +1019,7 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     CUDA_TRY(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
     CUDA_TRY(cudaMemsetAsync(M->ws + l.counter, 0, kAlign, stream_));
     CUDA_TRY(cudaMemsetAsync(M->ws + l.G, 0, sizeof(double) * (m + 1) * m, stream_));
+    CUDA_TRY(cudaMemsetAsync(M->ws + l.theta, 0, sizeof(double) * kMaxS, stream_));
     Epi e;
     e.st = st;
     e.mode = EPI_NF;
@@ -851,6 +1027,9 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     if (p->x0_guard && (rc = apply_x0_guard(M, l, st, f, x, stream_))) return rc;
     const double sigma = h.sigma;
     const int nb = m / s;
+    std::vector<double> theta(s, 0.0);   // Newton shifts (zero: monomial powers)
+    bool shifted = false;
+    M->shifts.clear();
     for (;;) {
         e = Epi();
         e.st = st;
@@ -859,11 +1038,11 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
         for (int k = 0; k < nb; ++k) {
             const int o = k * s;
             // Alg. 4.1 step 3: v_k^1 = u / ||u|| and its s scaled powers
-            TRACED(K_STENCIL, stream_, launch_stencil(M->A, uraw, sigma, U + (o + 1) * ld, 1.0, U + o * ld, &st->vscale, st, GATE_BUILDING,
-                           stream_));
+            TRACED(K_STENCIL, stream_, launch_stencil(M->A, uraw, sigma, U + (o + 1) * ld, 1.0, U + o * ld,
+                                                      &st->vscale, st, GATE_BUILDING, stream_, theta[0]));
             for (int j = 2; j <= s; ++j)
-                TRACED(K_STENCIL, stream_, launch_stencil(M->A, U + (o + j - 1) * ld, sigma, U + (o + j) * ld, 0.0, nullptr, nullptr, st,
-                               GATE_BUILDING, stream_));
+                TRACED(K_STENCIL, stream_, launch_stencil(M->A, U + (o + j - 1) * ld, sigma, U + (o + j) * ld, 0.0,
+                                                          nullptr, nullptr, st, GATE_BUILDING, stream_, theta[j - 1]));
             if (k > 0) {   // steps 4-5 and Scalar2: inner products with the earlier blocks
                 e = Epi();
                 e.st = st;
@@ -895,6 +1074,14 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
         CUDA_TRY(cudaGetLastError());
         if ((rc = read_header(M, st, stream_))) return rc;
         if (!M->hdr->active) break;
+        if (p->basis == SSTEP_BASIS_NEWTON && !shifted) {   // shifts from the first cycle's Ritz values
+            std::vector<double> th = newton_shifts_from_device(h.G, m, M->hdr->K, s, h.theta, stream_);
+            if (!th.empty()) {
+                theta = th;
+                M->shifts = th;
+            }
+            shifted = true;
+        }
     }
     return finish(M, l, st, f, x, p, res, stream_);
 }
@@ -1054,7 +1241,7 @@ int sstep_batch_create(sstep_batch* out, int nsys, const sstep_matrix* A, const 
     *out = nullptr;
     const int s = p->s, m = p->m;
     if (!(s == 1 || s == 2 || s == 4 || s == 8) || m < s || m > kBatchMaxM || m % s || p->max_cycles < 0 ||
-        !(p->tol > 0.0) || p->sigma < 0.0 || p->precision != SSTEP_PREC_FP64)
+        !(p->tol > 0.0) || p->sigma < 0.0 || p->precision != SSTEP_PREC_FP64 || p->basis != SSTEP_BASIS_MONOMIAL)
         return SSTEP_ERR_ARG;
     for (int i = 0; i < nsys; ++i)
         if (!A[i]) return SSTEP_ERR_ARG;

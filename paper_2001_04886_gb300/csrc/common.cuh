@@ -91,6 +91,7 @@ struct SolverState {
     double* hist;      // hist_cap residual history entries
     double* C;         // reduced Gram output (up to kMaxCols x (kMaxS+1))
     double* a;         // Omin: s step coefficients
+    double* theta;     // s shifts of the Newton basis (zero: the monomial powers)
 };
 
 // ------------------------------------------------------------------ reductions

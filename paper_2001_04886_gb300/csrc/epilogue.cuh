@@ -179,6 +179,12 @@ __device__ void epi_gm_nu(const Epi& e, const double* red) {
         else if (r < o + s) raw = st->S[r - o];
         else raw = (r == o + s) ? nu : 0.0;
         double val = raw / sigma;
+        {   // Newton basis: A y^{j+1} = y^{j+2} / sigma + theta_j y^{j+1} (theta_j = 0: monomial);
+            // y^1 is the start vector itself, y^{j+1} has coordinates T[:, j] and e_{o+j}
+            double rj = (r == o + j) ? 1.0 : 0.0;
+            if (j > 0 && r < o) rj = st->T[r + j * m];
+            val = fma(st->theta[j], rj, val);
+        }
         if (o > 0) {
             double acc = 0.0;
             for (int i = 0; i < o; ++i) acc = fma(st->G[r + i * ldg], st->T[i + j * m], acc);

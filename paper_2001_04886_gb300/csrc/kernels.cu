@@ -31,7 +31,8 @@ __device__ __forceinline__ void grid_xyz(const StencilDesc& A, int64_t p, int& x
 __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const double* __restrict__ v,
                                                            double fy, double* __restrict__ y, double fw,
                                                            double* __restrict__ w, const double* dscale,
-                                                           const SolverState* st, int gate, int zchunk) {
+                                                           const SolverState* st, int gate, int zchunk,
+                                                           double shift) {
     if (!gate_open(st, gate)) return;
     if (dscale) {
         const double d = *dscale;
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
     double c[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) c[q] = fy * A.c[q];
+    c[0] = fy * (A.c[0] - shift);
     double vm = (three && zb > 0) ? __ldg(v + p - pl) : 0.0;
     double vc = __ldg(v + p);
 #pragma unroll 2
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
                 if (z < A.nz - 1) acc = fma(c[6], vp, acc);
             }
         } else {
-            acc = __ldg(A.f[0] + p) * vc;
+            acc = (__ldg(A.f[0] + p) - shift) * vc;
             if (x > 0) acc = fma(__ldg(A.f[1] + p), __ldg(v + p - 1), acc);
             if (x < A.nx - 1) acc = fma(__ldg(A.f[2] + p), __ldg(v + p + 1), acc);
             if (yy > 0) acc = fma(__ldg(A.f[3] + p), __ldg(v + p - A.nx), acc);
@@ -85,14 +87,15 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
 }
 
 void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y, double fw, double* w,
-                    const double* dscale, const SolverState* st, int gate, cudaStream_t stream) {
+                    const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift) {
     const int tiles = ((A.nx + 31) / 32) * ((A.ny + 7) / 8);
     // z chunks: about one wave of 8 CTAs per SM, at least one plane per chunk
     int chunks = kMaxCtas / tiles;
     chunks = chunks < 1 ? 1 : (chunks > A.nz ? A.nz : chunks);
     const int zchunk = (A.nz + chunks - 1) / chunks;
     chunks = (A.nz + zchunk - 1) / zchunk;
-    stencil_kernel<<<dim3(tiles, chunks), dim3(32, 8), 0, stream>>>(A, v, fy, y, fw, w, dscale, st, gate, zchunk);
+    stencil_kernel<<<dim3(tiles, chunks), dim3(32, 8), 0, stream>>>(A, v, fy, y, fw, w, dscale, st, gate, zchunk,
+                                                                    shift);
 }
 
 // ================================================================== residual

@@ -50,8 +50,9 @@ __device__ __forceinline__ bool gate_open(const SolverState* st, int gate) {
 
 // ------------------------------------------------------------------ launchers (kernels.cu)
 // y = fy * (A v), w = fw * v (if w); fy and fw are multiplied by *dscale when dscale is set.
+// y = fy (A - shift I) v; w = fw v when w is set (shift: the Newton basis, 0 otherwise)
 void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y, double fw, double* w,
-                    const double* dscale, const SolverState* st, int gate, cudaStream_t stream);
+                    const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift = 0.0);
 
 // r = f - A x (x may be null: r = f); out (may be null) receives r; reduces ||r||^2.
 void launch_residual(const StencilDesc& A, const double* f, const double* x, double* out, Scratch sc,
@@ -106,7 +107,8 @@ inline size_t prec_bytes(int prec) { return prec == PREC_FP32 ? 4 : 8; }
 
 template <int P>
 void mp_launch_stencil(const StencilDesc& A, const void* v, double fy, void* y, double fw, void* w,
-                       const double* dscale, const SolverState* st, int gate, cudaStream_t stream);
+                       const double* dscale, const SolverState* st, int gate, cudaStream_t stream,
+                       double shift = 0.0);
 template <int P>
 void mp_launch_residual(const StencilDesc& A, const double* f, const double* x, void* out, Scratch sc,
                         const Epi& epi, int gate, cudaStream_t stream);

@@ -180,13 +180,15 @@ __global__ void __launch_bounds__(kThreads) mp_stencil_kernel(StencilDesc A, con
                                                               double fy, typename Mode<P>::T* __restrict__ y, double fw,
                                                               typename Mode<P>::T* __restrict__ w,
                                                               const double* dscale, const SolverState* st, int gate,
-                                                              int zchunk) {
+                                                              int zchunk, float2 c0s, float2 shs) {
     using M = Mode<P>;
     using Vt = typename M::V;
     __shared__ df64 fac[2];
     if (!gate_open(st, gate)) return;
     broadcast_factors(fy, fw, dscale, fac);
     const df64 vfy = fac[0], vfw = fac[1];
+    // the centre coefficient of A - shift I: constant (split on the host), or per point
+    const df64 c0 = df64{c0s.x, P == PREC_DF64 ? c0s.y : 0.f}, sh = df64{shs.x, shs.y};
     const int tx = (A.nx + 31) / 32;
     const int x = (int)(blockIdx.x % tx) * 32 + threadIdx.x;
     const int yy = (int)(blockIdx.x / tx) * 8 + threadIdx.y;
@@ -211,14 +213,15 @@ __global__ void __launch_bounds__(kThreads) mp_stencil_kernel(StencilDesc A, con
         if constexpr (P == PREC_DF64) {
             // centre, then the neighbours: exact products summed in double-float
             DfAcc acc;
+            acc.add_prod(A.variable ? df_add(mp_coef<P>(A, 0, p), df_neg(sh)) : c0, nb[0]);
 #pragma unroll
-            for (int q = 0; q < 7; ++q)
+            for (int q = 1; q < 7; ++q)
                 if (q < 2 * A.dim + 1) acc.add_prod(mp_coef<P>(A, q, p), nb[q]);
             acc.normalize();
             M::store(y + p, df_mul(vfy, df64{acc.hi, acc.lo}));
             if (w) M::store(w + p, df_mul(vfw, nb[0]));
         } else {
-            float acc = __fmul_rn(mp_coef<P>(A, 0, p).hi, nb[0]);
+            float acc = __fmul_rn(A.variable ? __fsub_rn(mp_coef<P>(A, 0, p).hi, sh.hi) : c0.hi, nb[0]);
 #pragma unroll
             for (int q = 1; q < 7; ++q)
                 if (q < 2 * A.dim + 1) acc = __fmaf_rn(mp_coef<P>(A, q, p).hi, nb[q], acc);
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(kThreads) mp_stencil_kernel(StencilDesc A, con
 
 template <int P>
 void mp_launch_stencil(const StencilDesc& A, const void* v, double fy, void* y, double fw, void* w,
-                       const double* dscale, const SolverState* st, int gate, cudaStream_t stream) {
+                       const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift) {
     using T = typename Mode<P>::T;
     const int tiles = ((A.nx + 31) / 32) * ((A.ny + 7) / 8);
     // z chunks: about one wave of 8 CTAs per SM, at least one plane per chunk
@@ -240,8 +243,13 @@ void mp_launch_stencil(const StencilDesc& A, const void* v, double fy, void* y, 
     chunks = chunks < 1 ? 1 : (chunks > A.nz ? A.nz : chunks);
     const int zchunk = (A.nz + chunks - 1) / chunks;
     chunks = (A.nz + zchunk - 1) / zchunk;
+    // A.c[0] - shift and shift itself as float pairs (hi + lo to ~48 bits)
+    const double c0 = A.c[0] - shift;
+    const float c0h = (float)c0, shh = (float)shift;
+    const float2 c0s = make_float2(c0h, (float)(c0 - (double)c0h));
+    const float2 shs = make_float2(shh, (float)(shift - (double)shh));
     mp_stencil_kernel<P><<<dim3(tiles, chunks), dim3(32, 8), 0, stream>>>(A, (const T*)v, fy, (T*)y, fw, (T*)w, dscale,
-                                                                          st, gate, zchunk);
+                                                                          st, gate, zchunk, c0s, shs);
 }
 
 // ================================================================== fused matrix powers
@@ -940,7 +948,7 @@ void launch_split_fields(const double* src, float2* dst, int64_t n, cudaStream_t
 // ------------------------------------------------------------------ instantiations
 #define SSTEP_MP_INST(P)                                                                                          \
     template void mp_launch_stencil<P>(const StencilDesc&, const void*, double, void*, double, void*,            \
-                                       const double*, const SolverState*, int, cudaStream_t);                    \
+                                       const double*, const SolverState*, int, cudaStream_t, double);            \
     template void mp_launch_residual<P>(const StencilDesc&, const double*, const double*, void*, Scratch,        \
                                         const Epi&, int, cudaStream_t);                                          \
     template void mp_launch_gram<P>(int64_t, const void*, int64_t, int, const void*, int64_t, int, Scratch,      \
