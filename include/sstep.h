@@ -81,6 +81,11 @@ int stencil_matrix_info(sstep_matrix A, int64_t* n, double* norm_inf);
  * when the last solve kept the monomial powers), or SSTEP_ERR_ARG. */
 int sstep_last_shifts(sstep_matrix A, double* theta, int cap);
 
+/* Caps the device workspace a solve may allocate (bytes; 0: no cap). A solve that needs
+ * more returns SSTEP_ERR_OOM before touching the device: the allocation-failure path,
+ * testable without a GPU. Process-global. */
+int sstep_set_workspace_limit(int64_t bytes);
+
 /* The shift computation on its own (host only, no GPU): theta[0..s) = the Leja-ordered
  * real parts of the eigenvalues of the K x K upper Hessenberg matrix G (HOST,
  * column-major, leading dimension ldg >= K), as the Newton basis uses them. Returns
@@ -298,8 +303,15 @@ int x0net_gradient(x0net X, const float* input, const float* target, int batch, 
  * cores. */
 int x0net_set_tensor_cores(x0net X, int on);
 /* Synchronises `stream` and reports SSTEP_ERR_TIMEOUT if a tensor-core kernel's bounded
- * wait ran out since the network was created (x0net_gradient reports it as well). */
+ * wait ran out since the last call (the flag is cleared; x0net_gradient reports it as
+ * well). A timed-out kernel waits (bounded again) for its MMAs in flight, frees its
+ * tensor memory and skips its output; the CUDA context stays usable. */
 int x0net_status(x0net X, void* stream);
+/* Polls per bounded wait of the tensor-core kernels before it counts as timed out
+ * (negative: the default, 2^24). A test sets 0, so every first wait runs out at once,
+ * to exercise the timeout path; the drain before freeing tensor memory always uses the
+ * default limit. */
+int x0net_set_wait_limit(x0net X, int64_t polls);
 int x0net_train_step(x0net X, const float* input, const float* target, int batch, float lr, float* loss_dev,
                      void* stream);
 

@@ -43,6 +43,7 @@ SIGNATURES = {
     "stencil_matrix_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "sstep_last_shifts": (c_int, [c_void_p, P(c_double), c_int]),
     "sstep_newton_shifts": (c_int, [P(c_double), c_int, c_int, c_int, P(c_double)]),
+    "sstep_set_workspace_limit": (c_int, [c_int64]),
     "stencil_matrix_smooth": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_void_p]),
     "stencil_matrix_smooth_batched": (c_int, [c_int, P(c_void_p), P(c_void_p), P(c_void_p), P(c_void_p), c_int,
                                               c_double, c_void_p]),
@@ -74,6 +75,7 @@ SIGNATURES = {
     "x0net_gradient": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "x0net_set_tensor_cores": (c_int, [c_void_p, c_int]),
     "x0net_status": (c_int, [c_void_p, c_void_p]),
+    "x0net_set_wait_limit": (c_int, [c_void_p, c_int64]),
     "x0net_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p, c_void_p]),
     "sstep_trace_select": (c_int, [ctypes.c_uint]),
     "sstep_trace_enable": (c_int, [c_int]),
@@ -486,6 +488,10 @@ class X0Net:
     def set_tensor_cores(self, on):
         """BF16 mode: 3x3 convolutions on the tensor cores (default) or on the CUDA cores."""
         _check("x0net_set_tensor_cores", lib().x0net_set_tensor_cores(self.handle, 1 if on else 0))
+
+    def set_wait_limit(self, polls):
+        """Polls per bounded tensor-core wait (negative: the default); tests set 0."""
+        _check("x0net_set_wait_limit", lib().x0net_set_wait_limit(self.handle, int(polls)))
 
     def status(self, stream=None):
         """Synchronises and raises if a tensor-core kernel's bounded wait ran out."""

@@ -330,7 +330,11 @@ Layout plan(int64_t n, int ncols, int m, int hist_cap, size_t elem_bytes = sizeo
     return l;
 }
 
+// A cap on the solver workspace (0: none), for tests of the allocation-failure path.
+int64_t g_workspace_limit = 0;
+
 int ensure_workspace(sstep_matrix M, size_t bytes) {
+    if (g_workspace_limit > 0 && (int64_t)bytes > g_workspace_limit) return SSTEP_ERR_OOM;
     if (!M->hdr) {
         if (cudaMallocHost((void**)&M->hdr, sizeof(SolverState)) != cudaSuccess) {
             M->hdr = nullptr;
@@ -921,6 +925,12 @@ int stencil_matrix_smooth_batched(int nsys, const sstep_matrix* A, const double*
     cudaFreeAsync(d, st);
     if (rc == SSTEP_OK) rc = check_launch();
     return rc;
+}
+
+int sstep_set_workspace_limit(int64_t bytes) {
+    if (bytes < 0) return SSTEP_ERR_ARG;
+    g_workspace_limit = bytes;
+    return SSTEP_OK;
 }
 
 int sstep_newton_shifts(const double* G, int ldg, int K, int s, double* theta) {

@@ -148,9 +148,9 @@ __host__ __device__ constexpr uint32_t idesc(int n) {   // BF16 x BF16 -> FP32, 
 
 __host__ __device__ constexpr int tmem_cols(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : 256)); }
 
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, long limit = kSpin) {
     uint32_t done = 0;
-    for (long it = 0; it < kSpin && !done; ++it)
+    for (long it = 0; it < limit && !done; ++it)
         asm volatile("{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\nselp.b32 %0, 1, 0, P;\n}"
                      : "=r"(done)
                      : "r"(bar), "r"(parity)
@@ -166,7 +166,8 @@ template <int NP, bool TRANSPOSED>
 __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const float* __restrict__ in, int Kc,
                                                         const __nv_bfloat16* __restrict__ W,
                                                         const float* __restrict__ bias, float* __restrict__ out,
-                                                        int N, int H, int Wd, int relu, int accumulate, int* err) {
+                                                        int N, int H, int Wd, int relu, int accumulate, int* err,
+                                                        long spin) {
     constexpr int kABytes = kM * kK * 2;          // one BF16 part of the A chunk
     constexpr int kBBytes = NP * kK * 2;
     constexpr int kStage = 3 * kABytes + kBBytes;
@@ -203,11 +204,13 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const float* __restrict_
     for (int i = 0; i < nchunks && ok; ++i) {
         const int st = i & 1;
         if (i >= 2) {   // the MMAs that read this stage (chunk i - 2) are done
-            if (!wait_bar(smem_u32(&bars[st]), (uint32_t)(((i >> 1) - 1) & 1))) {
+            if (!wait_bar(smem_u32(&bars[st]), (uint32_t)(((i >> 1) - 1) & 1), spin)) {
                 failed = 1;
             }
             __syncthreads();
-            if (failed) {
+            if (failed) {   // drain: the MMAs of chunks i - 2 and i - 1 are still in flight
+                wait_bar(smem_u32(&bars[st]), (uint32_t)(((i >> 1) - 1) & 1));
+                wait_bar(smem_u32(&bars[st ^ 1]), (uint32_t)(((i - 1) >> 1) & 1));
                 ok = false;
                 break;
             }
@@ -290,10 +293,15 @@ __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const float* __restrict_
     // the last commit covers every MMA this thread issued
     if (ok && nchunks > 0) {   // both stages' last commits, so no arrive is pending at exit
         const int last = nchunks - 1;
-        if (!wait_bar(smem_u32(&bars[last & 1]), (uint32_t)((last >> 1) & 1))) failed = 1;
-        if (last >= 1 && !wait_bar(smem_u32(&bars[(last - 1) & 1]), (uint32_t)(((last - 1) >> 1) & 1))) failed = 1;
+        if (!wait_bar(smem_u32(&bars[last & 1]), (uint32_t)((last >> 1) & 1), spin)) failed = 1;
+        if (last >= 1 && !wait_bar(smem_u32(&bars[(last - 1) & 1]), (uint32_t)(((last - 1) >> 1) & 1), spin))
+            failed = 1;
         __syncthreads();
         ok = !failed;
+        if (!ok) {   // drain both stages' last commits before the tensor memory is freed
+            wait_bar(smem_u32(&bars[last & 1]), (uint32_t)((last >> 1) & 1));
+            if (last >= 1) wait_bar(smem_u32(&bars[(last - 1) & 1]), (uint32_t)(((last - 1) >> 1) & 1));
+        }
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok) {
@@ -342,7 +350,7 @@ size_t smem_bytes() {
 
 template <int NP, bool TRANSPOSED>
 int launch_np(const float* in, int Kc, const __nv_bfloat16* W, const float* bias, float* out, int N, int B, int H,
-              int Wd, int relu, int accumulate, int* err, cudaStream_t s) {
+              int Wd, int relu, int accumulate, int* err, long spin, cudaStream_t s) {
     const size_t smem = smem_bytes<NP>();
     static bool attr = false;
     if (!attr) {
@@ -353,20 +361,22 @@ int launch_np(const float* in, int Kc, const __nv_bfloat16* W, const float* bias
     }
     const int64_t HW = (int64_t)H * Wd;
     dim3 grid((unsigned)((HW + kM - 1) / kM), (unsigned)B);
-    conv3x3_tc_kernel<NP, TRANSPOSED><<<grid, kM, smem, s>>>(in, Kc, W, bias, out, N, H, Wd, relu, accumulate, err);
+    conv3x3_tc_kernel<NP, TRANSPOSED><<<grid, kM, smem, s>>>(in, Kc, W, bias, out, N, H, Wd, relu, accumulate, err,
+                                                             spin);
     return 0;
 }
 
-// out (N channels) = conv3x3(in (Kc channels)); N up to 128
+// out (N channels) = conv3x3(in (Kc channels)); N up to 128. spin: polls per bounded wait
+// before it counts as timed out (kSpin normally; a test lowers it to exercise the path)
 template <bool TRANSPOSED>
 int conv3x3(const float* in, int Kc, const __nv_bfloat16* W, const float* bias, float* out, int N, int B, int H, int Wd,
-            int relu, int accumulate, int* err, cudaStream_t s) {
-    if (N <= 16) return launch_np<16, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
-    if (N <= 32) return launch_np<32, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
-    if (N <= 48) return launch_np<48, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
-    if (N <= 64) return launch_np<64, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
-    if (N <= 96) return launch_np<96, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
-    if (N <= 128) return launch_np<128, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, s);
+            int relu, int accumulate, int* err, long spin, cudaStream_t s) {
+    if (N <= 16) return launch_np<16, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, spin, s);
+    if (N <= 32) return launch_np<32, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, spin, s);
+    if (N <= 48) return launch_np<48, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, spin, s);
+    if (N <= 64) return launch_np<64, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, spin, s);
+    if (N <= 96) return launch_np<96, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, spin, s);
+    if (N <= 128) return launch_np<128, TRANSPOSED>(in, Kc, W, bias, out, N, B, H, Wd, relu, accumulate, err, spin, s);
     return -1;
 }
 
@@ -776,6 +786,7 @@ struct Net {
     int tc = 1;            // BF16 mode: 3x3 convolutions on the tensor cores (tcgen05)
     float* wpart = nullptr;   // weight-gradient partial sums (chunks x weights of a layer)
     int* err = nullptr;    // set by a tensor-core kernel whose bounded wait ran out
+    long spin = tc::kSpin; // polls per bounded wait
 };
 
 float* alloc(Net& n, int64_t count) {
@@ -795,7 +806,8 @@ void conv(const Net& n, int layer, const float* in, float* out, int B, int H, in
         return;
     }
     if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
-        if (n.tc && tc::conv3x3<false>(in, c.cin, W, bias, out, c.cout, B, H, Wd, c.relu, 0, n.err, s) == 0) return;
+        if (n.tc && tc::conv3x3<false>(in, c.cin, W, bias, out, c.cout, B, H, Wd, c.relu, 0, n.err, n.spin, s) == 0)
+            return;
     }
     dim3 grid((Wd + 15) / 16, (H + 15) / 16, B * ((c.cout + 15) / 16));
     conv3x3_kernel<WT, false><<<grid, kT, 0, s>>>(in, c.cin, W, bias, out, c.cout, H, Wd, c.relu, 0);
@@ -842,7 +854,8 @@ void conv_back(const Net& n, int layer, const float* in, const float* g, float* 
     }
     if (din) {
         if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
-            if (n.tc && tc::conv3x3<true>(g, c.cout, W, nullptr, din, c.cin, B, H, Wd, 0, 0, n.err, s) == 0) return;
+            if (n.tc && tc::conv3x3<true>(g, c.cout, W, nullptr, din, c.cin, B, H, Wd, 0, 0, n.err, n.spin, s) == 0)
+                return;
         }
         dim3 grid((Wd + 15) / 16, (H + 15) / 16, B * ((c.cin + 15) / 16));
         conv3x3_kernel<WT, true><<<grid, kT, 0, s>>>(g, c.cout, W, nullptr, din, c.cin, H, Wd, 0, 0);
@@ -1152,9 +1165,16 @@ int x0net_status(x0net X, void* stream) {
     if (!X) return SSTEP_ERR_ARG;
     int e = 0;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
-        cudaMemcpy(&e, X->n.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        cudaMemcpy(&e, X->n.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (e && cudaMemset(X->n.err, 0, sizeof(int)) != cudaSuccess))
         return SSTEP_ERR_CUDA;
     return e ? SSTEP_ERR_TIMEOUT : SSTEP_OK;
+}
+
+int x0net_set_wait_limit(x0net X, int64_t polls) {
+    if (!X) return SSTEP_ERR_ARG;
+    X->n.spin = polls >= 0 ? (long)polls : tc::kSpin;
+    return SSTEP_OK;
 }
 
 int x0net_train_step(x0net X, const float* input, const float* target, int batch, float lr, float* loss_dev,

@@ -54,3 +54,26 @@ def test_params_struct_layout_matches_header():
     assert P.basis.offset == 60
     assert ctypes.sizeof(P) == 64
     assert ctypes.sizeof(_binding.SStepResult) == 32
+
+
+def test_workspace_limit_gives_oom_before_any_device_call():
+    """The allocation-failure path without a GPU: a workspace cap below the solve's need
+    makes sstep_gmres_solve return SSTEP_ERR_OOM (the pointers are never dereferenced)."""
+    import ctypes
+
+    L = pkg.lib()
+    h = ctypes.c_void_p()
+    shp = (ctypes.c_int64 * 3)(16, 16, 1)
+    beta = (ctypes.c_double * 3)(10.0, 10.0, 0.0)
+    assert L.stencil_matrix_create_convdiff(ctypes.byref(h), 2, shp, beta) == 0
+    p = _binding.SStepParams(s=4, m=20, tol=1e-8, max_cycles=10)
+    r = _binding.SStepResult()
+    fake = ctypes.c_void_p(0x1000)
+    assert L.sstep_set_workspace_limit(1024) == 0
+    try:
+        rc = L.sstep_gmres_solve(h, fake, fake, ctypes.byref(p), ctypes.byref(r), None)
+        assert rc == -3   # SSTEP_ERR_OOM
+    finally:
+        assert L.sstep_set_workspace_limit(0) == 0
+        L.stencil_matrix_destroy(h)
+    assert L.sstep_set_workspace_limit(-1) == -1

@@ -107,3 +107,26 @@ def test_tensor_core_convolutions_match_cuda_cores(B, H, smooth, res_w):
     for sl in layer_slices():
         a, b = grads[1][sl], grads[0][sl]
         assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b) + 1e-12
+
+
+def test_tensor_core_wait_timeout_is_reported_and_recoverable():
+    """A bounded mbarrier wait that runs out (wait limit 0: no polls) makes the kernel
+    drain its MMAs, free its tensor memory and report SSTEP_ERR_TIMEOUT through
+    x0net_status; with the default limit restored the same network computes the
+    correct output again in the same CUDA context."""
+    net, theta, x, t, xd, td = setup(2, 16, 5, True)
+    out_ok = torch.empty((2, 1, 16, 16), dtype=torch.float32, device=xd.device)
+    net.forward(xd, out_ok)
+    net.status()
+    net.set_wait_limit(0)
+    out = torch.full((2, 1, 16, 16), float("nan"), dtype=torch.float32, device=xd.device)
+    net.forward(xd, out)
+    with pytest.raises(pkg.SStepError) as ei:
+        net.status()
+    assert ei.value.status == -6      # SSTEP_ERR_TIMEOUT
+    net.set_wait_limit(-1)
+    net.status()                      # the flag was cleared by the report
+    out2 = torch.empty_like(out_ok)
+    net.forward(xd, out2)
+    net.status()
+    assert torch.equal(out2, out_ok)
