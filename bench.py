@@ -305,7 +305,7 @@ def main():
         if method == "sstep":
             return pkg.sstep_gmres_solve(A, f, xv, kw.get("s", s), M, TOL, max_cycles=200, history_cap=8192,
                                          precision=kw.get("precision", args.precision),
-                                         basis=kw.get("basis", "monomial"))
+                                         basis=kw.get("basis", "monomial"), precond=kw.get("precond"))
         if method == "gmres":
             return pkg.gmres_solve(A, f, xv, M, TOL, max_cycles=200, history_cap=8192, precision=prec)
         return pkg.sstep_omin_solve(A, f, xv, kw["s"], kw["k"], TOL, max_iters=20000, history_cap=8192)
@@ -391,6 +391,8 @@ def main():
         for name, kw in [("sstep_gmres_s2", dict(method="sstep", s=2)), ("sstep_gmres_s4", dict(method="sstep", s=4)),
                          ("sstep_gmres_s8", dict(method="sstep", s=8)),
                          ("sstep_gmres_s8_newton", dict(method="sstep", s=8, basis="newton")),
+                         ("sstep_gmres_s4_rbilu0", dict(method="sstep", s=4, precond="rbilu0")),
+                         ("sstep_gmres_s8_rbilu0", dict(method="sstep", s=8, precond="rbilu0")),
                          ("gmres", dict(method="gmres")),
                          ("sstep_omin_s4_k1", dict(method="omin", s=4, k=1)),
                          ("omin_k1", dict(method="omin", s=1, k=1)), ("omin_k7", dict(method="omin", s=1, k=7)),

@@ -76,6 +76,11 @@ int stencil_matrix_destroy(sstep_matrix A);
 /* n (number of unknowns) and ||A||_inf (max absolute row sum). Host outputs. */
 int stencil_matrix_info(sstep_matrix A, int64_t* n, double* norm_inf);
 
+/* w = M^-1 v for the red-black ILU(0) of A (the preconditioner of SSTEP_PRECOND_RBILU0;
+ * its factor diagonal is built on first use and kept with A). v, w: DEVICE arrays of n,
+ * distinct. Stream-ordered. */
+int stencil_matrix_rbilu0_apply(sstep_matrix A, const double* v, double* w, void* stream);
+
 /* The Newton-basis shifts theta_1..theta_s of the last s-step GMRES solve on A with
  * basis = SSTEP_BASIS_NEWTON (HOST output, up to cap values). Returns their number (0
  * when the last solve kept the monomial powers), or SSTEP_ERR_ARG. */
@@ -187,10 +192,19 @@ typedef struct {
                            of the first cycle's Ritz values (eigenvalues of its Hessenberg G) in
                            Leja order. Same Krylov spaces, better-conditioned Gram blocks (Sec. 3
                            names such bases for large s). The batched solver is monomial only. */
+    int precond;        /* s-step GMRES, FP64 basis only (others: SSTEP_ERR_ARG):
+                           SSTEP_PRECOND_NONE;
+                           SSTEP_PRECOND_RBILU0: right preconditioning with ILU(0) in red-black
+                           ordering (the sparsity pattern of A, d~_b = a0_b - sum_r A[b,r] A[r,b] /
+                           a0_r); powers of A M^-1, x = x0 + M^-1 V y, true restart residual;
+                           sigma defaults to 1. The paper uses ILU(0) in the natural ordering. */
 } sstep_params;
 
 #define SSTEP_BASIS_MONOMIAL 0
 #define SSTEP_BASIS_NEWTON 1
+
+#define SSTEP_PRECOND_NONE 0
+#define SSTEP_PRECOND_RBILU0 1
 
 #define SSTEP_PREC_FP64 0
 #define SSTEP_PREC_DF64 1

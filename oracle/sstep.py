@@ -138,8 +138,18 @@ def block_update(Y, V, T):
 
 
 # ---------------------------------------------------------------- s-step GMRES
+class _RightPreconditioned:
+    """The operator A M^-1 (right preconditioning): apply(v) = A (M^-1 v)."""
+
+    def __init__(self, A, M):
+        self.A, self.M = A, M
+
+    def apply(self, v):
+        return self.A.apply(self.M.apply_inv(v))
+
+
 def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None, basis="monomial", shifts=None,
-                shift_rule=None):
+                shift_rule=None, precond=None):
     """Restarted s-step GMRES, Algorithm 4.2 over the s-step Arnoldi of Algorithm 4.1.
 
     Returns dict(x, status, cycles, iters, matvecs, history, relres, shifts); the
@@ -150,6 +160,9 @@ def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None, basis="
     Newton basis with the Leja-ordered real parts of the first cycle's Ritz values.
     `shifts` (test use): Newton shifts to apply from the first cycle on. `shift_rule`
     (test use): replaces newton_shifts(G, K, s) after the first cycle.
+    precond: an object with apply_inv(v) = M^-1 v (e.g. stencil.RedBlackILU0(A)): right
+    preconditioning, the s-step Arnoldi of A M^-1 and x = x0 + M^-1 V y; the restart
+    residual stays the true f - A x.
     """
     assert m % s == 0 and s >= 1
     n = f.shape[0]
@@ -160,6 +173,7 @@ def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None, basis="
     cycles = iters = mv = 0
     status = STATUS_NOT_CONVERGED
     shifts = None if shifts is None else list(shifts)
+    op = A if precond is None else _RightPreconditioned(A, precond)
     while True:
         r = f - A.apply(x)                                   # step 1 / step 5 (restart)
         mv += 1
@@ -180,7 +194,7 @@ def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None, basis="
         K = 0
         for k in range(nb):                                  # Algorithm 4.1, block k+1
             o = k * s
-            Y = matrix_powers(A, U[:, o], s, sigma, shifts=shifts)   # step 3: s products
+            Y = matrix_powers(op, U[:, o], s, sigma, shifts=shifts)   # step 3: s products
             mv += s
             T = np.zeros((o, s + 1))
             if o > 0:
@@ -242,7 +256,8 @@ def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None, basis="
             shifts = (shift_rule or newton_shifts)(G, K, s)
         if K > 0:
             y = lsq.solve()[:K] if lsq.j == K else lsq.solve()
-            x = x + U[:, : lsq.j] @ y                        # step 3: x_m = x_0 + V y
+            dx = U[:, : lsq.j] @ y                           # step 3: x_m = x_0 + V y
+            x = x + (dx if precond is None else precond.apply_inv(dx))
         if status == STATUS_BREAKDOWN:
             relres = norm(f - A.apply(x)) / nf
             break

@@ -116,3 +116,89 @@ def jacobi(A, f, x, sweeps, omega):
     for _ in range(sweeps):
         x = x + omega * (f - A.apply(x)) / d
     return x
+
+
+class RedBlackILU0:
+    """ILU(0) of a stencil operator in red-black ordering (red: x + y + z even).
+
+    Every neighbour of a point has the other colour, so with the red points first
+    A = [[D_r, E], [F, D_b]] with diagonal D_r, D_b. ILU(0) keeps the sparsity of A:
+    L = [[I, 0], [F D_r^-1, I]], U = [[D_r, E], [0, D~_b]], and the black diagonal
+    D~_b = D_b - diag(F D_r^-1 E) is the only entry that changes (the off-diagonal part of
+    F D_r^-1 E, between black points two steps apart, is the dropped fill). Applying
+    M^-1 = (L U)^-1: w_b = (v_b - sum_r A[b, r] v_r / a0_r) / d~_b for black points, then
+    w_r = (v_r - sum_b A[r, b] w_b) / a0_r for red points. (The paper's tables use ILU(0)
+    in the natural ordering; this ordering has the same sparsity and two parallel
+    half-sweeps instead of 3N - 2 sequential hyperplanes per triangular solve.)
+    """
+
+    def __init__(self, A):
+        self.A = A
+        sh = A.shape[::-1]                         # numpy axes (z, y, x) / (y, x)
+        grids = np.indices(sh)
+        self.black = (grids.sum(axis=0) % 2 == 1).reshape(-1)
+        a0 = np.broadcast_to(A._coef(A.a0), sh).reshape(-1).astype(np.float64)
+        self.a0 = a0.copy()
+        # d~_b = a0_b - sum over neighbours r of A[b, r] A[r, b] / a0_r
+        dt = a0.copy()
+        for (ax, coef_b, coef_r, step) in self._couplings():
+            dt -= coef_b * self._shift(coef_r / a0.reshape(sh), ax, step).reshape(-1)
+        self.dtilde = np.where(self.black, dt, a0)
+
+    def _couplings(self):
+        # (axis, A[b, b + step e_d] as an array over b, A[r, r - step e_d] over r, step)
+        A = self.A
+        sh = A.shape[::-1]
+        out = []
+        for d in range(A.dim):
+            ax = A._axis(d)
+            am = np.broadcast_to(A._coef(A.am[d]), sh)
+            ap = np.broadcast_to(A._coef(A.ap[d]), sh)
+            # neighbour r = b - e_d: A[b, r] = am_d(b); A[r, b] = ap_d(r)
+            out.append((ax, self._mask(am, ax, -1).reshape(-1), ap, -1))
+            # neighbour r = b + e_d: A[b, r] = ap_d(b); A[r, b] = am_d(r)
+            out.append((ax, self._mask(ap, ax, +1).reshape(-1), am, +1))
+        return out
+
+    @staticmethod
+    def _shift(X, ax, step):
+        """Y[p] = X[p + step e_ax] (zero outside the grid)."""
+        Y = np.zeros_like(X, dtype=np.float64)
+        src = [slice(None)] * X.ndim
+        dst = [slice(None)] * X.ndim
+        if step > 0:
+            src[ax], dst[ax] = slice(1, None), slice(None, -1)
+        else:
+            src[ax], dst[ax] = slice(None, -1), slice(1, None)
+        Y[tuple(dst)] = X[tuple(src)]
+        return Y
+
+    @staticmethod
+    def _mask(C, ax, step):
+        """C where the neighbour p + step e_ax exists, else 0."""
+        M = np.array(C, dtype=np.float64, copy=True)
+        idx = [slice(None)] * M.ndim
+        idx[ax] = -1 if step > 0 else 0
+        M[tuple(idx)] = 0.0
+        return M
+
+    def apply_inv(self, v):
+        """w = M^-1 v."""
+        A = self.A
+        sh = A.shape[::-1]
+        v = np.asarray(v, dtype=np.float64)
+        red_v = np.where(self.black, 0.0, v)
+        # black: w_b = (v_b - sum_r A[b, r] v_r / a0_r) / d~_b
+        t = np.zeros(A.n)
+        for (ax, coef_b, coef_r, step) in self._couplings():
+            t += coef_b * self._shift((red_v / self.a0).reshape(sh), ax, step).reshape(-1)
+        w = np.where(self.black, (v - t) / self.dtilde, 0.0)
+        # red: w_r = (v_r - sum_b A[r, b] w_b) / a0_r, with A[r, b] the row-r coefficient of b
+        s = np.zeros(A.n)
+        for d in range(A.dim):
+            ax = A._axis(d)
+            am = self._mask(np.broadcast_to(A._coef(A.am[d]), sh), ax, -1)
+            ap = self._mask(np.broadcast_to(A._coef(A.ap[d]), sh), ax, +1)
+            W = w.reshape(sh)
+            s += (am * self._shift(W, ax, -1) + ap * self._shift(W, ax, +1)).reshape(-1)
+        return np.where(self.black, w, (v - s) / self.a0)

@@ -21,7 +21,7 @@ P = ctypes.POINTER
 class SStepParams(ctypes.Structure):
     _fields_ = [("s", c_int), ("m", c_int), ("k", c_int), ("tol", c_double), ("max_cycles", c_int),
                 ("max_iters", c_int), ("sigma", c_double), ("history", P(c_double)), ("history_cap", c_int),
-                ("precision", c_int), ("x0_guard", c_int), ("basis", c_int)]
+                ("precision", c_int), ("x0_guard", c_int), ("basis", c_int), ("precond", c_int)]
 
 
 PRECISIONS = {"fp64": 0, "df64": 1, "fp32": 2}
@@ -42,6 +42,7 @@ SIGNATURES = {
     "stencil_matrix_info": (c_int, [c_void_p, P(c_int64), P(c_double)]),
     "stencil_matrix_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "sstep_last_shifts": (c_int, [c_void_p, P(c_double), c_int]),
+    "stencil_matrix_rbilu0_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "sstep_newton_shifts": (c_int, [P(c_double), c_int, c_int, c_int, P(c_double)]),
     "sstep_set_workspace_limit": (c_int, [c_int64]),
     "stencil_matrix_smooth": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_void_p]),
@@ -193,6 +194,11 @@ class StencilMatrix:
     def apply(self, x, y, stream=None):
         return stencil_matrix_apply(self, x, y, stream)
 
+    def rbilu0_apply(self, v, w, stream=None):
+        """w = M^-1 v, M the red-black ILU(0) of this operator."""
+        return _check("stencil_matrix_rbilu0_apply",
+                      lib().stencil_matrix_rbilu0_apply(self.handle, _ptr(v), _ptr(w), _stream(stream)))
+
     def smooth(self, f, x, work, sweeps, omega, stream=None):
         return stencil_matrix_smooth(self, f, x, work, sweeps, omega, stream)
 
@@ -285,17 +291,18 @@ def sstep_block_update(V, Y, T, work=None, stream=None):
 
 
 BASES = {"monomial": 0, "newton": 1}
+PRECONDS = {None: 0, "none": 0, "rbilu0": 1}
 
 
 def _solve(name, A, f, x, s=1, m=20, k=1, tol=1e-8, max_cycles=1000, max_iters=100000, sigma=0.0,
-           history_cap=4096, stream=None, precision="fp64", x0_guard=False, basis="monomial"):
+           history_cap=4096, stream=None, precision="fp64", x0_guard=False, basis="monomial", precond=None):
     import numpy as np
 
     hist = np.zeros(max(history_cap, 1), dtype=np.float64)
     p = SStepParams(s=s, m=m, k=k, tol=tol, max_cycles=max_cycles, max_iters=max_iters, sigma=sigma,
                     history=hist.ctypes.data_as(P(c_double)) if history_cap > 0 else None,
                     history_cap=history_cap, precision=PRECISIONS[precision], x0_guard=1 if x0_guard else 0,
-                    basis=BASES[basis])
+                    basis=BASES[basis], precond=PRECONDS[precond])
     r = SStepResult()
     rc = getattr(lib(), name)(A.handle, _ptr(f), _ptr(x), ctypes.byref(p), ctypes.byref(r), _stream(stream))
     _check(name, rc)
@@ -304,15 +311,17 @@ def _solve(name, A, f, x, s=1, m=20, k=1, tol=1e-8, max_cycles=1000, max_iters=1
 
 
 def sstep_gmres_solve(A, f, x, s, m, tol, max_cycles=1000, sigma=0.0, history_cap=4096, stream=None,
-                      precision="fp64", x0_guard=False, basis="monomial"):
+                      precision="fp64", x0_guard=False, basis="monomial", precond=None):
     """s-step GMRES (Alg. 4.1/4.2); x is updated in place. Returns the result as a dict
     (with "shifts": the Newton-basis shifts used, empty for the monomial basis).
 
     precision: "fp64", "df64" (double-float basis) or "fp32" (FP32 basis, FP32 iterative refinement).
     basis: "monomial" (as printed) or "newton" (shifts from the first cycle's Ritz values).
+    precond: None or "rbilu0" (right ILU(0) in red-black ordering; FP64 basis).
     """
     r = _solve("sstep_gmres_solve", A, f, x, s=s, m=m, tol=tol, max_cycles=max_cycles, sigma=sigma,
-               history_cap=history_cap, stream=stream, precision=precision, x0_guard=x0_guard, basis=basis)
+               history_cap=history_cap, stream=stream, precision=precision, x0_guard=x0_guard, basis=basis,
+               precond=precond)
     buf = (c_double * SSTEP_MAX_S)()
     cnt = _check("sstep_last_shifts", lib().sstep_last_shifts(A.handle, buf, SSTEP_MAX_S))
     r["shifts"] = list(buf[:cnt])

@@ -23,6 +23,7 @@ using namespace sstep;
 struct sstep_matrix_s {
     StencilDesc A;
     std::vector<double> shifts;      // Newton-basis shifts of the last s-step GMRES solve (host)
+    double* rbilu = nullptr;         // red-black ILU(0): d~ at black points (device, n), built on first use
     double norm_inf = 0.0;
     double* fields = nullptr;        // owned copies of variable coefficients (7 x n)
     float2* fields_df = nullptr;     // the same as float pairs (mixed-precision kernels)
@@ -203,9 +204,10 @@ bool fused_powers_enabled() {
 // Every launch is counted; when tracing is on, a pair of CUDA events brackets each
 // launch on its own stream and the elapsed times are summed per kernel kind at the
 // end of the call that issued them.
-enum Kind { K_STENCIL = 0, K_RESIDUAL, K_GRAM, K_UPDATE, K_NEXT, K_AXPY, K_OMIN_XR, K_OMIN_PUPDATE, K_LSQ, K_COUNT };
+enum Kind { K_STENCIL = 0, K_RESIDUAL, K_GRAM, K_UPDATE, K_NEXT, K_AXPY, K_OMIN_XR, K_OMIN_PUPDATE, K_LSQ, K_PRECOND,
+            K_COUNT };
 const char* const kKindNames[K_COUNT] = {"stencil_powers", "residual", "gram", "block_update", "next_vector",
-                                         "basis_axpy", "omin_xr", "omin_pupdate", "lsq_solve"};
+                                         "basis_axpy", "omin_xr", "omin_pupdate", "lsq_solve", "precond"};
 struct Tracer {
     bool on = false;
     unsigned mask = ~0u;          // kinds that get event pairs
@@ -861,6 +863,7 @@ int stencil_matrix_destroy(sstep_matrix M) {
     if (M->fields_df) cudaFree(M->fields_df);
     if (M->ws) cudaFree(M->ws);
     if (M->hdr) cudaFreeHost(M->hdr);
+    if (M->rbilu) cudaFree(M->rbilu);
     delete M;
     return SSTEP_OK;
 }
@@ -942,6 +945,21 @@ int sstep_newton_shifts(const double* G, int ldg, int K, int s, double* theta) {
     return SSTEP_OK;
 }
 
+int stencil_matrix_rbilu0_apply(sstep_matrix M, const double* v, double* w, void* stream) {
+    if (!M || !v || !w || v == w) return SSTEP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!M->rbilu) {
+        if (cudaMalloc((void**)&M->rbilu, sizeof(double) * M->A.n) != cudaSuccess) {
+            cudaGetLastError();
+            M->rbilu = nullptr;
+            return SSTEP_ERR_OOM;
+        }
+        launch_rbilu_setup(M->A, M->rbilu, st);
+    }
+    launch_rbilu_apply(M->A, M->rbilu, v, w, nullptr, GATE_NONE, st);
+    return check_launch();
+}
+
 int sstep_last_shifts(sstep_matrix M, double* theta, int cap) {
     if (!M || cap < 0 || (cap > 0 && !theta)) return SSTEP_ERR_ARG;
     const int n = (int)M->shifts.size();
@@ -1012,19 +1030,32 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     const int s = p->s, m = p->m;
     if (s < 1 || s > SSTEP_MAX_S || m < s || m > SSTEP_MAX_M || m % s != 0 || p->max_cycles < 0) return SSTEP_ERR_ARG;
     if (p->basis != SSTEP_BASIS_MONOMIAL && p->basis != SSTEP_BASIS_NEWTON) return SSTEP_ERR_ARG;
+    if (p->precond != SSTEP_PRECOND_NONE && (p->precond != SSTEP_PRECOND_RBILU0 || p->precision != SSTEP_PREC_FP64))
+        return SSTEP_ERR_ARG;
+    const bool pre = p->precond == SSTEP_PRECOND_RBILU0;
     cudaStream_t stream_ = (cudaStream_t)stream;
     if (p->precision == SSTEP_PREC_DF64) return sstep_gmres_mp<PREC_DF64>(M, f, x, p, res, stream_);
     if (p->precision == SSTEP_PREC_FP32) return sstep_gmres_mp<PREC_FP32>(M, f, x, p, res, stream_);
     if (p->precision != SSTEP_PREC_FP64) return SSTEP_ERR_ARG;
     const int64_t n = M->A.n, ld = col_ld(n);
-    // columns: U (m+1) and the raw start vector
-    Layout l = plan(n, m + 2, m, p->history ? p->history_cap : 0);
+    // columns: U (m+1), the raw start vector and, preconditioned, M^-1 of a power
+    Layout l = plan(n, m + 2 + (pre ? 1 : 0), m, p->history ? p->history_cap : 0);
     if ((rc = ensure_workspace(M, l.total))) return rc;
+    if (pre && !M->rbilu) {   // d~ of the red-black ILU(0), once per matrix
+        if (cudaMalloc((void**)&M->rbilu, sizeof(double) * n) != cudaSuccess) {
+            cudaGetLastError();
+            M->rbilu = nullptr;
+            return SSTEP_ERR_OOM;
+        }
+        launch_rbilu_setup(M->A, M->rbilu, stream_);
+    }
     SolverState h = init_state(l, M->ws, p, s, m, 0);
-    h.sigma = p->sigma > 0.0 ? p->sigma : 1.0 / M->norm_inf;
+    // sigma: 1 / ||A||_inf; preconditioned, A M^-1 has its spectrum near 1 and sigma = 1
+    h.sigma = p->sigma > 0.0 ? p->sigma : (pre ? 1.0 : 1.0 / M->norm_inf);
     SolverState* st = (SolverState*)(M->ws + l.state);
     double* U = (double*)(M->ws + l.cols);
     double* uraw = U + (int64_t)(m + 1) * ld;
+    double* ptmp = U + (int64_t)(m + 2) * ld;   // preconditioned: M^-1 y^j, then V y
     Scratch sc{(double*)(M->ws + l.partials), (unsigned*)(M->ws + l.counter)};
     CUDA_TRY(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
     CUDA_TRY(cudaMemsetAsync(M->ws + l.counter, 0, kAlign, stream_));
@@ -1048,11 +1079,22 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
         for (int k = 0; k < nb; ++k) {
             const int o = k * s;
             // Alg. 4.1 step 3: v_k^1 = u / ||u|| and its s scaled powers
-            TRACED(K_STENCIL, stream_, launch_stencil(M->A, uraw, sigma, U + (o + 1) * ld, 1.0, U + o * ld,
-                                                      &st->vscale, st, GATE_BUILDING, stream_, theta[0]));
-            for (int j = 2; j <= s; ++j)
-                TRACED(K_STENCIL, stream_, launch_stencil(M->A, U + (o + j - 1) * ld, sigma, U + (o + j) * ld, 0.0,
-                                                          nullptr, nullptr, st, GATE_BUILDING, stream_, theta[j - 1]));
+            if (!pre) {
+                TRACED(K_STENCIL, stream_, launch_stencil(M->A, uraw, sigma, U + (o + 1) * ld, 1.0, U + o * ld,
+                                                          &st->vscale, st, GATE_BUILDING, stream_, theta[0]));
+                for (int j = 2; j <= s; ++j)
+                    TRACED(K_STENCIL, stream_, launch_stencil(M->A, U + (o + j - 1) * ld, sigma, U + (o + j) * ld, 0.0,
+                                                              nullptr, nullptr, st, GATE_BUILDING, stream_, theta[j - 1]));
+            } else {   // right preconditioning: y^{j+1} = sigma (A M^-1 y^j - theta_j y^j)
+                launch_scale_copy(uraw, U + o * ld, n, &st->vscale, st, GATE_BUILDING, stream_);
+                for (int j = 1; j <= s; ++j) {
+                    TRACED(K_PRECOND, stream_, launch_rbilu_apply(M->A, M->rbilu, U + (o + j - 1) * ld, ptmp, st,
+                                                                  GATE_BUILDING, stream_));
+                    TRACED(K_STENCIL, stream_, launch_stencil(M->A, ptmp, sigma, U + (o + j) * ld, 0.0, nullptr,
+                                                              nullptr, st, GATE_BUILDING, stream_, theta[j - 1],
+                                                              U + (o + j - 1) * ld));
+                }
+            }
             if (k > 0) {   // steps 4-5 and Scalar2: inner products with the earlier blocks
                 e = Epi();
                 e.st = st;
@@ -1080,7 +1122,16 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
         TRACED(K_LSQ, stream_, launch_lsq_solve(st, GATE_ACTIVE, stream_));
         e = Epi();
         e.st = st;
-        TRACED(K_AXPY, stream_, launch_update(n, U, ld, -1, x, n, x, n, 1, 0, nullptr, 0, 1.0, false, sc, e, GATE_ACTIVE, stream_));
+        if (!pre) {
+            TRACED(K_AXPY, stream_, launch_update(n, U, ld, -1, x, n, x, n, 1, 0, nullptr, 0, 1.0, false, sc, e,
+                                                  GATE_ACTIVE, stream_));
+        } else {   // x += M^-1 (V y)
+            CUDA_TRY(cudaMemsetAsync(ptmp, 0, sizeof(double) * n, stream_));
+            TRACED(K_AXPY, stream_, launch_update(n, U, ld, -1, ptmp, ld, ptmp, ld, 1, 0, nullptr, 0, 1.0, false, sc,
+                                                  e, GATE_ACTIVE, stream_));
+            TRACED(K_PRECOND, stream_, launch_rbilu_apply(M->A, M->rbilu, ptmp, uraw, st, GATE_ACTIVE, stream_));
+            launch_add(x, uraw, n, st, GATE_ACTIVE, stream_);
+        }
         CUDA_TRY(cudaGetLastError());
         if ((rc = read_header(M, st, stream_))) return rc;
         if (!M->hdr->active) break;
@@ -1101,7 +1152,7 @@ int gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_params* 
     int rc = common_checks(M, f, x, p, res);
     if (rc) return rc;
     const int m = p->m;
-    if (m < 1 || m > SSTEP_MAX_M || p->max_cycles < 0) return SSTEP_ERR_ARG;
+    if (m < 1 || m > SSTEP_MAX_M || p->max_cycles < 0 || p->precond != SSTEP_PRECOND_NONE) return SSTEP_ERR_ARG;
     cudaStream_t stream_ = (cudaStream_t)stream;
     if (p->precision == SSTEP_PREC_DF64) return gmres_mp<PREC_DF64>(M, f, x, p, res, stream_);
     if (p->precision == SSTEP_PREC_FP32) return gmres_mp<PREC_FP32>(M, f, x, p, res, stream_);
@@ -1163,7 +1214,7 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
     if (rc) return rc;
     const int s = p->s, k = p->k;
     if (s < 1 || s > SSTEP_MAX_S || k < 0 || (int64_t)k * s > SSTEP_MAX_COLS || p->max_iters < 0) return SSTEP_ERR_ARG;
-    if (p->precision != SSTEP_PREC_FP64) return SSTEP_ERR_ARG;
+    if (p->precision != SSTEP_PREC_FP64 || p->precond != SSTEP_PRECOND_NONE) return SSTEP_ERR_ARG;
     cudaStream_t stream_ = (cudaStream_t)stream;
     const int64_t n = M->A.n, ld = col_ld(n);
     const int keep = std::max(k, 1);
@@ -1251,7 +1302,8 @@ int sstep_batch_create(sstep_batch* out, int nsys, const sstep_matrix* A, const 
     *out = nullptr;
     const int s = p->s, m = p->m;
     if (!(s == 1 || s == 2 || s == 4 || s == 8) || m < s || m > kBatchMaxM || m % s || p->max_cycles < 0 ||
-        !(p->tol > 0.0) || p->sigma < 0.0 || p->precision != SSTEP_PREC_FP64 || p->basis != SSTEP_BASIS_MONOMIAL)
+        !(p->tol > 0.0) || p->sigma < 0.0 || p->precision != SSTEP_PREC_FP64 || p->basis != SSTEP_BASIS_MONOMIAL ||
+        p->precond != SSTEP_PRECOND_NONE)
         return SSTEP_ERR_ARG;
     for (int i = 0; i < nsys; ++i)
         if (!A[i]) return SSTEP_ERR_ARG;

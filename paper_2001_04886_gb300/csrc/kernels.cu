@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
                                                            double fy, double* __restrict__ y, double fw,
                                                            double* __restrict__ w, const double* dscale,
                                                            const SolverState* st, int gate, int zchunk,
-                                                           double shift) {
+                                                           double shift, const double* __restrict__ u) {
     if (!gate_open(st, gate)) return;
     if (dscale) {
         const double d = *dscale;
@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
     double c[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) c[q] = fy * A.c[q];
-    c[0] = fy * (A.c[0] - shift);
+    if (!u) c[0] = fy * (A.c[0] - shift);
+    const double fs = -fy * shift;   // with u: the shift term -fy shift u_p
     double vm = (three && zb > 0) ? __ldg(v + p - pl) : 0.0;
     double vc = __ldg(v + p);
 #pragma unroll 2
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
                 if (z < A.nz - 1) acc = fma(c[6], vp, acc);
             }
         } else {
-            acc = (__ldg(A.f[0] + p) - shift) * vc;
+            acc = (__ldg(A.f[0] + p) - (u ? 0.0 : shift)) * vc;
             if (x > 0) acc = fma(__ldg(A.f[1] + p), __ldg(v + p - 1), acc);
             if (x < A.nx - 1) acc = fma(__ldg(A.f[2] + p), __ldg(v + p + 1), acc);
             if (yy > 0) acc = fma(__ldg(A.f[3] + p), __ldg(v + p - A.nx), acc);
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
             }
             acc *= fy;
         }
+        if (u) acc = fma(fs, __ldg(u + p), acc);
         y[p] = acc;
         if (w) w[p] = fw * vc;
         vm = vc;
@@ -87,7 +89,8 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
 }
 
 void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y, double fw, double* w,
-                    const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift) {
+                    const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift,
+                    const double* u) {
     const int tiles = ((A.nx + 31) / 32) * ((A.ny + 7) / 8);
     // z chunks: about one wave of 8 CTAs per SM, at least one plane per chunk
     int chunks = kMaxCtas / tiles;
@@ -95,7 +98,7 @@ void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y,
     const int zchunk = (A.nz + chunks - 1) / chunks;
     chunks = (A.nz + zchunk - 1) / zchunk;
     stencil_kernel<<<dim3(tiles, chunks), dim3(32, 8), 0, stream>>>(A, v, fy, y, fw, w, dscale, st, gate, zchunk,
-                                                                    shift);
+                                                                    shift, u);
 }
 
 // ================================================================== residual

@@ -50,9 +50,11 @@ __device__ __forceinline__ bool gate_open(const SolverState* st, int gate) {
 
 // ------------------------------------------------------------------ launchers (kernels.cu)
 // y = fy * (A v), w = fw * v (if w); fy and fw are multiplied by *dscale when dscale is set.
-// y = fy (A - shift I) v; w = fw v when w is set (shift: the Newton basis, 0 otherwise)
+// y = fy (A v - shift u) with u = v unless given; w = fw v when w is set (shift: the
+// Newton basis, 0 otherwise; u: the unpreconditioned power when v = M^-1 u)
 void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y, double fw, double* w,
-                    const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift = 0.0);
+                    const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift = 0.0,
+                    const double* u = nullptr);
 
 // r = f - A x (x may be null: r = f); out (may be null) receives r; reduces ||r||^2.
 void launch_residual(const StencilDesc& A, const double* f, const double* x, double* out, Scratch sc,
@@ -88,6 +90,14 @@ int max_partials_doubles();
 // out = [a0 | am_x | ap_x | am_y | ap_y] (5 arrays of n) for -Lap u + beta (u_x + u_y):
 // a0 = 4, am = -1 - beta h/2, ap = -1 + beta h/2
 void launch_convdiff_fields(const double* beta, double h, int64_t n, double* out, cudaStream_t stream);
+// red-black ILU(0) right preconditioner (precond.cu): setup of d~, w = M^-1 v (w != v),
+// dst = *dscale src, x += d
+void launch_rbilu_setup(const StencilDesc& A, double* dt, cudaStream_t s);
+void launch_rbilu_apply(const StencilDesc& A, const double* dt, const double* v, double* w, const SolverState* st,
+                        int gate, cudaStream_t s);
+void launch_scale_copy(const double* src, double* dst, int64_t n, const double* dscale, const SolverState* st,
+                       int gate, cudaStream_t s);
+void launch_add(double* x, const double* d, int64_t n, const SolverState* st, int gate, cudaStream_t s);
 // damped Jacobi sweep y = x + omega (f - A x) / a0 (smooth.cu)
 void launch_jacobi(const StencilDesc& A, const double* f, const double* x, double* y, double omega,
                    cudaStream_t stream);

@@ -51,8 +51,8 @@ def test_params_struct_layout_matches_header():
     P = _binding.SStepParams
     assert P.tol.offset == 16 and P.sigma.offset == 32 and P.history.offset == 40
     assert P.history_cap.offset == 48 and P.precision.offset == 52 and P.x0_guard.offset == 56
-    assert P.basis.offset == 60
-    assert ctypes.sizeof(P) == 64
+    assert P.basis.offset == 60 and P.precond.offset == 64
+    assert ctypes.sizeof(P) == 72
     assert ctypes.sizeof(_binding.SStepResult) == 32
 
 
