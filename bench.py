@@ -91,10 +91,11 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32"],
                     help="basis precision of the headline solve")
     ap.add_argument("--no-variants", action="store_true", help="the headline solve only")
-    ap.add_argument("--variants", default="solvers,precision,batched",
+    ap.add_argument("--variants", default="solvers,precision,batched,paper",
                     help="comma list of the extra measurements: solvers (s = 2/4/8, GMRES, Orthomin, "
-                         "mixed-precision bases), precision (the 256^3 FP32-refinement form), batched "
-                         "(512 systems), learned (the learned initial guess; minutes)")
+                         "mixed-precision bases, Newton basis, red-black ILU(0)), precision (the 256^3 "
+                         "FP32-refinement form), batched (512 systems), paper (the paper's test problem, "
+                         "Sec. 5), learned (the learned initial guess; minutes)")
     ap.add_argument("--learned", action="store_true", help="add 'learned' to --variants")
     ap.add_argument("--learned-train", type=int, default=20000)
     ap.add_argument("--learned-test", type=int, default=1000)
@@ -470,6 +471,39 @@ def main():
         variants["batched_512_s4_m20"] = out
         Bs.close()
         del mats, fs, xs
+
+    if "paper" in args.groups:
+        # the paper's test problem (Sec. 5): variable coefficients, gamma = 50, beta = 1,
+        # the paper's initial guess, to 1e-8 relative; Table 6.1's settings: GMRES(10),
+        # 2-step GMRES(10) (the paper's 2-GMRES(5): m = 10 Krylov vectors per cycle), Omin(4)
+        # and 2-step Omin(2); GMRES with red-black ILU(0) (the paper: natural-ordering ILU(0))
+        paper = {}
+        for Np in (64, 128, 192, 256):
+            Pp = inputs.paper_problem(Np)
+            Ap = pkg.StencilMatrix(2, (Np, Np), fields=[torch.tensor(c, device=dev) for c in Pp["coef"]])
+            gp = torch.tensor(Pp["g"], device=dev)
+            row = {}
+            for name, kw in (("gmres10_rbilu0", dict(s=1, m=10, precond="rbilu0")),
+                             ("sstep2_gmres10_rbilu0", dict(s=2, m=10, precond="rbilu0")),
+                             ("sstep2_gmres10", dict(s=2, m=10)),
+                             ("omin4", dict(omin=True, s=1, k=4)), ("sstep2_omin2", dict(omin=True, s=2, k=2))):
+                xp = torch.tensor(Pp["x0"], device=dev)
+                for rep in range(2):
+                    xp.copy_(torch.tensor(Pp["x0"], device=dev))
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    if kw.get("omin"):
+                        rp = pkg.sstep_omin_solve(Ap, gp, xp, kw["s"], kw["k"], TOL, max_iters=100000, history_cap=0)
+                    else:
+                        rp = pkg.sstep_gmres_solve(Ap, gp, xp, kw["s"], kw["m"], TOL, max_cycles=20000, history_cap=0,
+                                                   precond=kw.get("precond"))
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                row[name] = {"ms": e0.elapsed_time(e1), "status": rp["status"], "cycles": rp["cycles"],
+                             "iters": rp["iters"], "matvecs": rp["matvecs"],
+                             "max_err_vs_analytic_u": float((xp - torch.tensor(Pp["u"], device=dev)).abs().max())}
+            paper[str(Np)] = row
+        variants["paper_problem_sec5"] = paper
 
     if "learned" in args.groups:
         from paper_2001_04886_gb300 import learned

@@ -23,7 +23,7 @@ using namespace sstep;
 struct sstep_matrix_s {
     StencilDesc A;
     std::vector<double> shifts;      // Newton-basis shifts of the last s-step GMRES solve (host)
-    double* rbilu = nullptr;         // red-black ILU(0): d~ at black points (device, n), built on first use
+    double* rbilu = nullptr;         // red-black ILU(0) reciprocal pivots (device, n), built on first use
     double norm_inf = 0.0;
     double* fields = nullptr;        // owned copies of variable coefficients (7 x n)
     float2* fields_df = nullptr;     // the same as float pairs (mixed-precision kernels)

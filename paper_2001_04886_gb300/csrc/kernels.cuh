@@ -90,7 +90,8 @@ int max_partials_doubles();
 // out = [a0 | am_x | ap_x | am_y | ap_y] (5 arrays of n) for -Lap u + beta (u_x + u_y):
 // a0 = 4, am = -1 - beta h/2, ap = -1 + beta h/2
 void launch_convdiff_fields(const double* beta, double h, int64_t n, double* out, cudaStream_t stream);
-// red-black ILU(0) right preconditioner (precond.cu): setup of d~, w = M^-1 v (w != v),
+// red-black ILU(0) right preconditioner (precond.cu): setup of the reciprocal pivots
+// (1/d~ at black points, 1/a0 at red points), w = M^-1 v (w != v),
 // dst = *dscale src, x += d
 void launch_rbilu_setup(const StencilDesc& A, double* dt, cudaStream_t s);
 void launch_rbilu_apply(const StencilDesc& A, const double* dt, const double* v, double* w, const SolverState* st,

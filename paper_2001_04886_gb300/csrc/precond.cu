@@ -37,7 +37,9 @@ __device__ __forceinline__ void xyz(const StencilDesc& A, int64_t p, int& x, int
 
 }  // namespace
 
-// d~ at black points (a0 elsewhere): a0_b - sum_r A[b, r] A[r, b] / a0_r
+// The reciprocal pivots: 1 / d~_b at black points, d~_b = a0_b - sum_r A[b, r] A[r, b] / a0_r,
+// and 1 / a0_r at red points (the sweeps then multiply instead of divide: an FP64
+// division costs many FP64 FMAs on this part)
 __global__ void __launch_bounds__(kThreads) rbilu_setup_kernel(StencilDesc A, double* __restrict__ dt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.n; p += stride) {
@@ -50,12 +52,12 @@ __global__ void __launch_bounds__(kThreads) rbilu_setup_kernel(StencilDesc A, do
                 if (r >= 0) d -= coef(A, q, p) * coef(A, opposite(q), r) / coef(A, 0, r);
             }
         }
-        dt[p] = d;
+        dt[p] = 1.0 / d;
     }
 }
 
-// black points: w_b = (v_b - sum_r A[b, r] v_r / a0_r) / d~_b
-__global__ void __launch_bounds__(kThreads) rbilu_black_kernel(StencilDesc A, const double* __restrict__ dt,
+// black points: w_b = (v_b - sum_r A[b, r] v_r / a0_r) / d~_b, with rp = the reciprocal pivots
+__global__ void __launch_bounds__(kThreads) rbilu_black_kernel(StencilDesc A, const double* __restrict__ rp,
                                                                const double* __restrict__ v, double* __restrict__ w,
                                                                const SolverState* st, int gate) {
     if (!gate_open(st, gate)) return;
@@ -67,15 +69,16 @@ __global__ void __launch_bounds__(kThreads) rbilu_black_kernel(StencilDesc A, co
         double t = __ldg(v + p);
         for (int q = 1; q <= 2 * A.dim; ++q) {
             const int64_t r = nbr(A, p, x, y, z, q);
-            if (r >= 0) t -= coef(A, q, p) * __ldg(v + r) / coef(A, 0, r);
+            if (r >= 0) t = fma(-coef(A, q, p), __ldg(v + r) * __ldg(rp + r), t);
         }
-        w[p] = t / __ldg(dt + p);
+        w[p] = t * __ldg(rp + p);
     }
 }
 
 // red points: w_r = (v_r - sum_b A[r, b] w_b) / a0_r (w holds the black results)
-__global__ void __launch_bounds__(kThreads) rbilu_red_kernel(StencilDesc A, const double* __restrict__ v,
-                                                             double* w, const SolverState* st, int gate) {
+__global__ void __launch_bounds__(kThreads) rbilu_red_kernel(StencilDesc A, const double* __restrict__ rp,
+                                                             const double* __restrict__ v, double* w,
+                                                             const SolverState* st, int gate) {
     if (!gate_open(st, gate)) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.n; p += stride) {
@@ -85,9 +88,9 @@ __global__ void __launch_bounds__(kThreads) rbilu_red_kernel(StencilDesc A, cons
         double t = __ldg(v + p);
         for (int q = 1; q <= 2 * A.dim; ++q) {
             const int64_t b = nbr(A, p, x, y, z, q);
-            if (b >= 0) t -= coef(A, q, p) * w[b];
+            if (b >= 0) t = fma(-coef(A, q, p), w[b], t);
         }
-        w[p] = t / coef(A, 0, p);
+        w[p] = t * __ldg(rp + p);
     }
 }
 
@@ -117,7 +120,7 @@ void launch_rbilu_apply(const StencilDesc& A, const double* dt, const double* v,
                         int gate, cudaStream_t s) {
     const int grid = grid_for(A.n, 152 * 8);
     rbilu_black_kernel<<<grid, kThreads, 0, s>>>(A, dt, v, w, st, gate);
-    rbilu_red_kernel<<<grid, kThreads, 0, s>>>(A, v, w, st, gate);
+    rbilu_red_kernel<<<grid, kThreads, 0, s>>>(A, dt, v, w, st, gate);
 }
 
 void launch_scale_copy(const double* src, double* dst, int64_t n, const double* dscale, const SolverState* st,

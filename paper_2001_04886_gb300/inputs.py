@@ -95,3 +95,49 @@ def fourier_fields(seed: int, N: int, modes: int = 8):
         b, p, r = st.uniform(3)
         f += (2.0 * b - 1.0) * np.sin(np.pi * (1 + math.floor(4 * p)) * X) * np.sin(np.pi * (1 + math.floor(4 * r)) * Yc)
     return beta.reshape(-1), (h * h) * f.reshape(-1)
+
+
+def paper_problem(N: int, gamma: float = 50.0, beta: float = 1.0):
+    """The test problem of Sec. 5 on an N x N interior grid (h = 1/(N+1), x fastest):
+
+        -(b u_x)_x - (c u_y)_y + (d u)_x + (e u)_y + f u = g  on (0,1)^2, u = 0 on the boundary,
+        b = exp(-xy), c = exp(xy), d = beta (x + y), e = gamma (x + y), f = 1 / (1 + xy),
+
+    with g made from the analytic solution u = x exp(xy) sin(pi x) sin(pi y) (the printed
+    sin(pi y) sin(pi y) read as sin(pi x) sin(pi y), which vanishes on the boundary).
+    Five-point differences in conservative form for the diffusion terms (b, c at the cell
+    faces), centred differences of the products d u and e u; every row scaled by h^2.
+
+    Returns dict(coef=[a0, a_west, a_east, a_south, a_north] (n each), g (h^2 g at the
+    nodes), u (analytic u at the nodes), x0 (the paper's initial guess x_i = 0.05 mod(i, 50),
+    i = 1..n)). Generator of input data only: no arithmetic of the solvers.
+    """
+    h = 1.0 / (N + 1)
+    t = (np.arange(N) + 1) * h
+    X, Y = np.meshgrid(t, t)                       # rows: y, columns: x (x fastest)
+    b = lambda x, y: np.exp(-x * y)
+    c = lambda x, y: np.exp(x * y)
+    d = lambda x, y: beta * (x + y)
+    e = lambda x, y: gamma * (x + y)
+    bw, be = b(X - h / 2, Y), b(X + h / 2, Y)
+    cs, cn = c(X, Y - h / 2), c(X, Y + h / 2)
+    a0 = bw + be + cs + cn + h * h / (1.0 + X * Y)
+    aw = -bw - 0.5 * h * d(X - h, Y)
+    ae = -be + 0.5 * h * d(X + h, Y)
+    as_ = -cs - 0.5 * h * e(X, Y - h)
+    an = -cn + 0.5 * h * e(X, Y + h)
+    # g = L u by hand: u = x E S Sy with E = exp(xy), S = sin(pi x), Sy = sin(pi y)
+    pi = np.pi
+    E, S, C, Sy, Cy = np.exp(X * Y), np.sin(pi * X), np.cos(pi * X), np.sin(pi * Y), np.cos(pi * Y)
+    u = X * E * S * Sy
+    ux = E * Sy * (S + X * Y * S + pi * X * C)
+    uy = X * E * S * (X * Sy + pi * Cy)
+    uxx = E * Sy * (2 * Y * S + X * Y * Y * S + 2 * pi * X * Y * C + 2 * pi * C - pi * pi * X * S)
+    uyy = X * E * S * (X * X * Sy + 2 * pi * X * Cy - pi * pi * Sy)
+    bx, cy = -Y * np.exp(-X * Y), X * np.exp(X * Y)
+    g = (-bx * ux - b(X, Y) * uxx - cy * uy - c(X, Y) * uyy + beta * u + d(X, Y) * ux + gamma * u + e(X, Y) * uy
+         + u / (1.0 + X * Y))
+    n = N * N
+    i = np.arange(1, n + 1)
+    return dict(coef=[a.reshape(-1).copy() for a in (a0, aw, ae, as_, an)], g=(h * h * g).reshape(-1),
+                u=u.reshape(-1), x0=0.05 * np.mod(i, 50).astype(np.float64))
