@@ -486,14 +486,17 @@ def main():
             for name, kw in (("gmres10_rbilu0", dict(s=1, m=10, precond="rbilu0")),
                              ("sstep2_gmres10_rbilu0", dict(s=2, m=10, precond="rbilu0")),
                              ("sstep2_gmres10", dict(s=2, m=10)),
-                             ("omin4", dict(omin=True, s=1, k=4)), ("sstep2_omin2", dict(omin=True, s=2, k=2))):
+                             ("omin4", dict(omin=True, s=1, k=4)), ("sstep2_omin2", dict(omin=True, s=2, k=2)),
+                             ("omin4_rbilu0", dict(omin=True, s=1, k=4, precond="rbilu0")),
+                             ("sstep2_omin2_rbilu0", dict(omin=True, s=2, k=2, precond="rbilu0"))):
                 xp = torch.tensor(Pp["x0"], device=dev)
                 for rep in range(2):
                     xp.copy_(torch.tensor(Pp["x0"], device=dev))
                     torch.cuda.synchronize()
                     e0.record(stream)
                     if kw.get("omin"):
-                        rp = pkg.sstep_omin_solve(Ap, gp, xp, kw["s"], kw["k"], TOL, max_iters=100000, history_cap=0)
+                        rp = pkg.sstep_omin_solve(Ap, gp, xp, kw["s"], kw["k"], TOL, max_iters=100000, history_cap=0,
+                                                  precond=kw.get("precond"))
                     else:
                         rp = pkg.sstep_gmres_solve(Ap, gp, xp, kw["s"], kw["m"], TOL, max_cycles=20000, history_cap=0,
                                                    precond=kw.get("precond"))

@@ -192,12 +192,14 @@ typedef struct {
                            of the first cycle's Ritz values (eigenvalues of its Hessenberg G) in
                            Leja order. Same Krylov spaces, better-conditioned Gram blocks (Sec. 3
                            names such bases for large s). The batched solver is monomial only. */
-    int precond;        /* s-step GMRES, FP64 basis only (others: SSTEP_ERR_ARG):
+    int precond;        /* s-step GMRES and s-step Orthomin, FP64 only (others: SSTEP_ERR_ARG):
                            SSTEP_PRECOND_NONE;
                            SSTEP_PRECOND_RBILU0: right preconditioning with ILU(0) in red-black
                            ordering (the sparsity pattern of A, d~_b = a0_b - sum_r A[b,r] A[r,b] /
-                           a0_r); powers of A M^-1, x = x0 + M^-1 V y, true restart residual;
-                           sigma defaults to 1. The paper uses ILU(0) in the natural ordering. */
+                           a0_r); powers of A M^-1, x = x0 + M^-1 V y (Orthomin: the steps P a
+                           accumulate and x += M^-1 of them before every explicit residual), true
+                           restart residual; sigma defaults to 1. The paper uses ILU(0) in the
+                           natural ordering. */
 } sstep_params;
 
 #define SSTEP_BASIS_MONOMIAL 0

@@ -278,7 +278,7 @@ def omin_powers(A, r, s, sigma):
     return R, AR
 
 
-def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None):
+def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None, precond=None):
     """s-step Orthomin(k), Algorithm 3.1.
 
     Per step i: m_i = (A P_i)^T r_i and W_i = (A P_i)^T A P_i; a = W_i^{-1} m_i
@@ -287,6 +287,9 @@ def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None):
     j = max(0, i-k+1)..i; P_{i+1} = R_{i+1} + sum_j P_j B_j and
     A P_{i+1} = A R_{i+1} + sum_j A P_j B_j. s = 1 is Orthomin(k) (Alg. 2.1).
     If `trace` is a dict it receives the A P blocks of the last window.
+    precond (apply_inv(v) = M^-1 v): right preconditioning, the method on A M^-1 (the
+    residual is the true f - A x); the steps P a accumulate in du and x += M^-1 du before
+    every explicit residual.
     """
     nf = norm(f)
     x = np.array(x0, dtype=np.float64, copy=True)
@@ -295,8 +298,17 @@ def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None):
     status = STATUS_NOT_CONVERGED
     it = 0
     P = None
+    op = A if precond is None else _RightPreconditioned(A, precond)
+    du = np.zeros_like(x)
+
+    def fold(x, du):
+        if precond is None:
+            return x, du
+        return x + precond.apply_inv(du), np.zeros_like(du)
+
     while True:
         if P is None:
+            x, du = fold(x, du)
             r = f - A.apply(x)
             mv += 1
             relres = norm(r) / nf
@@ -306,7 +318,7 @@ def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None):
                 break
             if it >= max_iters:
                 break
-            R, AR = omin_powers(A, r, s, sigma)             # R_0, P_0 = R_0
+            R, AR = omin_powers(op, r, s, sigma)            # R_0, P_0 = R_0
             mv += s
             L0 = cholesky_upper(AR.T @ AR)
             if L0 is None:
@@ -315,7 +327,10 @@ def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None):
             P, AP, Ls = [R], [AR], [L0]
         mvec = AP[-1].T @ r                                  # step 1
         a = cholesky_solve(Ls[-1], mvec)                     # step 2 (Scalar1)
-        x = x + P[-1] @ a                                    # step 3
+        if precond is None:
+            x = x + P[-1] @ a                                # step 3
+        else:
+            du = du + P[-1] @ a
         r = r - AP[-1] @ a                                   # step 4
         it += 1
         rr = norm(r) / nf
@@ -323,6 +338,7 @@ def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None):
         if rr <= tol or it >= max_iters:
             P = None
             if it >= max_iters:
+                x, du = fold(x, du)
                 relres = norm(f - A.apply(x)) / nf
                 mv += 1
                 hist.append(relres)
@@ -330,7 +346,7 @@ def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None):
                     status = STATUS_OK
                 break
             continue
-        R, AR = omin_powers(A, r, s, sigma)                  # step 5
+        R, AR = omin_powers(op, r, s, sigma)                 # step 5
         mv += s
         Pn = R.copy()
         APn = AR.copy()
@@ -343,6 +359,7 @@ def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None):
         Ln = cholesky_upper(APn.T @ APn)
         if Ln is None:
             status = STATUS_BREAKDOWN
+            x, du = fold(x, du)
             relres = norm(f - A.apply(x)) / nf
             break
         P.append(Pn)

@@ -334,10 +334,10 @@ def gmres_solve(A, f, x, m, tol, max_cycles=1000, history_cap=4096, stream=None,
                   stream=stream, precision=precision)
 
 
-def sstep_omin_solve(A, f, x, s, k, tol, max_iters=100000, sigma=0.0, history_cap=4096, stream=None):
-    """s-step Orthomin(k) (Alg. 3.1); s = 1 is Orthomin(k)."""
+def sstep_omin_solve(A, f, x, s, k, tol, max_iters=100000, sigma=0.0, history_cap=4096, stream=None, precond=None):
+    """s-step Orthomin(k) (Alg. 3.1); s = 1 is Orthomin(k). precond: None or "rbilu0"."""
     return _solve("sstep_omin_solve", A, f, x, s=s, k=k, tol=tol, max_iters=max_iters, sigma=sigma,
-                  history_cap=history_cap, stream=stream)
+                  history_cap=history_cap, stream=stream, precond=precond)
 
 
 def sstep_newton_shifts(G, K, s):

@@ -1214,41 +1214,72 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
     if (rc) return rc;
     const int s = p->s, k = p->k;
     if (s < 1 || s > SSTEP_MAX_S || k < 0 || (int64_t)k * s > SSTEP_MAX_COLS || p->max_iters < 0) return SSTEP_ERR_ARG;
-    if (p->precision != SSTEP_PREC_FP64 || p->precond != SSTEP_PRECOND_NONE) return SSTEP_ERR_ARG;
+    if (p->precision != SSTEP_PREC_FP64 || (p->precond != SSTEP_PRECOND_NONE && p->precond != SSTEP_PRECOND_RBILU0))
+        return SSTEP_ERR_ARG;
+    const bool pre = p->precond == SSTEP_PRECOND_RBILU0;
     cudaStream_t stream_ = (cudaStream_t)stream;
     const int64_t n = M->A.n, ld = col_ld(n);
     const int keep = std::max(k, 1);
     const int nslots = keep + 1;
-    // columns: P and AP panels (nslots*s each), AR (s), r (1)
-    Layout l = plan(n, 2 * nslots * s + s + 1, 1, p->history ? p->history_cap : 0);
+    // columns: P and AP panels (nslots*s each), AR (s), r (1); preconditioned also the
+    // accumulated correction du (the method runs on A M^-1: x = x0 + M^-1 du) and a scratch
+    Layout l = plan(n, 2 * nslots * s + s + 1 + (pre ? 2 : 0), 1, p->history ? p->history_cap : 0);
     if ((rc = ensure_workspace(M, l.total))) return rc;
+    if (pre && !M->rbilu) {
+        if (cudaMalloc((void**)&M->rbilu, sizeof(double) * n) != cudaSuccess) {
+            cudaGetLastError();
+            M->rbilu = nullptr;
+            return SSTEP_ERR_OOM;
+        }
+        launch_rbilu_setup(M->A, M->rbilu, stream_);
+    }
     SolverState h = init_state(l, M->ws, p, s, 1, k);
-    h.sigma = p->sigma > 0.0 ? p->sigma : 1.0 / M->norm_inf;
+    h.sigma = p->sigma > 0.0 ? p->sigma : (pre ? 1.0 : 1.0 / M->norm_inf);
     SolverState* st = (SolverState*)(M->ws + l.state);
     double* Ppanel = (double*)(M->ws + l.cols);
     double* APpanel = Ppanel + (int64_t)nslots * s * ld;
     double* AR = APpanel + (int64_t)nslots * s * ld;
     double* r = AR + (int64_t)s * ld;
+    double* du = r + ld;          // preconditioned: sum of the steps P a since the last explicit residual
+    double* ptmp = du + ld;       // preconditioned: M^-1 of a power, M^-1 du
     Scratch sc{(double*)(M->ws + l.partials), (unsigned*)(M->ws + l.counter)};
     CUDA_TRY(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
     CUDA_TRY(cudaMemsetAsync(M->ws + l.counter, 0, kAlign, stream_));
+    if (pre) CUDA_TRY(cudaMemsetAsync(du, 0, sizeof(double) * n, stream_));
     Epi e;
     e.st = st;
     e.mode = EPI_NF;
     TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, nullptr, nullptr, sc, e, GATE_NONE, stream_));
     if (p->x0_guard && (rc = apply_x0_guard(M, l, st, f, x, stream_))) return rc;
     const double sigma = h.sigma;
-    auto powers = [&]() {   // A R_{i+1}: A r, then A (sigma A R_j)
-        TRACED(K_STENCIL, stream_, launch_stencil(M->A, r, 1.0, AR, 0.0, nullptr, nullptr, st, GATE_BUILDING, stream_));
-        for (int j = 1; j < s; ++j)
-            TRACED(K_STENCIL, stream_, launch_stencil(M->A, AR + (j - 1) * ld, sigma, AR + j * ld, 0.0, nullptr, nullptr, st, GATE_BUILDING,
-                           stream_));
+    auto powers = [&]() {   // A R_{i+1}: A r, then A (sigma A R_j); preconditioned: A M^-1 ...
+        if (!pre) {
+            TRACED(K_STENCIL, stream_, launch_stencil(M->A, r, 1.0, AR, 0.0, nullptr, nullptr, st, GATE_BUILDING, stream_));
+            for (int j = 1; j < s; ++j)
+                TRACED(K_STENCIL, stream_, launch_stencil(M->A, AR + (j - 1) * ld, sigma, AR + j * ld, 0.0, nullptr,
+                                                          nullptr, st, GATE_BUILDING, stream_));
+            return;
+        }
+        for (int j = 0; j < s; ++j) {
+            TRACED(K_PRECOND, stream_, launch_rbilu_apply(M->A, M->rbilu, j == 0 ? r : AR + (j - 1) * ld, ptmp, st,
+                                                          GATE_BUILDING, stream_));
+            TRACED(K_STENCIL, stream_, launch_stencil(M->A, ptmp, j == 0 ? 1.0 : sigma, AR + j * ld, 0.0, nullptr,
+                                                      nullptr, st, GATE_BUILDING, stream_));
+        }
+    };
+    // x += M^-1 du, du = 0 (at a restart the solve is active, so the gated kernels run)
+    auto fold = [&](int gate) -> int {
+        if (!pre) return SSTEP_OK;
+        TRACED(K_PRECOND, stream_, launch_rbilu_apply(M->A, M->rbilu, du, ptmp, st, gate, stream_));
+        launch_add(x, ptmp, n, st, gate, stream_);
+        return cudaMemsetAsync(du, 0, sizeof(double) * n, stream_) == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA;
     };
     std::vector<int> ring;
     bool restart = true;
     const int batch = 8;
     for (;;) {
         if (restart) {
+            if ((rc = fold(GATE_ACTIVE))) return rc;
             e = Epi();
             e.st = st;
             e.mode = EPI_OM_RESTART;
@@ -1268,8 +1299,8 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
             e = Epi();
             e.st = st;
             e.mode = EPI_OM_R;
-            TRACED(K_OMIN_XR, stream_, launch_omin_xr(n, Ppanel + (int64_t)cur * s * ld, APpanel + (int64_t)cur * s * ld, ld, s, x, r, sc, e,
-                           GATE_BUILDING, stream_));   // steps 3-4
+            TRACED(K_OMIN_XR, stream_, launch_omin_xr(n, Ppanel + (int64_t)cur * s * ld, APpanel + (int64_t)cur * s * ld,
+                                                      ld, s, pre ? du : x, r, sc, e, GATE_BUILDING, stream_));   // steps 3-4
             powers();                                 // step 5
             const int nwin = std::min<int>(k, (int)ring.size());
             Epi w;
@@ -1293,6 +1324,7 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
         if (!M->hdr->active) break;
         if (M->hdr->confirm) restart = true;
     }
+    if ((rc = fold(GATE_NONE))) return rc;   // steps taken since the last explicit residual
     return finish(M, l, st, f, x, p, res, stream_);
 }
 

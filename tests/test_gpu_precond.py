@@ -95,3 +95,24 @@ def test_preconditioner_argument_errors():
             pkg.sstep_gmres_solve(A, f, x, 4, 20, 1e-8, precond="rbilu0", **kw)
     with pytest.raises(pkg.SStepError):
         A.rbilu0_apply(f, f)
+
+
+@pytest.mark.parametrize("s,k", [(1, 4), (2, 2), (4, 1)])
+def test_preconditioned_orthomin_matches_oracle(s, k):
+    """Right-preconditioned (s-step) Orthomin on the paper's test problem from its
+    initial guess: the oracle's step count, products and solution."""
+    d = dev()
+    N = 48
+    P = inputs.paper_problem(N)
+    a0, aw, ae, as_, an = P["coef"]
+    Ao = ostencil.Stencil((N, N), a0, [aw, as_], [ae, an])
+    A = pkg.StencilMatrix(2, (N, N), fields=[to_dev(c, d) for c in P["coef"]])
+    xd = to_dev(P["x0"], d)
+    r = pkg.sstep_omin_solve(A, to_dev(P["g"], d), xd, s, k, 1e-9, max_iters=20000, precond="rbilu0")
+    torch.cuda.synchronize()
+    ref = osstep.sstep_omin(Ao, P["g"], P["x0"], s, k, 1e-9, 1.0, 20000, precond=ostencil.RedBlackILU0(Ao))
+    x = xd.cpu().numpy()
+    assert r["status"] == 0 and ref["status"] == 0
+    assert r["iters"] == ref["iters"] and r["matvecs"] == ref["matvecs"]
+    assert np.linalg.norm(x - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+    assert np.linalg.norm(P["g"] - Ao.apply(x)) <= 1e-9 * np.linalg.norm(P["g"])

@@ -69,3 +69,17 @@ def test_preconditioned_sstep_gmres_reaches_the_dense_solution_with_fewer_produc
     r0 = osstep.sstep_gmres(A, f, np.zeros(A.n), 4, 16, 1e-12, 1.0 / A.norm_inf(), 200)
     r1 = osstep.sstep_gmres(A, f, np.zeros(A.n), 4, 16, 1e-12, 1.0, 200, precond=P)
     assert r1["matvecs"] < r0["matvecs"]
+
+
+def test_preconditioned_sstep_orthomin_reaches_the_dense_solution_with_fewer_steps():
+    N = 15
+    P = inputs.paper_problem(N)
+    a0, aw, ae, as_, an = P["coef"]
+    A = ostencil.Stencil((N, N), a0, [aw, as_], [ae, an])
+    xs = np.linalg.solve(dense.dense_matrix(A), P["g"])
+    M = ostencil.RedBlackILU0(A)
+    for s, k in ((1, 4), (2, 2)):
+        r0 = osstep.sstep_omin(A, P["g"], P["x0"], s, k, 1e-11, 1.0 / A.norm_inf(), 100000)
+        r1 = osstep.sstep_omin(A, P["g"], P["x0"], s, k, 1e-11, 1.0, 100000, precond=M)
+        assert r1["status"] == 0 and r1["iters"] < r0["iters"]
+        assert np.linalg.norm(r1["x"] - xs) <= 1e-9 * np.linalg.norm(xs)
