@@ -29,6 +29,13 @@ solvers where relevant):
     is read as m_i); c_j^l is read as C_j = (A P_j)^T A R_{i+1} with
     A R = [A r, A R_2, ..., A R_s] and R = [r, sigma A r, ..., sigma A R_{s-1}];
     step 5 computes R_{i+1}; the window is j_i = max(0, i-k+1).
+  * Sec. 3's remedy for large s (not implemented in the paper): each new direction
+    block is made A^T A-orthogonal by modified Gram-Schmidt once it is formed, so
+    that W_i is diagonal and Scalar1/Scalar2 are diagonal solves. It is read as
+    applying to P_{i+1} after the projection against the window (steps 8-9), and to
+    P_0 = R_0, so that every W_j of the window is diagonal; the columns are also
+    normalised (A p_j^l of unit length), the diagonal then being the identity up to
+    rounding, and the diagonal solves divide by the computed diagonal of W.
 """
 from __future__ import annotations
 
@@ -266,6 +273,22 @@ def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None, basis="
 
 
 # ---------------------------------------------------------------- s-step Orthomin
+def _omin_factor(AP, ortho):
+    """What Scalar1/Scalar2 need of W = (A P)^T A P: its Cholesky factor, or (ortho)
+    its diagonal (None on a non-positive pivot or diagonal entry)."""
+    if ortho:
+        d = np.einsum("ij,ij->j", AP, AP)
+        return d if np.all(d > 0.0) else None
+    return cholesky_upper(AP.T @ AP)
+
+
+def _omin_solve(Lw, rhs, ortho):
+    """W x = rhs with W given by _omin_factor (rhs a vector or an s-row matrix)."""
+    if ortho:
+        return rhs / (Lw if np.ndim(rhs) == 1 else Lw[:, None])
+    return cholesky_solve(Lw, rhs)
+
+
 def omin_powers(A, r, s, sigma):
     """R = [r, sigma A r, ..., sigma A R_{s-1}] and A R, with s products."""
     R = np.zeros((r.shape[0], s))
@@ -278,7 +301,31 @@ def omin_powers(A, r, s, sigma):
     return R, AR
 
 
-def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None, precond=None):
+def ata_mgs(P, AP):
+    """Modified Gram-Schmidt of the block P in the A^T A inner product (Sec. 3).
+
+    Works on the columns of A P and applies every operation to P as well: for
+    l = 1..s, A p^l is normalised, then its component is removed from the later
+    columns. Returns (P Q, A P Q) with Q upper triangular and (A P Q)^T (A P Q) = I
+    up to rounding, or None when a column has no component left (breakdown).
+    """
+    P = np.array(P, dtype=np.float64, copy=True)
+    AP = np.array(AP, dtype=np.float64, copy=True)
+    s = P.shape[1]
+    for l in range(s):
+        nrm = norm(AP[:, l])
+        if not nrm > 0.0:
+            return None
+        AP[:, l] /= nrm
+        P[:, l] /= nrm
+        for j in range(l + 1, s):
+            d = np.dot(AP[:, l], AP[:, j])
+            AP[:, j] -= d * AP[:, l]
+            P[:, j] -= d * P[:, l]
+    return P, AP
+
+
+def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None, precond=None, basis="monomial"):
     """s-step Orthomin(k), Algorithm 3.1.
 
     Per step i: m_i = (A P_i)^T r_i and W_i = (A P_i)^T A P_i; a = W_i^{-1} m_i
@@ -290,7 +337,13 @@ def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None, precond
     precond (apply_inv(v) = M^-1 v): right preconditioning, the method on A M^-1 (the
     residual is the true f - A x); the steps P a accumulate in du and x += M^-1 du before
     every explicit residual.
+    basis="ortho": every direction block is A^T A-orthonormalised by ata_mgs once
+    formed (P_0 and each P_{i+1}); W_j is then diagonal and Scalar1 (a = m / diag W)
+    and Scalar2 (B_j = -C_j / diag W_j, row-wise) are diagonal solves (Sec. 3).
     """
+    if basis not in ("monomial", "ortho"):
+        raise ValueError(basis)
+    ortho = basis == "ortho"
     nf = norm(f)
     x = np.array(x0, dtype=np.float64, copy=True)
     mv = 0
@@ -320,13 +373,19 @@ def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None, precond
                 break
             R, AR = omin_powers(op, r, s, sigma)            # R_0, P_0 = R_0
             mv += s
-            L0 = cholesky_upper(AR.T @ AR)
+            if ortho:
+                Q = ata_mgs(R, AR)
+                if Q is None:
+                    status = STATUS_BREAKDOWN
+                    break
+                R, AR = Q
+            L0 = _omin_factor(AR, ortho)
             if L0 is None:
                 status = STATUS_BREAKDOWN
                 break
             P, AP, Ls = [R], [AR], [L0]
         mvec = AP[-1].T @ r                                  # step 1
-        a = cholesky_solve(Ls[-1], mvec)                     # step 2 (Scalar1)
+        a = _omin_solve(Ls[-1], mvec, ortho)                 # step 2 (Scalar1)
         if precond is None:
             x = x + P[-1] @ a                                # step 3
         else:
@@ -353,15 +412,17 @@ def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None, precond
         lo = len(P) - min(k, len(P))
         for j in range(lo, len(P)):
             C = AP[j].T @ AR                                 # step 6
-            B = -cholesky_solve(Ls[j], C)                    # step 7 (Scalar2)
+            B = -_omin_solve(Ls[j], C, ortho)                # step 7 (Scalar2)
             Pn = Pn + P[j] @ B                               # step 8
             APn = APn + AP[j] @ B                            # step 9
-        Ln = cholesky_upper(APn.T @ APn)
+        Q = ata_mgs(Pn, APn) if ortho else (Pn, APn)
+        Ln = None if Q is None else _omin_factor(Q[1], ortho)
         if Ln is None:
             status = STATUS_BREAKDOWN
             x, du = fold(x, du)
             relres = norm(f - A.apply(x)) / nf
             break
+        Pn, APn = Q
         P.append(Pn)
         AP.append(APn)
         Ls.append(Ln)

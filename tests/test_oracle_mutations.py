@@ -86,7 +86,7 @@ def test_sstep_gmres_mutation_caught(old, new):
 
 
 OMIN_MUTATIONS = [
-    ("B = -cholesky_solve(Ls[j], C)", "B = cholesky_solve(Ls[j], C)"),    # wrong sign of Scalar2
+    ("B = -_omin_solve(Ls[j], C, ortho)", "B = _omin_solve(Ls[j], C, ortho)"),  # wrong sign of Scalar2
     ("C = AP[j].T @ AR", "C = AR.T @ AP[j]"),                            # transposed C_j
     ("Pn = Pn + P[j] @ B", "Pn = Pn + P[j] @ B.T"),                      # transposed coefficients
     ("x = x + P[-1] @ a", "x = x + P[-1] @ a[::-1]"),                    # wrong column order

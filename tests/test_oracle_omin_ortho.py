@@ -1,0 +1,141 @@
+"""Pins for the oracle's A^T A-orthonormal direction blocks in s-step Orthomin (Sec. 3).
+
+Sec. 3 says that making each block R_i A^T A-orthogonal by modified Gram-Schmidt
+turns Scalar1/Scalar2 into diagonal solves and allows a larger s. The pins:
+  * ata_mgs is a QR factorisation of A P, so it must agree with numpy's Householder
+    QR (up to column signs) and apply the same triangular transform to P;
+  * the transform changes the basis of each block, not its span, so the iterates
+    equal those of the Cholesky form of Algorithm 3.1 on a well-conditioned system;
+  * with s = 1 it is Orthomin(k) of Algorithm 2.1 with normalised directions;
+  * every block of the window is A^T A-orthonormal and the blocks are mutually
+    A^T A-orthogonal;
+  * at s = 10 and 12 on the paper's test problem it needs fewer steps than the
+    Cholesky form (the loss of stability it is meant to remedy).
+"""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import STATUS_OK, krylov, sstep, stencil
+from paper_2001_04886_gb300 import inputs
+
+
+def system(shape, beta, seed=0):
+    A = stencil.convdiff(shape, beta)
+    return A, A.apply(inputs.x_true(seed, A.n))
+
+
+def test_ata_mgs_is_qr_of_AP():
+    A, _ = system((9, 9), (20.0, 10.0))
+    rng = np.random.default_rng(4)
+    P = rng.standard_normal((A.n, 5))
+    AP = np.column_stack([A.apply(P[:, j]) for j in range(5)])
+    PQ, APQ = sstep.ata_mgs(P, AP)
+    Qn, Rn = np.linalg.qr(AP)
+    sg = np.sign(np.diag(Rn))
+    Qn, Rn = Qn * sg, Rn * sg[:, None]                 # positive diagonal: the unique QR
+    assert np.allclose(APQ, Qn, atol=1e-12)
+    assert np.allclose(PQ, P @ np.linalg.inv(Rn), rtol=1e-10, atol=1e-12)
+    assert np.allclose(APQ.T @ APQ, np.eye(5), atol=1e-13)
+    # A (P Q) = (A P) Q: the same transform was applied to both
+    APQ2 = np.column_stack([A.apply(PQ[:, j]) for j in range(5)])
+    assert np.allclose(APQ2, APQ, atol=1e-12)
+
+
+def test_ata_mgs_breakdown_on_a_zero_column():
+    A, _ = system((4, 4), (4.0, 4.0))
+    P = np.ones((A.n, 3))
+    P[:, 1] = 0.0
+    AP = np.column_stack([A.apply(P[:, j]) for j in range(3)])
+    assert sstep.ata_mgs(P, AP) is None
+
+
+@pytest.mark.parametrize("s,k", [(2, 1), (3, 2), (4, 1), (3, 0)])
+def test_ortho_blocks_leave_iterates_unchanged(s, k):
+    A, f = system((14, 14), (20.0, 10.0))
+    z = np.zeros(A.n)
+    a = sstep.sstep_omin(A, f, z, s, k, 1e-9, 0.125, 400)
+    b = sstep.sstep_omin(A, f, z, s, k, 1e-9, 0.125, 400, basis="ortho")
+    assert a["status"] == b["status"] == STATUS_OK
+    assert a["iters"] == b["iters"]
+    ha, hb = np.array(a["history"]), np.array(b["history"])
+    assert np.all(np.abs(ha - hb) <= 1e-7 * ha + 1e-14)   # 1e-14: rounding of ||f - A x|| / ||f||
+    assert np.linalg.norm(a["x"] - b["x"]) <= 1e-8 * np.linalg.norm(a["x"])
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_ortho_s1_is_orthomin(k):
+    A, f = system((12, 12), (16.0, 8.0))
+    z = np.zeros(A.n)
+    a = krylov.omin(A, f, z, k, 1e-8, 2000)
+    b = sstep.sstep_omin(A, f, z, 1, k, 1e-8, 0.125, 2000, basis="ortho")
+    assert a["iters"] == b["iters"]
+    n = min(len(a["history"]), len(b["history"]))
+    ha, hb = np.array(a["history"][:n]), np.array(b["history"][:n])
+    assert np.all(np.abs(ha - hb) <= 1e-8 * ha)
+
+
+def test_ortho_window_is_orthonormal():
+    A, f = system((20, 20), (20.0, 20.0))
+    tr = {}
+    sstep.sstep_omin(A, f, np.zeros(A.n), 4, 2, 1e-9, 0.125, 12, trace=tr, basis="ortho")
+    AP = tr["AP"]
+    assert len(AP) == 2
+    for blk in AP:
+        assert np.allclose(blk.T @ blk, np.eye(4), atol=1e-12)     # W_j = I: diagonal solves
+    assert np.max(np.abs(AP[0].T @ AP[1])) <= 1e-11
+
+
+def test_ortho_allows_larger_s_on_the_paper_problem():
+    P = inputs.paper_problem(64)
+    a0, aw, ae, as_, an = [np.asarray(c) for c in P["coef"]]
+    A = stencil.Stencil((64, 64), a0, [aw, as_], [ae, an])
+    f = np.asarray(P["g"])
+    z = np.zeros(A.n)
+    sig = 1.0 / A.norm_inf()
+    for s, ratio in ((10, 0.92), (12, 0.75)):
+        a = sstep.sstep_omin(A, f, z, s, 1, 1e-8, sig, 600)
+        b = sstep.sstep_omin(A, f, z, s, 1, 1e-8, sig, 600, basis="ortho")
+        assert a["status"] == b["status"] == STATUS_OK
+        assert b["iters"] <= ratio * a["iters"], (s, a["iters"], b["iters"])
+
+
+def _mutated_sstep(old, new):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "sstep.py")).read()
+    assert src.count(old) == 1, old
+    spec = importlib.util.spec_from_loader("oracle._mut_sstep_ortho", loader=None)
+    mod = importlib.util.module_from_spec(spec)
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(old, new), "sstep_mut.py", "exec"), mod.__dict__)
+    return mod
+
+
+@pytest.mark.parametrize("old,new", [
+    ("            P[:, j] -= d * P[:, l]\n", "\n"),                       # transform not applied to P
+    ("        P[:, l] /= nrm\n", "\n"),                                   # P not normalised with A P
+    ("AP[:, j] -= d * AP[:, l]", "AP[:, j] -= d * AP[:, j]"),          # wrong column
+    ("Q = ata_mgs(Pn, APn) if ortho else (Pn, APn)", "Q = (Pn, APn)"),  # only P_0 orthonormalised
+])
+def test_planted_mistakes_caught(old, new):
+    mod = _mutated_sstep(old, new)
+    A, f = system((14, 14), (20.0, 10.0))
+    z = np.zeros(A.n)
+    ref = sstep.sstep_omin(A, f, z, 3, 2, 1e-9, 0.125, 400)
+    try:
+        with np.errstate(all="ignore"):
+            b = mod.sstep_omin(A, f, z, 3, 2, 1e-9, 0.125, 400, basis="ortho")
+    except Exception:
+        return
+    hr, hb = np.array(ref["history"]), np.array(b["history"])
+    same = b["iters"] == ref["iters"] and len(hr) == len(hb) and np.all(np.abs(hr - hb) <= 1e-7 * hr + 1e-14)
+    if not same:
+        return
+    rng = np.random.default_rng(4)
+    Pm = rng.standard_normal((A.n, 4))
+    APm = np.column_stack([A.apply(Pm[:, j]) for j in range(4)])
+    out = mod.ata_mgs(Pm, APm)
+    APQ2 = np.column_stack([A.apply(out[0][:, j]) for j in range(4)])
+    assert not (np.allclose(out[1].T @ out[1], np.eye(4), atol=1e-12) and np.allclose(APQ2, out[1], atol=1e-12))
