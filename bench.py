@@ -43,9 +43,9 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.0
 # Keyed by precision mode, with a hash of the kernel sources it was taken on: once the
 # sources change, the figure no longer describes the kernel and the bench reports null.
 TRAFFIC = {
-    "fp64": {"kernel": "block_update", "bytes_per_launch": 471.4e6,
+    "fp64": {"kernel": "block_update", "bytes_per_launch": 471.3e6,
              "sources": ("common.cuh", "kernels.cuh", "epilogue.cuh", "kernels.cu"),
-             "sha256": "910d6d98584c34d2"},
+             "sha256": "0dad0385d7b59f2b"},
 }
 
 
@@ -309,7 +309,8 @@ def main():
                                          basis=kw.get("basis", "monomial"), precond=kw.get("precond"))
         if method == "gmres":
             return pkg.gmres_solve(A, f, xv, M, TOL, max_cycles=200, history_cap=8192, precision=prec)
-        return pkg.sstep_omin_solve(A, f, xv, kw["s"], kw["k"], TOL, max_iters=20000, history_cap=8192)
+        return pkg.sstep_omin_solve(A, f, xv, kw["s"], kw["k"], TOL, max_iters=20000, history_cap=8192,
+                                    basis=kw.get("basis", "monomial"))
 
     nw = max(args.warmup, 3)
     for i in range(nw):
@@ -396,6 +397,9 @@ def main():
                          ("sstep_gmres_s8_rbilu0", dict(method="sstep", s=8, precond="rbilu0")),
                          ("gmres", dict(method="gmres")),
                          ("sstep_omin_s4_k1", dict(method="omin", s=4, k=1)),
+                         ("sstep_omin_s4_k1_ortho", dict(method="omin", s=4, k=1, basis="ortho")),
+                         ("sstep_omin_s8_k1", dict(method="omin", s=8, k=1)),
+                         ("sstep_omin_s8_k1_ortho", dict(method="omin", s=8, k=1, basis="ortho")),
                          ("omin_k1", dict(method="omin", s=1, k=1)), ("omin_k7", dict(method="omin", s=1, k=7)),
                          ("df64_sstep_gmres_s4", dict(method="sstep", s=4, precision="df64")),
                          ("df64_sstep_gmres_s8", dict(method="sstep", s=8, precision="df64")),

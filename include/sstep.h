@@ -191,7 +191,12 @@ typedef struct {
                            y^{j+1} = sigma (A - theta_j I) y^j with theta_1..theta_s the real parts
                            of the first cycle's Ritz values (eigenvalues of its Hessenberg G) in
                            Leja order. Same Krylov spaces, better-conditioned Gram blocks (Sec. 3
-                           names such bases for large s). The batched solver is monomial only. */
+                           names such bases for large s). The batched solver is monomial only.
+                           s-step Orthomin: SSTEP_BASIS_MONOMIAL (Alg. 3.1 as printed) or
+                           SSTEP_BASIS_ORTHO: every direction block P_i (P_0 = R_0 and each
+                           projected P_{i+1}) is made A^T A-orthonormal, the remedy Sec. 3 gives
+                           for large s, so that W_i is the identity up to rounding; then
+                           (k + 1) s <= SSTEP_MAX_COLS. Other values: SSTEP_ERR_ARG. */
     int precond;        /* s-step GMRES and s-step Orthomin, FP64 only (others: SSTEP_ERR_ARG):
                            SSTEP_PRECOND_NONE;
                            SSTEP_PRECOND_RBILU0: right preconditioning with ILU(0) in red-black
@@ -204,6 +209,7 @@ typedef struct {
 
 #define SSTEP_BASIS_MONOMIAL 0
 #define SSTEP_BASIS_NEWTON 1
+#define SSTEP_BASIS_ORTHO 2
 
 #define SSTEP_PRECOND_NONE 0
 #define SSTEP_PRECOND_RBILU0 1
@@ -238,7 +244,13 @@ int gmres_solve(sstep_matrix A, const double* f, double* x, const sstep_params* 
 /* s-step Orthomin(k) (Alg. 3.1); s = 1 is Orthomin(k) (Alg. 2.1). The updated
  * residual is tested after each s-step; at tol it is recomputed explicitly and
  * the method restarts if the explicit residual is still above tol. History: the
- * explicit relres at (re)starts and the updated relres after each s-step. */
+ * explicit relres at (re)starts and the updated relres after each s-step.
+ * With p->basis = SSTEP_BASIS_ORTHO the new block is orthonormalised in the A^T A
+ * inner product by the triangular factor of its Gram matrix, predicted in the pass
+ * that forms the window's inner products (W_new = A R^T A R - sum_j C_j^T W_j^-1 C_j)
+ * and folded into the block update (no extra pass over the vectors); Scalar1/Scalar2
+ * then solve with Gram blocks equal to the identity up to rounding. Where the
+ * predicted Gram is not positive definite the block is left as formed. */
 int sstep_omin_solve(sstep_matrix A, const double* f, double* x, const sstep_params* p,
                      sstep_result* res, void* stream);
 

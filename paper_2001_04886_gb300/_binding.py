@@ -290,7 +290,7 @@ def sstep_block_update(V, Y, T, work=None, stream=None):
     return G.t()
 
 
-BASES = {"monomial": 0, "newton": 1}
+BASES = {"monomial": 0, "newton": 1, "ortho": 2}
 PRECONDS = {None: 0, "none": 0, "rbilu0": 1}
 
 
@@ -334,10 +334,12 @@ def gmres_solve(A, f, x, m, tol, max_cycles=1000, history_cap=4096, stream=None,
                   stream=stream, precision=precision)
 
 
-def sstep_omin_solve(A, f, x, s, k, tol, max_iters=100000, sigma=0.0, history_cap=4096, stream=None, precond=None):
-    """s-step Orthomin(k) (Alg. 3.1); s = 1 is Orthomin(k). precond: None or "rbilu0"."""
+def sstep_omin_solve(A, f, x, s, k, tol, max_iters=100000, sigma=0.0, history_cap=4096, stream=None, precond=None,
+                     basis="monomial"):
+    """s-step Orthomin(k) (Alg. 3.1); s = 1 is Orthomin(k). precond: None or "rbilu0".
+    basis: "monomial" (as printed) or "ortho" (A^T A-orthonormal direction blocks, Sec. 3)."""
     return _solve("sstep_omin_solve", A, f, x, s=s, k=k, tol=tol, max_iters=max_iters, sigma=sigma,
-                  history_cap=history_cap, stream=stream, precond=precond)
+                  history_cap=history_cap, stream=stream, precond=precond, basis=basis)
 
 
 def sstep_newton_shifts(G, K, s):

@@ -1216,7 +1216,10 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
     if (s < 1 || s > SSTEP_MAX_S || k < 0 || (int64_t)k * s > SSTEP_MAX_COLS || p->max_iters < 0) return SSTEP_ERR_ARG;
     if (p->precision != SSTEP_PREC_FP64 || (p->precond != SSTEP_PRECOND_NONE && p->precond != SSTEP_PRECOND_RBILU0))
         return SSTEP_ERR_ARG;
+    if (p->basis != SSTEP_BASIS_MONOMIAL && p->basis != SSTEP_BASIS_ORTHO) return SSTEP_ERR_ARG;
     const bool pre = p->precond == SSTEP_PRECOND_RBILU0;
+    const int ortho = p->basis == SSTEP_BASIS_ORTHO;
+    if (ortho && (int64_t)(k + 1) * s > SSTEP_MAX_COLS) return SSTEP_ERR_ARG;
     cudaStream_t stream_ = (cudaStream_t)stream;
     const int64_t n = M->A.n, ld = col_ld(n);
     const int keep = std::max(k, 1);
@@ -1287,9 +1290,15 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
             powers();   // R_0, A R_0; P_0 = R_0
             e = Epi();
             e.st = st;
+            e.nwin = 0;
+            if (ortho) {   // A R^T A R: the factor that makes P_0 A^T A-orthonormal
+                e.mode = EPI_OM_B;
+                e.ortho = 1;
+                e.win[0] = nslots;   // A R sits right after the A P slots
+                TRACED(K_GRAM, stream_, launch_gram(n, APpanel, ld, s, AR, ld, s, s, sc, e, GATE_BUILDING, stream_));
+            }
             e.mode = EPI_OM_W;
             e.slot = 0;
-            e.nwin = 0;
             TRACED(K_OMIN_PUPDATE, stream_, launch_omin_pupdate(n, r, AR, Ppanel, APpanel, ld, s, sigma, sc, e, GATE_BUILDING, stream_));
             ring.assign(1, 0);
             restart = false;
@@ -1306,10 +1315,13 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
             Epi w;
             w.st = st;
             w.nwin = nwin;
+            w.ortho = ortho;
             for (int i = 0; i < nwin; ++i) w.win[i] = ring[ring.size() - nwin + i];
-            if (nwin > 0) {   // steps 6-7
+            w.win[nwin] = nslots;   // ortho: the A R block, right after the A P slots
+            if (nwin + ortho > 0) {   // steps 6-7
                 w.mode = EPI_OM_B;
-                TRACED(K_GRAM, stream_, launch_gram(n, APpanel, ld, nwin * s, AR, ld, s, s, sc, w, GATE_BUILDING, stream_));
+                TRACED(K_GRAM, stream_, launch_gram(n, APpanel, ld, (nwin + ortho) * s, AR, ld, s, s, sc, w,
+                                                    GATE_BUILDING, stream_));
             }
             int nslot = 0;
             while (std::find(ring.begin(), ring.end(), nslot) != ring.end()) ++nslot;

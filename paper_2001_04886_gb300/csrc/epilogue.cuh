@@ -369,9 +369,15 @@ __device__ void epi_om_r(SolverState* st, double rr) {
 
 // Orthomin Scalar2 (Alg. 3.1 step 7): B_w = -W_w^{-1} C_w for each window block w.
 // B is stored in st->T as (nwin*s) x s, col-major, ld kMaxCols.
+// e.ortho: C has a last block A R^T A R. The Gram matrix of the projected block
+// A R + sum_w A P_w B_w is then W = A R^T A R + sum_w C_w^T B_w (exact arithmetic);
+// with W = L^T L, F = L^{-1} makes (A R + sum_w A P_w B_w) F A^T A-orthonormal. F is
+// folded into the coefficients (B_w <- B_w F) and stored below them in T (rows
+// nwin*s..), so the block update forms the orthonormal block directly. F = I where the
+// predicted W is not positive definite.
 __device__ void epi_om_B(const Epi& e, const double* C) {
     SolverState* st = e.st;
-    const int s = st->s, rows = e.nwin * s;
+    const int s = st->s, rows = (e.nwin + e.ortho) * s;
     for (int t = threadIdx.x; t < e.nwin * s; t += blockDim.x) {
         const int w = t / s, j = t % s;
         double rhs[kMaxS], x[kMaxS];
@@ -379,6 +385,41 @@ __device__ void epi_om_B(const Epi& e, const double* C) {
         chol_solve(st->L + e.win[w] * s * s, s, rhs, x);
         for (int q = 0; q < s; ++q) st->T[(w * s + q) + j * kMaxCols] = -x[q];
     }
+    if (!e.ortho) return;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const int o = e.nwin * s;
+    double W[kMaxS * kMaxS], L[kMaxS * kMaxS], F[kMaxS * kMaxS];
+    for (int j = 0; j < s; ++j)
+        for (int q = 0; q <= j; ++q) {
+            double t = C[(o + q) + j * rows];
+            for (int i = 0; i < o; ++i) t = add(t, mul(C[i + q * rows], st->T[i + j * kMaxCols]));
+            W[q + j * s] = t;
+        }
+    for (int i = 0; i < s * s; ++i) F[i] = 0.0;
+    if (chol_upper(W, s, s, L)) {
+        for (int c = 0; c < s; ++c) {   // column c of L^{-1}: back substitution, upper triangular
+            F[c + c * s] = 1.0 / L[c + c * s];
+            for (int i = c - 1; i >= 0; --i) {
+                double t = 0.0;
+                for (int q = i + 1; q <= c; ++q) t = add(t, mul(L[i + q * s], F[q + c * s]));
+                F[i + c * s] = -t / L[i + i * s];
+            }
+        }
+    } else {
+        for (int c = 0; c < s; ++c) F[c + c * s] = 1.0;
+    }
+    for (int i = 0; i < o; ++i) {
+        double b[kMaxS];
+        for (int q = 0; q < s; ++q) b[q] = st->T[i + q * kMaxCols];
+        for (int j = 0; j < s; ++j) {
+            double t = 0.0;
+            for (int q = 0; q <= j; ++q) t = add(t, mul(b[q], F[q + j * s]));
+            st->T[i + j * kMaxCols] = t;
+        }
+    }
+    for (int j = 0; j < s; ++j)
+        for (int q = 0; q < s; ++q) st->T[(o + q) + j * kMaxCols] = F[q + j * s];
 }
 
 // Orthomin Scalar1 (Alg. 3.1 steps 1-2): W = L^T L, a = W^{-1} m for the new block.

@@ -374,12 +374,13 @@ __global__ void __launch_bounds__(kThreads) omin_pupdate_kernel(int64_t n, const
     __shared__ double Bs[kMaxCols * S];
     __shared__ double red[(kWarps + 1) * NV];
     if (!gate_open(epi.st, gate)) return;
-    const int nwin = epi.nwin, rows = nwin * S;
+    const int nwin = epi.nwin, rows = (nwin + epi.ortho) * S;
     for (int t = threadIdx.x; t < rows * S; t += blockDim.x) {
         const int i = t % rows, j = t / rows;
         Bs[i * S + j] = epi.st->T[i + j * kMaxCols];
     }
     __syncthreads();
+    const double* Fs = Bs + nwin * S * S;   // ortho: upper triangular factor of the R block
     double* Pn = (double*)Ppanel + (int64_t)epi.slot * S * ld;
     double* APn = (double*)APpanel + (int64_t)epi.slot * S * ld;
     double acc[NV];
@@ -392,7 +393,20 @@ __global__ void __launch_bounds__(kThreads) omin_pupdate_kernel(int64_t n, const
 #pragma unroll
         for (int j = 0; j < S; ++j) {
             apv[j] = __ldg(AR + p + j * ld);
-            pv[j] = (j == 0) ? rv : sigma * __ldg(AR + p + (j - 1) * ld);
+            pv[j] = (j == 0) ? rv : sigma * apv[j - 1];
+        }
+        if (epi.ortho) {   // [R, A R] F, F upper triangular: column j from columns q <= j
+#pragma unroll
+            for (int j = S - 1; j >= 0; --j) {
+                double tp = 0.0, tap = 0.0;
+#pragma unroll
+                for (int q = 0; q <= j; ++q) {
+                    tp = fma(pv[q], Fs[q * S + j], tp);
+                    tap = fma(apv[q], Fs[q * S + j], tap);
+                }
+                pv[j] = tp;
+                apv[j] = tap;
+            }
         }
         for (int w = 0; w < nwin; ++w) {
             const double* Pw = Ppanel + (int64_t)epi.win[w] * S * ld;

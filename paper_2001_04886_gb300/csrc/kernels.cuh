@@ -35,6 +35,8 @@ struct Epi {
     int slot = 0;            // Orthomin: slot of the new direction block
     int nwin = 0;            // Orthomin: blocks in the window
     int win[kMaxCols];       // Orthomin: window slots, oldest first
+    int ortho = 0;           // Orthomin: A^T A-orthonormal blocks; the Gram pass has the
+                             // A R block last (win[nwin]) and T holds its factor F after B
 };
 
 struct Scratch {
