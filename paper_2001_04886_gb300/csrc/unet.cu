@@ -162,6 +162,14 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
+// v = h + m + l exactly: three BF16 parts of an FP32 value (8 significand bits each)
+__device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(v);
+    const float r1 = __fsub_rn(v, __bfloat162float(h));
+    m = __float2bfloat16_rn(r1);
+    l = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(m)));
+}
+
 template <int NP, bool TRANSPOSED>
 __global__ void __launch_bounds__(kM) conv3x3_tc_kernel(const float* __restrict__ in, int Kc,
                                                         const __nv_bfloat16* __restrict__ W,
@@ -364,6 +372,257 @@ int launch_np(const float* in, int Kc, const __nv_bfloat16* W, const float* bias
     conv3x3_tc_kernel<NP, TRANSPOSED><<<grid, kM, smem, s>>>(in, Kc, W, bias, out, N, H, Wd, relu, accumulate, err,
                                                              spin);
     return 0;
+}
+
+// Weight gradient on the tensor cores. With r = ci*9 + tap and the pixels P of all
+// images as the reduction index, dW[co][r] = sum_P g[co][P] x_r[P], where x_r is input
+// channel ci shifted by the tap (zero outside the image). CTA (z, t) accumulates the
+// rows of input channels 14 t .. 14 t + 13 (126 rows; rows 126-127 of the M tile stay
+// zero) against all NP output channels over the 16-pixel chunks [z cpc, (z+1) cpc):
+// A = x (128 rows x 16 pixels, K-major), B = g (NP rows x 16 pixels, K-major). A thread
+// gathers the 3 x 3 neighbourhoods of two pixels in one channel (the nine rows of that
+// channel), so the index arithmetic is done once per pixel. Both are FP32, split into three BF16 parts (h + m + l, exact); the six part
+// products of weight down to 2^-16 are accumulated in FP32 in tensor memory (the three
+// dropped ones are below 2^-24 of the product, under the accumulation's own rounding).
+// Partial sums go to partial[z][co][r]; wgrad_reduce_kernel adds them in z order.
+constexpr int kWgCh = 14;   // input channels per M tile of the weight gradient (126 of 128 rows)
+
+template <int NP>
+__global__ void __launch_bounds__(kM) wgrad_tc_kernel(const float* __restrict__ in, int Cin,
+                                                      const float* __restrict__ g, int Cout, int B, int H, int Wd,
+                                                      int cpc, float* __restrict__ partial, int* err, long spin) {
+    constexpr int kABytes = kM * kK * 2;          // one BF16 part of the A chunk
+    constexpr int kBBytes = NP * kK * 2;          // one BF16 part of the B chunk
+    constexpr int kStage = 3 * kABytes + 3 * kBBytes;
+    constexpr uint32_t kCols = tmem_cols(NP);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int failed;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int rows = Cin * 9, ci0 = blockIdx.y * kWgCh;
+    const int64_t HW = (int64_t)H * Wd, npix = (int64_t)B * HW;
+    const int64_t all_chunks = (npix + kK - 1) / kK, c0 = (int64_t)blockIdx.x * cpc;
+    const int nchunks = (int)(c0 < all_chunks ? (all_chunks - c0 < cpc ? all_chunks - c0 : cpc) : 0);
+    // staging roles: pixels 2 pp and 2 pp + 1 of a chunk (pp = 4 kq + kp4); A: channel
+    // ci0 + cl (its nine tap rows cl*9 + tap, threads with cl >= 14 stage none); B: output
+    // channels cl + 16 j. The 32 lanes of a warp store to 32 distinct banks (cl*9 = cl mod 8).
+    const int kp4 = tid & 3, rg = (tid >> 2) & 7, kq = (tid >> 5) & 1, rhi = tid >> 6;
+    const int pp = kq * 4 + kp4, cl = rg + 8 * rhi;
+    const bool a_task = cl < kWgCh && ci0 + cl < Cin;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        failed = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (tid < 24) {   // rows 126 and 127 of A: zero in both stages and all three parts
+        const int stg = tid / 12, part = (tid / 4) % 3, row = 126 + ((tid >> 1) & 1), k8 = tid & 1;
+        *(uint4*)(smem + stg * kStage + part * kABytes + kmaj(row, k8)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    // the FP32 operands of one chunk, all loads of a chunk in flight together; the next
+    // chunk is loaded while the current one's MMAs run
+    float va[9][2], vb[NP / 16][2];
+    auto load_chunk = [&](int64_t c) {
+        int64_t base[2], q[2];
+        int py[2], px[2];
+        bool live[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t P = c * kK + 2 * pp + e;
+            live[e] = P < npix;
+            base[e] = live[e] ? P / HW : 0;
+            q[e] = live[e] ? P - base[e] * HW : 0;
+            py[e] = (int)(q[e] / Wd);
+            px[e] = (int)(q[e] - (int64_t)py[e] * Wd);
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const bool on = a_task && live[e];
+            const float* src = in + (base[e] * Cin + ci0 + (on ? cl : 0)) * HW + q[e];
+            const bool up = py[e] > 0, down = py[e] < H - 1, left = px[e] > 0, right = px[e] < Wd - 1;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+                const bool inb = on && (dy >= 0 || up) && (dy <= 0 || down) && (dx >= 0 || left) && (dx <= 0 || right);
+                va[tap][e] = inb ? __ldg(src + dy * Wd + dx) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NP / 16; ++j) {
+            const int co = rg + 8 * rhi + 16 * j;
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                vb[j][e] = (co < Cout && live[e]) ? __ldg(g + (base[e] * Cout + co) * HW + q[e]) : 0.f;
+        }
+    };
+    if (nchunks > 0) load_chunk(c0);
+    bool ok = true;
+    for (int i = 0; i < nchunks && ok; ++i) {
+        const int st = i & 1;
+        if (i >= 2) {   // the MMAs that read this stage (chunk i - 2) are done
+            if (!wait_bar(smem_u32(&bars[st]), (uint32_t)(((i >> 1) - 1) & 1), spin)) failed = 1;
+            __syncthreads();
+            if (failed) {   // drain: the MMAs of chunks i - 2 and i - 1 are still in flight
+                wait_bar(smem_u32(&bars[st]), (uint32_t)(((i >> 1) - 1) & 1));
+                wait_bar(smem_u32(&bars[st ^ 1]), (uint32_t)(((i - 1) >> 1) & 1));
+                ok = false;
+                break;
+            }
+        }
+        unsigned char* stage = smem + st * kStage;
+        // A: the nine tap rows of channel ci0 + cl at the two pixels
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            if (cl >= kWgCh) break;
+            const int rl = cl * 9 + tap;
+            __nv_bfloat16 h[2], m[2], l[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) split3(va[tap][e], h[e], m[e], l[e]);
+            const uint32_t off = kmaj(rl, kq) + kp4 * 4;
+            *(uint32_t*)(stage + 0 * kABytes + off) = pack2(h[0], h[1]);
+            *(uint32_t*)(stage + 1 * kABytes + off) = pack2(m[0], m[1]);
+            *(uint32_t*)(stage + 2 * kABytes + off) = pack2(l[0], l[1]);
+        }
+        // B: the output gradients of channels rg + 8 rhi + 16 j at the two pixels
+#pragma unroll
+        for (int j = 0; j < NP / 16; ++j) {
+            const int co = rg + 8 * rhi + 16 * j;
+            __nv_bfloat16 h[2], m[2], l[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) split3(vb[j][e], h[e], m[e], l[e]);
+            const uint32_t off = kmaj(co, kq) + kp4 * 4;
+            unsigned char* bs = stage + 3 * kABytes;
+            *(uint32_t*)(bs + 0 * kBBytes + off) = pack2(h[0], h[1]);
+            *(uint32_t*)(bs + 1 * kBBytes + off) = pack2(m[0], m[1]);
+            *(uint32_t*)(bs + 2 * kBBytes + off) = pack2(l[0], l[1]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // part pairs (A, B): hh, hm, mh, mm, hl, lh
+            const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                const uint64_t da = sdesc(smem_u32(stage + pa[t] * kABytes));
+                const uint64_t db = sdesc(smem_u32(stage + 3 * kABytes + pb[t] * kBBytes));
+                const uint32_t acc = (i > 0 || t > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                             ::"r"(tmem), "l"(da), "l"(db), "r"(idesc(NP)), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&bars[st])));
+        }
+        if (i + 1 < nchunks) load_chunk(c0 + i + 1);   // in flight while the MMAs run
+    }
+    if (ok && nchunks > 0) {   // both stages' last commits, so no arrive is pending at exit
+        const int last = nchunks - 1;
+        if (!wait_bar(smem_u32(&bars[last & 1]), (uint32_t)((last >> 1) & 1), spin)) failed = 1;
+        if (last >= 1 && !wait_bar(smem_u32(&bars[(last - 1) & 1]), (uint32_t)(((last - 1) >> 1) & 1), spin))
+            failed = 1;
+        __syncthreads();
+        ok = !failed;
+        if (!ok) {   // drain both stages' last commits before the tensor memory is freed
+            wait_bar(smem_u32(&bars[last & 1]), (uint32_t)((last >> 1) & 1));
+            if (last >= 1) wait_bar(smem_u32(&bars[(last - 1) & 1]), (uint32_t)(((last - 1) >> 1) & 1));
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        // this thread's TMEM lane is row tid of the tile: channel ci0 + tid / 9
+        const int r = (tid < kWgCh * 9 && ci0 + tid / 9 < Cin) ? ci0 * 9 + tid : rows;
+#pragma unroll
+        for (int n0 = 0; n0 < NP; n0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (r < rows) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int co = n0 + j;
+                    if (co < Cout)
+                        partial[((int64_t)blockIdx.x * Cout + co) * rows + r] = nchunks > 0 ? __uint_as_float(v[j]) : 0.f;
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+}
+
+// Grid of the tensor-core weight gradient: z ranges of at least 8 chunks of 16 pixels,
+// about 1200 CTAs over the M tiles (up to 8 resident per SM), partials of at most 2^23 floats
+struct WgradTcShape {
+    int z, cpc, mtiles;
+};
+
+inline WgradTcShape wgrad_tc_shape(int Cin, int Cout, int64_t npix) {
+    WgradTcShape w;
+    w.mtiles = (Cin + kWgCh - 1) / kWgCh;
+    const int64_t chunks = (npix + kK - 1) / kK;
+    int64_t z = (1200 + w.mtiles - 1) / w.mtiles;
+    const int64_t zcap = ((int64_t)1 << 23) / ((int64_t)Cout * Cin * 9);
+    z = z < zcap ? z : zcap;
+    const int64_t zmax = (chunks + 7) / 8;
+    z = z < zmax ? z : zmax;
+    z = z < 1 ? 1 : z;
+    w.cpc = (int)((chunks + z - 1) / z);
+    w.z = (int)((chunks + w.cpc - 1) / w.cpc);
+    return w;
+}
+
+template <int NP>
+size_t wgrad_smem_bytes() {
+    constexpr size_t need = 2 * (3 * kM * kK * 2 + 3 * NP * kK * 2);
+    const size_t per_sm = 228 * 1024, ctas = 512 / tmem_cols(NP);
+    const size_t pad = per_sm / ctas + 1;
+    return need > pad ? need : pad;
+}
+
+template <int NP>
+int launch_wgrad_np(const float* in, int Cin, const float* g, int Cout, int B, int H, int Wd, float* partial, int* nz,
+                    int* err, long spin, cudaStream_t s) {
+    const size_t smem = wgrad_smem_bytes<NP>();
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(wgrad_tc_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return -1;
+        attr = true;
+    }
+    const WgradTcShape w = wgrad_tc_shape(Cin, Cout, (int64_t)B * H * Wd);
+    wgrad_tc_kernel<NP><<<dim3((unsigned)w.z, (unsigned)w.mtiles), kM, smem, s>>>(in, Cin, g, Cout, B, H, Wd, w.cpc,
+                                                                                   partial, err, spin);
+    *nz = w.z;
+    return 0;
+}
+
+// partial[z][co][ci*9 + tap] for z < *nz (Cout up to 64); -1: not handled here
+int wgrad(const float* in, int Cin, const float* g, int Cout, int B, int H, int Wd, float* partial, int* nz, int* err,
+          long spin, cudaStream_t s) {
+    if (Cout <= 16) return launch_wgrad_np<16>(in, Cin, g, Cout, B, H, Wd, partial, nz, err, spin, s);
+    if (Cout <= 32) return launch_wgrad_np<32>(in, Cin, g, Cout, B, H, Wd, partial, nz, err, spin, s);
+    if (Cout <= 64) return launch_wgrad_np<64>(in, Cin, g, Cout, B, H, Wd, partial, nz, err, spin, s);
+    return -1;
 }
 
 // out (N channels) = conv3x3(in (Kc channels)); N up to 128. spin: polls per bounded wait
@@ -831,7 +1090,16 @@ void conv_back(const Net& n, int layer, const float* in, const float* g, float* 
         if (din) conv1x1_dgrad_kernel<WT><<<blocks_for(B * plane), kT, 0, s>>>(g, c.cin, W, din, B, plane);
         return;
     }
-    {
+    bool wdone = false;
+    if constexpr (std::is_same<WT, __nv_bfloat16>::value) {
+        int nz = 0;
+        if (n.tc && tc::wgrad(in, c.cin, g, c.cout, B, H, Wd, n.wpart, &nz, n.err, n.spin, s) == 0) {
+            const int64_t nw = (int64_t)c.cout * c.cin * 9;
+            wgrad_reduce_kernel<<<blocks_for(nw), kT, 0, s>>>(n.wpart, nz, nw, dW);
+            wdone = true;
+        }
+    }
+    if (!wdone) {
         const int cog = (c.cout + 15) / 16, cig = (c.cin + 15) / 16;
         const WgradShape ws = wgrad_shape(H, Wd, cog * cig * B);
         const int nz = B * ws.chunks_per_image;
@@ -1049,8 +1317,12 @@ int x0net_create(x0net* out, int H, int W, int batch_max, int bf16_weights, int 
             for (int bb = 1; bb <= B; ++bb) {   // the chunking depends on the batch of the call
                 if (kLayers[l].k == 3) {
                     const WgradShape ws = wgrad_shape(H / lvl[l], W / lvl[l], cog * cig * bb);
-                    const int64_t v = bb * ws.chunks_per_image * (int64_t)kLayers[l].cout * kLayers[l].cin * 9;
+                    const int64_t nw = (int64_t)kLayers[l].cout * kLayers[l].cin * 9;
+                    const int64_t v = bb * ws.chunks_per_image * nw;
                     need = v > need ? v : need;
+                    const tc::WgradTcShape wt =
+                        tc::wgrad_tc_shape(kLayers[l].cin, kLayers[l].cout, (int64_t)bb * (H / lvl[l]) * (W / lvl[l]));
+                    need = wt.z * nw > need ? wt.z * nw : need;
                 }
                 // channel sums (bias and 1x1 gradients): chunks of kRedChunk pixels
                 const int64_t px = (int64_t)(H / lvl[l]) * (W / lvl[l]);

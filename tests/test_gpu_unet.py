@@ -85,6 +85,7 @@ def test_training_reduces_loss():
 @pytest.mark.parametrize("B,H,smooth,res_w", [(2, 16, 0, 0.0), (3, 40, 3, 1.0), (2, 128, 2, 0.0)])
 def test_tensor_core_convolutions_match_cuda_cores(B, H, smooth, res_w):
     """BF16 mode: the tcgen05 convolutions (FP32 activations split into three BF16 parts)
+    and weight gradients (activations and output gradients split, six part products)
     give the CUDA-core result up to the FP32 accumulation inside the tensor core and the
     order of the sums (observed 2e-5 relative on the output at 128^2 over 15 layers):
     forward output, loss and every layer's gradient. H = 40 leaves a ragged pixel tile at
@@ -130,3 +131,16 @@ def test_tensor_core_wait_timeout_is_reported_and_recoverable():
     net.forward(xd, out2)
     net.status()
     assert torch.equal(out2, out_ok)
+    # the backward kernels (tensor-core weight gradient and backward-data convolutions)
+    loss_ok, g_ok = net.gradient(xd, td)
+    net.status()
+    net.set_wait_limit(0)
+    with pytest.raises(pkg.SStepError) as ei:
+        net.gradient(xd, td)          # the gradient call reports the flag itself
+    assert ei.value.status == -6
+    with pytest.raises(pkg.SStepError):
+        net.status()                  # ... and x0net_status reports it once more and clears it
+    net.set_wait_limit(-1)
+    loss2, g2 = net.gradient(xd, td)
+    net.status()
+    assert loss2 == loss_ok and np.array_equal(g2, g_ok)
