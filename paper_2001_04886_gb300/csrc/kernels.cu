@@ -88,6 +88,50 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
     }
 }
 
+// The common case of the powers: constant coefficients, the factor known on the host,
+// no separate shift vector. The scaled coefficients fy c (fy (c_0 - shift) on the
+// diagonal) come in from the host, so a point costs its 7 (5 in 2-D) FP64 multiply-adds
+// and nothing else on the FP64 pipe; same values, bit for bit, as stencil_kernel.
+struct ScaledCoef {
+    double c[7];
+};
+
+template <bool THREE, bool WCOPY>
+__global__ void __launch_bounds__(kThreads) stencil_const_kernel(int nx, int ny, int nz, ScaledCoef k,
+                                                                 const double* __restrict__ v,
+                                                                 double* __restrict__ y, double fw,
+                                                                 double* __restrict__ w, const SolverState* st,
+                                                                 int gate, int zchunk) {
+    if (!gate_open(st, gate)) return;
+    const int tx = (nx + 31) / 32;
+    const int x = (int)(blockIdx.x % tx) * 32 + threadIdx.x;
+    const int yy = (int)(blockIdx.x / tx) * 8 + threadIdx.y;
+    const int zb = blockIdx.y * zchunk, ze = min(nz, zb + zchunk);
+    if (x >= nx || yy >= ny || zb >= ze) return;
+    const int64_t pl = (int64_t)nx * ny;
+    int64_t p = (int64_t)zb * pl + (int64_t)yy * nx + x;
+    const bool xl = x > 0, xr = x < nx - 1, yl = yy > 0, yr = yy < ny - 1;
+    double vm = (THREE && zb > 0) ? __ldg(v + p - pl) : 0.0;
+    double vc = __ldg(v + p);
+#pragma unroll 2
+    for (int z = zb; z < ze; ++z, p += pl) {
+        const double vp = (THREE && z + 1 < nz) ? __ldg(v + p + pl) : 0.0;
+        double acc = k.c[0] * vc;
+        if (xl) acc = fma(k.c[1], __ldg(v + p - 1), acc);
+        if (xr) acc = fma(k.c[2], __ldg(v + p + 1), acc);
+        if (yl) acc = fma(k.c[3], __ldg(v + p - nx), acc);
+        if (yr) acc = fma(k.c[4], __ldg(v + p + nx), acc);
+        if (THREE) {
+            if (z > 0) acc = fma(k.c[5], vm, acc);
+            if (z < nz - 1) acc = fma(k.c[6], vp, acc);
+        }
+        y[p] = acc;
+        if (WCOPY) w[p] = fw * vc;
+        vm = vc;
+        vc = vp;
+    }
+}
+
 void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y, double fw, double* w,
                     const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift,
                     const double* u) {
@@ -97,8 +141,23 @@ void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y,
     chunks = chunks < 1 ? 1 : (chunks > A.nz ? A.nz : chunks);
     const int zchunk = (A.nz + chunks - 1) / chunks;
     chunks = (A.nz + zchunk - 1) / zchunk;
-    stencil_kernel<<<dim3(tiles, chunks), dim3(32, 8), 0, stream>>>(A, v, fy, y, fw, w, dscale, st, gate, zchunk,
-                                                                    shift, u);
+    const dim3 grid(tiles, chunks), block(32, 8);
+    if (!A.variable && !dscale && !u) {
+        ScaledCoef k;
+        for (int q = 0; q < 7; ++q) k.c[q] = fy * A.c[q];
+        k.c[0] = fy * (A.c[0] - shift);
+        const bool three = A.dim == 3;
+        if (three && w)
+            stencil_const_kernel<true, true><<<grid, block, 0, stream>>>(A.nx, A.ny, A.nz, k, v, y, fw, w, st, gate, zchunk);
+        else if (three)
+            stencil_const_kernel<true, false><<<grid, block, 0, stream>>>(A.nx, A.ny, A.nz, k, v, y, fw, w, st, gate, zchunk);
+        else if (w)
+            stencil_const_kernel<false, true><<<grid, block, 0, stream>>>(A.nx, A.ny, A.nz, k, v, y, fw, w, st, gate, zchunk);
+        else
+            stencil_const_kernel<false, false><<<grid, block, 0, stream>>>(A.nx, A.ny, A.nz, k, v, y, fw, w, st, gate, zchunk);
+        return;
+    }
+    stencil_kernel<<<grid, block, 0, stream>>>(A, v, fy, y, fw, w, dscale, st, gate, zchunk, shift, u);
 }
 
 // ================================================================== residual
