@@ -318,6 +318,13 @@ int x0net_set_residual_weight(x0net X, float w, float kappa);
 /* params: host or device float32 array of x0net_num_params values; resets Adam */
 int x0net_set_params(x0net X, const float* params, void* stream);
 int x0net_get_params(x0net X, float* params, void* stream);
+/* The training state: FP32 master weights, Adam's first and second moments (num_params
+ * floats each, host or device pointers) and the Adam step count. get synchronises
+ * `stream`; set also re-derives the BF16 weights. Saving the state after a step and
+ * setting it on a fresh network resumes training bit for bit (every kernel of a step
+ * reduces in a fixed order). */
+int x0net_get_state(x0net X, float* params, float* m, float* v, int64_t* step, void* stream);
+int x0net_set_state(x0net X, const float* params, const float* m, const float* v, int64_t step, void* stream);
 int x0net_forward(x0net X, const float* input, float* output, int batch, void* stream);
 /* loss = mean over batch*H*W of (out - target)^2 and its gradient with respect to
  * every parameter (host or device outputs; either may be NULL). Synchronises. */

@@ -72,6 +72,8 @@ SIGNATURES = {
     "x0net_set_residual_weight": (c_int, [c_void_p, ctypes.c_float, ctypes.c_float]),
     "x0net_set_params": (c_int, [c_void_p, c_void_p, c_void_p]),
     "x0net_get_params": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "x0net_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(c_int64), c_void_p]),
+    "x0net_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "x0net_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "x0net_gradient": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "x0net_set_tensor_cores": (c_int, [c_void_p, c_int]),
@@ -476,6 +478,29 @@ class X0Net:
         out = np.zeros(self.num_params, dtype=np.float32)
         _check("x0net_get_params", lib().x0net_get_params(self.handle, c_void_p(out.ctypes.data), _stream(stream)))
         return out
+
+    def get_state(self, stream=None):
+        """The training state: dict(params, m, v) float32 host arrays and step (Adam)."""
+        import numpy as np
+
+        st = {k: np.zeros(self.num_params, dtype=np.float32) for k in ("params", "m", "v")}
+        step = c_int64()
+        _check("x0net_get_state", lib().x0net_get_state(self.handle, c_void_p(st["params"].ctypes.data),
+                                                        c_void_p(st["m"].ctypes.data), c_void_p(st["v"].ctypes.data),
+                                                        ctypes.byref(step), _stream(stream)))
+        st["step"] = int(step.value)
+        return st
+
+    def set_state(self, state, stream=None):
+        """Restores a state from get_state (or a checkpoint file's contents)."""
+        import numpy as np
+
+        arr = {k: np.ascontiguousarray(state[k], dtype=np.float32) for k in ("params", "m", "v")}
+        if any(a.shape != (self.num_params,) for a in arr.values()):
+            raise ValueError("state arrays must hold num_params floats each")
+        _check("x0net_set_state", lib().x0net_set_state(self.handle, c_void_p(arr["params"].ctypes.data),
+                                                        c_void_p(arr["m"].ctypes.data), c_void_p(arr["v"].ctypes.data),
+                                                        int(state["step"]), _stream(stream)))
 
     def forward(self, inp, out, stream=None):
         _check("x0net_forward", lib().x0net_forward(self.handle, self._f32(inp), self._f32(out), inp.shape[0],

@@ -88,21 +88,40 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
     }
 }
 
-// The common case of the powers: constant coefficients, the factor known on the host,
-// no separate shift vector. The scaled coefficients fy c (fy (c_0 - shift) on the
-// diagonal) come in from the host, so a point costs its 7 (5 in 2-D) FP64 multiply-adds
-// and nothing else on the FP64 pipe; same values, bit for bit, as stencil_kernel.
-struct ScaledCoef {
-    double c[7];
+// The common case of the powers: constant coefficients and no separate shift vector.
+// With the factor known on the host the scaled coefficients fy c (fy (c_0 - shift) on
+// the diagonal) come in from the host; with a device factor d (DSCALE: the first power
+// of a block, d = 1/||u||) eight threads of each CTA form (fy d) c and fw d once in
+// shared memory. Either way a point costs its 7 (5 in 2-D) FP64 multiply-adds and
+// nothing else on the FP64 pipe, with the same operations as stencil_kernel.
+struct ConstCoef {
+    double c[7];       // !DSCALE: fy c (diagonal fy (c_0 - shift)); DSCALE: the raw c
+    double fy, shift;  // DSCALE only
 };
 
-template <bool THREE, bool WCOPY>
-__global__ void __launch_bounds__(kThreads) stencil_const_kernel(int nx, int ny, int nz, ScaledCoef k,
+template <bool THREE, bool WCOPY, bool DSCALE>
+__global__ void __launch_bounds__(kThreads) stencil_const_kernel(int nx, int ny, int nz, ConstCoef k,
                                                                  const double* __restrict__ v,
                                                                  double* __restrict__ y, double fw,
-                                                                 double* __restrict__ w, const SolverState* st,
-                                                                 int gate, int zchunk) {
+                                                                 double* __restrict__ w, const double* dscale,
+                                                                 const SolverState* st, int gate, int zchunk) {
     if (!gate_open(st, gate)) return;
+    __shared__ double sk[8];
+    if (DSCALE) {
+        const int t = threadIdx.y * 32 + threadIdx.x;
+        if (t < 8) {
+            const double d = *dscale, fyd = k.fy * d;
+            double ct = k.c[0] - k.shift;   // t == 0; the others select their raw c without indexing
+#pragma unroll
+            for (int q = 1; q < 7; ++q)
+                if (t == q) ct = k.c[q];
+            sk[t] = t < 7 ? fyd * ct : fw * d;
+        }
+        __syncthreads();
+    }
+    const double c0 = DSCALE ? sk[0] : k.c[0], c1 = DSCALE ? sk[1] : k.c[1], c2 = DSCALE ? sk[2] : k.c[2];
+    const double c3 = DSCALE ? sk[3] : k.c[3], c4 = DSCALE ? sk[4] : k.c[4], c5 = DSCALE ? sk[5] : k.c[5];
+    const double c6 = DSCALE ? sk[6] : k.c[6], fwd = DSCALE ? sk[7] : fw;
     const int tx = (nx + 31) / 32;
     const int x = (int)(blockIdx.x % tx) * 32 + threadIdx.x;
     const int yy = (int)(blockIdx.x / tx) * 8 + threadIdx.y;
@@ -116,20 +135,28 @@ __global__ void __launch_bounds__(kThreads) stencil_const_kernel(int nx, int ny,
 #pragma unroll 2
     for (int z = zb; z < ze; ++z, p += pl) {
         const double vp = (THREE && z + 1 < nz) ? __ldg(v + p + pl) : 0.0;
-        double acc = k.c[0] * vc;
-        if (xl) acc = fma(k.c[1], __ldg(v + p - 1), acc);
-        if (xr) acc = fma(k.c[2], __ldg(v + p + 1), acc);
-        if (yl) acc = fma(k.c[3], __ldg(v + p - nx), acc);
-        if (yr) acc = fma(k.c[4], __ldg(v + p + nx), acc);
+        double acc = c0 * vc;
+        if (xl) acc = fma(c1, __ldg(v + p - 1), acc);
+        if (xr) acc = fma(c2, __ldg(v + p + 1), acc);
+        if (yl) acc = fma(c3, __ldg(v + p - nx), acc);
+        if (yr) acc = fma(c4, __ldg(v + p + nx), acc);
         if (THREE) {
-            if (z > 0) acc = fma(k.c[5], vm, acc);
-            if (z < nz - 1) acc = fma(k.c[6], vp, acc);
+            if (z > 0) acc = fma(c5, vm, acc);
+            if (z < nz - 1) acc = fma(c6, vp, acc);
         }
         y[p] = acc;
-        if (WCOPY) w[p] = fw * vc;
+        if (WCOPY) w[p] = fwd * vc;
         vm = vc;
         vc = vp;
     }
+}
+
+template <bool THREE, bool WCOPY, bool DSCALE>
+void launch_const(const StencilDesc& A, const ConstCoef& k, const double* v, double* y, double fw, double* w,
+                  const double* dscale, const SolverState* st, int gate, int zchunk, dim3 grid, dim3 block,
+                  cudaStream_t stream) {
+    stencil_const_kernel<THREE, WCOPY, DSCALE><<<grid, block, 0, stream>>>(A.nx, A.ny, A.nz, k, v, y, fw, w, dscale,
+                                                                           st, gate, zchunk);
 }
 
 void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y, double fw, double* w,
@@ -142,20 +169,24 @@ void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y,
     const int zchunk = (A.nz + chunks - 1) / chunks;
     chunks = (A.nz + zchunk - 1) / zchunk;
     const dim3 grid(tiles, chunks), block(32, 8);
-    if (!A.variable && !dscale && !u) {
-        ScaledCoef k;
-        for (int q = 0; q < 7; ++q) k.c[q] = fy * A.c[q];
-        k.c[0] = fy * (A.c[0] - shift);
-        const bool three = A.dim == 3;
-        if (three && w)
-            stencil_const_kernel<true, true><<<grid, block, 0, stream>>>(A.nx, A.ny, A.nz, k, v, y, fw, w, st, gate, zchunk);
-        else if (three)
-            stencil_const_kernel<true, false><<<grid, block, 0, stream>>>(A.nx, A.ny, A.nz, k, v, y, fw, w, st, gate, zchunk);
-        else if (w)
-            stencil_const_kernel<false, true><<<grid, block, 0, stream>>>(A.nx, A.ny, A.nz, k, v, y, fw, w, st, gate, zchunk);
-        else
-            stencil_const_kernel<false, false><<<grid, block, 0, stream>>>(A.nx, A.ny, A.nz, k, v, y, fw, w, st, gate, zchunk);
-        return;
+    if (!A.variable && !u) {
+        ConstCoef k;
+        k.fy = fy;
+        k.shift = shift;
+        for (int q = 0; q < 7; ++q) k.c[q] = dscale ? A.c[q] : fy * A.c[q];
+        if (!dscale) k.c[0] = fy * (A.c[0] - shift);
+        const bool three = A.dim == 3, wc = w != nullptr, ds = dscale != nullptr;
+#define SSTEP_CONST(T3, WC, DS) \
+    if (three == T3 && wc == WC && ds == DS) return launch_const<T3, WC, DS>(A, k, v, y, fw, w, dscale, st, gate, zchunk, grid, block, stream);
+        SSTEP_CONST(true, false, false)
+        SSTEP_CONST(true, true, true)
+        SSTEP_CONST(true, true, false)
+        SSTEP_CONST(true, false, true)
+        SSTEP_CONST(false, false, false)
+        SSTEP_CONST(false, true, true)
+        SSTEP_CONST(false, true, false)
+        SSTEP_CONST(false, false, true)
+#undef SSTEP_CONST
     }
     stencil_kernel<<<grid, block, 0, stream>>>(A, v, fy, y, fw, w, dscale, st, gate, zchunk, shift, u);
 }

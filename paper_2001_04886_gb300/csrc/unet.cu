@@ -1397,6 +1397,33 @@ int x0net_get_params(x0net X, float* params, void* stream) {
     return SSTEP_OK;
 }
 
+int x0net_get_state(x0net X, float* params, float* m, float* v, int64_t* step, void* stream) {
+    if (!X || !params || !m || !v || !step) return SSTEP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Net& n = X->n;
+    const size_t bytes = sizeof(float) * n.nparams;
+    if (cudaMemcpyAsync(params, n.w, bytes, cudaMemcpyDefault, s) != cudaSuccess ||
+        cudaMemcpyAsync(m, n.m, bytes, cudaMemcpyDefault, s) != cudaSuccess ||
+        cudaMemcpyAsync(v, n.v, bytes, cudaMemcpyDefault, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return SSTEP_ERR_CUDA;
+    *step = n.step;
+    return SSTEP_OK;
+}
+
+int x0net_set_state(x0net X, const float* params, const float* m, const float* v, int64_t step, void* stream) {
+    if (!X || !params || !m || !v || step < 0) return SSTEP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Net& n = X->n;
+    const size_t bytes = sizeof(float) * n.nparams;
+    if (cudaMemcpyAsync(n.w, params, bytes, cudaMemcpyDefault, s) != cudaSuccess ||
+        cudaMemcpyAsync(n.m, m, bytes, cudaMemcpyDefault, s) != cudaSuccess ||
+        cudaMemcpyAsync(n.v, v, bytes, cudaMemcpyDefault, s) != cudaSuccess)
+        return SSTEP_ERR_CUDA;
+    to_bf16_kernel<<<blocks_for(n.nparams), kT, 0, s>>>(n.w, n.wb, n.nparams);
+    n.step = step;
+    return cudaStreamSynchronize(s) == cudaSuccess && cudaGetLastError() == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA;
+}
+
 int x0net_forward(x0net X, const float* input, float* output, int batch, void* stream) {
     if (!X || !input || !output || batch < 1 || batch > X->n.Bmax) return SSTEP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;

@@ -99,15 +99,72 @@ def generate(seeds, N, device, chunk=1024, report=None):
     return torch.cat(feats), torch.stack(targets)
 
 
-def train(net, feats, targets, epochs, batch=32, lr=1e-3, seed=0, log=None):
-    """Adam on the mean-squared error; learning rate halved for the last third of the epochs."""
+# checkpoint file: magic, format version, then little-endian int64 num_params, Adam
+# step, epochs done, shuffle seed, and the float32 arrays params, m, v (num_params each)
+_CKPT_MAGIC = b"SSX0"
+_CKPT_VERSION = 1
+
+
+def save_checkpoint(path, net, epoch, seed):
+    """Writes the network's training state after `epoch` completed epochs (atomically:
+    a temporary file renamed over `path`)."""
+    import os
+
+    st = net.get_state()
+    n = st["params"].shape[0]
+    head = np.array([n, st["step"], epoch, seed], dtype="<i8")
+    tmp = str(path) + ".tmp"
+    with open(tmp, "wb") as fh:
+        fh.write(_CKPT_MAGIC)
+        fh.write(np.array([_CKPT_VERSION], dtype="<u4").tobytes())
+        fh.write(head.tobytes())
+        for k in ("params", "m", "v"):
+            fh.write(np.ascontiguousarray(st[k], dtype="<f4").tobytes())
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path):
+    """Reads a checkpoint: dict(params, m, v, step, epoch, seed); ValueError if the file is
+    not one, is of another version or is truncated."""
+    with open(path, "rb") as fh:
+        raw = fh.read()
+    if len(raw) < 40 or raw[:4] != _CKPT_MAGIC:
+        raise ValueError(f"{path}: not a checkpoint")
+    if int(np.frombuffer(raw[4:8], dtype="<u4")[0]) != _CKPT_VERSION:
+        raise ValueError(f"{path}: unsupported checkpoint version")
+    n, step, epoch, seed = (int(v) for v in np.frombuffer(raw[8:40], dtype="<i8"))
+    if n < 0 or len(raw) != 40 + 12 * n:
+        raise ValueError(f"{path}: truncated checkpoint")
+    arr = [np.frombuffer(raw[40 + 4 * n * i : 40 + 4 * n * (i + 1)], dtype="<f4").astype(np.float32) for i in range(3)]
+    return {"params": arr[0], "m": arr[1], "v": arr[2], "step": step, "epoch": epoch, "seed": seed}
+
+
+def train(net, feats, targets, epochs, batch=32, lr=1e-3, seed=0, log=None, checkpoint=None, resume=False):
+    """Adam on the mean-squared error; learning rate halved for the last third of the epochs.
+
+    checkpoint: a path written after every epoch (save_checkpoint). resume: if that file
+    exists, training continues from it (the same seed required): the state is restored
+    and the shuffles of the completed epochs are drawn again, so the result equals an
+    uninterrupted run. Returns the per-epoch losses of the epochs run here.
+    """
+    import os
+
     import torch
 
     S = feats.shape[0]
     g = torch.Generator(device="cpu").manual_seed(seed)
     lossd = torch.zeros(1, dtype=torch.float32, device=feats.device)
     history = []
-    for ep in range(epochs):
+    start = 0
+    if resume and checkpoint is not None and os.path.exists(checkpoint):
+        ck = load_checkpoint(checkpoint)
+        if ck["seed"] != seed:
+            raise ValueError("checkpoint was written with another shuffle seed")
+        net.set_state(ck)
+        start = min(ck["epoch"], epochs)
+        for _ in range(start):
+            torch.randperm(S, generator=g)
+    for ep in range(start, epochs):
         rate = lr if ep < (2 * epochs) // 3 else lr / 2
         perm = torch.randperm(S, generator=g).to(feats.device)
         tot, nb = 0.0, 0
@@ -120,6 +177,8 @@ def train(net, feats, targets, epochs, batch=32, lr=1e-3, seed=0, log=None):
                 nb += 1
         net.status()   # raises if a tensor-core kernel's bounded wait ran out
         history.append(tot / max(nb, 1))
+        if checkpoint is not None:
+            save_checkpoint(checkpoint, net, ep + 1, seed)
         if log:
             log(f"epoch {ep}: loss {history[-1]:.4e}")
     return history

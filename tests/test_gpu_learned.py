@@ -68,3 +68,51 @@ def test_trained_network_reduces_krylov_steps():
     # fewer Krylov steps than from x0 = 0 and than from x0 = 0 after the same smoothing sweeps
     assert ev["predicted"]["mean_iters"] < ev["zero"]["mean_iters"]
     assert ev["predicted"]["mean_iters"] < ev["zero_smoothed"]["mean_iters"]
+
+
+class _DiesAfter:
+    """The real network, except that the process 'dies' at a given training step."""
+
+    def __init__(self, net, steps):
+        self.net, self.left = net, steps
+
+    def __getattr__(self, name):
+        return getattr(self.net, name)
+
+    def train_step(self, *args, **kwargs):
+        if self.left == 0:
+            raise RuntimeError("the process dies here")
+        self.left -= 1
+        return self.net.train_step(*args, **kwargs)
+
+
+def test_training_resumes_bit_for_bit(tmp_path):
+    """Checkpoint after every epoch; a run that dies inside epoch 1 and is resumed from
+    the file on a fresh network ends with the uninterrupted run's weights, Adam moments
+    and step count, bit for bit (every kernel of a step reduces in a fixed order)."""
+    d = dev()
+    N, B = 16, 4
+    g = torch.Generator().manual_seed(8)
+    feats = torch.randn(24, 2, N, N, generator=g).to(d)
+    targets = torch.randn(24, 1, N, N, generator=g).to(d)
+
+    def fresh():
+        net = pkg.X0Net(N, N, B, bf16=True, smooth=2, residual_weight=0.5, kappa=2.0)
+        net.set_params(learned._init_params(inputs.uniform01(1, net.num_params)))
+        return net
+
+    full = fresh()
+    learned.train(full, feats, targets, epochs=3, batch=B, lr=1e-3, seed=2)
+    ref = full.get_state()
+    ck = tmp_path / "unet.ckpt"
+    with pytest.raises(RuntimeError):
+        learned.train(_DiesAfter(fresh(), 8), feats, targets, epochs=3, batch=B, lr=1e-3, seed=2, checkpoint=ck)
+    assert learned.load_checkpoint(ck)["epoch"] == 1
+    resumed = fresh()
+    learned.train(resumed, feats, targets, epochs=3, batch=B, lr=1e-3, seed=2, checkpoint=ck, resume=True)
+    got = resumed.get_state()
+    assert got["step"] == ref["step"] == 18
+    for k in ("params", "m", "v"):
+        assert np.array_equal(got[k], ref[k]), k
+    for net in (full, resumed):
+        net.close()
