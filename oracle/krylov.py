@@ -25,6 +25,14 @@ def norm(v):
     return float(np.sqrt(np.dot(v, v)))
 
 
+def residual_scale(f):
+    """||f||, the denominator of the relative residual test ||f - A x|| / ||f|| <= tol;
+    1 when f = 0 (A is nonsingular, so x = 0 is the solution and the test is made on
+    ||f - A x|| itself: from x0 = 0 the solve ends at once)."""
+    nf = norm(f)
+    return nf if nf > 0.0 else 1.0
+
+
 class GivensLSQ:
     """min_y || g0 e_1 - H y || for an upper Hessenberg H given column by column (eq. 2).
 
@@ -85,7 +93,7 @@ def gmres(A, f, x0, m, tol, max_cycles=1000, orth="cgs"):
     Returns dict(x, status, cycles, iters, matvecs, history, relres).
     """
     n = f.shape[0]
-    nf = norm(f)
+    nf = residual_scale(f)
     x = np.array(x0, dtype=np.float64, copy=True)
     hist = []
     cycles = iters = mv = 0
@@ -138,7 +146,7 @@ def omin(A, f, x0, k, tol, max_iters=100000):
     directions; the printed min(0, i-k+1) would always give GCR). k = 0 keeps
     no previous direction (the minimal-residual steepest descent of Sec. 3).
     """
-    nf = norm(f)
+    nf = residual_scale(f)
     x = np.array(x0, dtype=np.float64, copy=True)
     mv = 0
     hist = []

@@ -42,7 +42,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import STATUS_BREAKDOWN, STATUS_NOT_CONVERGED, STATUS_OK
-from .krylov import GivensLSQ, norm
+from .krylov import GivensLSQ, norm, residual_scale
 
 
 # ---------------------------------------------------------------- small dense algebra
@@ -174,7 +174,7 @@ def sstep_gmres(A, f, x0, s, m, tol, sigma, max_cycles=1000, trace=None, basis="
     assert m % s == 0 and s >= 1
     n = f.shape[0]
     nb = m // s
-    nf = norm(f)
+    nf = residual_scale(f)
     x = np.array(x0, dtype=np.float64, copy=True)
     hist = []
     cycles = iters = mv = 0
@@ -344,7 +344,7 @@ def sstep_omin(A, f, x0, s, k, tol, sigma, max_iters=100000, trace=None, precond
     if basis not in ("monomial", "ortho"):
         raise ValueError(basis)
     ortho = basis == "ortho"
-    nf = norm(f)
+    nf = residual_scale(f)
     x = np.array(x0, dtype=np.float64, copy=True)
     mv = 0
     hist = []

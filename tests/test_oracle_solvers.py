@@ -199,3 +199,34 @@ def test_cholesky_helpers():
     b = rng.standard_normal((6, 2))
     assert np.allclose(sstep.cholesky_solve(L, b), np.linalg.solve(W, b), atol=1e-10)
     assert sstep.cholesky_upper(-np.eye(3)) is None
+
+
+def test_zero_right_hand_side():
+    """f = 0: A is nonsingular, so x = 0 is the solution. From x0 = 0 every solver ends
+    at the first residual (one product, relres 0); from x0 != 0 the test is made on
+    ||A x|| itself and the iterate goes to 0."""
+    A, _, _ = system((6, 6), (20.0, 20.0))
+    f, z = np.zeros(A.n), np.zeros(A.n)
+    for res in (krylov.gmres(A, f, z, 10, 1e-8), krylov.omin(A, f, z, 2, 1e-8),
+                sstep.sstep_gmres(A, f, z, 4, 20, 1e-8, 0.125), sstep.sstep_omin(A, f, z, 2, 1, 1e-8, 0.125)):
+        assert res["status"] == STATUS_OK and res["history"] == [0.0] and res["matvecs"] == 1
+        assert not np.any(res["x"]) and res["relres"] == 0.0
+    x0 = inputs.x_true(3, A.n)
+    r = sstep.sstep_gmres(A, f, x0, 4, 20, 1e-10, 0.125)
+    assert r["status"] == STATUS_OK and np.linalg.norm(A.apply(r["x"])) <= 1e-10
+
+
+def test_lucky_breakdown_and_degenerate_block():
+    """A = I: the Krylov space of f has dimension 1. GMRES (and s-step GMRES with s = 1)
+    meets the lucky breakdown (h_21 = 0, nu = 0) and returns x = f exactly after one
+    step; a block of s = 2 monomial powers is then linearly dependent, its Gram matrix
+    singular, and the method reports a breakdown (status -4) without taking a step."""
+    n = 25
+    A = stencil.Stencil((5, 5), np.ones(n), [np.zeros(n), np.zeros(n)], [np.zeros(n), np.zeros(n)])
+    f = inputs.x_true(4, n)
+    z = np.zeros(n)
+    for res in (krylov.gmres(A, f, z, 10, 1e-12), sstep.sstep_gmres(A, f, z, 1, 10, 1e-12, 1.0)):
+        assert res["status"] == STATUS_OK and res["iters"] == 1
+        assert np.allclose(res["x"], f, rtol=0, atol=1e-15)
+    bad = sstep.sstep_gmres(A, f, z, 2, 10, 1e-12, 1.0)
+    assert bad["status"] == STATUS_BREAKDOWN and bad["iters"] == 0
