@@ -451,8 +451,11 @@ __device__ __noinline__ void run_epilogue(const Epi& e, const double* red, int k
         case EPI_NONE:
             for (int t = threadIdx.x; t < ka * kb; t += blockDim.x) e.out[(t % ka) + (t / ka) * e.ldo] = red[t];
             break;
-        case EPI_NF:
-            if (threadIdx.x == 0) e.st->nf = sqrt(red[0]);
+        case EPI_NF:   // the denominator of every relative residual below
+            if (threadIdx.x == 0) {   // f = 0: x = 0 is the solution; test ||f - A x|| itself
+                const double nf = sqrt(red[0]);
+                e.st->nf = nf > 0.0 ? nf : 1.0;
+            }
             break;
         case EPI_FINAL:
             if (threadIdx.x == 0) e.st->relres = sqrt(red[0]) / e.st->nf;

@@ -739,45 +739,6 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int nz, i
     }
 }
 
-// dW[co][ci][k] = sum_{b,y,x} g[b,co,y,x] in[b,ci,y+ky-1,x+kx-1], one CTA per (ci, co):
-// each thread sums its pixels, then a fixed-order CTA reduction.
-__global__ void __launch_bounds__(kT) conv3x3_wgrad_kernel(const float* __restrict__ in, int Cin,
-                                                           const float* __restrict__ g, int Cout, int B, int H, int Wd,
-                                                           float* __restrict__ dW) {
-    const int ci = blockIdx.x, co = blockIdx.y;
-    const int64_t plane = (int64_t)H * Wd, npix = (int64_t)B * plane;
-    float acc[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] = 0.f;
-    for (int64_t p = threadIdx.x; p < npix; p += kT) {
-        const int b = (int)(p / plane);
-        const int64_t rem = p - (int64_t)b * plane;
-        const int y = (int)(rem / Wd), x = (int)(rem - (int64_t)y * Wd);
-        const float gv = g[((int64_t)b * Cout + co) * plane + rem];
-        const float* src = in + ((int64_t)b * Cin + ci) * plane;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int yy = y + k / 3 - 1, xx = x + k % 3 - 1;
-            const float v = (yy >= 0 && yy < H && xx >= 0 && xx < Wd) ? src[(int64_t)yy * Wd + xx] : 0.f;
-            acc[k] = fmaf(gv, v, acc[k]);
-        }
-    }
-    __shared__ float red[kT / 32][9];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        float t = acc[k];
-        for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-        if (lane == 0) red[warp][k] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < 9) {
-        float t = 0.f;
-        for (int w = 0; w < kT / 32; ++w) t += red[w][threadIdx.x];
-        dW[((int64_t)co * Cin + ci) * 9 + threadIdx.x] = t;
-    }
-}
-
 // db[c] = sum_{b,y,x} g[b,c,y,x]   (one CTA per channel)
 // Channel sums over pixels in chunks: CTA (c, z) sums chunk z (kRedChunk pixels of one
 // image) of channel c into partial[z][c]; wgrad_reduce_kernel adds the chunks in order.

@@ -72,3 +72,40 @@ def test_full_solve_properties(big, method, kw):
     if method != "sstep_omin_solve":
         # Remark 4.1: every s gives the iterates of GMRES(m), so the same number of cycles
         assert res["cycles"] == 11
+
+
+def test_batched_512_full_workload():
+    """The batched form at its full size (512 systems, L ~ U{32..256}, beta ~ U[0, 50],
+    s = 4, m = 20, tol 1e-8) in the tuned launch configuration the bench measures
+    (256 threads, 2 CTAs per SM, largest first, clusters of 4 CTAs for n >= 16384): every
+    system converges, each final residual recomputed by the oracle's operator meets the
+    tolerance, and the smallest, a middle and the largest system match whole oracle
+    solves (restart cycles, solution to 1e-8)."""
+    d = dev()
+    systems = inputs.batched_systems(0, 512)
+    mats, fs, xs, ops = [], [], [], []
+    for sy in systems:
+        L, beta = sy["L"], sy["beta"]
+        Ao = ostencil.convdiff((L, L), (beta, beta))
+        f = Ao.apply(inputs.x_true(sy["xseed"], Ao.n))
+        mats.append(pkg.StencilMatrix(2, (L, L), beta=(beta, beta)))
+        fs.append(to_dev(f, d))
+        xs.append(torch.zeros(Ao.n, dtype=torch.float64, device=d))
+        ops.append((Ao, f))
+    B = pkg.BatchSolver(mats, 4, 20, 1e-8, max_cycles=2000)
+    B.configure(threads=256, ctas_per_sm=2, largest_first=1, cluster=4, coop_min_n=16384)
+    res = B.solve(fs, xs, mode=B.PERSISTENT)
+    torch.cuda.synchronize()
+    assert all(r["status"] == 0 for r in res)
+    for i, ((Ao, f), x) in enumerate(zip(ops, xs)):
+        rel = np.linalg.norm(f - Ao.apply(x.cpu().numpy())) / np.linalg.norm(f)
+        assert rel <= 1e-8, (i, rel)
+    sides = [sy["L"] for sy in systems]
+    order = np.argsort(sides, kind="stable")
+    for i in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        Ao, f = ops[i]
+        ref = osstep.sstep_gmres(Ao, f, np.zeros(Ao.n), 4, 20, 1e-8, 1.0 / Ao.norm_inf(), 2000)
+        assert ref["status"] == 0 and res[i]["cycles"] == ref["cycles"], (i, sides[i], res[i]["cycles"], ref["cycles"])
+        x = xs[i].cpu().numpy()
+        assert np.linalg.norm(x - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"]), (i, sides[i])
+    B.close()

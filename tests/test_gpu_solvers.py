@@ -148,3 +148,46 @@ def test_not_converged_returns_last_iterate():
     res = pkg.sstep_gmres_solve(A, to_dev(f, d), xd, 2, 4, 1e-12, max_cycles=3, sigma=sigma)
     assert res["status"] == ref["status"] == 1 and res["cycles"] == 3
     assert np.linalg.norm(xd.cpu().numpy() - ref["x"]) <= 1e-10 * np.linalg.norm(ref["x"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64", "fp32"])
+def test_zero_right_hand_side(precision):
+    """f = 0 (x = 0 is the solution): from x0 = 0 each solver ends at its first residual
+    with relres 0, as the oracle does; from x0 != 0 it drives ||A x|| below tol."""
+    d, Ao, A, _ = system((32, 32), (20.0, 20.0))
+    f = torch.zeros(Ao.n, dtype=torch.float64, device=d)
+    calls = [lambda x: pkg.sstep_gmres_solve(A, f, x, 4, 20, 1e-8, precision=precision),
+             lambda x: pkg.gmres_solve(A, f, x, 20, 1e-8, precision=precision)]
+    if precision == "fp64":
+        calls.append(lambda x: pkg.sstep_omin_solve(A, f, x, 4, 1, 1e-8))
+    for call in calls:
+        x = torch.zeros_like(f)
+        r = call(x)
+        assert r["status"] == 0 and r["history"] == [0.0] and r["matvecs"] == 1 and r["relres"] == 0.0
+        assert float(x.abs().max()) == 0.0
+    x0 = inputs.x_true(3, Ao.n)
+    ref = osstep.sstep_gmres(Ao, np.zeros(Ao.n), x0, 4, 20, 1e-10, 1.0 / Ao.norm_inf(), 200)
+    x = to_dev(x0, d)
+    r = pkg.sstep_gmres_solve(A, f, x, 4, 20, 1e-10, sigma=1.0 / Ao.norm_inf(), precision=precision)
+    assert r["status"] == ref["status"] == 0
+    assert np.linalg.norm(Ao.apply(x.cpu().numpy())) <= 1e-10
+    if precision == "fp64":
+        assert r["cycles"] == ref["cycles"]
+
+
+def test_lucky_breakdown_and_degenerate_block():
+    """A = I: GMRES and s-step GMRES with s = 1 end after one step with x = f (lucky
+    breakdown); with s = 2 the block's Gram matrix is singular and the status is
+    breakdown, as in the oracle."""
+    d = dev()
+    A = pkg.StencilMatrix(2, (5, 5), coef=[1.0, 0.0, 0.0, 0.0, 0.0])
+    fh = inputs.x_true(4, 25)
+    f = to_dev(fh, d)
+    for call in (lambda x: pkg.gmres_solve(A, f, x, 10, 1e-12),
+                 lambda x: pkg.sstep_gmres_solve(A, f, x, 1, 10, 1e-12, sigma=1.0)):
+        x = torch.zeros_like(f)
+        r = call(x)
+        assert r["status"] == 0 and r["iters"] == 1
+        assert np.allclose(x.cpu().numpy(), fh, rtol=0, atol=1e-15)
+    x = torch.zeros_like(f)
+    assert pkg.sstep_gmres_solve(A, f, x, 2, 10, 1e-12, sigma=1.0)["status"] == -4
