@@ -1317,7 +1317,7 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
             w.nwin = nwin;
             w.ortho = ortho;
             for (int i = 0; i < nwin; ++i) w.win[i] = ring[ring.size() - nwin + i];
-            w.win[nwin] = nslots;   // ortho: the A R block, right after the A P slots
+            if (ortho) w.win[nwin] = nslots;   // the A R block, right after the A P slots ((k+1) s <= 64)
             if (nwin + ortho > 0) {   // steps 6-7
                 w.mode = EPI_OM_B;
                 TRACED(K_GRAM, stream_, launch_gram(n, APpanel, ld, (nwin + ortho) * s, AR, ld, s, s, sc, w,

@@ -98,6 +98,7 @@ def test_gmres_parity(shape, beta, m):
     ((32, 32), (20.0, 20.0), 2, 2),
     ((32, 32), (20.0, 20.0), 3, 0),     # s-MR
     ((16, 16, 16), (30.0, 20.0, 10.0), 4, 1),
+    ((48, 48), (20.0, 20.0), 1, 64),    # the largest window (k s = 64), filled before convergence
 ])
 def test_sstep_omin_parity(shape, beta, s, k):
     d, Ao, A, f = system(shape, beta)
