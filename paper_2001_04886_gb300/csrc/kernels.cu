@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
 // With the factor known on the host the scaled coefficients fy c (fy (c_0 - shift) on
 // the diagonal) come in from the host; with a device factor d (DSCALE: the first power
 // of a block, d = 1/||u||) eight threads of each CTA form (fy d) c and fw d once in
-// shared memory. Either way a point costs its 7 (5 in 2-D) FP64 multiply-adds and
-// nothing else on the FP64 pipe, with the same operations as stencil_kernel.
+// shared memory. Either way a point costs its 7 (5 in 2-D) FP64 multiply-adds (and one
+// multiply where the scaled v is stored as well), the same operations as stencil_kernel.
 struct ConstCoef {
     double c[7];       // !DSCALE: fy c (diagonal fy (c_0 - shift)); DSCALE: the raw c
     double fy, shift;  // DSCALE only
@@ -453,7 +453,9 @@ void launch_omin_xr(int64_t n, const double* P, const double* AP, int64_t ld, in
 }
 
 // P_new[:, j] = R_j + sum_w sum_q P_w[:, q] B_w[q, j] (same for AP with AR), R_0 = r,
-// R_j = sigma AR_{j-1}; reduces W = AP_new^T AP_new (packed) and m = AP_new^T r.
+// R_j = sigma AR_{j-1}; with epi.ortho, R and AR first go through the upper triangular
+// factor F stored below the B blocks (A^T A-orthonormal blocks). Reduces
+// W = AP_new^T AP_new (packed) and m = AP_new^T r.
 template <int S>
 __global__ void __launch_bounds__(kThreads) omin_pupdate_kernel(int64_t n, const double* __restrict__ r,
                                                                 const double* __restrict__ AR,
