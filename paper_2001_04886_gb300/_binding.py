@@ -130,6 +130,16 @@ def _ptr(t):
     return c_void_p(t.data_ptr())
 
 
+def _vec(t, n, name):
+    """The device pointer of a contiguous float64 CUDA vector of exactly n entries (the
+    kernels read and write n entries from it, so a shorter or strided view is refused)."""
+    p = _ptr(t)
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name}: expected a contiguous float64 CUDA vector of {n} entries, got shape "
+                         f"{tuple(t.shape)}")
+    return p
+
+
 def _stream(stream):
     import torch
 
@@ -159,7 +169,8 @@ class StencilMatrix:
         shp = (c_int64 * 3)(*(list(shape) + [1] * (3 - len(shape))))
         if beta_field is not None:
             _check("stencil_matrix_create_convdiff_variable",
-                   L.stencil_matrix_create_convdiff_variable(ctypes.byref(h), shape[0], _ptr(beta_field),
+                   L.stencil_matrix_create_convdiff_variable(ctypes.byref(h), shape[0],
+                                                             _vec(beta_field, shape[0] * shape[0], "beta_field"),
                                                              _stream(stream)))
         elif beta is not None:
             b = (c_double * 3)(*list(beta))
@@ -168,7 +179,12 @@ class StencilMatrix:
             c = (c_double * 7)(*list(coef))
             _check("stencil_matrix_create", L.stencil_matrix_create(ctypes.byref(h), dim, shp, c))
         elif fields is not None:
-            ptrs = (c_void_p * 7)(*[_ptr(f).value for f in fields])
+            npts = 1
+            for d in shape:
+                npts *= int(d)
+            if len(fields) != 2 * dim + 1:
+                raise ValueError(f"fields: expected {2 * dim + 1} coefficient arrays")
+            ptrs = (c_void_p * 7)(*[_vec(f, npts, "fields").value for f in fields])
             _check("stencil_matrix_create_fields",
                    L.stencil_matrix_create_fields(ctypes.byref(h), dim, shp, ptrs, _stream(stream)))
         else:
@@ -199,38 +215,47 @@ class StencilMatrix:
     def rbilu0_apply(self, v, w, stream=None):
         """w = M^-1 v, M the red-black ILU(0) of this operator."""
         return _check("stencil_matrix_rbilu0_apply",
-                      lib().stencil_matrix_rbilu0_apply(self.handle, _ptr(v), _ptr(w), _stream(stream)))
+                      lib().stencil_matrix_rbilu0_apply(self.handle, _vec(v, self.n, "v"), _vec(w, self.n, "w"),
+                                                        _stream(stream)))
 
     def smooth(self, f, x, work, sweeps, omega, stream=None):
         return stencil_matrix_smooth(self, f, x, work, sweeps, omega, stream)
 
 
 def stencil_matrix_apply(A, x, y, stream=None):
-    return _check("stencil_matrix_apply", lib().stencil_matrix_apply(A.handle, _ptr(x), _ptr(y), _stream(stream)))
+    return _check("stencil_matrix_apply", lib().stencil_matrix_apply(A.handle, _vec(x, A.n, "x"), _vec(y, A.n, "y"),
+                                                                     _stream(stream)))
 
 
 def stencil_matrix_smooth_batched(mats, fs, xs, works, sweeps, omega, stream=None):
     """`sweeps` damped Jacobi sweeps on every x in place, all systems per launch."""
     n = len(mats)
-    arr = lambda ts: (c_void_p * n)(*[_ptr(t).value for t in ts])
+    if not (len(fs) == len(xs) == len(works) == n):
+        raise ValueError("one f, x and work vector per matrix")
+    arr = lambda ts, nm: (c_void_p * n)(*[_vec(t, A.n, nm).value for t, A in zip(ts, mats)])
     hs = (c_void_p * n)(*[A.handle for A in mats])
     return _check("stencil_matrix_smooth_batched",
-                  lib().stencil_matrix_smooth_batched(n, hs, arr(fs), arr(xs), arr(works), int(sweeps), float(omega),
+                  lib().stencil_matrix_smooth_batched(n, hs, arr(fs, "f"), arr(xs, "x"), arr(works, "work"), int(sweeps),
+                                                      float(omega),
                                                       _stream(stream)))
 
 
 def stencil_matrix_smooth(A, f, x, work, sweeps, omega, stream=None):
     """`sweeps` damped Jacobi sweeps on x in place (work: scratch of n doubles)."""
-    return _check("stencil_matrix_smooth", lib().stencil_matrix_smooth(A.handle, _ptr(f), _ptr(x), _ptr(work),
-                                                                       int(sweeps), float(omega), _stream(stream)))
+    return _check("stencil_matrix_smooth", lib().stencil_matrix_smooth(A.handle, _vec(f, A.n, "f"), _vec(x, A.n, "x"),
+                                                                       _vec(work, A.n, "work"), int(sweeps),
+                                                                       float(omega), _stream(stream)))
 
 
 def sstep_matrix_powers(A, v, scale, sigma, s, Y, stream=None):
     n, k, ld = _col_major(Y, "Y")
     if k < s + 1:
         raise ValueError("Y needs s+1 columns")
+    if n != A.n:
+        raise ValueError(f"Y: expected {A.n} rows, got {n}")
     return _check("sstep_matrix_powers",
-                  lib().sstep_matrix_powers(A.handle, _ptr(v), scale, sigma, s, _ptr(Y), ld, _stream(stream)))
+                  lib().sstep_matrix_powers(A.handle, _vec(v, A.n, "v"), scale, sigma, s, _ptr(Y), ld,
+                                            _stream(stream)))
 
 
 def sstep_gram_workspace_size(n, ka, kb):
@@ -306,7 +331,8 @@ def _solve(name, A, f, x, s=1, m=20, k=1, tol=1e-8, max_cycles=1000, max_iters=1
                     history_cap=history_cap, precision=PRECISIONS[precision], x0_guard=1 if x0_guard else 0,
                     basis=BASES[basis], precond=PRECONDS[precond])
     r = SStepResult()
-    rc = getattr(lib(), name)(A.handle, _ptr(f), _ptr(x), ctypes.byref(p), ctypes.byref(r), _stream(stream))
+    rc = getattr(lib(), name)(A.handle, _vec(f, A.n, "f"), _vec(x, A.n, "x"), ctypes.byref(p), ctypes.byref(r),
+                              _stream(stream))
     _check(name, rc)
     return dict(status=r.status, cycles=r.cycles, iters=r.iters, matvecs=r.matvecs, relres=r.relres,
                 history=hist[: r.history_len].tolist())
@@ -405,18 +431,20 @@ class BatchSolver:
         _check("sstep_batch_create", lib().sstep_batch_create(ctypes.byref(h), self.n, arr, ctypes.byref(p)))
         self.handle = h
 
-    def _ptrs(self, ts):
-        return (c_void_p * self.n)(*[_ptr(t).value for t in ts])
+    def _ptrs(self, ts, name):
+        if len(ts) != self.n:
+            raise ValueError(f"{name}: expected {self.n} vectors, one per system")
+        return (c_void_p * self.n)(*[_vec(t, A.n, name).value for t, A in zip(ts, self.mats)])
 
     def solve(self, f, x, mode=0, stream=None):
         res = (SStepResult * self.n)()
-        _check("sstep_batch_solve", lib().sstep_batch_solve(self.handle, self._ptrs(f), self._ptrs(x), res, mode,
+        _check("sstep_batch_solve", lib().sstep_batch_solve(self.handle, self._ptrs(f, "f"), self._ptrs(x, "x"), res, mode,
                                                             _stream(stream)))
         return [dict(status=r.status, cycles=r.cycles, iters=r.iters, matvecs=r.matvecs, relres=r.relres) for r in res]
 
     def tune(self, f, x, stream=None):
         t, c, o, g, nb = c_int(), c_int(), c_int(), c_int(), c_int64()
-        _check("sstep_batch_tune", lib().sstep_batch_tune(self.handle, self._ptrs(f), self._ptrs(x), ctypes.byref(t),
+        _check("sstep_batch_tune", lib().sstep_batch_tune(self.handle, self._ptrs(f, "f"), self._ptrs(x, "x"), ctypes.byref(t),
                                                           ctypes.byref(c), ctypes.byref(o), ctypes.byref(g),
                                                           ctypes.byref(nb), _stream(stream)))
         return dict(threads=t.value, ctas_per_sm=c.value, largest_first=o.value, cluster=g.value,
@@ -463,6 +491,15 @@ class X0Net:
             raise TypeError("expected a contiguous float32 CUDA tensor")
         return c_void_p(t.data_ptr())
 
+    def _io(self, inp, other, name):
+        """Pointers of an input (B, 2, H, W) and an output or target (B, 1, H, W) batch."""
+        pi, po = self._f32(inp), self._f32(other)
+        B = inp.shape[0] if inp.dim() == 4 else -1
+        if tuple(inp.shape) != (B, 2, self.H, self.W) or tuple(other.shape) != (B, 1, self.H, self.W):
+            raise ValueError(f"expected input (B, 2, {self.H}, {self.W}) and {name} (B, 1, {self.H}, {self.W}), got "
+                             f"{tuple(inp.shape)} and {tuple(other.shape)}")
+        return pi, po
+
     def set_params(self, theta, stream=None):
         import torch
 
@@ -503,7 +540,8 @@ class X0Net:
                                                         int(state["step"]), _stream(stream)))
 
     def forward(self, inp, out, stream=None):
-        _check("x0net_forward", lib().x0net_forward(self.handle, self._f32(inp), self._f32(out), inp.shape[0],
+        pi, po = self._io(inp, out, "output")
+        _check("x0net_forward", lib().x0net_forward(self.handle, pi, po, inp.shape[0],
                                                     _stream(stream)))
 
     def gradient(self, inp, target, stream=None):
@@ -511,14 +549,16 @@ class X0Net:
 
         g = np.zeros(self.num_params, dtype=np.float32)
         loss = np.zeros(1, dtype=np.float32)
-        _check("x0net_gradient", lib().x0net_gradient(self.handle, self._f32(inp), self._f32(target), inp.shape[0],
+        pi, pt = self._io(inp, target, "target")
+        _check("x0net_gradient", lib().x0net_gradient(self.handle, pi, pt, inp.shape[0],
                                                       c_void_p(loss.ctypes.data), c_void_p(g.ctypes.data),
                                                       _stream(stream)))
         return float(loss[0]), g
 
     def train_step(self, inp, target, lr, loss_out=None, stream=None):
         lp = self._f32(loss_out) if loss_out is not None else c_void_p(0)
-        _check("x0net_train_step", lib().x0net_train_step(self.handle, self._f32(inp), self._f32(target), inp.shape[0],
+        pi, pt = self._io(inp, target, "target")
+        _check("x0net_train_step", lib().x0net_train_step(self.handle, pi, pt, inp.shape[0],
                                                           lr, lp, _stream(stream)))
 
     def set_tensor_cores(self, on):

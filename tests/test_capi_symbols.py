@@ -77,3 +77,18 @@ def test_workspace_limit_gives_oom_before_any_device_call():
         assert L.sstep_set_workspace_limit(0) == 0
         L.stencil_matrix_destroy(h)
     assert L.sstep_set_workspace_limit(-1) == -1
+
+
+def test_binding_refuses_host_tensors_without_gpu():
+    """Host (CPU) tensors never reach the library: the binding raises before the call."""
+    import torch
+
+    A = pkg.StencilMatrix(2, (8, 8), beta=(20.0, 20.0))   # a host-only operator handle
+    f = torch.ones(A.n, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        pkg.sstep_gmres_solve(A, f, torch.zeros_like(f), 4, 20, 1e-8)
+    with pytest.raises(TypeError):
+        pkg.sstep_omin_solve(A, f, torch.zeros_like(f), 4, 1, 1e-8)
+    with pytest.raises(TypeError):
+        A.apply(f, torch.empty_like(f))
+    A.close()

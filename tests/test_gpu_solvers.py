@@ -192,3 +192,31 @@ def test_lucky_breakdown_and_degenerate_block():
         assert np.allclose(x.cpu().numpy(), fh, rtol=0, atol=1e-15)
     x = torch.zeros_like(f)
     assert pkg.sstep_gmres_solve(A, f, x, 2, 10, 1e-12, sigma=1.0)["status"] == -4
+
+
+def test_binding_refuses_vectors_the_kernels_would_overrun():
+    """The binding passes raw pointers, so it checks every vector against the operator:
+    a short, long or strided vector is refused before any launch (ValueError), a host or
+    float32 tensor too (TypeError)."""
+    d, Ao, A, f = system((16, 16), (20.0, 20.0))
+    fd = to_dev(f, d)
+    x = torch.zeros(Ao.n, dtype=torch.float64, device=d)
+    for bad in (fd[:-1], torch.cat([fd, fd[:1]]), torch.zeros(2 * Ao.n, dtype=torch.float64, device=d)[::2]):
+        with pytest.raises(ValueError):
+            pkg.sstep_gmres_solve(A, bad, x, 4, 20, 1e-8)
+        with pytest.raises(ValueError):
+            pkg.sstep_omin_solve(A, fd, bad, 4, 1, 1e-8)
+        with pytest.raises(ValueError):
+            A.apply(fd, bad)
+    with pytest.raises(TypeError):
+        pkg.gmres_solve(A, torch.tensor(f), x, 20, 1e-8)
+    with pytest.raises(TypeError):
+        pkg.gmres_solve(A, fd.float(), x, 20, 1e-8)
+    B = pkg.BatchSolver([A, A], 4, 20, 1e-8)
+    with pytest.raises(ValueError):
+        B.solve([fd, fd[:-1]], [x, x.clone()])
+    with pytest.raises(ValueError):
+        B.solve([fd], [x])
+    assert float(x.abs().max()) == 0.0      # nothing ran
+    r = pkg.sstep_gmres_solve(A, fd, x, 4, 20, 1e-8)
+    assert r["status"] == 0

@@ -144,3 +144,18 @@ def test_tensor_core_wait_timeout_is_reported_and_recoverable():
     loss2, g2 = net.gradient(xd, td)
     net.status()
     assert loss2 == loss_ok and np.array_equal(g2, g_ok)
+
+
+def test_binding_refuses_batches_of_the_wrong_shape():
+    net, theta, x, t, xd, td = setup(2, 16, 5, True)
+    out = torch.empty((2, 1, 16, 16), dtype=torch.float32, device=xd.device)
+    with pytest.raises(ValueError):
+        net.forward(xd, out[:1])
+    with pytest.raises(ValueError):
+        net.forward(xd[:, :1].contiguous(), out)
+    with pytest.raises(ValueError):
+        net.gradient(xd, torch.empty((2, 1, 8, 8), dtype=torch.float32, device=xd.device))
+    with pytest.raises(TypeError):
+        net.forward(xd.double(), out)
+    net.forward(xd, out)
+    net.status()
