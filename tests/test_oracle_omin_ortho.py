@@ -139,3 +139,73 @@ def test_planted_mistakes_caught(old, new):
     out = mod.ata_mgs(Pm, APm)
     APQ2 = np.column_stack([A.apply(out[0][:, j]) for j in range(4)])
     assert not (np.allclose(out[1].T @ out[1], np.eye(4), atol=1e-12) and np.allclose(APQ2, out[1], atol=1e-12))
+
+
+def _omin_predicted_factor(A, f, s, k, tol, sigma, max_iters):
+    """The library's form of the orthonormal blocks, restated in numpy for comparison: the
+    Gram matrix of the projected block is predicted from A R^T A R and the window's inner
+    products, its Cholesky factor's inverse is folded into the block coefficients, and
+    Scalar1/Scalar2 solve with the blocks' measured Gram matrices (near the identity)."""
+    nf = np.linalg.norm(f)
+    x = np.zeros(A.n)
+    r = f.copy()
+    it = 0
+
+    def orthonormal(R, AR, Pw, APw, Lw):
+        G = AR.T @ AR
+        Bs = []
+        for P_, AP_, L_ in zip(Pw, APw, Lw):
+            C = AP_.T @ AR
+            B = -sstep.cholesky_solve(L_, C)
+            G = G + C.T @ B
+            Bs.append(B)
+        Lp = sstep.cholesky_upper(np.triu(G) + np.triu(G, 1).T)   # the upper triangle, as the library reads it
+        F = np.linalg.inv(Lp) if Lp is not None else np.eye(s)
+        Pn, APn = R @ F, AR @ F
+        for P_, AP_, B in zip(Pw, APw, Bs):
+            Pn, APn = Pn + P_ @ (B @ F), APn + AP_ @ (B @ F)
+        return Pn, APn, sstep.cholesky_upper(APn.T @ APn)
+
+    R, AR = sstep.omin_powers(A, r, s, sigma)
+    P, AP, L = orthonormal(R, AR, [], [], [])
+    Pw, APw, Lw = [P], [AP], [L]
+    while it < max_iters:
+        if Lw[-1] is None:
+            return None   # a measured Gram matrix is not positive definite: breakdown
+        a = sstep.cholesky_solve(Lw[-1], APw[-1].T @ r)
+        x = x + Pw[-1] @ a
+        r = r - APw[-1] @ a
+        it += 1
+        if np.linalg.norm(r) / nf <= tol:
+            break
+        R, AR = sstep.omin_powers(A, r, s, sigma)
+        lo = len(Pw) - min(k, len(Pw))
+        P, AP, L = orthonormal(R, AR, Pw[lo:], APw[lo:], Lw[lo:])
+        Pw, APw, Lw = (Pw + [P])[-max(k, 1):], (APw + [AP])[-max(k, 1):], (Lw + [L])[-max(k, 1):]
+    return it
+
+
+def test_predicted_factor_takes_the_gram_schmidt_steps():
+    """The library orthonormalises with the Cholesky factor of a predicted Gram matrix, the
+    paper with modified Gram-Schmidt. On the Sec. 5 problem the two take the same number of
+    steps for s <= 10 (fewer than the printed form at s = 8 and 10) and within one step of
+    each other at s = 12 (the printed form needs half as many more); from s = 14 only
+    Gram-Schmidt converges. The library allows s <= 8."""
+    P = inputs.paper_problem(64)
+    a0, aw, ae, as_, an = [np.asarray(c) for c in P["coef"]]
+    A = stencil.Stencil((64, 64), a0, [aw, as_], [ae, an])
+    f = np.asarray(P["g"])
+    sig = 1.0 / A.norm_inf()
+    for s in (4, 8, 10):
+        mgs = sstep.sstep_omin(A, f, np.zeros(A.n), s, 1, 1e-8, sig, 600, basis="ortho")["iters"]
+        assert _omin_predicted_factor(A, f, s, 1, 1e-8, sig, 600) == mgs, s
+    mgs = sstep.sstep_omin(A, f, np.zeros(A.n), 12, 1, 1e-8, sig, 600, basis="ortho")["iters"]
+    printed = sstep.sstep_omin(A, f, np.zeros(A.n), 12, 1, 1e-8, sig, 600)["iters"]
+    pred = _omin_predicted_factor(A, f, 12, 1, 1e-8, sig, 600)
+    assert abs(pred - mgs) <= 1 and pred <= 0.75 * printed, (pred, mgs, printed)
+    # s = 14: the printed form breaks down at once, the predicted factor later, and only
+    # Gram-Schmidt converges (the limit of the library's form, were s raised past 12)
+    ref = sstep.sstep_omin(A, f, np.zeros(A.n), 14, 1, 1e-8, sig, 600, basis="ortho")
+    assert ref["status"] == 0
+    assert sstep.sstep_omin(A, f, np.zeros(A.n), 14, 1, 1e-8, sig, 600)["status"] == -4
+    assert _omin_predicted_factor(A, f, 14, 1, 1e-8, sig, 600) is None
