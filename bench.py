@@ -37,6 +37,19 @@ TOL = 1e-8
 WORKLOAD = "3-D convection-diffusion 128^3 (n=2,097,152), beta=(30,20,10), 7-point, FP64, x0=0, tol 1e-8"
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz, FMA = 2 flops
 
+
+def _hbm_peak_gbs():
+    """The measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json), else the
+    6800 GB/s of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak_gbs()   # the algorithmic GB/s of the dominant kernel are reported against it
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
 # kernel, averaged over the launches of one solve in an ncu capture of this bench
 # (profiles/sstep_gmres_fp64_128cube_traffic.md has the command and the per-kernel table).
@@ -369,6 +382,7 @@ def main():
                 "launches_per_solve": launches_dom, "algorithmic_bytes_per_launch": bytes_ / launches_dom,
                 "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
                 "hbm_gbs": bytes_ / t_dom / 1e9,
+                "hbm_peak_gbs": HBM_PEAK_GBS, "hbm_frac": bytes_ / t_dom / 1e9 / HBM_PEAK_GBS,
                 "share_of_step": kinds[dom][0] / args.steps / ms}
 
     # end to end through the public API: inputs from pinned host memory, x back to the host
