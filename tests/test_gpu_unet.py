@@ -159,3 +159,38 @@ def test_binding_refuses_batches_of_the_wrong_shape():
         net.forward(xd.double(), out)
     net.forward(xd, out)
     net.status()
+
+
+def test_full_size_forward_and_gradient_match_the_oracle():
+    """The learned form at its full size, in the configuration the bench trains and infers
+    with (128^2, BF16 weights on the tensor cores, 4 smoothing passes): a batch of 32
+    forwards, two of which (first and last) the oracle recomputes, and one gradient at
+    batch 2 against the oracle's."""
+    d = dev()
+    H, B = 128, 32
+    theta = ounet.init_params(inputs.uniform01(21, ounet.num_params())).astype(np.float32).astype(np.float64)
+    th = theta.copy()
+    for sl, (ci, co, k, _) in zip(layer_slices(), ounet.LAYERS):
+        nw = co * ci * k * k
+        th[sl.start : sl.start + nw] = bf16_round(theta[sl.start : sl.start + nw])
+    rng = np.random.default_rng(22)
+    x = rng.standard_normal((B, 2, H, H)).astype(np.float32)
+    t = rng.standard_normal((B, 1, H, H)).astype(np.float32)
+    net = pkg.X0Net(H, H, B, bf16=True, smooth=4, residual_weight=0.0, kappa=KAPPA)
+    net.set_params(theta.astype(np.float32))
+    xd = torch.tensor(x, device=d)
+    out = torch.empty((B, 1, H, H), dtype=torch.float32, device=d)
+    net.forward(xd, out)
+    net.status()
+    got = out.cpu().numpy().astype(np.float64)
+    for i in (0, B - 1):
+        ref = ounet.forward(th, x[i : i + 1].astype(np.float64), smooth=4)
+        assert np.linalg.norm(got[i : i + 1] - ref) <= 1e-4 * np.linalg.norm(ref), i
+    loss, g = net.gradient(xd[:2].contiguous(), torch.tensor(t[:2], device=d))
+    lref, gref = ounet.gradient(th, x[:2].astype(np.float64), t[:2].astype(np.float64), smooth=4, res_w=0.0,
+                                kappa=KAPPA)
+    assert abs(loss - lref) <= 1e-4 * lref
+    for sl in layer_slices():
+        a, b = g[sl].astype(np.float64), gref[sl]
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b) + 1e-12
+    net.close()
