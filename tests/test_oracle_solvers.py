@@ -230,3 +230,28 @@ def test_lucky_breakdown_and_degenerate_block():
         assert np.allclose(res["x"], f, rtol=0, atol=1e-15)
     bad = sstep.sstep_gmres(A, f, z, 2, 10, 1e-12, 1.0)
     assert bad["status"] == STATUS_BREAKDOWN and bad["iters"] == 0
+
+
+def test_givens_least_squares_equals_lstsq():
+    """eq. 2-3: the Givens QR of an upper Hessenberg H, column by column, gives after every
+    column the residual norm and (at the end) the minimiser of ||g0 e1 - H y|| that a
+    dense least-squares solve (LAPACK) gives; a column with a zero subdiagonal is the
+    lucky breakdown (residual 0)."""
+    rng = np.random.default_rng(11)
+    for m in (1, 5, 20, 40):
+        H = np.triu(rng.standard_normal((m + 1, m)), -1)
+        H[np.arange(m), np.arange(m)] += 4.0      # well conditioned, so y is compared tightly
+        g0 = 2.5
+        lsq = krylov.GivensLSQ(m, g0)
+        for j in range(m):
+            est = lsq.add_column(H[:, j])
+            rhs = np.zeros(j + 2)
+            rhs[0] = g0
+            y, *_ = np.linalg.lstsq(H[: j + 2, : j + 1], rhs, rcond=None)
+            true = np.linalg.norm(rhs - H[: j + 2, : j + 1] @ y)
+            assert abs(est - true) <= 1e-12 * g0, (m, j)
+        assert np.allclose(lsq.solve(), y, rtol=1e-9, atol=1e-12)
+    H = np.array([[2.0, 1.0], [0.0, 3.0], [0.0, 0.0]])
+    lsq = krylov.GivensLSQ(2, 1.0)
+    lsq.add_column(H[:, 0])
+    assert lsq.add_column(H[:, 1]) == 0.0
