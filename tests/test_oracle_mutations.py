@@ -141,3 +141,35 @@ def test_gmres_window_and_orth_mutations_caught():
     a = np.array(gcr["history"][1:25])
     b = np.array(gm["history"][1:25])
     assert np.max(np.abs(a - b) / b) > 1e-6
+
+
+PRECOND_MUTATIONS = [
+    ("dt -= coef_b * self._shift(coef_r / a0.reshape(sh), ax, step).reshape(-1)",
+     "dt += coef_b * self._shift(coef_r / a0.reshape(sh), ax, step).reshape(-1)"),   # wrong sign of the fill
+    ("s += (am * self._shift(W, ax, -1) + ap * self._shift(W, ax, +1)).reshape(-1)",
+     "s += (am * self._shift(W, ax, +1) + ap * self._shift(W, ax, -1)).reshape(-1)"),  # swapped neighbours
+    ("out.append((ax, self._mask(am, ax, -1).reshape(-1), ap, -1))",
+     "out.append((ax, self._mask(am, ax, +1).reshape(-1), ap, -1))"),                 # wrong boundary mask
+    ("w = np.where(self.black, (v - t) / self.dtilde, 0.0)",
+     "w = np.where(self.black, (v - t) / self.a0, 0.0)"),                              # unmodified pivot
+]
+
+
+@pytest.mark.parametrize("old,new", PRECOND_MUTATIONS)
+def test_precond_mutation_caught(old, new):
+    """The red-black ILU(0) pins (L U equals A on its pattern, M^-1 equals the dense solve
+    with L U) catch each planted slip."""
+    mod = mutated("stencil", old, new)
+    from tests.test_oracle_precond import dense_factors
+
+    A = mod.convdiff((4, 4, 4), (30.0, 20.0, 10.0))
+    P = mod.RedBlackILU0(A)
+    Ap, L, U, perm = dense_factors(A, P)
+    LU = L @ U
+    pat = Ap != 0
+    on_pattern = np.max(np.abs((LU - Ap)[pat])) <= 1e-14 * np.max(np.abs(Ap))
+    v = inputs.x_true(3, A.n)
+    want = np.zeros(A.n)
+    want[perm] = np.linalg.solve(LU, v[perm])
+    applies = np.max(np.abs(P.apply_inv(v) - want)) <= 1e-13 * np.max(np.abs(want))
+    assert not (on_pattern and applies)
