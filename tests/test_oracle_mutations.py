@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+import oracle.sstep  # noqa: F401  (oracle.sstep is used through the package below)
 from oracle import dense, krylov, stencil
 from paper_2001_04886_gb300 import inputs
 
