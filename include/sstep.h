@@ -171,7 +171,8 @@ typedef struct {
     int s;              /* block size (>= 1, <= SSTEP_MAX_S) */
     int m;              /* GMRES: Krylov dimension per cycle, a multiple of s (<= SSTEP_MAX_M) */
     int k;              /* Orthomin: number of previous direction blocks kept (>= 0) */
-    double tol;         /* stop when ||f - A x|| / ||f|| <= tol */
+    double tol;         /* stop when ||f - A x|| / ||f|| <= tol (||f|| read as 1 when f = 0:
+                           x = 0 solves, and from x0 = 0 the solve ends at its first residual) */
     int max_cycles;     /* GMRES: maximum restart cycles */
     int max_iters;      /* Orthomin: maximum (s-)steps */
     double sigma;       /* basis scale of the monomial powers; 0 => 1 / ||A||_inf */
