@@ -411,6 +411,48 @@ def trace_read():
     return out
 
 
+def tune_cache_key(shapes, s, m, device):
+    """The key of a batch's tuned launch configuration: the device name, s, m and a hash
+    of the systems' grid shapes in batch order (what the timing depends on)."""
+    import hashlib
+
+    h = hashlib.sha256(repr([tuple(int(v) for v in sh) for sh in shapes]).encode()).hexdigest()[:16]
+    return f"{device}|s={int(s)}|m={int(m)}|n={len(shapes)}|{h}"
+
+
+def tune_cache_get(path, key):
+    """The cached configuration for key, or None (no file, no entry, or an unreadable file)."""
+    import json
+
+    try:
+        with open(path) as fh:
+            cfg = json.load(fh).get(key)
+    except (OSError, ValueError, AttributeError):
+        return None
+    names = ("threads", "ctas_per_sm", "largest_first", "cluster", "coop_min_n")
+    if not isinstance(cfg, dict) or any(not isinstance(cfg.get(k), int) for k in names):
+        return None
+    return {k: cfg[k] for k in names}
+
+
+def tune_cache_put(path, key, cfg):
+    """Adds (or replaces) key's configuration, rewriting the file atomically."""
+    import json
+
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+        if not isinstance(data, dict):
+            data = {}
+    except (OSError, ValueError):
+        data = {}
+    data[key] = dict(cfg)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class BatchSolver:
     """Batched s-step GMRES over many systems (include/sstep.h, batched solves).
 
@@ -424,6 +466,7 @@ class BatchSolver:
     def __init__(self, mats, s, m, tol, max_cycles=1000, sigma=0.0, x0_guard=False):
         self.mats = list(mats)
         self.n = len(self.mats)
+        self.s, self.m = s, m
         h = c_void_p()
         arr = (c_void_p * self.n)(*[A.handle.value for A in self.mats])
         p = SStepParams(s=s, m=m, k=0, tol=tol, max_cycles=max_cycles, max_iters=0, sigma=sigma, history=None,
@@ -442,13 +485,30 @@ class BatchSolver:
                                                             _stream(stream)))
         return [dict(status=r.status, cycles=r.cycles, iters=r.iters, matvecs=r.matvecs, relres=r.relres) for r in res]
 
-    def tune(self, f, x, stream=None):
+    def tune(self, f, x, stream=None, cache=None):
+        """Time the launch configurations on this batch and keep the fastest (the initial
+        guesses are restored). cache: a JSON file (default: $SSTEP_TUNE_CACHE, if set) of
+        earlier results, keyed by the device and the batch's shape (tune_cache_key); a hit
+        configures without timing."""
+        cache = cache if cache is not None else os.environ.get("SSTEP_TUNE_CACHE")
+        key = None
+        if cache:
+            import torch
+
+            key = tune_cache_key([A.shape for A in self.mats], self.s, self.m, torch.cuda.get_device_name())
+            hit = tune_cache_get(cache, key)
+            if hit is not None:
+                self.configure(**hit)
+                return dict(hit)
         t, c, o, g, nb = c_int(), c_int(), c_int(), c_int(), c_int64()
         _check("sstep_batch_tune", lib().sstep_batch_tune(self.handle, self._ptrs(f, "f"), self._ptrs(x, "x"), ctypes.byref(t),
                                                           ctypes.byref(c), ctypes.byref(o), ctypes.byref(g),
                                                           ctypes.byref(nb), _stream(stream)))
-        return dict(threads=t.value, ctas_per_sm=c.value, largest_first=o.value, cluster=g.value,
-                    coop_min_n=nb.value)
+        cfg = dict(threads=t.value, ctas_per_sm=c.value, largest_first=o.value, cluster=g.value,
+                   coop_min_n=nb.value)
+        if key is not None:
+            tune_cache_put(cache, key, cfg)
+        return cfg
 
     def configure(self, threads=256, ctas_per_sm=1, largest_first=1, cluster=1, coop_min_n=0):
         """Set the launch configuration by hand (what tune() would choose)."""

@@ -102,3 +102,20 @@ def test_configure_rejects_bad_arguments():
     for bad in (dict(threads=100), dict(cluster=0), dict(cluster=9), dict(ctas_per_sm=0), dict(coop_min_n=-1)):
         with pytest.raises(pkg.SStepError):
             B.configure(**bad)
+
+
+def test_tune_cache_configures_without_timing(tmp_path):
+    """A second solver over the same batch shape takes the cached configuration (no
+    timing runs) and solves with it."""
+    import time
+
+    d = dev()
+    mats, ora, fs, xs = batch(11, 40, 16, 64, d)
+    cache = str(tmp_path / "tune.json")
+    cfg = pkg.BatchSolver(mats, 4, 20, 1e-8).tune(fs, xs, cache=cache)
+    B2 = pkg.BatchSolver(mats, 4, 20, 1e-8)
+    t0 = time.perf_counter()
+    cfg2 = B2.tune(fs, xs, cache=cache)
+    assert cfg2 == cfg and time.perf_counter() - t0 < 0.5
+    res = B2.solve(fs, xs, mode=B2.PERSISTENT)
+    assert all(r["status"] == 0 for r in res)
