@@ -70,6 +70,31 @@ def test_stencil_variable_coefficients():
     assert abs(A.norm_inf - Ao.norm_inf()) <= 1e-13 * Ao.norm_inf()
 
 
+@pytest.mark.parametrize("N,kind", [(33, "fourier"), (128, "uniform"), (57, "signed")])
+def test_convdiff_variable_closed_form(N, kind):
+    """The library's own variable-coefficient operator (beta field in, coefficients built on
+    the device) against the closed form of Sec. 5's non-conservative convection-diffusion:
+    exact on u = x(1-x) y(1-y) for any beta, so a slip in c = beta h / 2 or its sign fails."""
+    from tests.test_oracle_stencil import variable_closed_form
+
+    d = dev()
+    rng = np.random.default_rng(N)
+    if kind == "fourier":
+        beta, _ = inputs.fourier_fields(5, N)
+    elif kind == "uniform":
+        beta = rng.uniform(0.0, 60.0, N * N)
+    else:
+        beta = rng.uniform(-50.0, 50.0, N * N)
+    A = pkg.StencilMatrix(2, (N, N), beta_field=to_dev(beta, d))
+    u, expect = variable_closed_form(N, beta)
+    y = torch.empty(N * N, dtype=torch.float64, device=d)
+    A.apply(to_dev(u, d), y)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(y.cpu().numpy() - expect)) <= 1e-14 * np.max(np.abs(expect))
+    Ao = ostencil.convdiff_variable(N, beta)
+    assert abs(A.norm_inf - Ao.norm_inf()) <= 1e-13 * Ao.norm_inf()
+
+
 @pytest.mark.parametrize("shape,beta", [SHAPES[0], SHAPES[1], SHAPES[4], SHAPES[5]])
 @pytest.mark.parametrize("s", [1, 4, 8])
 def test_matrix_powers(shape, beta, s):

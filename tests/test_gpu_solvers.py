@@ -80,10 +80,8 @@ def test_sstep_gmres_parity(shape, beta, s, m):
 
 
 @pytest.mark.parametrize("shape,beta,m", [((64, 64), (20.0, 20.0), 20), ((20, 20, 20), (30.0, 20.0, 10.0), 40),
-                                          ((9, 7), (20.0, 20.0), 5)])
+                                          ((13, 13), (20.0, 20.0), 5)])
 def test_gmres_parity(shape, beta, m):
-    if len(set(shape)) != 1:
-        pytest.skip("convdiff needs equal sides")
     d, Ao, A, f = system(shape, beta)
     ref = okrylov.gmres(Ao, f, np.zeros(Ao.n), m, 1e-8, 500)
     xd = torch.zeros(Ao.n, dtype=torch.float64, device=d)

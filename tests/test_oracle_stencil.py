@@ -128,3 +128,65 @@ def test_jacobi_matches_dense_iteration_and_keeps_the_solution():
     np.testing.assert_allclose(stencil.jacobi(A, f, x, 4, 0.7), want, rtol=1e-13, atol=1e-13)
     xs = np.linalg.solve(D, f)
     np.testing.assert_allclose(stencil.jacobi(A, f, xs, 3, 0.8), xs, rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------------------------ variable coefficients (Sec. 5, eq. 10 form)
+def variable_closed_form(N, beta_field):
+    """h^2 [ -Lap u + beta(x, y) (u_x + u_y) ] at the nodes for u = x(1-x) y(1-y).
+
+    u is quadratic in each variable, so the centred second and first differences of the
+    five-point row are exact whatever beta is at the node: the row of the h^2-scaled
+    operator equals the continuous operator times h^2, point by point.
+    """
+    (X, Y), h = grid_coords((N, N))
+    u = X * (1 - X) * Y * (1 - Y)
+    ux = (1 - 2 * X) * Y * (1 - Y)
+    uy = (1 - 2 * Y) * X * (1 - X)
+    neg_lap = 2 * Y * (1 - Y) + 2 * X * (1 - X)
+    return u, h * h * (neg_lap + np.asarray(beta_field) * (ux + uy))
+
+
+def matches_closed_form(A, N, beta_field):
+    u, expect = variable_closed_form(N, beta_field)
+    return np.max(np.abs(A.apply(u) - expect)) <= 1e-14 * np.max(np.abs(expect))
+
+
+@pytest.mark.parametrize("N,kind", [(9, "uniform"), (16, "fourier"), (23, "signed")])
+def test_variable_quadratic_closed_form(N, kind):
+    """P1 for the variable-coefficient operator: exact on u = x(1-x) y(1-y) for any beta field.
+
+    The fields are a rough random field, the learned form's 8-mode Fourier field and a field
+    of both signs; c(p) = beta(x_p, y_p) h / 2 multiplies both first differences of row p.
+    """
+    from paper_2001_04886_gb300 import inputs
+
+    rng = np.random.default_rng(11)
+    if kind == "uniform":
+        beta = rng.uniform(0.0, 60.0, N * N)
+    elif kind == "fourier":
+        beta, _ = inputs.fourier_fields(7, N)
+    else:
+        beta = rng.uniform(-50.0, 50.0, N * N)
+    assert matches_closed_form(stencil.convdiff_variable(N, beta), N, beta)
+
+
+def test_variable_closed_form_catches_planted_slips():
+    """Each slip a restatement could make fails the closed form: c = beta h instead of
+    beta h / 2, the signs of c swapped between u_{p-e} and u_{p+e}, beta applied to x only,
+    the field transposed (beta(y, x)), and a centre of 2 d - 1."""
+    N = 12
+    rng = np.random.default_rng(12)
+    beta = rng.uniform(5.0, 60.0, N * N)
+    h = 1.0 / (N + 1)
+    c = beta * h / 2
+    cT = (beta.reshape(N, N).T.reshape(-1)) * h / 2
+    planted = {
+        "beta h": stencil.Stencil((N, N), 4.0, [-1.0 - 2 * c, -1.0 - 2 * c], [-1.0 + 2 * c, -1.0 + 2 * c]),
+        "sign swap": stencil.Stencil((N, N), 4.0, [-1.0 + c, -1.0 + c], [-1.0 - c, -1.0 - c]),
+        "x only": stencil.Stencil((N, N), 4.0, [-1.0 - c, -1.0], [-1.0 + c, -1.0]),
+        "transposed": stencil.Stencil((N, N), 4.0, [-1.0 - cT, -1.0 - cT], [-1.0 + cT, -1.0 + cT]),
+        "centre": stencil.Stencil((N, N), 3.0, [-1.0 - c, -1.0 - c], [-1.0 + c, -1.0 + c]),
+    }
+    assert matches_closed_form(stencil.convdiff_variable(N, beta), N, beta)
+    for name, A in planted.items():
+        assert not matches_closed_form(A, N, beta), name
