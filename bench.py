@@ -12,8 +12,9 @@ With N GPUs (torchrun) every rank solves its own system (replicas, weak
 scaling); the step time is the maximum over ranks.
 
 --impl reference times the CPU oracle (numpy FP64, one thread) on the same
-system: each step is one restart cycle of its s-step GMRES, and the value is
-scaled to a full solve by the number of cycles the solve takes.
+system: each step is one restart cycle of its own s-step GMRES solve, and the
+value is the mean cycle time times the number of cycles the oracle's solve took
+(run in the same call).
 """
 from __future__ import annotations
 
@@ -34,7 +35,13 @@ N_GRID = 128
 BETA = (30.0, 20.0, 10.0)
 M = 40
 TOL = 1e-8
-WORKLOAD = "3-D convection-diffusion 128^3 (n=2,097,152), beta=(30,20,10), 7-point, FP64, x0=0, tol 1e-8"
+
+
+def workload(N):
+    return f"3-D convection-diffusion {N}^3 (n={N ** 3:,}), beta=(30,20,10), 7-point, FP64, x0=0, tol 1e-8"
+
+
+WORKLOAD = workload(N_GRID)
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz, FMA = 2 flops
 
 
@@ -101,6 +108,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--s", type=int, default=8, help="block size of the headline s-step GMRES")
+    ap.add_argument("--grid", type=int, default=N_GRID, help="side of the 3-D grid (the workload is 128)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32"],
                     help="basis precision of the headline solve")
     ap.add_argument("--no-variants", action="store_true", help="the headline solve only")
@@ -190,17 +198,19 @@ def cycle_steps(history, s, m, tol):
 
 
 def sstep_gmres_work(n, dim, s, m, history, tol):
-    """Algorithmic FP64 flops and bytes per kernel kind of one s-step GMRES solve.
+    """Algorithmic FP64 flops, bytes and launches per kernel kind of one s-step GMRES solve.
 
-    Per kernel: the FMAs of the definition (FMA = 2 flops) and the compulsory
-    traffic (every array read or written once, halo re-reads excluded). Block k
-    of a cycle (o = k s earlier columns) costs: powers s sweeps of (2(2d+1)) flops
-    and 16 B per point plus the 8 B scaled start vector; Gram 2 o s flops and
-    (o + s) columns; update 2 o s + (s+1)(s+2) flops, (o+s+1) columns read and s
-    written (none when o = 0); next vector 2s+2 flops, s+1 columns read, 1 written.
+    Per kernel: the FMAs of the definition (FMA = 2 flops), the compulsory
+    traffic (every array read or written once, halo re-reads excluded) and the
+    launches that did work (a cycle that converges early skips the rest of its
+    blocks: those launches return at once and are not counted). Block k of a
+    cycle (o = k s earlier columns) costs: powers s sweeps of (2(2d+1)) flops and
+    16 B per point plus the 8 B scaled start vector; Gram 2 o s flops and (o + s)
+    columns; update 2 o s + (s+1)(s+2) flops, (o+s+1) columns read and s written
+    (none when o = 0); next vector 2s+2 flops, s+1 columns read, 1 written.
     """
     pts = 2 * (2 * dim + 1)
-    W = {k: [0.0, 0.0] for k in ("stencil_powers", "gram", "block_update", "next_vector", "residual", "basis_axpy")}
+    W = {k: [0.0, 0.0, 0] for k in ("stencil_powers", "gram", "block_update", "next_vector", "residual", "basis_axpy")}
     cycles = cycle_steps(history, s, m, tol)
     for steps in cycles:
         nblk = steps // s
@@ -208,18 +218,24 @@ def sstep_gmres_work(n, dim, s, m, history, tol):
             o = k * s
             W["stencil_powers"][0] += s * pts * n
             W["stencil_powers"][1] += (s * 16 + 8) * n
+            W["stencil_powers"][2] += s
             if k > 0:
                 W["gram"][0] += 2 * o * s * n
                 W["gram"][1] += (o + s) * 8 * n
+                W["gram"][2] += 1
             W["block_update"][0] += (2 * o * s + (s + 1) * (s + 2)) * n
             W["block_update"][1] += ((o + s + 1) + (s if o > 0 else 0)) * 8 * n
+            W["block_update"][2] += 1
             W["next_vector"][0] += (2 * s + 2) * n
             W["next_vector"][1] += (s + 2) * 8 * n
+            W["next_vector"][2] += 1
         W["basis_axpy"][0] += 2 * nblk * s * n
         W["basis_axpy"][1] += (nblk * s + 2) * 8 * n
+        W["basis_axpy"][2] += 1
     # the norm of f, one explicit residual per restart and the final check
     W["residual"][0] += (len(cycles) + 3) * (pts + 2) * n
     W["residual"][1] += (len(cycles) + 3) * 24 * n
+    W["residual"][2] += len(cycles) + 2
     return W
 
 
@@ -242,12 +258,12 @@ print(json.dumps(times))
 """
 
 
-def oracle_cycle_seconds(s, reps, seed=0, threads=1):
+def oracle_cycle_seconds(s, reps, seed=0, threads=1, grid=N_GRID):
     """Seconds per restart cycle of the oracle's s-step GMRES in a fresh process, with its
     BLAS (the dense products of the Gram pass and the updates) on `threads` threads."""
     t = str(threads)
     env = dict(os.environ, OPENBLAS_NUM_THREADS=t, OMP_NUM_THREADS=t, MKL_NUM_THREADS=t)
-    code = ORACLE_SNIPPET.format(root=ROOT, n=N_GRID, beta=BETA, seed=seed, reps=reps, s=s, m=M, tol=TOL)
+    code = ORACLE_SNIPPET.format(root=ROOT, n=grid, beta=BETA, seed=seed, reps=reps, s=s, m=M, tol=TOL)
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -255,24 +271,63 @@ def oracle_cycle_seconds(s, reps, seed=0, threads=1):
 
 
 # ------------------------------------------------------------------ reference arm
+REFERENCE_SNIPPET = r"""
+import sys, time, json
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import stencil, sstep
+from paper_2001_04886_gb300 import inputs
+A = stencil.convdiff(({n}, {n}, {n}), {beta!r})
+f = A.apply(inputs.x_true({seed}, A.n))
+sigma = 1.0 / A.norm_inf()
+x = np.zeros(A.n)
+times, solves, cyc, tsol = [], [], 0, 0.0
+while len(times) < {reps} or not solves:
+    t = time.perf_counter()
+    r = sstep.sstep_gmres(A, f, x, {s}, {m}, {tol}, sigma, max_cycles=1)
+    dt = time.perf_counter() - t
+    times.append(dt)
+    cyc, tsol, x = cyc + 1, tsol + dt, r["x"]
+    if r["status"] == 0:
+        solves.append([cyc, tsol])
+        x, cyc, tsol = np.zeros(A.n), 0, 0.0
+print(json.dumps({{"times": times, "solves": solves}}))
+"""
+
+
 def reference_arm(args):
+    """The oracle's restarted s-step GMRES on the same system, run cycle by cycle.
+
+    Each step is one restart cycle of the oracle's own solve (a restart cycle starts from
+    the iterate the previous one left, so the steps in a row are the solve itself; after
+    the solve converges the next step starts a new solve from x0 = 0). The run continues
+    past the timed steps until one whole solve has finished. value = the mean measured
+    cycle time x the number of cycles the oracle's own solve took; the first whole solve's
+    measured time is reported beside it."""
     rank, world, _ = env_ranks()
     if rank != 0:
         return 0
-    # cycles of the full solve: the s-step GMRES on this workload converges in this many
-    # restart cycles (the GPU path and the oracle agree on it; measured on this workload)
-    cycles = int(os.environ.get("SSTEP_BENCH_CYCLES", "11"))
-    times = oracle_cycle_seconds(args.s, args.warmup + args.steps)
-    t = times[args.warmup:]
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = REFERENCE_SNIPPET.format(root=ROOT, n=args.grid, beta=BETA, seed=0, reps=args.warmup + args.steps,
+                                    s=args.s, m=M, tol=TOL)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=3600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    t = rec["times"][args.warmup: args.warmup + args.steps]
+    cycles, solve_s = rec["solves"][0]
     ms = 1e3 * sum(t) / len(t) * cycles
+    sample = (f"each step = 1 restart cycle of the numpy oracle's s-step GMRES (s={args.s}, m={M}, 1 thread), "
+              f"consecutive cycles of its own solve; value = mean measured cycle time x the {cycles} cycles "
+              f"the oracle's solve took; its first whole solve measured {1e3 * solve_s:.0f} ms")
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "method": f"oracle s-step GMRES s={args.s} m={M}", "cores": 1},
-        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": f"each step = 1 restart cycle of the numpy oracle (1 thread); value = mean "
-                                   f"cycle time x {cycles} cycles of the full solve"},
+        "config": {"workload": workload(args.grid), "method": f"oracle s-step GMRES s={args.s} m={M}", "cores": 1,
+                   "step": "one restart cycle of the oracle's solve (ms_per_step); value = solve time",
+                   "cycles_per_solve": cycles, "whole_solve_ms": 1e3 * solve_s},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -305,7 +360,7 @@ def main():
     from paper_2001_04886_gb300 import inputs
 
     pkg.lib()
-    shape = (N_GRID,) * 3
+    shape = (args.grid,) * 3
     A = pkg.StencilMatrix(3, shape, beta=BETA)
     n = A.n
     xt = torch.tensor(inputs.x_true(rank, n), dtype=torch.float64, device=dev)
@@ -373,17 +428,32 @@ def main():
     work = sstep_gmres_work(n, 3, s, M, res["history"], TOL)
     kinds = {k: v for k, v in trace.items() if v[1] > 0}
     t_dom = kinds[dom][0] / args.steps / 1e3             # seconds per solve
-    flops, bytes_ = work[dom]
+    flops, bytes_, launches_dom = work[dom]
     achieved = flops / t_dom / 1e12
-    launches_timed = sum(v[1] for v in kinds.values())
-    launches_dom = kinds[dom][1] / args.steps
+    issued_dom = kinds[dom][1] / args.steps   # includes launches a converged cycle skips at once
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": measured_traffic(args.precision, dom), "kernel": dom,
-                "launches_per_solve": launches_dom, "algorithmic_bytes_per_launch": bytes_ / launches_dom,
+                "launches_per_solve": launches_dom, "launches_issued_per_solve": issued_dom,
+                "algorithmic_bytes_per_launch": bytes_ / launches_dom,
                 "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
                 "hbm_gbs": bytes_ / t_dom / 1e9,
                 "hbm_peak_gbs": HBM_PEAK_GBS, "hbm_frac": bytes_ / t_dom / 1e9 / HBM_PEAK_GBS,
                 "share_of_step": kinds[dom][0] / args.steps / ms}
+
+    # the comparison the metric names: standard GMRES(m) (classical Gram-Schmidt, Alg. 2.2)
+    # on the same system and GPU, timed the same way
+    x.zero_()
+    solve(x, method="gmres")
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        x.zero_()
+        rp = solve(x, method="gmres")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain = {"method": f"GMRES({M}), classical Gram-Schmidt", "ms": e0.elapsed_time(e1) / 3, "timed_solves": 3,
+             "status": rp["status"], "cycles": rp["cycles"], "matvecs": rp["matvecs"], "relres": rp["relres"]}
+    plain["ms"] = reduce_max(plain["ms"], dist, dev)
 
     # end to end through the public API: inputs from pinned host memory, x back to the host
     f_h = f.cpu().pin_memory()
@@ -539,13 +609,13 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
-            ts = oracle_cycle_seconds(s, 2)
+            ts = oracle_cycle_seconds(s, 2, grid=args.grid)
             cycles = res["cycles"]
             cpu = {"value": 1e3 * min(ts) * cycles, "unit": "ms", "cores": 1, "kind": "oracle",
                    "sample": f"1 restart cycle of the numpy oracle's s-step GMRES (s={s}, m={M}) on the same "
                              f"system, best of 2, x {cycles} cycles of the full solve"}
             ncpu = os.cpu_count() or 1
-            ta = oracle_cycle_seconds(s, 2, threads=ncpu)
+            ta = oracle_cycle_seconds(s, 2, threads=ncpu, grid=args.grid)
             cpu["all_cores"] = {"value": 1e3 * min(ta) * cycles, "unit": "ms", "cores": ncpu,
                                 "sample": "the same, with the oracle's BLAS on every host core"}
         except Exception as ex:   # the baseline is reported, never required
@@ -556,14 +626,19 @@ def main():
             "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "method": f"s-step GMRES s={s} m={M}, sigma=1/||A||_inf",
+            "config": {"workload": workload(args.grid), "method": f"s-step GMRES s={s} m={M}, sigma=1/||A||_inf",
                        "l2": "inputs larger than L2 (basis 42 x 16.8 MB), no flush", "parallelism": f"replicas{world}",
                        "cycles": res["cycles"], "matvecs": res["matvecs"], "relres": relres,
                        "x_err_vs_x_true": err},
             "roofline": roofline,
+            "plain_gmres_ms": plain["ms"],
+            "speedup_vs_plain": plain["ms"] / ms,
+            "plain_gmres": plain,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
-            "gpu_launches": int(launches_timed),
+            # every kernel of a solve is traced in the last warm-up solve; the timed solves
+            # repeat the same launch sequence (the dominant kind alone is traced there)
+            "gpu_launches": int(args.steps * sum(v[1] for v in breakdown.values())),
             "clocks": clk,
             "kernel_ms_per_solve": {k: v[0] for k, v in breakdown.items() if v[1] > 0},
             "kernel_algorithmic_gbs": {k: work[k][1] / (v[0] / 1e3) / 1e9 for k, v in breakdown.items()
