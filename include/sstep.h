@@ -126,7 +126,8 @@ int stencil_matrix_smooth_batched(int nsys, const sstep_matrix* A, const double*
 int sstep_matrix_powers(sstep_matrix A, const double* v, double scale, double sigma, int s,
                         double* Y, int64_t ldy, void* stream);
 
-/* Bytes of device workspace the Gram pass needs for ka x kb outputs over n rows. */
+/* Bytes of device workspace the Gram pass (sstep_gram or sstep_gram_tc) needs for ka x kb
+ * outputs over n rows. */
 int sstep_gram_workspace_size(int64_t n, int ka, int kb, size_t* bytes);
 
 /* The simultaneous inner products of one s-step (Sec. 1; Alg. 4.1 steps 4-5;
@@ -138,16 +139,40 @@ int sstep_gram_workspace_size(int64_t n, int ka, int kb, size_t* bytes);
 int sstep_gram(int64_t n, const double* V, int64_t ldv, int ka, const double* Y, int64_t ldy, int kb,
                double* C, int ldc, void* work, size_t work_bytes, void* stream);
 
+/* The same inner products (Sec. 1; Alg. 4.1 steps 4-5) on the tensor cores, the Gram pass
+ * the FP64 s-step GMRES uses. Every column is scaled by a power of two from its largest
+ * entry and written as a 61-bit fixed-point integer of eight balanced 8-bit digits (an
+ * Ozaki-Ogita-Oishi-Rump error-free splitting); the digit products run as FP16 MMAs whose
+ * FP32 sums stay exact integers, the sums over rows are exact 128-bit integers, and each
+ * entry of C is rounded to FP64 once. Error per entry before that rounding: at most
+ * 2^-65 sum_rows(Bv By) + 2^-60 sum_rows(Bv |y| + |v| By), where Bv, By are the two
+ * columns' power-of-two bounds (below 2 max|entry|) -- the digit pairs left out and the
+ * truncation to 61 bits; subnormal entries count as zero. The result is independent of the
+ * grid and of the order of the rows. A column holding Inf or NaN gives NaN in its row or
+ * column of C.
+ * Arguments, work and ranges as for sstep_gram; in addition n <= 2^27, else SSTEP_ERR_ARG. */
+int sstep_gram_tc(int64_t n, const double* V, int64_t ldv, int ka, const double* Y, int64_t ldy, int kb,
+                  double* C, int ldc, void* work, size_t work_bytes, void* stream);
+
+/* Test hook: the number of polls of each bounded mbarrier wait in the tensor-core Gram
+ * pass (process-global; 0: every wait runs out at once; < 0 restores the default 2^24).
+ * A wait that runs out makes the results of that call NaN; the kernel still waits for
+ * its tensor-core work in flight, frees its tensor memory and ends normally. */
+int sstep_set_tc_wait_limit(long limit);
+
 /* The same Gram pass as sstep_gram, for callers that cannot allocate device
- * memory when they call it: code running while a stream is captured into a CUDA
- * graph, applications that fix their device-memory budget at start-up, or plug-in
- * hosts whose allocator owns all device memory. The paper has no counterpart; this
- * is a property of the library's interface, not of the method.
+ * memory when they call it: applications that fix their device-memory budget at
+ * start-up and forbid later allocations, and plug-in hosts whose own allocator owns
+ * all device memory, so that a library allocating behind their back would break
+ * their accounting or fail. The paper has no counterpart; this is a property of the
+ * library's interface, not of the method.
  *   - Allocates nothing: the scratch is a fixed 700,672-byte array in the library's
  *     device image, present on every GPU that loads the library until the process
  *     exits. ka <= SSTEP_MAX_COLS and kb <= SSTEP_MAX_S + 1, else SSTEP_ERR_ARG.
  *   - The first call on each device looks up the array's device address (with that
- *     device current); make that first call before any stream capture begins.
+ *     device current); make that first call before any stream capture begins. Later
+ *     calls on a stream that is not being captured look the address up again, so a
+ *     cudaDeviceReset in between is harmless.
  *   - Every call shares the one array per device, and its contents persist between
  *     calls: calls whose executions overlap on the GPU (other streams, other host
  *     threads) race and give wrong results. Serialise them on one stream.

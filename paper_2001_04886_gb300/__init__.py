@@ -22,7 +22,9 @@ from ._binding import (  # noqa: F401
     lib,
     sstep_block_update,
     sstep_gmres_solve,
+    set_tc_wait_limit,
     sstep_gram,
+    sstep_gram_tc,
     sstep_gram_workspace_size,
     sstep_matrix_powers,
     sstep_newton_shifts,
@@ -44,6 +46,8 @@ __all__ = [
     "stencil_matrix_smooth_batched",
     "sstep_matrix_powers",
     "sstep_gram",
+    "sstep_gram_tc",
+    "set_tc_wait_limit",
     "sstep_gram_workspace_size",
     "sstep_block_update",
     "sstep_gmres_solve",

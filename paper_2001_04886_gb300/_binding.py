@@ -52,6 +52,9 @@ SIGNATURES = {
     "sstep_gram_workspace_size": (c_int, [c_int64, c_int, c_int, P(c_size_t)]),
     "sstep_gram": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
                            c_void_p, c_size_t, c_void_p]),
+    "sstep_gram_tc": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
+                              c_void_p, c_size_t, c_void_p]),
+    "sstep_set_tc_wait_limit": (c_int, [ctypes.c_long]),
     "sstep_gram_noalloc": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
                                    c_void_p]),
     "sstep_block_update": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
@@ -290,6 +293,28 @@ def sstep_gram(V, Y, C=None, work=None, stream=None):
     _check("sstep_gram", lib().sstep_gram(n, _ptr(V), ldv, ka, _ptr(Y), ldy, kb, c_void_p(C.data_ptr()), ka,
                                           _aligned_ptr(work), nbytes, _stream(stream)))
     return C
+
+
+def sstep_gram_tc(V, Y, C=None, work=None, stream=None):
+    """C = V^T Y on the tensor cores (exact 61-bit fixed point, one rounding per entry)."""
+    import torch
+
+    n, ka, ldv = _col_major(V, "V")
+    n2, kb, ldy = _col_major(Y, "Y")
+    assert n == n2
+    if C is None:
+        C = torch.empty((kb, ka), dtype=torch.float64, device=V.device).t()
+    nbytes = sstep_gram_workspace_size(n, ka, kb)
+    if work is None:
+        work = _workspace(nbytes, V.device)
+    _check("sstep_gram_tc", lib().sstep_gram_tc(n, _ptr(V), ldv, ka, _ptr(Y), ldy, kb, c_void_p(C.data_ptr()), ka,
+                                                _aligned_ptr(work), nbytes, _stream(stream)))
+    return C
+
+
+def set_tc_wait_limit(limit):
+    """Polls per bounded mbarrier wait of the tensor-core Gram pass (0: none; < 0: the default)."""
+    return _check("sstep_set_tc_wait_limit", lib().sstep_set_tc_wait_limit(int(limit)))
 
 
 def sstep_block_update(V, Y, T, work=None, stream=None):

@@ -36,6 +36,9 @@ struct sstep_matrix_s {
 namespace {
 
 constexpr size_t kAlign = 256;
+// column bounds of the tensor-core Gram pass: m + 1 basis columns, then s + 1 power
+// columns per block (m + 1 + (m / s)(s + 1) <= 3 SSTEP_MAX_M + 1)
+constexpr int kBndSlots = 4 * SSTEP_MAX_M;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 inline int64_t col_ld(int64_t n) { return (n + 31) / 32 * 32; }   // 256-byte aligned columns
 
@@ -192,6 +195,16 @@ std::vector<double> newton_shifts_from_device(const double* G_dev, int m, int K,
 // default: on GB300 the 16.8 MB columns of a 128^3 solve stay in the 129 MB L2 between
 // separate sweeps, so fusion saves only L2 reads while its tile halos recompute ~4x the
 // points (measured slower). SSTEP_FUSED_POWERS=1 turns it on.
+// The Gram pass of the FP64 s-step GMRES runs on the tensor cores (exact fixed point,
+// ozaki.cu) unless SSTEP_TC_GRAM=0 selects the FP64 CUDA-core kernel (for comparisons).
+bool tc_gram_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("SSTEP_TC_GRAM");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 bool fused_powers_enabled() {
     static const bool on = [] {
         const char* v = getenv("SSTEP_FUSED_POWERS");
@@ -298,7 +311,7 @@ int make_desc(StencilDesc& A, int dim, const int64_t shape[3]) {
 
 // Device workspace of one solve. Small arrays first, then the columns.
 struct Layout {
-    size_t state, L, T, S, G, R, gc, gs, g, y, hist, C, a, theta, counter, partials, cols;
+    size_t state, L, T, S, G, R, gc, gs, g, y, hist, C, a, theta, counter, bnd, partials, cols;
     size_t total;
 };
 
@@ -326,6 +339,7 @@ Layout plan(int64_t n, int ncols, int m, int hist_cap, size_t elem_bytes = sizeo
     l.a = take(sizeof(double) * kMaxCols);
     l.theta = take(sizeof(double) * kMaxS);
     l.counter = take(kAlign);
+    l.bnd = take(sizeof(unsigned) * kBndSlots);
     l.partials = take(sizeof(double) * (size_t)max_partials_doubles());
     l.cols = take(elem_bytes * (size_t)col_ld(n) * ncols);
     l.total = off;
@@ -977,9 +991,44 @@ int sstep_matrix_powers(sstep_matrix M, const double* v, double scale, double si
     return check_launch();
 }
 
+// work: the arrival counter and error flag (256 B), the partials, then the column bounds of
+// the tensor-core pass (ka + kb <= 73 words: 512 B)
+constexpr size_t kGramBndBytes = 2 * kAlign;
 int sstep_gram_workspace_size(int64_t n, int ka, int kb, size_t* bytes) {
     if (!bytes || n < 0 || ka < 1 || ka > SSTEP_MAX_COLS || kb < 1 || kb > SSTEP_MAX_S + 1) return SSTEP_ERR_ARG;
-    *bytes = kAlign + sizeof(double) * (size_t)max_partials_doubles();
+    *bytes = kAlign + sizeof(double) * (size_t)max_partials_doubles() + kGramBndBytes;
+    return SSTEP_OK;
+}
+
+int sstep_gram_tc(int64_t n, const double* V, int64_t ldv, int ka, const double* Y, int64_t ldy, int kb, double* C,
+                  int ldc, void* work, size_t work_bytes, void* stream) {
+    size_t need = 0;
+    if (sstep_gram_workspace_size(n, ka, kb, &need)) return SSTEP_ERR_ARG;
+    if (!V || !Y || !C || !work || work_bytes < need || ldv < n || ldy < n || ldc < ka) return SSTEP_ERR_ARG;
+    if (((uintptr_t)work) % kAlign) return SSTEP_ERR_ARG;
+    if (n > ((int64_t)1 << 27) || ((uintptr_t)V & 7) || ((uintptr_t)Y & 7)) return SSTEP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0)
+        return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * ka, kb, st) == cudaSuccess ? SSTEP_OK
+                                                                                                       : SSTEP_ERR_CUDA;
+    Scratch sc{(double*)((char*)work + kAlign), (unsigned*)work};
+    unsigned* bnd = (unsigned*)((char*)work + kAlign + sizeof(double) * (size_t)max_partials_doubles());
+    CUDA_TRY(cudaMemsetAsync(work, 0, kAlign, st));
+    CUDA_TRY(cudaMemsetAsync(bnd, 0, kGramBndBytes, st));
+    launch_colmax(n, V, ldv, ka, bnd, st);
+    launch_colmax(n, Y, ldy, kb, bnd + ka, st);
+    Epi e;
+    e.mode = EPI_NONE;
+    e.out = C;
+    e.ldo = ldc;
+    if (!launch_gram_oz(n, V, ldv, ka, bnd, Y, ldy, kb, bnd + ka, sc, e, GATE_NONE, st)) return SSTEP_ERR_ARG;
+    return check_launch();
+}
+
+// mbarrier poll limit of the tensor-core Gram pass (tests of its timeout path); < 0 restores the default
+int sstep_set_tc_wait_limit(long limit) {
+    static const long dflt = g_oz_spin;
+    g_oz_spin = limit >= 0 ? limit : dflt;
     return SSTEP_OK;
 }
 
@@ -989,9 +1038,11 @@ int sstep_gram(int64_t n, const double* V, int64_t ldv, int ka, const double* Y,
     if (sstep_gram_workspace_size(n, ka, kb, &need)) return SSTEP_ERR_ARG;
     if (!V || !Y || !C || !work || work_bytes < need || ldv < n || ldy < n || ldc < ka) return SSTEP_ERR_ARG;
     if (((uintptr_t)work) % kAlign) return SSTEP_ERR_ARG;
-    if (n == 0) return cudaMemsetAsync(C, 0, sizeof(double) * ldc * kb, (cudaStream_t)stream) == cudaSuccess
-                           ? SSTEP_OK
-                           : SSTEP_ERR_CUDA;
+    if (n == 0)   // C = 0: the ka x kb entries only (the rows below ka of each column are the caller's)
+        return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * ka, kb, (cudaStream_t)stream) ==
+                       cudaSuccess
+                   ? SSTEP_OK
+                   : SSTEP_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     Scratch sc{(double*)((char*)work + kAlign), (unsigned*)work};
     CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned), st));
@@ -1068,23 +1119,32 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     if (p->x0_guard && (rc = apply_x0_guard(M, l, st, f, x, stream_))) return rc;
     const double sigma = h.sigma;
     const int nb = m / s;
+    // tensor-core Gram pass: the producers of every basis and power column record its bound
+    // (bnd[c] for basis column c, pbnd(k)[j] for power j of block k), zeroed per cycle
+    const bool tcg = !pre && tc_gram_enabled();
+    unsigned* bnd = (unsigned*)(M->ws + l.bnd);
+    auto pbnd = [&](int k) { return tcg ? bnd + (m + 1) + k * (s + 1) : nullptr; };
     std::vector<double> theta(s, 0.0);   // Newton shifts (zero: monomial powers)
     bool shifted = false;
     M->shifts.clear();
     for (;;) {
+        if (tcg) CUDA_TRY(cudaMemsetAsync(bnd, 0, sizeof(unsigned) * kBndSlots, stream_));
         e = Epi();
         e.st = st;
         e.mode = EPI_RESTART;
         TRACED(K_RESIDUAL, stream_, launch_residual(M->A, f, x, uraw, sc, e, GATE_ACTIVE, stream_));
         for (int k = 0; k < nb; ++k) {
             const int o = k * s;
+            unsigned* pb = pbnd(k);
             // Alg. 4.1 step 3: v_k^1 = u / ||u|| and its s scaled powers
             if (!pre) {
                 TRACED(K_STENCIL, stream_, launch_stencil(M->A, uraw, sigma, U + (o + 1) * ld, 1.0, U + o * ld,
-                                                          &st->vscale, st, GATE_BUILDING, stream_, theta[0]));
+                                                          &st->vscale, st, GATE_BUILDING, stream_, theta[0], nullptr,
+                                                          tcg ? pb + 1 : nullptr, tcg ? bnd + o : nullptr));
                 for (int j = 2; j <= s; ++j)
                     TRACED(K_STENCIL, stream_, launch_stencil(M->A, U + (o + j - 1) * ld, sigma, U + (o + j) * ld, 0.0,
-                                                              nullptr, nullptr, st, GATE_BUILDING, stream_, theta[j - 1]));
+                                                              nullptr, nullptr, st, GATE_BUILDING, stream_, theta[j - 1],
+                                                              nullptr, tcg ? pb + j : nullptr));
             } else {   // right preconditioning: y^{j+1} = sigma (A M^-1 y^j - theta_j y^j)
                 launch_scale_copy(uraw, U + o * ld, n, &st->vscale, st, GATE_BUILDING, stream_);
                 for (int j = 1; j <= s; ++j) {
@@ -1100,7 +1160,10 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
                 e.st = st;
                 e.mode = EPI_GM_T;
                 e.o = o;
-                TRACED(K_GRAM, stream_, launch_gram(n, U, ld, o, U + (o + 1) * ld, ld, s, 0, sc, e, GATE_BUILDING, stream_));
+                TRACED(K_GRAM, stream_,
+                       if (!tcg || !launch_gram_oz(n, U, ld, o, bnd, U + (o + 1) * ld, ld, s, pb + 1, sc, e,
+                                                   GATE_BUILDING, stream_))
+                           launch_gram(n, U, ld, o, U + (o + 1) * ld, ld, s, 0, sc, e, GATE_BUILDING, stream_));
             }
             // step 7 and Scalar1: project, then Gram of the projected block
             e = Epi();
@@ -1108,7 +1171,7 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
             e.mode = EPI_GM_W;
             e.o = o;
             TRACED(K_UPDATE, stream_, launch_update(n, U, ld, o, U + o * ld, ld, U + o * ld, ld, s + 1, 1, h.T, m, -1.0, true, sc, e,
-                          GATE_BUILDING, stream_));
+                          GATE_BUILDING, stream_, tcg ? bnd + o + 1 : nullptr, s));
             // step 2: the next start vector u = z - V_k S and its norm; G, Givens
             e = Epi();
             e.st = st;

@@ -3,6 +3,8 @@
 // the Hessenberg least squares, which runs in the last CTA of each reduction.
 #include <math.h>
 
+#include <algorithm>
+
 #include "epilogue.cuh"
 
 namespace sstep {
@@ -11,7 +13,8 @@ constexpr int kMaxCtas = 152 * 8;      // 8 CTAs of 256 threads per SM at most
 constexpr int kGramKA = 8;             // V columns per Gram CTA (grid.y splits ka)
 constexpr int kMaxNV = kGramKA * (kMaxS + 1);   // largest per-CTA partial vector
 
-int max_partials_doubles() { return kMaxCtas * kMaxNV; }
+int fp64_gram_partials_doubles() { return kMaxCtas * kMaxNV; }
+int max_partials_doubles() { return std::max(kMaxCtas * kMaxNV, oz_partials_doubles()); }
 
 // ================================================================== stencil sweep
 __device__ __forceinline__ void grid_xyz(const StencilDesc& A, int64_t p, int& x, int& y, int& z) {
@@ -23,6 +26,24 @@ __device__ __forceinline__ void grid_xyz(const StencilDesc& A, int64_t p, int& x
     z = (int)zz;
 }
 
+// high word of |v|: its maximum over a column is the column bound of the tensor-core Gram pass
+__device__ __forceinline__ unsigned abs_hi(double v) {
+    return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7FFFFFFFu;
+}
+
+// warp maximum of the bounds, one atomicMax per warp and column (every lane of the warp
+// must reach this call)
+__device__ __forceinline__ void publish_bounds(unsigned ym, unsigned* ybnd, unsigned wm, unsigned* wbnd) {
+    if (ybnd) {
+        ym = __reduce_max_sync(0xffffffffu, ym);
+        if ((threadIdx.x & 31) == 0 && ym) atomicMax(ybnd, ym);
+    }
+    if (wbnd) {
+        wm = __reduce_max_sync(0xffffffffu, wm);
+        if ((threadIdx.x & 31) == 0 && wm) atomicMax(wbnd, wm);
+    }
+}
+
 // A CTA owns a (32 x 8)-point x-y tile and a chunk of z planes and marches through z,
 // keeping planes z-1, z, z+1 of each (x, y) column in registers: a point costs one new
 // load plus the four in-plane neighbours (L1 hits), with no per-point division. With
@@ -32,7 +53,8 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
                                                            double fy, double* __restrict__ y, double fw,
                                                            double* __restrict__ w, const double* dscale,
                                                            const SolverState* st, int gate, int zchunk,
-                                                           double shift, const double* __restrict__ u) {
+                                                           double shift, const double* __restrict__ u,
+                                                           unsigned* ybnd, unsigned* wbnd) {
     if (!gate_open(st, gate)) return;
     if (dscale) {
         const double d = *dscale;
@@ -43,7 +65,8 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
     const int x = (int)(blockIdx.x % tx) * 32 + threadIdx.x;
     const int yy = (int)(blockIdx.x / tx) * 8 + threadIdx.y;
     const int zb = blockIdx.y * zchunk, ze = min(A.nz, zb + zchunk);
-    if (x >= A.nx || yy >= A.ny || zb >= ze) return;
+    unsigned ym = 0, wm = 0;   // column bounds of this thread's outputs
+    if (x < A.nx && yy < A.ny && zb < ze) {
     const bool three = A.dim == 3;
     const int64_t pl = (int64_t)A.nx * A.ny;
     int64_t p = (int64_t)zb * pl + (int64_t)yy * A.nx + x;
@@ -82,10 +105,17 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
         }
         if (u) acc = fma(fs, __ldg(u + p), acc);
         y[p] = acc;
-        if (w) w[p] = fw * vc;
+        ym = max(ym, abs_hi(acc));
+        if (w) {
+            const double wv = fw * vc;
+            w[p] = wv;
+            wm = max(wm, abs_hi(wv));
+        }
         vm = vc;
         vc = vp;
     }
+    }
+    publish_bounds(ym, ybnd, wm, wbnd);
 }
 
 // The common case of the powers: constant coefficients and no separate shift vector.
@@ -104,7 +134,8 @@ __global__ void __launch_bounds__(kThreads) stencil_const_kernel(int nx, int ny,
                                                                  const double* __restrict__ v,
                                                                  double* __restrict__ y, double fw,
                                                                  double* __restrict__ w, const double* dscale,
-                                                                 const SolverState* st, int gate, int zchunk) {
+                                                                 const SolverState* st, int gate, int zchunk,
+                                                                 unsigned* ybnd, unsigned* wbnd) {
     if (!gate_open(st, gate)) return;
     __shared__ double sk[8];
     if (DSCALE) {
@@ -126,7 +157,8 @@ __global__ void __launch_bounds__(kThreads) stencil_const_kernel(int nx, int ny,
     const int x = (int)(blockIdx.x % tx) * 32 + threadIdx.x;
     const int yy = (int)(blockIdx.x / tx) * 8 + threadIdx.y;
     const int zb = blockIdx.y * zchunk, ze = min(nz, zb + zchunk);
-    if (x >= nx || yy >= ny || zb >= ze) return;
+    unsigned ym = 0, wm = 0;   // column bounds of this thread's outputs
+    if (x < nx && yy < ny && zb < ze) {
     const int64_t pl = (int64_t)nx * ny;
     int64_t p = (int64_t)zb * pl + (int64_t)yy * nx + x;
     const bool xl = x > 0, xr = x < nx - 1, yl = yy > 0, yr = yy < ny - 1;
@@ -145,23 +177,30 @@ __global__ void __launch_bounds__(kThreads) stencil_const_kernel(int nx, int ny,
             if (z < nz - 1) acc = fma(c6, vp, acc);
         }
         y[p] = acc;
-        if (WCOPY) w[p] = fwd * vc;
+        ym = max(ym, abs_hi(acc));
+        if (WCOPY) {
+            const double wv = fwd * vc;
+            w[p] = wv;
+            wm = max(wm, abs_hi(wv));
+        }
         vm = vc;
         vc = vp;
     }
+    }
+    publish_bounds(ym, ybnd, wm, wbnd);
 }
 
 template <bool THREE, bool WCOPY, bool DSCALE>
 void launch_const(const StencilDesc& A, const ConstCoef& k, const double* v, double* y, double fw, double* w,
                   const double* dscale, const SolverState* st, int gate, int zchunk, dim3 grid, dim3 block,
-                  cudaStream_t stream) {
+                  cudaStream_t stream, unsigned* ybnd, unsigned* wbnd) {
     stencil_const_kernel<THREE, WCOPY, DSCALE><<<grid, block, 0, stream>>>(A.nx, A.ny, A.nz, k, v, y, fw, w, dscale,
-                                                                           st, gate, zchunk);
+                                                                           st, gate, zchunk, ybnd, wbnd);
 }
 
 void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y, double fw, double* w,
                     const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift,
-                    const double* u) {
+                    const double* u, unsigned* ybnd, unsigned* wbnd) {
     const int tiles = ((A.nx + 31) / 32) * ((A.ny + 7) / 8);
     // z chunks: about one wave of 8 CTAs per SM, at least one plane per chunk
     int chunks = kMaxCtas / tiles;
@@ -177,7 +216,7 @@ void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y,
         if (!dscale) k.c[0] = fy * (A.c[0] - shift);
         const bool three = A.dim == 3, wc = w != nullptr, ds = dscale != nullptr;
 #define SSTEP_CONST(T3, WC, DS) \
-    if (three == T3 && wc == WC && ds == DS) return launch_const<T3, WC, DS>(A, k, v, y, fw, w, dscale, st, gate, zchunk, grid, block, stream);
+    if (three == T3 && wc == WC && ds == DS) return launch_const<T3, WC, DS>(A, k, v, y, fw, w, dscale, st, gate, zchunk, grid, block, stream, ybnd, wbnd);
         SSTEP_CONST(true, false, false)
         SSTEP_CONST(true, true, true)
         SSTEP_CONST(true, true, false)
@@ -188,7 +227,7 @@ void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y,
         SSTEP_CONST(false, false, true)
 #undef SSTEP_CONST
     }
-    stencil_kernel<<<grid, block, 0, stream>>>(A, v, fy, y, fw, w, dscale, st, gate, zchunk, shift, u);
+    stencil_kernel<<<grid, block, 0, stream>>>(A, v, fy, y, fw, w, dscale, st, gate, zchunk, shift, u, ybnd, wbnd);
 }
 
 // ================================================================== residual
@@ -304,7 +343,8 @@ template <int KB, bool GRAM>
 __global__ void __launch_bounds__(kThreads) update_kernel(int64_t n, const double* __restrict__ V, int64_t ldv,
                                                           int ka, const double* Yin, int64_t ldy, double* Yout,
                                                           int64_t ldo, int j0, const double* __restrict__ T,
-                                                          int ldt, double sgn, Scratch sc, Epi epi, int gate) {
+                                                          int ldt, double sgn, Scratch sc, Epi epi, int gate,
+                                                          unsigned* bnd, int bnd_hi) {
     constexpr int NV = GRAM ? KB * (KB + 1) / 2 : 1;
     __shared__ double Ts[kMaxCols * KB];
     __shared__ double red[(kWarps + 1) * NV];
@@ -324,6 +364,9 @@ __global__ void __launch_bounds__(kThreads) update_kernel(int64_t n, const doubl
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = 0.0;
     const bool inplace = (Yin == Yout) && (ldy == ldo);
+    unsigned bm[KB];   // column bounds of the outputs j0 <= j < bnd_hi
+#pragma unroll
+    for (int j = 0; j < KB; ++j) bm[j] = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
         double yv[KB];
@@ -342,6 +385,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(int64_t n, const doubl
         for (int j = 0; j < KB; ++j) {
             if (j >= j0 && ka > 0) yv[j] = yv[j] + sum[j];
             if (!inplace || (j >= j0 && ka > 0)) Yout[p + j * ldo] = yv[j];
+            bm[j] = max(bm[j], abs_hi(yv[j]));
         }
         if (GRAM) {
             int idx = 0;
@@ -353,6 +397,11 @@ __global__ void __launch_bounds__(kThreads) update_kernel(int64_t n, const doubl
                     ++idx;
                 }
         }
+    }
+    if (bnd) {
+#pragma unroll
+        for (int j = 0; j < KB; ++j)
+            if (j >= j0 && j < bnd_hi) publish_bounds(bm[j], bnd + (j - j0), 0u, nullptr);
     }
     if (!GRAM) return;
     block_reduce<NV>(acc, red);
@@ -375,17 +424,20 @@ __global__ void __launch_bounds__(kThreads) update_kernel(int64_t n, const doubl
 
 void launch_update(int64_t n, const double* V, int64_t ldv, int ka, const double* Yin, int64_t ldy,
                    double* Yout, int64_t ldo, int kb, int j0, const double* T, int ldt, double sgn,
-                   bool gram, Scratch sc, const Epi& epi, int gate, cudaStream_t stream) {
+                   bool gram, Scratch sc, const Epi& epi, int gate, cudaStream_t stream, unsigned* bnd,
+                   int bnd_hi) {
     int grid = grid_for(n, kMaxCtas / 2);
     switch (kb) {
 #define SSTEP_UPD_CASE(KB)                                                                                \
     case KB:                                                                                              \
         if (gram)                                                                                         \
             update_kernel<KB, true><<<grid, kThreads, 0, stream>>>(n, V, ldv, ka, Yin, ldy, Yout, ldo, j0, \
-                                                                   T, ldt, sgn, sc, epi, gate);          \
+                                                                   T, ldt, sgn, sc, epi, gate, bnd,      \
+                                                                   bnd_hi);                              \
         else                                                                                              \
             update_kernel<KB, false><<<grid, kThreads, 0, stream>>>(n, V, ldv, ka, Yin, ldy, Yout, ldo,    \
-                                                                    j0, T, ldt, sgn, sc, epi, gate);     \
+                                                                    j0, T, ldt, sgn, sc, epi, gate, bnd, \
+                                                                    bnd_hi);                             \
         break;
         SSTEP_UPD_CASE(1)
         SSTEP_UPD_CASE(2)

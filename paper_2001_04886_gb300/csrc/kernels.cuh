@@ -54,9 +54,11 @@ __device__ __forceinline__ bool gate_open(const SolverState* st, int gate) {
 // y = fy * (A v), w = fw * v (if w); fy and fw are multiplied by *dscale when dscale is set.
 // y = fy (A v - shift u) with u = v unless given; w = fw v when w is set (shift: the
 // Newton basis, 0 otherwise; u: the unpreconditioned power when v = M^-1 u)
+// ybnd / wbnd (may be null): atomicMax of the high word of |y_p| / |w_p| over the sweep
+// (the column bound of the tensor-core Gram pass; the slots must start at 0).
 void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y, double fw, double* w,
                     const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift = 0.0,
-                    const double* u = nullptr);
+                    const double* u = nullptr, unsigned* ybnd = nullptr, unsigned* wbnd = nullptr);
 
 // r = f - A x (x may be null: r = f); out (may be null) receives r; reduces ||r||^2.
 void launch_residual(const StencilDesc& A, const double* f, const double* x, double* out, Scratch sc,
@@ -70,9 +72,27 @@ void launch_gram(int64_t n, const double* V, int64_t ldv, int ka, const double* 
 // Yout[:, j] = Yin[:, j] + sgn * V T[:, j] for j >= j0 (columns j < j0 copied as is only
 // when Yout != Yin); with gram, reduces Yout^T Yout (kb x kb). ka < 0: ka = st->K and
 // T = st->y (the least-squares solution).
+// bnd (may be null): bnd[j - j0] receives the column bound (atomicMax of the high word of
+// |Yout[:, j]|) of the output columns j0 <= j < bnd_hi.
 void launch_update(int64_t n, const double* V, int64_t ldv, int ka, const double* Yin, int64_t ldy,
                    double* Yout, int64_t ldo, int kb, int j0, const double* T, int ldt, double sgn,
-                   bool gram, Scratch sc, const Epi& epi, int gate, cudaStream_t stream);
+                   bool gram, Scratch sc, const Epi& epi, int gate, cudaStream_t stream, unsigned* bnd = nullptr,
+                   int bnd_hi = 0);
+
+// ------------------------------------------------------------------ tensor-core Gram pass (ozaki.cu)
+// C = V^T Y as launch_gram (contiguous V columns), computed exactly in 61-bit fixed point on
+// the tensor cores and rounded once; vmax[ka] / ymax[kb] are the column bounds (largest high
+// word of |x| per column, launch_colmax or the producing kernel). Returns false, launching
+// nothing, for shapes it does not take (ka > 64, kb > 9, n > 2^27, V or Y not 8-byte
+// aligned). A bounded wait that runs out gives NaN entries.
+bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, const double* Y,
+                    int64_t ldy, int kb, const unsigned* ymax, Scratch sc, const Epi& epi, int gate,
+                    cudaStream_t stream);
+// out[c] = column bound of column c (out must be zeroed first)
+void launch_colmax(int64_t n, const double* X, int64_t ld, int ncols, unsigned* out, cudaStream_t stream);
+int oz_partials_doubles();      // per-CTA partials of the tensor-core Gram pass, all CTAs
+int device_sms();               // multiprocessors of the current device
+extern long g_oz_spin;          // mbarrier poll limit of the tensor-core Gram pass
 
 // Orthomin: x += P a, r -= AP a (a = st->a), reduces ||r||^2.
 void launch_omin_xr(int64_t n, const double* P, const double* AP, int64_t ld, int s, double* x, double* r,
@@ -87,7 +107,8 @@ void launch_omin_pupdate(int64_t n, const double* r, const double* AR, const dou
 // One CTA: y = R^{-1} g over the first st->K columns (back substitution).
 void launch_lsq_solve(SolverState* st, int gate, cudaStream_t stream);
 
-int max_partials_doubles();
+int max_partials_doubles();          // partials of every reduction kernel (workspace size)
+int fp64_gram_partials_doubles();    // partials of the FP64 Gram kernel alone
 
 // out = [a0 | am_x | ap_x | am_y | ap_y] (5 arrays of n) for -Lap u + beta (u_x + u_y):
 // a0 = 4, am = -1 - beta h/2, ap = -1 + beta h/2

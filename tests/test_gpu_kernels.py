@@ -70,12 +70,12 @@ def test_stencil_variable_coefficients():
     assert abs(A.norm_inf - Ao.norm_inf()) <= 1e-13 * Ao.norm_inf()
 
 
-@pytest.mark.parametrize("N,kind", [(33, "fourier"), (128, "uniform"), (57, "signed")])
+@pytest.mark.parametrize("N,kind", [(31, "fourier"), (127, "uniform"), (63, "signed"), (511, "uniform")])
 def test_convdiff_variable_closed_form(N, kind):
     """The library's own variable-coefficient operator (beta field in, coefficients built on
     the device) against the closed form of Sec. 5's non-conservative convection-diffusion:
     exact on u = x(1-x) y(1-y) for any beta, so a slip in c = beta h / 2 or its sign fails."""
-    from tests.test_oracle_stencil import variable_closed_form
+    from tests.test_oracle_stencil import closed_form_ok, variable_closed_form
 
     d = dev()
     rng = np.random.default_rng(N)
@@ -90,8 +90,8 @@ def test_convdiff_variable_closed_form(N, kind):
     y = torch.empty(N * N, dtype=torch.float64, device=d)
     A.apply(to_dev(u, d), y)
     torch.cuda.synchronize()
-    assert np.max(np.abs(y.cpu().numpy() - expect)) <= 1e-14 * np.max(np.abs(expect))
-    Ao = ostencil.convdiff_variable(N, beta)
+    Ao = ostencil.convdiff_variable(N, beta)   # only for the rounding scale of each row
+    assert closed_form_ok(y.cpu().numpy(), u, expect, Ao)
     assert abs(A.norm_inf - Ao.norm_inf()) <= 1e-13 * Ao.norm_inf()
 
 

@@ -1,0 +1,180 @@
+"""The tensor-core Gram pass (sstep_gram_tc) against the oracle and against the exact
+host emulation of its own fixed-point arithmetic.
+
+Bars: every entry within 1e-14 of the product of the two column norms of the oracle's
+FP64 inner products (the parity bar of the Gram pass), equal bit for bit to the host
+emulation (every sum is an exact integer, rounded once, so no reduction order enters),
+and bitwise reproducible from call to call.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import sstep as osstep
+from paper_2001_04886_gb300 import inputs
+from tests.gpu_util import dev, to_dev, torch
+
+import paper_2001_04886_gb300 as pkg
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def emu():
+    cxx = shutil.which("g++")
+    if not cxx:
+        pytest.skip("g++ not available")
+    d = tempfile.mkdtemp(prefix="ozemu_")
+    so = os.path.join(d, "libozemu.so")
+    r = subprocess.run([cxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-I",
+                        os.path.join(ROOT, "paper_2001_04886_gb300", "csrc"),
+                        os.path.join(ROOT, "tests", "ozaki_emulation.cpp"), "-o", so], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    L = ctypes.CDLL(so)
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oz_gram.argtypes = [ctypes.c_int64, dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp]
+    yield L
+    shutil.rmtree(d, ignore_errors=True)
+
+
+def emulate(L, V, Y):
+    Vc, Yc = np.asfortranarray(V), np.asfortranarray(Y)
+    C = np.zeros(V.shape[1] * Y.shape[1])
+    p = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    L.oz_gram(V.shape[0], p(Vc), V.shape[1], p(Yc), Y.shape[1], 8, p(C))
+    return C.reshape(Y.shape[1], V.shape[1]).T
+
+
+def panel(A, d, ld=None):
+    """Column-major device panel of A with leading dimension ld (default: the row count)."""
+    n, k = A.shape
+    ld = ld or n
+    buf = torch.zeros((k, ld), dtype=torch.float64, device=d)
+    buf[:, :n] = torch.tensor(A.T, dtype=torch.float64, device=d)
+    return buf.t()[:n]
+
+
+def spread_columns(n, k, seed):
+    """Columns of different scales and spreads: uniform, decaying over 40 binades, smooth,
+    one large spike, and an all-zero column."""
+    rng = np.random.default_rng(seed)
+    t = np.linspace(0, 1, n)
+    cols = []
+    for j in range(k):
+        kind = j % 5
+        if kind == 0:
+            c = inputs.x_true(1000 * seed + j, n)
+        elif kind == 1:
+            c = rng.standard_normal(n) * 2.0 ** (-40 * t) * 10.0 ** (j % 7 - 3)
+        elif kind == 2:
+            c = np.sin((j + 1) * 3 * t) * 1e-4
+        elif kind == 3:
+            c = rng.uniform(-1, 1, n)
+            c[n // 2] = 1e6
+        else:
+            c = np.zeros(n) if j == 4 else rng.uniform(-1, 1, n) * 1e-9
+        cols.append(c)
+    return np.stack(cols, axis=1)
+
+
+def check(V, Y, C):
+    ref = osstep.inner_products(V, Y)
+    scale = np.outer(np.linalg.norm(V, axis=0), np.linalg.norm(Y, axis=0))
+    scale[scale == 0] = 1.0
+    assert np.max(np.abs(C - ref) / scale) <= 1e-14
+
+
+@pytest.mark.parametrize("n,ka,kb", [(4096, 8, 8), (5000, 32, 9), (1, 1, 1), (63, 3, 2), (1025, 33, 5),
+                                     (3000, 64, 9), (2047, 17, 1)])
+def test_tc_gram_matches_oracle_and_emulation(emu, n, ka, kb):
+    d = dev()
+    V = spread_columns(n, ka, 1)
+    Y = spread_columns(n, kb, 2)
+    Vd, Yd = panel(V, d), panel(Y, d)
+    C = pkg.sstep_gram_tc(Vd, Yd)
+    C2 = pkg.sstep_gram_tc(Vd, Yd)
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()
+    check(V, Y, got)
+    assert np.array_equal(got, emulate(emu, V, Y))        # exact integer sums: bit for bit
+    assert np.array_equal(got, C2.cpu().numpy())
+
+
+@pytest.mark.parametrize("n,ka,kb,ld", [(300001, 33, 9, 300001), (2_097_152, 32, 8, 2_097_152), (100003, 8, 9, 100010)])
+def test_tc_gram_large_and_ragged(n, ka, kb, ld):
+    """Many chunks of 1024 rows, an odd leading dimension (unaligned columns) and the
+    headline block shape at 128^3 (32 earlier columns against 8 powers)."""
+    d = dev()
+    V = np.stack([inputs.x_true(10 + i, n) for i in range(ka)], axis=1)
+    Y = np.stack([inputs.x_true(100 + j, n) * 10.0 ** (j % 5 - 2) for j in range(kb)], axis=1)
+    C = pkg.sstep_gram_tc(panel(V, d, ld), panel(Y, d, ld))
+    torch.cuda.synchronize()
+    check(V, Y, C.cpu().numpy())
+
+
+def test_tc_gram_symmetric_bit_for_bit():
+    """V^T V from exact integer sums is symmetric bit for bit (an FP64 sum need not be)."""
+    d = dev()
+    n = 200000
+    V = np.stack([inputs.x_true(40 + i, n) * 3.0 ** i for i in range(8)], axis=1)
+    G = pkg.sstep_gram_tc(panel(V, d), panel(V, d)).cpu().numpy()
+    assert np.array_equal(G, G.T)
+    check(V, V, G)
+
+
+def test_tc_gram_nonfinite_and_zero():
+    d = dev()
+    n = 3000
+    V = np.stack([inputs.x_true(1, n), np.zeros(n), inputs.x_true(2, n)], axis=1)
+    V[17, 2] = np.nan
+    Y = np.stack([inputs.x_true(3, n)], axis=1)
+    C = pkg.sstep_gram_tc(panel(V, d), panel(Y, d)).cpu().numpy()
+    assert np.isfinite(C[0, 0]) and C[1, 0] == 0.0 and np.isnan(C[2, 0])
+    check(V[:, :2], Y, C[:2])
+
+
+def test_tc_gram_n_zero_leaves_padding():
+    """n = 0 writes the ka x kb entries only (C = 0), not the rows below ka."""
+    import ctypes as ct
+
+    d = dev()
+    C = torch.full((3, 4), 7.0, dtype=torch.float64, device=d)   # 3 columns, leading dimension 4
+    dummy = torch.zeros(8, dtype=torch.float64, device=d)
+    nbytes = pkg.sstep_gram_workspace_size(0, 2, 3)
+    work = torch.zeros(nbytes // 8 + 64, dtype=torch.float64, device=d)
+    wp = ct.c_void_p((work.data_ptr() + 255) // 256 * 256)
+    rc = pkg.lib().sstep_gram_tc(0, ct.c_void_p(dummy.data_ptr()), 0, 2, ct.c_void_p(dummy.data_ptr()), 0, 3,
+                                 ct.c_void_p(C.data_ptr()), 4, wp, nbytes, None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    c = C.cpu().numpy()   # c[j, i] = row i of column j
+    assert np.all(c[:, :2] == 0.0) and np.all(c[:, 2:] == 7.0)
+
+
+def test_tc_gram_wait_timeout_gives_nan_and_recovers():
+    """A bounded mbarrier wait that runs out (a poll limit of 0: every wait gives up at once)
+    makes the result NaN and the kernel still ends normally; with the default limit the
+    next call is exact."""
+    d = dev()
+    n = 50000
+    V = np.stack([inputs.x_true(60 + i, n) for i in range(16)], axis=1)
+    Y = np.stack([inputs.x_true(70 + j, n) for j in range(4)], axis=1)
+    Vd, Yd = panel(V, d), panel(Y, d)
+    try:
+        pkg.set_tc_wait_limit(0)
+        C = pkg.sstep_gram_tc(Vd, Yd)
+        torch.cuda.synchronize()
+        bad = C.cpu().numpy()
+    finally:
+        pkg.set_tc_wait_limit(-1)
+    assert np.all(np.isnan(bad))
+    C = pkg.sstep_gram_tc(Vd, Yd)
+    torch.cuda.synchronize()
+    check(V, Y, C.cpu().numpy())
