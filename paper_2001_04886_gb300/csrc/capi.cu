@@ -311,7 +311,7 @@ int make_desc(StencilDesc& A, int dim, const int64_t shape[3]) {
 
 // Device workspace of one solve. Small arrays first, then the columns.
 struct Layout {
-    size_t state, L, T, S, G, R, gc, gs, g, y, hist, C, a, theta, counter, bnd, partials, cols;
+    size_t state, L, T, S, G, R, gc, gs, g, y, hist, C, a, theta, counter, bnd, ozacc, partials, cols;
     size_t total;
 };
 
@@ -340,6 +340,7 @@ Layout plan(int64_t n, int ncols, int m, int hist_cap, size_t elem_bytes = sizeo
     l.theta = take(sizeof(double) * kMaxS);
     l.counter = take(kAlign);
     l.bnd = take(sizeof(unsigned) * kBndSlots);
+    l.ozacc = take(sizeof(unsigned long long) * kOzAccWords);
     l.partials = take(sizeof(double) * (size_t)max_partials_doubles());
     l.cols = take(elem_bytes * (size_t)col_ld(n) * ncols);
     l.total = off;
@@ -1012,8 +1013,10 @@ int sstep_gram_tc(int64_t n, const double* V, int64_t ldv, int ka, const double*
         return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * ka, kb, st) == cudaSuccess ? SSTEP_OK
                                                                                                        : SSTEP_ERR_CUDA;
     Scratch sc{(double*)((char*)work + kAlign), (unsigned*)work};
+    sc.acc = (unsigned long long*)sc.partials;   // the exact accumulators, in the partials area
     unsigned* bnd = (unsigned*)((char*)work + kAlign + sizeof(double) * (size_t)max_partials_doubles());
     CUDA_TRY(cudaMemsetAsync(work, 0, kAlign, st));
+    CUDA_TRY(cudaMemsetAsync(sc.acc, 0, sizeof(unsigned long long) * kOzAccWords, st));
     CUDA_TRY(cudaMemsetAsync(bnd, 0, kGramBndBytes, st));
     launch_colmax(n, V, ldv, ka, bnd, st);
     launch_colmax(n, Y, ldy, kb, bnd + ka, st);
@@ -1124,6 +1127,10 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     const bool tcg = !pre && tc_gram_enabled();
     unsigned* bnd = (unsigned*)(M->ws + l.bnd);
     auto pbnd = [&](int k) { return tcg ? bnd + (m + 1) + k * (s + 1) : nullptr; };
+    if (tcg) {   // the exact accumulators start at zero; every launch leaves them at zero
+        sc.acc = (unsigned long long*)(M->ws + l.ozacc);
+        CUDA_TRY(cudaMemsetAsync(sc.acc, 0, sizeof(unsigned long long) * kOzAccWords, stream_));
+    }
     std::vector<double> theta(s, 0.0);   // Newton shifts (zero: monomial powers)
     bool shifted = false;
     M->shifts.clear();

@@ -14,7 +14,7 @@ constexpr int kGramKA = 8;             // V columns per Gram CTA (grid.y splits 
 constexpr int kMaxNV = kGramKA * (kMaxS + 1);   // largest per-CTA partial vector
 
 int fp64_gram_partials_doubles() { return kMaxCtas * kMaxNV; }
-int max_partials_doubles() { return std::max(kMaxCtas * kMaxNV, oz_partials_doubles()); }
+int max_partials_doubles() { return std::max(std::max(kMaxCtas * kMaxNV, oz_partials_doubles()), kOzAccWords); }
 
 // ================================================================== stencil sweep
 __device__ __forceinline__ void grid_xyz(const StencilDesc& A, int64_t p, int& x, int& y, int& z) {

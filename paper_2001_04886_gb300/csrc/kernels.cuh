@@ -41,8 +41,11 @@ struct Epi {
 
 struct Scratch {
     double* partials;        // per-CTA partial results
-    unsigned* counter;       // arrival counter (zero between launches)
+    unsigned* counter;       // arrival counter (zero between launches); [1]: error flag
+    unsigned long long* acc = nullptr;   // exact 128-bit sums of the tensor-core Gram pass
+                                         // (kOzAccWords words, zero between launches)
 };
+constexpr int kOzAccWords = 2 * SSTEP_MAX_COLS * (SSTEP_MAX_S + 1);
 
 __device__ __forceinline__ bool gate_open(const SolverState* st, int gate) {
     if (gate == GATE_NONE) return true;
@@ -84,13 +87,13 @@ void launch_update(int64_t n, const double* V, int64_t ldv, int ka, const double
 // the tensor cores and rounded once; vmax[ka] / ymax[kb] are the column bounds (largest high
 // word of |x| per column, launch_colmax or the producing kernel). Returns false, launching
 // nothing, for shapes it does not take (ka > 64, kb > 9, n > 2^27, V or Y not 8-byte
-// aligned). A bounded wait that runs out gives NaN entries.
+// aligned, no Scratch::acc). A bounded wait that runs out gives NaN entries.
 bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, const double* Y,
                     int64_t ldy, int kb, const unsigned* ymax, Scratch sc, const Epi& epi, int gate,
                     cudaStream_t stream);
 // out[c] = column bound of column c (out must be zeroed first)
 void launch_colmax(int64_t n, const double* X, int64_t ld, int ncols, unsigned* out, cudaStream_t stream);
-int oz_partials_doubles();      // per-CTA partials of the tensor-core Gram pass, all CTAs
+int oz_partials_doubles();      // per-CTA partials of the tensor-core Gram pass (none: sums go to Scratch::acc)
 int device_sms();               // multiprocessors of the current device
 extern long g_oz_spin;          // mbarrier poll limit of the tensor-core Gram pass
 

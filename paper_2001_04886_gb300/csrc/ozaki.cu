@@ -1,22 +1,26 @@
 // The Gram pass C = V^T Y of the s-step block on the tensor cores (tcgen05), exact in
 // fixed point (ozaki.cuh has the arithmetic and its error bound).
 //
-// One CTA owns a contiguous range of rows and walks it in stages of 64 rows. Every thread
-// loads the FP64 entries of its (column, row pair) items straight from global memory into
-// registers (the next stage's loads are issued before the current stage is split), turns
-// each entry into its 8 balanced digits, and stores them as FP16 pairs in shared memory in
-// the K-major no-swizzle layout of the MMA operands (K = the rows): A holds the digits of
-// the V columns (M = digit x column, two 128-row tiles per 32 columns: digits 0-3 and
-// 4-7), B those of the Y columns (N = digit x column, 80 rows). One thread issues
-// tcgen05.mma.kind::f16 (FP16 x FP16 -> FP32 in tensor memory) for the kept digit pairs
-// and commits to the stage's mbarrier; the shared-memory stage is double buffered.
-// After at most 1024 rows (16 stages), while every FP32 sum in tensor memory is still an
-// exact integer, the warps drain the accumulators into 128-bit integers in registers.
-// At the end of its range the CTA publishes its exact integer partial sums; the last CTA
-// to arrive adds them in CTA order (exact, so the result does not depend on the grid) and
-// rounds each entry to FP64 once, then runs the solver epilogue like the FP64 kernel.
-// Every mbarrier wait is bounded: a wait that runs out marks the result NaN (the solver
-// then stops on its NaN checks) and the kernel still frees its tensor memory.
+// One CTA per SM owns a contiguous range of rows and walks it in stages (128 rows, or 64
+// when V has more than 32 columns). The split warps load the FP64 entries of their
+// (column, row pair) items straight from global memory into registers (the next stage's
+// loads are issued before the current stage is split), turn each entry into its 8
+// balanced digits and store them as FP16 pairs in shared memory in the K-major no-swizzle
+// layout of the MMA operands (K = the rows): A holds the digits of the V columns (M =
+// digit x column, two 128-row tiles per 32 columns: digits 0-3 and 4-7), B those of the Y
+// columns (N = digit x column, 80 rows). A dedicated MMA warp waits for a stage to be full
+// (an mbarrier every split warp arrives on), issues tcgen05.mma.kind::f16 (FP16 x FP16 ->
+// FP32 in tensor memory) for the kept digit pairs and commits to the stage's empty
+// barrier; shared-memory stages and tensor-memory accumulators are both double buffered,
+// so no CTA-wide barrier sits in the loop. After at most 1024 rows, while every FP32 sum
+// is still an exact integer, the split warps drain the accumulators into 128-bit integers
+// (while the MMAs of the next chunk run into the other accumulator buffer). At the end the
+// CTA adds its exact partial sums into a 128-bit accumulator per entry with 64-bit
+// atomicAdds (carry handled: integer addition is exact and order-free, so the result does
+// not depend on the grid), and the last CTA to arrive rounds each entry to FP64 once and
+// runs the solver epilogue like the FP64 kernel. Every mbarrier wait is bounded: a wait
+// that runs out marks the result NaN (the solver then stops on its checks) and the kernel
+// still waits for its tensor-core work in flight and frees its tensor memory.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -27,29 +31,59 @@
 namespace sstep {
 namespace {
 
-constexpr int kOzThreads = 256;
-constexpr int kOzWarps = kOzThreads / 32;
-constexpr int kStageRows = 64;                       // rows per stage (K of 4 MMAs)
-constexpr int kTileBytes = 128 * kStageRows * 2;     // one A tile: 128 rows x 64 K x FP16
 constexpr int kBRows = 80;                           // B rows: 8 digits x up to 9 columns, padded
-constexpr int kBBytes = kBRows * kStageRows * 2;     // B: 80 rows x 64 K x FP16
 constexpr int kN0 = 80, kN1 = 48;                    // MMA N of the digit-0..3 and digit-4..7 tiles
 constexpr int kGroupCols = kN0 + kN1;                // tensor-memory columns per 32 V columns
-constexpr int kStagesPerChunk = oz::kChunkRows / kStageRows;
 constexpr long kOzSpin = 1L << 24;                   // bounded mbarrier polls
+
+// Shapes of one instantiation: G groups of 32 V columns.
+// (14 split warps + the MMA warp: at most 4 warps per SM sub-partition, so 128 registers
+// per thread; a stage of 112 rows is 7 MMA K-steps and 9 stages make a chunk of 1008 rows.)
+template <int G>
+struct OzCfg {
+    static constexpr int kSplitWarps = G == 1 ? 14 : 8;
+    static constexpr int kThreads = (kSplitWarps + 1) * 32;   // + the MMA warp
+    static constexpr int kRows = 8 * kSplitWarps;             // rows per stage (one K group per split warp)
+    static constexpr int kSbo = kRows * 16;                   // bytes between 8-row groups of an operand
+    static constexpr int kTile = 128 * kRows * 2;             // one A tile (FP16)
+    static constexpr int kB = kBRows * kRows * 2;             // B
+    static constexpr int kStage = 2 * G * kTile + kB;
+    static constexpr int kSmem = 2 * kStage;                  // two stages
+    static constexpr int kStagesPerChunk = oz::kChunkRows / kRows;
+    static constexpr int kBuf = G * kGroupCols;               // accumulator columns per buffer
+    static constexpr uint32_t kCols = 2 * kBuf <= 256 ? 256u : 512u;
+    static_assert(kRows % 16 == 0 && kStagesPerChunk * kRows <= oz::kChunkRows, "stage shape");
+};
+constexpr int kDrainWarps = 8;   // split warps 0..7 drain: TMEM lane quarter warp % 4, tile warp / 4
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+
 // byte offset of element (row m, k) of a K-major operand: 8-row x 16-byte core matrices,
-// 128 B between K-adjacent and 1024 B between row-adjacent core matrices
+// 128 B between K-adjacent and SBO bytes between row-adjacent core matrices
+template <int SBO>
 __device__ __forceinline__ uint32_t op_off(int m, int k) {
-    return (uint32_t)((m >> 3) * 1024 + (k >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2);
+    return (uint32_t)((m >> 3) * SBO + (k >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2);
 }
 
-// shared-memory matrix descriptor (no swizzle, LBO 128 B, SBO 1024 B)
+// shared-memory matrix descriptor (no swizzle, LBO 128 B)
+template <int SBO>
 __device__ __forceinline__ uint64_t op_desc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
            ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count));
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_addr(b)) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(b))
+                 : "memory");
 }
 
 // instruction descriptor: FP16 x FP16 -> FP32, K-major A and B, M = 128, N = n
@@ -118,18 +152,19 @@ __global__ void __launch_bounds__(kThreads) colmax_kernel(int64_t n, const doubl
 }  // namespace
 }  // namespace sstep
 
+
 namespace sstep {
 namespace {
 
-// The digit-pair sums of one drained tile: TMEM lane (warp quarter q, lane) is the V
-// digit ta of column a; its columns are (tb, b), b fastest. Each exact FP32 integer S is
-// added into acc[b] with weight 256^(kCut - tb); the thread's contribution is acc >> 8 ta
-// (every kept term has kCut - tb >= ta, so the shift is exact).
+// The digit-pair sums of one drained tile: TMEM lane (warp quarter, lane) is the V digit
+// ta of column a; its columns are (tb, b), b fastest, read 16 at a time. Each exact FP32
+// integer S is added into acc[b] with weight 256^(kCut - tb); the thread's contribution is
+// acc >> 8 ta (every kept term has kCut - tb >= ta, so that shift is exact).
 template <int KB, int NC>
 __device__ __forceinline__ void drain_tile(uint32_t taddr, int ta, oz::i128 (&acc)[KB]) {
 #pragma unroll
     for (int c0 = 0; c0 < NC; c0 += 16) {
-        if (c0 >= (oz::kCut + 1 - ta) * KB) break;   // warp-uniform: the rest are dropped pairs
+        if (c0 >= (oz::kCut + 1 - ta) * KB) break;       // warp-uniform: the rest are dropped pairs
         uint32_t r[16];
         tmem_ld<16>(taddr + (uint32_t)c0, r);
 #pragma unroll
@@ -144,101 +179,155 @@ __device__ __forceinline__ void drain_tile(uint32_t taddr, int ta, oz::i128 (&ac
 }
 
 template <int G, int KB>
-__global__ void __launch_bounds__(kOzThreads, G == 1 ? 2 : 1)
+__global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
     gram_oz_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int ka, const unsigned* __restrict__ vmax,
                    const double* __restrict__ Y, int64_t ldy, const unsigned* __restrict__ ymax, Scratch sc, Epi epi,
                    int gate, long spin) {
-    constexpr int kStageBytes = 2 * G * kTileBytes + kBBytes;
-    constexpr uint32_t kCols = G == 1 ? 128u : 256u;   // kGroupCols accumulator columns per 32 V columns
-    constexpr int kItems = 4 * G + (KB + 7) / 8;        // column octets per warp and stage
+    using C = OzCfg<G>;
+    constexpr int kItems = 4 * G + (KB + 7) / 8;        // column octets per split warp and stage
+    constexpr int SBO = C::kSbo;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t full[2], empty[2], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int failed;
+    __shared__ volatile int failed;
+    __shared__ bool last;
     __shared__ uint32_t ex[kMaxCols + kMaxS + 1];
     __shared__ double res[kMaxCols * (kMaxS + 1)];
     if (!gate_open(epi.st, gate)) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int c = tid; c < ka + KB; c += kOzThreads) ex[c] = oz::bound_exponent(c < ka ? vmax[c] : ymax[c - ka]);
+    for (int c = tid; c < ka + KB; c += C::kThreads) ex[c] = oz::bound_exponent(c < ka ? vmax[c] : ymax[c - ka]);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
-                     "r"(kCols));
+                     "r"(C::kCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         failed = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[1])));
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&full[b], C::kSplitWarps);
+            bar_init(&empty[b], 1);
+            bar_init(&tfull[b], 1);
+            bar_init(&tempty[b], C::kSplitWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base, sbase = smem_addr(smem);
-
-    // item j of this warp: column octet j (V octets first, then Y octets), the warp's K
-    // group of 8 rows; lane: column c8 of the octet, rows kk and kk + 1 of the stage
-    const int noct_v = (ka + 7) >> 3, noct = noct_v + (KB + 7) / 8;
-    const int c8 = lane >> 2, kk = warp * 8 + (lane & 3) * 2;
-    const int64_t nst = (n + kStageRows - 1) / kStageRows;
+    const int64_t nst = (n + C::kRows - 1) / C::kRows;
     const int64_t s0 = nst * blockIdx.x / gridDim.x, s1 = nst * (blockIdx.x + 1) / gridDim.x;
-    const int h = warp >> 2, q = warp & 3, ta = 4 * h + q;   // drain role: V digit ta
+    const int64_t nstages = s1 - s0;
 
+    // drain role of split warps 0..7: TMEM lane quarter q, V digit ta
+    const int q = warp & 3, ta = 4 * ((warp >> 2) & 1) + q;
+    const bool drains = warp < kDrainWarps;
     oz::i128 acc[G][KB];
 #pragma unroll
     for (int g = 0; g < G; ++g)
 #pragma unroll
         for (int b = 0; b < KB; ++b) acc[g][b] = 0;
 
-    auto load = [&](int64_t st, double2 (&buf)[kItems]) {
-        const int64_t r = st * kStageRows + kk;
+    if (warp == C::kSplitWarps) {
+        // ---------------------------------------------------------------- MMA warp
+        if (lane == 0) {
+            int n_empty[2] = {0, 0}, n_tfull[2] = {0, 0};
+            for (int64_t gs = 0; gs < nstages && !failed; ++gs) {
+                const int sb = (int)(gs & 1);
+                const int chunk = (int)(gs / C::kStagesPerChunk), sic = (int)(gs % C::kStagesPerChunk);
+                const int tb = chunk & 1;
+                if (sic == 0 && chunk >= 2 &&   // the accumulators of chunk - 2 are drained
+                    !oz_wait(smem_addr(&tempty[tb]), (uint32_t)(((chunk >> 1) - 1) & 1), spin)) {
+                    failed = 1;
+                    break;
+                }
+                if (!oz_wait(smem_addr(&full[sb]), (uint32_t)((gs >> 1) & 1), spin)) {
+                    failed = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t so = sbase + (uint32_t)(sb * C::kStage);
+                const uint32_t dt = tmem + (uint32_t)(tb * C::kBuf);
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int ks = 0; ks < C::kRows / 16; ++ks) {
+                        const uint32_t accf = (sic > 0 || ks > 0) ? 1u : 0u;
+                        const uint32_t a0 = so + (uint32_t)(2 * g * C::kTile + ks * 256);
+                        const uint64_t db = op_desc<SBO>(so + (uint32_t)(2 * G * C::kTile + ks * 256));
+                        mma_f16(dt + (uint32_t)(g * kGroupCols), op_desc<SBO>(a0), db, oz_idesc(kN0), accf);
+                        mma_f16(dt + (uint32_t)(g * kGroupCols + kN0), op_desc<SBO>(a0 + C::kTile), db, oz_idesc(kN1),
+                                accf);
+                    }
+                mma_commit(&empty[sb]);
+                ++n_empty[sb];
+                if (sic == C::kStagesPerChunk - 1 || gs == nstages - 1) {
+                    mma_commit(&tfull[tb]);
+                    ++n_tfull[tb];
+                }
+            }
+            // every commit has landed before the CTA leaves (no arrive is left pending)
+            for (int b = 0; b < 2; ++b) {
+                if (n_empty[b]) oz_wait(smem_addr(&empty[b]), (uint32_t)((n_empty[b] - 1) & 1), kOzSpin);
+                if (n_tfull[b]) oz_wait(smem_addr(&tfull[b]), (uint32_t)((n_tfull[b] - 1) & 1), kOzSpin);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------------- split warps
+        // item j: column octet j (V octets first, then Y octets) of this warp's K group of 8
+        // rows; lane: column c8 of the octet, rows kk and kk + 1 of the stage
+        const int noct_v = (ka + 7) >> 3, noct = noct_v + (KB + 7) / 8;
+        const int c8 = lane >> 2, kk = warp * 8 + (lane & 3) * 2;
+        const double* cp[kItems];
+        uint32_t ce[kItems];
+        int cc[kItems];
+        bool cv[kItems];
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
-            buf[j] = make_double2(0.0, 0.0);
-            if (j < noct) {
-                const bool isv = j < noct_v;
-                const int c = isv ? j * 8 + c8 : (j - noct_v) * 8 + c8;
-                if (c < (isv ? ka : KB)) {
-                    const double* col = isv ? V + (int64_t)c * ldv : Y + (int64_t)c * ldy;
+            const bool isv = j < noct_v;
+            const int c = isv ? j * 8 + c8 : (j - noct_v) * 8 + c8;
+            cv[j] = j < noct && c < (isv ? ka : KB);
+            cc[j] = c;
+            cp[j] = cv[j] ? (isv ? V + (int64_t)c * ldv : Y + (int64_t)c * ldy) : nullptr;
+            ce[j] = cv[j] ? ex[isv ? c : ka + c] : 0u;
+        }
+        auto load = [&](int64_t st, double2 (&buf)[kItems]) {
+            const int64_t r = (s0 + st) * C::kRows + kk;
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) {
+                buf[j] = make_double2(0.0, 0.0);
+                if (cv[j]) {
+                    const double* p = cp[j] + r;
                     if (r + 1 < n) {
-                        if (((uintptr_t)(col + r) & 15) == 0) buf[j] = __ldg(reinterpret_cast<const double2*>(col + r));
-                        else buf[j] = make_double2(__ldg(col + r), __ldg(col + r + 1));
+                        if (((uintptr_t)p & 15) == 0) buf[j] = __ldg(reinterpret_cast<const double2*>(p));
+                        else buf[j] = make_double2(__ldg(p), __ldg(p + 1));
                     } else if (r < n) {
-                        buf[j].x = __ldg(col + r);
+                        buf[j].x = __ldg(p);
                     }
                 }
             }
-        }
-    };
-
-    int64_t last_commit[2] = {-1, -1};
-    bool ok = true;
-    double2 cur[kItems];
-    if (s0 < s1) load(s0, cur);
-    for (int64_t st = s0; st < s1; ++st) {
-        const int64_t gs = st - s0;
-        const int sb = (int)(gs & 1);
-        double2 nxt[kItems];
-        if (st + 1 < s1) load(st + 1, nxt);
-        if (gs >= 2) {   // the MMAs of stage gs - 2 read this buffer
-            if (!oz_wait(smem_addr(&bars[sb]), (uint32_t)(((gs - 2) >> 1) & 1), spin)) failed = 1;
-            __syncthreads();
-            if (failed) {
-                ok = false;
+        };
+        double2 cur[kItems];
+        if (nstages > 0) load(0, cur);
+        for (int64_t gs = 0; gs < nstages; ++gs) {
+            if (failed) break;
+            double2 nxt[kItems];
+            if (gs + 1 < nstages) load(gs + 1, nxt);
+            const int sb = (int)(gs & 1);
+            if (gs >= 2 && !oz_wait(smem_addr(&empty[sb]), (uint32_t)(((gs >> 1) - 1) & 1), spin)) {
+                failed = 1;
                 break;
             }
-        }
-        unsigned char* sp = smem + sb * kStageBytes;
+            unsigned char* sp = smem + sb * C::kStage;
 #pragma unroll
-        for (int j = 0; j < kItems; ++j) {
-            if (j < noct) {
-                const bool isv = j < noct_v;
-                const int c = isv ? j * 8 + c8 : (j - noct_v) * 8 + c8;
-                if (c < (isv ? ka : KB)) {
-                    const uint32_t e = ex[isv ? c : ka + c];
-                    const uint64_t b0 = (uint64_t)__double_as_longlong(cur[j].x), b1 = (uint64_t)__double_as_longlong(cur[j].y);
-                    const uint64_t w0 = oz::fixed_biased((uint32_t)b0, (uint32_t)(b0 >> 32), e);
-                    const uint64_t w1 = oz::fixed_biased((uint32_t)b1, (uint32_t)(b1 >> 32), e);
+            for (int j = 0; j < kItems; ++j) {
+                if (j < noct) {   // warp-uniform
+                    const bool isv = j < noct_v;
+                    const uint64_t b0 = (uint64_t)__double_as_longlong(cur[j].x);
+                    const uint64_t b1 = (uint64_t)__double_as_longlong(cur[j].y);
+                    const uint64_t w0 = oz::fixed_biased((uint32_t)b0, (uint32_t)(b0 >> 32), ce[j]);
+                    const uint64_t w1 = oz::fixed_biased((uint32_t)b1, (uint32_t)(b1 >> 32), ce[j]);
                     uint32_t d[oz::kDigits];
                     d[0] = digit_pair<0>(w0, w1);
                     d[1] = digit_pair<1>(w0, w1);
@@ -248,98 +337,85 @@ __global__ void __launch_bounds__(kOzThreads, G == 1 ? 2 : 1)
                     d[5] = digit_pair<5>(w0, w1);
                     d[6] = digit_pair<6>(w0, w1);
                     d[7] = digit_pair<7>(w0, w1);
-                    if (isv) {
-                        unsigned char* base = sp + (c >> 5) * 2 * kTileBytes;
+                    const int c = cc[j];
+                    if (isv) {   // unused columns of an octet land in unused A rows
+                        unsigned char* base = sp + (c >> 5) * 2 * C::kTile + op_off<SBO>(c & 31, kk);
 #pragma unroll
                         for (int t = 0; t < oz::kDigits; ++t)
-                            *reinterpret_cast<uint32_t*>(base + (t >> 2) * kTileBytes + op_off((t & 3) * 32 + (c & 31), kk)) = d[t];
-                    } else {
-                        unsigned char* base = sp + 2 * G * kTileBytes;
+                            *reinterpret_cast<uint32_t*>(base + (t >> 2) * C::kTile + (t & 3) * 4 * SBO) = d[t];
+                    } else if (cv[j]) {
+                        unsigned char* base = sp + 2 * G * C::kTile;
 #pragma unroll
                         for (int t = 0; t < oz::kDigits; ++t)
-                            *reinterpret_cast<uint32_t*>(base + op_off(t * KB + c, kk)) = d[t];
+                            *reinterpret_cast<uint32_t*>(base + op_off<SBO>(t * KB + c, kk)) = d[t];
                     }
                 }
             }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        const int sic = (int)(gs % kStagesPerChunk);
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t so = sbase + (uint32_t)(sb * kStageBytes);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) bar_arrive(&full[sb]);
 #pragma unroll
-            for (int g = 0; g < G; ++g)
-#pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {
-                    const uint32_t accf = (sic > 0 || ks > 0) ? 1u : 0u;
-                    const uint32_t a0 = so + (uint32_t)(2 * g * kTileBytes + ks * 256);
-                    const uint64_t db = op_desc(so + (uint32_t)(2 * G * kTileBytes + ks * 256));
-                    mma_f16(tmem + (uint32_t)(g * kGroupCols), op_desc(a0), db, oz_idesc(kN0), accf);
-                    mma_f16(tmem + (uint32_t)(g * kGroupCols + kN0), op_desc(a0 + kTileBytes), db, oz_idesc(kN1), accf);
+            for (int j = 0; j < kItems; ++j) cur[j] = nxt[j];
+            const int sic = (int)(gs % C::kStagesPerChunk);
+            if (sic == C::kStagesPerChunk - 1 || gs == nstages - 1) {   // drain the chunk's exact sums
+                const int chunk = (int)(gs / C::kStagesPerChunk), tb = chunk & 1;
+                if (!oz_wait(smem_addr(&tfull[tb]), (uint32_t)((chunk >> 1) & 1), spin)) {
+                    failed = 1;
+                    break;
                 }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(&bars[sb])));
-        }
-        last_commit[sb] = gs;
-        if (sic == kStagesPerChunk - 1 || st + 1 == s1) {   // drain the chunk's exact sums
-            if (!oz_wait(smem_addr(&bars[sb]), (uint32_t)((gs >> 1) & 1), spin)) failed = 1;
-            __syncthreads();
-            if (failed) {
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;");
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t tb0 = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tb * C::kBuf);
+                if (drains) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * kGroupCols);
-                if (h == 0) drain_tile<KB, kN0>(taddr, ta, acc[g]);
-                else drain_tile<KB, kN1>(taddr + (uint32_t)kN0, ta, acc[g]);
+                    for (int g = 0; g < G; ++g) {
+                        if (ta < 4) drain_tile<KB, kN0>(tb0 + (uint32_t)(g * kGroupCols), ta, acc[g]);
+                        else drain_tile<KB, kN1>(tb0 + (uint32_t)(g * kGroupCols + kN0), ta, acc[g]);
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) bar_arrive(&tempty[tb]);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
         }
-#pragma unroll
-        for (int j = 0; j < kItems; ++j) cur[j] = nxt[j];
-    }
-    if (!ok) {   // a wait ran out: let the MMAs in flight finish before the tensor memory is freed
-        for (int b = 0; b < 2; ++b)
-            if (last_commit[b] >= 0) oz_wait(smem_addr(&bars[b]), (uint32_t)((last_commit[b] >> 1) & 1), kOzSpin);
-        if (tid == 0) atomicExch(sc.counter + 1, 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kCols));
+    if (failed && tid == 0) atomicExch(sc.counter + 1, 1u);
 
     // the CTA's exact partial sums: per (digit ta, column a, column b) in shared memory (the
-    // stage buffers are free), then summed over ta; published as the two 64-bit words of
-    // each 128-bit integer
-    oz::i128* part = reinterpret_cast<oz::i128*>(smem);   // [8][32 G][KB]
+    // stage buffers are free), summed over the digits, then added
+    // into the 128-bit accumulators: atomicAdd of the low words, whose old value gives the
+    // carry, then of the high words (addition of integers is exact and order-free)
+    oz::i128* part = reinterpret_cast<oz::i128*>(smem);   // [8 digits][32 G][KB]
+    if (drains)
 #pragma unroll
-    for (int g = 0; g < G; ++g)
+        for (int g = 0; g < G; ++g)
 #pragma unroll
-        for (int b = 0; b < KB; ++b) part[(ta * 32 * G + g * 32 + lane) * KB + b] = acc[g][b] >> (8 * ta);
+            for (int b = 0; b < KB; ++b) part[(ta * 32 * G + g * 32 + lane) * KB + b] = acc[g][b] >> (8 * ta);
     __syncthreads();
-    double* red = reinterpret_cast<double*>(smem + oz::kDigits * 32 * G * KB * sizeof(oz::i128));
-    for (int e = tid; e < ka * KB; e += kOzThreads) {
+    for (int e = tid; e < ka * KB; e += C::kThreads) {
         const int a = e % ka, b = e / ka;
         oz::i128 s = 0;
-        for (int t = 0; t < oz::kDigits; ++t) s += part[(t * 32 * G + a) * KB + b];
-        red[2 * e] = __longlong_as_double((long long)(uint64_t)s);
-        red[2 * e + 1] = __longlong_as_double((long long)(uint64_t)((oz::u128)s >> 64));
+        for (int k = 0; k < oz::kDigits; ++k) s += part[(k * 32 * G + a) * KB + b];
+        const unsigned long long lo = (unsigned long long)(uint64_t)s;
+        const unsigned long long hi = (unsigned long long)(uint64_t)((oz::u128)s >> 64);
+        const unsigned long long old = atomicAdd(sc.acc + 2 * e, lo);
+        atomicAdd(sc.acc + 2 * e + 1, hi + ((old + lo < old) ? 1ull : 0ull));
     }
+    __threadfence();
     __syncthreads();
-    if (!publish_partial(red, 2 * ka * KB, sc.partials, sc.counter)) return;
-    // last CTA: exact sums over the CTAs in order, one rounding per entry
+    if (tid == 0) last = atomicAdd(sc.counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // last CTA: one rounding per entry, then the accumulators go back to zero for the next launch
     const bool err = ((volatile unsigned*)sc.counter)[1] != 0u;
-    const int nctas = gridDim.x;
-    for (int e = tid; e < ka * KB; e += kOzThreads) {
-        oz::i128 s = 0;
-        for (int bx = 0; bx < nctas; ++bx) {
-            const double* p = sc.partials + (int64_t)bx * (2 * ka * KB) + 2 * e;
-            const uint64_t lo = (uint64_t)__double_as_longlong(ld_cg(p)), hi = (uint64_t)__double_as_longlong(ld_cg(p + 1));
-            s += (oz::i128)(((oz::u128)hi << 64) | (oz::u128)lo);
-        }
+    for (int e = tid; e < ka * KB; e += C::kThreads) {
+        const uint64_t lo = __ldcg(sc.acc + 2 * e), hi = __ldcg(sc.acc + 2 * e + 1);
+        sc.acc[2 * e] = 0ull;
+        sc.acc[2 * e + 1] = 0ull;
+        const oz::i128 s = (oz::i128)(((oz::u128)hi << 64) | (oz::u128)lo);
         const uint32_t ea = ex[e % ka], eb = ex[ka + e / ka];
         res[e] = (err || ea == oz::kNonFinite || eb == oz::kNonFinite) ? __longlong_as_double(0x7FF8000000000000ll)
                                                                        : oz::i128_to_double(s, oz::gram_scale_exp(ea, eb));
@@ -353,9 +429,6 @@ __global__ void __launch_bounds__(kOzThreads, G == 1 ? 2 : 1)
 }
 
 }  // namespace
-}  // namespace sstep
-
-namespace sstep {
 
 int device_sms() {
     static int cached[64] = {0};
@@ -376,8 +449,8 @@ int device_sms() {
     return cached[dev];
 }
 
-// one CTA per SM with ka <= 64 or two with ka <= 32: at most 2 SMs x 2 x 32 x 9 doubles
-int oz_partials_doubles() { return 2 * device_sms() * 2 * 32 * (kMaxS + 1); }
+// the tensor-core Gram pass keeps no per-CTA partials (its exact sums go to Scratch::acc)
+int oz_partials_doubles() { return 0; }
 
 void launch_colmax(int64_t n, const double* X, int64_t ld, int ncols, unsigned* out, cudaStream_t stream) {
     if (n <= 0 || ncols <= 0) return;
@@ -389,18 +462,19 @@ namespace {
 template <int G, int KB>
 void launch_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, const double* Y, int64_t ldy,
                const unsigned* ymax, Scratch sc, const Epi& epi, int gate, cudaStream_t stream, long spin) {
-    constexpr int kSmem = 2 * (2 * G * kTileBytes + kBBytes);
+    using C = OzCfg<G>;
     static bool attr[64] = {false};   // once per device
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !attr[dev]) {
-        cudaFuncSetAttribute(gram_oz_kernel<G, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        cudaFuncSetAttribute(gram_oz_kernel<G, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
         if (dev >= 0 && dev < 64) attr[dev] = true;
     }
-    const int64_t nst = (n + kStageRows - 1) / kStageRows;
-    int grid = (G == 1 ? 2 : 1) * device_sms();
+    const int64_t nst = (n + C::kRows - 1) / C::kRows;
+    int grid = device_sms();
     if (grid > nst) grid = (int)std::max<int64_t>(nst, 1);
-    gram_oz_kernel<G, KB><<<grid, kOzThreads, kSmem, stream>>>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, spin);
+    gram_oz_kernel<G, KB><<<grid, C::kThreads, C::kSmem, stream>>>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate,
+                                                                    spin);
 }
 }  // namespace
 
@@ -409,7 +483,7 @@ long g_oz_spin = kOzSpin;
 bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, const double* Y,
                     int64_t ldy, int kb, const unsigned* ymax, Scratch sc, const Epi& epi, int gate,
                     cudaStream_t stream) {
-    if (ka < 1 || ka > kMaxCols || kb < 1 || kb > kMaxS + 1 || n < 1 || n > ((int64_t)1 << 27)) return false;
+    if (ka < 1 || ka > kMaxCols || kb < 1 || kb > kMaxS + 1 || n < 1 || n > ((int64_t)1 << 27) || !sc.acc) return false;
     if (((uintptr_t)V & 7) || ((uintptr_t)Y & 7)) return false;
     const bool one = ka <= 32;
     switch (kb) {
