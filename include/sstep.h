@@ -187,6 +187,18 @@ int sstep_gram_noalloc(int64_t n, const double* V, int64_t ldv, int ka, const do
 int sstep_block_update(int64_t n, const double* V, int64_t ldv, int ka, double* Y, int64_t ldy, int kb,
                        const double* T, int ldt, double* Gout, void* work, size_t work_bytes, void* stream);
 
+/* The same block update on the tensor cores, as the FP64 s-step GMRES runs it: every V
+ * column in 61-bit fixed point relative to its power-of-two bound, T folded with those
+ * bounds and split the same way per column, the digit products summed exactly per digit
+ * diagonal on the tensor cores, V T rounded to FP64 once per entry and subtracted from Y
+ * in FP64; then Gout = Y^T Y by sstep_gram_tc. Error of V T per entry before its rounding:
+ * at most 2^-65 sum_a(Bv_a Bt_j) + 2^-60 sum_a(Bv_a |t_aj| + |v_a| Bt_j) in the scaled
+ * quantities (the bounds of sstep_gram_tc, for the products v_a t_aj). 0 <= ka <= 32,
+ * 1 <= kb <= SSTEP_MAX_S + 1, n <= 2^27; work as for sstep_gram(n, 1, kb). A bounded
+ * device wait that runs out leaves Y partly updated and Gout NaN. */
+int sstep_block_update_tc(int64_t n, const double* V, int64_t ldv, int ka, double* Y, int64_t ldy, int kb,
+                          const double* T, int ldt, double* Gout, void* work, size_t work_bytes, void* stream);
+
 /* ------------------------------------------------------------------ solvers */
 #define SSTEP_MAX_S 8        /* largest block size s on the GPU path */
 #define SSTEP_MAX_M 64       /* largest Krylov dimension per cycle */

@@ -59,6 +59,8 @@ SIGNATURES = {
                                    c_void_p]),
     "sstep_block_update": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
                                    c_void_p, c_void_p, c_size_t, c_void_p]),
+    "sstep_block_update_tc": (c_int, [c_int64, c_void_p, c_int64, c_int, c_void_p, c_int64, c_int, c_void_p, c_int,
+                                      c_void_p, c_void_p, c_size_t, c_void_p]),
     "sstep_gmres_solve": (c_int, [c_void_p, c_void_p, c_void_p, P(SStepParams), P(SStepResult), c_void_p]),
     "gmres_solve": (c_int, [c_void_p, c_void_p, c_void_p, P(SStepParams), P(SStepResult), c_void_p]),
     "sstep_omin_solve": (c_int, [c_void_p, c_void_p, c_void_p, P(SStepParams), P(SStepResult), c_void_p]),
@@ -317,8 +319,9 @@ def set_tc_wait_limit(limit):
     return _check("sstep_set_tc_wait_limit", lib().sstep_set_tc_wait_limit(int(limit)))
 
 
-def sstep_block_update(V, Y, T, work=None, stream=None):
-    """In place Y <- Y - V T; returns G = Y^T Y of the updated Y."""
+def sstep_block_update(V, Y, T, work=None, stream=None, tc=False):
+    """In place Y <- Y - V T; returns G = Y^T Y of the updated Y (tc: on the tensor cores,
+    sstep_block_update_tc)."""
     import torch
 
     n, kb, ldy = _col_major(Y, "Y")
@@ -336,9 +339,9 @@ def sstep_block_update(V, Y, T, work=None, stream=None):
     nbytes = sstep_gram_workspace_size(max(n, 1), 1, kb)
     if work is None:
         work = _workspace(nbytes, Y.device)
-    _check("sstep_block_update", lib().sstep_block_update(n, vp, ldv, ka, _ptr(Y), ldy, kb, tp, ldt,
-                                                          c_void_p(G.data_ptr()), _aligned_ptr(work), nbytes,
-                                                          _stream(stream)))
+    name = "sstep_block_update_tc" if tc else "sstep_block_update"
+    _check(name, getattr(lib(), name)(n, vp, ldv, ka, _ptr(Y), ldy, kb, tp, ldt, c_void_p(G.data_ptr()),
+                                      _aligned_ptr(work), nbytes, _stream(stream)))
     return G.t()
 
 

@@ -36,9 +36,9 @@ struct sstep_matrix_s {
 namespace {
 
 constexpr size_t kAlign = 256;
-// column bounds of the tensor-core Gram pass: m + 1 basis columns, then s + 1 power
-// columns per block (m + 1 + (m / s)(s + 1) <= 3 SSTEP_MAX_M + 1)
-constexpr int kBndSlots = 4 * SSTEP_MAX_M;
+// column bounds of the tensor-core passes: m + 1 basis columns, then s + 1 power columns
+// per block, then s + 1 updated columns per block (m + 1 + 2 (m / s)(s + 1) <= 5 SSTEP_MAX_M + 1)
+constexpr int kBndSlots = 8 * SSTEP_MAX_M;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 inline int64_t col_ld(int64_t n) { return (n + 31) / 32 * 32; }   // 256-byte aligned columns
 
@@ -1076,6 +1076,39 @@ int sstep_block_update(int64_t n, const double* V, int64_t ldv, int ka, double* 
     return check_launch();
 }
 
+int sstep_block_update_tc(int64_t n, const double* V, int64_t ldv, int ka, double* Y, int64_t ldy, int kb,
+                          const double* T, int ldt, double* Gout, void* work, size_t work_bytes, void* stream) {
+    size_t need = 0;
+    if (sstep_gram_workspace_size(n, 1, kb, &need)) return SSTEP_ERR_ARG;
+    if (ka < 0 || ka > 32 || !Y || !Gout || !work || work_bytes < need || ldy < n) return SSTEP_ERR_ARG;
+    if (ka > 0 && (!V || !T || ldv < n || ldt < ka)) return SSTEP_ERR_ARG;
+    if (((uintptr_t)work) % kAlign || n > ((int64_t)1 << 27) || ((uintptr_t)Y & 7)) return SSTEP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) return cudaMemsetAsync(Gout, 0, sizeof(double) * kb * kb, st) == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA;
+    Scratch sc{(double*)((char*)work + kAlign), (unsigned*)work};
+    sc.acc = (unsigned long long*)sc.partials;
+    unsigned* bnd = (unsigned*)((char*)work + kAlign + sizeof(double) * (size_t)max_partials_doubles());
+    unsigned* vb = bnd;          // ka bounds of V
+    unsigned* yb = bnd + 32;     // kb bounds of the updated Y
+    CUDA_TRY(cudaMemsetAsync(work, 0, kAlign, st));
+    CUDA_TRY(cudaMemsetAsync(sc.acc, 0, sizeof(unsigned long long) * kOzAccWords, st));
+    CUDA_TRY(cudaMemsetAsync(bnd, 0, kGramBndBytes, st));
+    if (ka > 0) {
+        launch_colmax(n, V, ldv, ka, vb, st);
+        if (!launch_update_oz(n, V, ldv, ka, vb, Y, ldy, 0, kb, T, ldt, yb, nullptr, 0, nullptr, nullptr, nullptr,
+                              GATE_NONE, st, (unsigned*)work + 1))
+            return SSTEP_ERR_ARG;
+    } else {
+        launch_colmax(n, Y, ldy, kb, yb, st);
+    }
+    Epi e;
+    e.mode = EPI_NONE;
+    e.out = Gout;
+    e.ldo = kb;
+    if (!launch_gram_oz(n, Y, ldy, kb, yb, Y, ldy, kb, yb, sc, e, GATE_NONE, st)) return SSTEP_ERR_ARG;
+    return check_launch();
+}
+
 // ------------------------------------------------------------------ s-step GMRES (Alg. 4.1 / 4.2)
 int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_params* p, sstep_result* res,
                       void* stream) {
@@ -1127,6 +1160,7 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     const bool tcg = !pre && tc_gram_enabled();
     unsigned* bnd = (unsigned*)(M->ws + l.bnd);
     auto pbnd = [&](int k) { return tcg ? bnd + (m + 1) + k * (s + 1) : nullptr; };
+    auto ubnd = [&](int k) { return tcg ? bnd + (m + 1) + (nb + k) * (s + 1) : nullptr; };
     if (tcg) {   // the exact accumulators start at zero; every launch leaves them at zero
         sc.acc = (unsigned long long*)(M->ws + l.ozacc);
         CUDA_TRY(cudaMemsetAsync(sc.acc, 0, sizeof(unsigned long long) * kOzAccWords, stream_));
@@ -1143,15 +1177,20 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
         for (int k = 0; k < nb; ++k) {
             const int o = k * s;
             unsigned* pb = pbnd(k);
+            unsigned* ub = ubnd(k);
+            // bounds: the copy v_k^1 -> bnd[o] and pb[0]; power j -> pb[j]; in the first block
+            // the powers 1..s-1 are final basis columns as they stand -> bnd[o + j] too
+            auto fin = [&](int j) { return (tcg && k == 0 && j < s) ? bnd + o + j : nullptr; };
             // Alg. 4.1 step 3: v_k^1 = u / ||u|| and its s scaled powers
             if (!pre) {
                 TRACED(K_STENCIL, stream_, launch_stencil(M->A, uraw, sigma, U + (o + 1) * ld, 1.0, U + o * ld,
                                                           &st->vscale, st, GATE_BUILDING, stream_, theta[0], nullptr,
-                                                          tcg ? pb + 1 : nullptr, tcg ? bnd + o : nullptr));
+                                                          tcg ? pb + 1 : nullptr, tcg ? bnd + o : nullptr, fin(1),
+                                                          tcg ? pb : nullptr));
                 for (int j = 2; j <= s; ++j)
                     TRACED(K_STENCIL, stream_, launch_stencil(M->A, U + (o + j - 1) * ld, sigma, U + (o + j) * ld, 0.0,
                                                               nullptr, nullptr, st, GATE_BUILDING, stream_, theta[j - 1],
-                                                              nullptr, tcg ? pb + j : nullptr));
+                                                              nullptr, tcg ? pb + j : nullptr, nullptr, fin(j)));
             } else {   // right preconditioning: y^{j+1} = sigma (A M^-1 y^j - theta_j y^j)
                 launch_scale_copy(uraw, U + o * ld, n, &st->vscale, st, GATE_BUILDING, stream_);
                 for (int j = 1; j <= s; ++j) {
@@ -1177,8 +1216,27 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
             e.st = st;
             e.mode = EPI_GM_W;
             e.o = o;
-            TRACED(K_UPDATE, stream_, launch_update(n, U, ld, o, U + o * ld, ld, U + o * ld, ld, s + 1, 1, h.T, m, -1.0, true, sc, e,
-                          GATE_BUILDING, stream_, tcg ? bnd + o + 1 : nullptr, s));
+            bool done = false;
+            if (tcg) {   // tensor cores: projection (k > 0), then the Gram pass of the s + 1 columns
+                bool proj = k == 0;
+                if (k > 0)
+                    TRACED(K_UPDATE, stream_,
+                           proj = launch_update_oz(n, U, ld, o, bnd, U + o * ld, ld, 1, s, h.T, m, ub + 1, bnd + o + 1,
+                                                   s - 1, pb, ub, st, GATE_BUILDING, stream_));
+                unsigned* yb = k > 0 ? ub : pb;
+                if (proj)
+                    TRACED(K_UPDATE, stream_,
+                           done = launch_gram_oz(n, U + o * ld, ld, s + 1, yb, U + o * ld, ld, s + 1, yb, sc, e,
+                                                 GATE_BUILDING, stream_));
+                if (proj && !done)   // projected on the tensor cores; Gram in FP64
+                    TRACED(K_UPDATE, stream_, launch_update(n, U, ld, 0, U + o * ld, ld, U + o * ld, ld, s + 1, 1, h.T, m,
+                                                            -1.0, true, sc, e, GATE_BUILDING, stream_));
+                done = done || proj;
+            }
+            if (!done)
+                TRACED(K_UPDATE, stream_, launch_update(n, U, ld, o, U + o * ld, ld, U + o * ld, ld, s + 1, 1, h.T, m, -1.0,
+                                                        true, sc, e, GATE_BUILDING, stream_, tcg ? bnd + o + 1 : nullptr,
+                                                        s));
             // step 2: the next start vector u = z - V_k S and its norm; G, Givens
             e = Epi();
             e.st = st;

@@ -33,14 +33,21 @@ __device__ __forceinline__ unsigned abs_hi(double v) {
 
 // warp maximum of the bounds, one atomicMax per warp and column (every lane of the warp
 // must reach this call)
-__device__ __forceinline__ void publish_bounds(unsigned ym, unsigned* ybnd, unsigned wm, unsigned* wbnd) {
-    if (ybnd) {
+__device__ __forceinline__ void publish_bounds(unsigned ym, unsigned* ybnd, unsigned wm, unsigned* wbnd,
+                                               unsigned* ybnd2 = nullptr, unsigned* wbnd2 = nullptr) {
+    if (ybnd || ybnd2) {
         ym = __reduce_max_sync(0xffffffffu, ym);
-        if ((threadIdx.x & 31) == 0 && ym) atomicMax(ybnd, ym);
+        if ((threadIdx.x & 31) == 0 && ym) {
+            if (ybnd) atomicMax(ybnd, ym);
+            if (ybnd2) atomicMax(ybnd2, ym);
+        }
     }
-    if (wbnd) {
+    if (wbnd || wbnd2) {
         wm = __reduce_max_sync(0xffffffffu, wm);
-        if ((threadIdx.x & 31) == 0 && wm) atomicMax(wbnd, wm);
+        if ((threadIdx.x & 31) == 0 && wm) {
+            if (wbnd) atomicMax(wbnd, wm);
+            if (wbnd2) atomicMax(wbnd2, wm);
+        }
     }
 }
 
@@ -54,7 +61,8 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
                                                            double* __restrict__ w, const double* dscale,
                                                            const SolverState* st, int gate, int zchunk,
                                                            double shift, const double* __restrict__ u,
-                                                           unsigned* ybnd, unsigned* wbnd) {
+                                                           unsigned* ybnd, unsigned* wbnd, unsigned* ybnd2,
+                                                           unsigned* wbnd2) {
     if (!gate_open(st, gate)) return;
     if (dscale) {
         const double d = *dscale;
@@ -115,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) stencil_kernel(StencilDesc A, const 
         vc = vp;
     }
     }
-    publish_bounds(ym, ybnd, wm, wbnd);
+    publish_bounds(ym, ybnd, wm, wbnd, ybnd2, wbnd2);
 }
 
 // The common case of the powers: constant coefficients and no separate shift vector.
@@ -135,7 +143,8 @@ __global__ void __launch_bounds__(kThreads) stencil_const_kernel(int nx, int ny,
                                                                  double* __restrict__ y, double fw,
                                                                  double* __restrict__ w, const double* dscale,
                                                                  const SolverState* st, int gate, int zchunk,
-                                                                 unsigned* ybnd, unsigned* wbnd) {
+                                                                 unsigned* ybnd, unsigned* wbnd, unsigned* ybnd2,
+                                                                 unsigned* wbnd2) {
     if (!gate_open(st, gate)) return;
     __shared__ double sk[8];
     if (DSCALE) {
@@ -187,20 +196,20 @@ __global__ void __launch_bounds__(kThreads) stencil_const_kernel(int nx, int ny,
         vc = vp;
     }
     }
-    publish_bounds(ym, ybnd, wm, wbnd);
+    publish_bounds(ym, ybnd, wm, wbnd, ybnd2, wbnd2);
 }
 
 template <bool THREE, bool WCOPY, bool DSCALE>
 void launch_const(const StencilDesc& A, const ConstCoef& k, const double* v, double* y, double fw, double* w,
                   const double* dscale, const SolverState* st, int gate, int zchunk, dim3 grid, dim3 block,
-                  cudaStream_t stream, unsigned* ybnd, unsigned* wbnd) {
+                  cudaStream_t stream, unsigned* ybnd, unsigned* wbnd, unsigned* ybnd2, unsigned* wbnd2) {
     stencil_const_kernel<THREE, WCOPY, DSCALE><<<grid, block, 0, stream>>>(A.nx, A.ny, A.nz, k, v, y, fw, w, dscale,
-                                                                           st, gate, zchunk, ybnd, wbnd);
+                                                                           st, gate, zchunk, ybnd, wbnd, ybnd2, wbnd2);
 }
 
 void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y, double fw, double* w,
                     const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift,
-                    const double* u, unsigned* ybnd, unsigned* wbnd) {
+                    const double* u, unsigned* ybnd, unsigned* wbnd, unsigned* ybnd2, unsigned* wbnd2) {
     const int tiles = ((A.nx + 31) / 32) * ((A.ny + 7) / 8);
     // z chunks: about one wave of 8 CTAs per SM, at least one plane per chunk
     int chunks = kMaxCtas / tiles;
@@ -216,7 +225,7 @@ void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y,
         if (!dscale) k.c[0] = fy * (A.c[0] - shift);
         const bool three = A.dim == 3, wc = w != nullptr, ds = dscale != nullptr;
 #define SSTEP_CONST(T3, WC, DS) \
-    if (three == T3 && wc == WC && ds == DS) return launch_const<T3, WC, DS>(A, k, v, y, fw, w, dscale, st, gate, zchunk, grid, block, stream, ybnd, wbnd);
+    if (three == T3 && wc == WC && ds == DS) return launch_const<T3, WC, DS>(A, k, v, y, fw, w, dscale, st, gate, zchunk, grid, block, stream, ybnd, wbnd, ybnd2, wbnd2);
         SSTEP_CONST(true, false, false)
         SSTEP_CONST(true, true, true)
         SSTEP_CONST(true, true, false)
@@ -227,7 +236,8 @@ void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y,
         SSTEP_CONST(false, false, true)
 #undef SSTEP_CONST
     }
-    stencil_kernel<<<grid, block, 0, stream>>>(A, v, fy, y, fw, w, dscale, st, gate, zchunk, shift, u, ybnd, wbnd);
+    stencil_kernel<<<grid, block, 0, stream>>>(A, v, fy, y, fw, w, dscale, st, gate, zchunk, shift, u, ybnd, wbnd,
+                                               ybnd2, wbnd2);
 }
 
 // ================================================================== residual

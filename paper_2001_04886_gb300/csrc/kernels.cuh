@@ -61,7 +61,8 @@ __device__ __forceinline__ bool gate_open(const SolverState* st, int gate) {
 // (the column bound of the tensor-core Gram pass; the slots must start at 0).
 void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y, double fw, double* w,
                     const double* dscale, const SolverState* st, int gate, cudaStream_t stream, double shift = 0.0,
-                    const double* u = nullptr, unsigned* ybnd = nullptr, unsigned* wbnd = nullptr);
+                    const double* u = nullptr, unsigned* ybnd = nullptr, unsigned* wbnd = nullptr,
+                    unsigned* ybnd2 = nullptr, unsigned* wbnd2 = nullptr);
 
 // r = f - A x (x may be null: r = f); out (may be null) receives r; reduces ||r||^2.
 void launch_residual(const StencilDesc& A, const double* f, const double* x, double* out, Scratch sc,
@@ -91,6 +92,16 @@ void launch_update(int64_t n, const double* V, int64_t ldv, int ka, const double
 bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, const double* Y,
                     int64_t ldy, int kb, const unsigned* ymax, Scratch sc, const Epi& epi, int gate,
                     cudaStream_t stream);
+// Yhat[:, j] = Y[:, j] - V T[:, j], j0 <= j < j0 + kbo, in place, on the tensor cores (exact
+// 61-bit fixed-point products, one rounding of V T, then the FP64 difference); vmax: the
+// bounds of the ka V columns. bout[j - j0] (and bout2[j - j0] for j - j0 < nb2) receive the
+// bounds of the outputs; *bcopy_dst = *bcopy_src (may be null). Returns false, launching
+// nothing, for ka > 32 or kbo > 9. A bounded wait that runs out sets st->status to
+// SSTEP_ERR_TIMEOUT (ends the solve) and *err (either may be null).
+bool launch_update_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, double* Y, int64_t ldy,
+                      int j0, int kbo, const double* T, int ldt, unsigned* bout, unsigned* bout2, int nb2,
+                      const unsigned* bcopy_src, unsigned* bcopy_dst, const SolverState* st, int gate,
+                      cudaStream_t stream, unsigned* err = nullptr);
 // out[c] = column bound of column c (out must be zeroed first)
 void launch_colmax(int64_t n, const double* X, int64_t ld, int ncols, unsigned* out, cudaStream_t stream);
 int oz_partials_doubles();      // per-CTA partials of the tensor-core Gram pass (none: sums go to Scratch::acc)

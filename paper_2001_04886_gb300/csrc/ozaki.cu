@@ -24,6 +24,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "epilogue.cuh"
 #include "ozaki.cuh"
@@ -182,7 +183,7 @@ template <int G, int KB>
 __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
     gram_oz_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int ka, const unsigned* __restrict__ vmax,
                    const double* __restrict__ Y, int64_t ldy, const unsigned* __restrict__ ymax, Scratch sc, Epi epi,
-                   int gate, long spin) {
+                   int gate, long spin, int sym) {
     using C = OzCfg<G>;
     constexpr int kItems = 4 * G + (KB + 7) / 8;        // column octets per split warp and stage
     constexpr int SBO = C::kSbo;
@@ -277,30 +278,35 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
         // ---------------------------------------------------------------- split warps
         // item j: column octet j (V octets first, then Y octets) of this warp's K group of 8
         // rows; lane: column c8 of the octet, rows kk and kk + 1 of the stage
-        const int noct_v = (ka + 7) >> 3, noct = noct_v + (KB + 7) / 8;
+        // sym (V = Y): the V columns only, each digit stored into A and B
+        const int noct_v = (ka + 7) >> 3, noct = noct_v + (sym ? 0 : (KB + 7) / 8);
         const int c8 = lane >> 2, kk = warp * 8 + (lane & 3) * 2;
+        // per item: the entry (row kk of this CTA's first stage) and whether it is 16-byte
+        // aligned (kk and the stage height are even, so that holds for every stage)
         const double* cp[kItems];
         uint32_t ce[kItems];
         int cc[kItems];
-        bool cv[kItems];
+        bool cv[kItems], al[kItems];
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             const bool isv = j < noct_v;
             const int c = isv ? j * 8 + c8 : (j - noct_v) * 8 + c8;
             cv[j] = j < noct && c < (isv ? ka : KB);
             cc[j] = c;
-            cp[j] = cv[j] ? (isv ? V + (int64_t)c * ldv : Y + (int64_t)c * ldy) : nullptr;
+            cp[j] = cv[j] ? (isv ? V + (int64_t)c * ldv : Y + (int64_t)c * ldy) + s0 * C::kRows + kk : nullptr;
+            al[j] = ((uintptr_t)cp[j] & 15) == 0;
             ce[j] = cv[j] ? ex[isv ? c : ka + c] : 0u;
         }
         auto load = [&](int64_t st, double2 (&buf)[kItems]) {
-            const int64_t r = (s0 + st) * C::kRows + kk;
+            const int64_t off = st * C::kRows, r = (s0 + st) * C::kRows + kk;
+            const bool whole = (s0 + st + 1) * C::kRows <= n;   // warp-uniform: no row past n
 #pragma unroll
             for (int j = 0; j < kItems; ++j) {
                 buf[j] = make_double2(0.0, 0.0);
                 if (cv[j]) {
-                    const double* p = cp[j] + r;
-                    if (r + 1 < n) {
-                        if (((uintptr_t)p & 15) == 0) buf[j] = __ldg(reinterpret_cast<const double2*>(p));
+                    const double* p = cp[j] + off;
+                    if (whole || r + 1 < n) {
+                        if (al[j]) buf[j] = __ldg(reinterpret_cast<const double2*>(p));
                         else buf[j] = make_double2(__ldg(p), __ldg(p + 1));
                     } else if (r < n) {
                         buf[j].x = __ldg(p);
@@ -343,6 +349,12 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
 #pragma unroll
                         for (int t = 0; t < oz::kDigits; ++t)
                             *reinterpret_cast<uint32_t*>(base + (t >> 2) * C::kTile + (t & 3) * 4 * SBO) = d[t];
+                        if (sym && cv[j]) {
+                            unsigned char* bb = sp + 2 * G * C::kTile;
+#pragma unroll
+                            for (int t = 0; t < oz::kDigits; ++t)
+                                *reinterpret_cast<uint32_t*>(bb + op_off<SBO>(t * KB + c, kk)) = d[t];
+                        }
                     } else if (cv[j]) {
                         unsigned char* base = sp + 2 * G * C::kTile;
 #pragma unroll
@@ -461,7 +473,7 @@ void launch_colmax(int64_t n, const double* X, int64_t ld, int ncols, unsigned* 
 namespace {
 template <int G, int KB>
 void launch_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, const double* Y, int64_t ldy,
-               const unsigned* ymax, Scratch sc, const Epi& epi, int gate, cudaStream_t stream, long spin) {
+               const unsigned* ymax, Scratch sc, const Epi& epi, int gate, cudaStream_t stream, long spin, int sym) {
     using C = OzCfg<G>;
     static bool attr[64] = {false};   // once per device
     int dev = 0;
@@ -474,7 +486,7 @@ void launch_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* 
     int grid = device_sms();
     if (grid > nst) grid = (int)std::max<int64_t>(nst, 1);
     gram_oz_kernel<G, KB><<<grid, C::kThreads, C::kSmem, stream>>>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate,
-                                                                    spin);
+                                                                    spin, sym);
 }
 }  // namespace
 
@@ -486,11 +498,12 @@ bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsig
     if (ka < 1 || ka > kMaxCols || kb < 1 || kb > kMaxS + 1 || n < 1 || n > ((int64_t)1 << 27) || !sc.acc) return false;
     if (((uintptr_t)V & 7) || ((uintptr_t)Y & 7)) return false;
     const bool one = ka <= 32;
+    const int sym = (V == Y && ldv == ldy && ka == kb) ? 1 : 0;   // V^T V: split each column once
     switch (kb) {
 #define SSTEP_OZ_CASE(KB)                                                                                       \
     case KB:                                                                                                    \
-        if (one) launch_oz<1, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin);         \
-        else launch_oz<2, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin);             \
+        if (one) launch_oz<1, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym);    \
+        else launch_oz<2, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym);        \
         return true;
         SSTEP_OZ_CASE(1)
         SSTEP_OZ_CASE(2)
@@ -502,6 +515,382 @@ bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsig
         SSTEP_OZ_CASE(8)
         SSTEP_OZ_CASE(9)
 #undef SSTEP_OZ_CASE
+        default: return false;
+    }
+}
+
+}  // namespace sstep
+
+// ================================================================== block update on the tensor cores
+// Yhat[:, j] = Y[:, j] - V T[:, j] for j0 <= j < j0 + KBO, in place (Alg. 4.1 step 7; the
+// Gram matrix of the result is the tensor-core Gram pass's next launch). Every V column a
+// is in 61-bit fixed point relative to its bound (q 2^(ea - kFrac)); T is folded with those
+// scales, T'[a][j] = 2^(ea - kFrac) T[a][j], so V_ra T_aj = q_ra T'_aj, and every column j
+// of T' is in fixed point relative to its own bound: T'_aj = p_aj 2^(Fj - kFrac). Then
+// P_rj = 2^(Fj - kFrac) sum_a q_ra p_aj, an exact integer sum of digit products. The A
+// operand holds V's digit planes (M = 128 rows, K = digit x column), the B operand T's
+// digits with the digit order reversed, so that one digit diagonal ta + tb = d is one
+// contiguous K window of both: each of the 9 kept diagonals is one FP32 accumulator in
+// tensor memory, exact (at most 8 x 32 products of 2^14). The epilogue warps combine the
+// diagonals into a 128-bit integer (Horner in 256), round P once and form Y - P in FP64.
+namespace sstep {
+namespace {
+
+// warps 0..7 split tile t and then run the epilogue of tile t - 1 (warps w and w + 4 share
+// tensor-memory lane quarter w % 4 and take half of the outputs each); warp 8 issues the MMAs
+constexpr int kUpSplitWarps = 8, kUpMmaWarp = 8;
+constexpr int kUpThreads = (kUpSplitWarps + 1) * 32;
+
+constexpr int kUpRows = 128;                      // rows per tile (MMA M)
+constexpr int kUpDiags = oz::kCut + 1;            // kept digit diagonals
+constexpr uint32_t kUpBuf = 256;                  // tensor-memory columns per accumulator buffer
+
+template <int KAP>
+struct UpCfg {
+    static constexpr int kK = oz::kDigits * KAP;  // K of one row: 8 digit planes of KAP columns
+    static constexpr int kSbo = KAP * 128;        // bytes between 8-row groups
+    static constexpr int kA = kUpRows * kK * 2;   // one A buffer (FP16)
+    static constexpr int kB = 16 * kK * 2;        // B: 16 rows (outputs, padded)
+    static constexpr int kSmem = 2 * kA + kB;
+};
+
+__device__ __forceinline__ uint64_t op_desc_rt(uint32_t addr, int sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+template <int KAP, int KBO>
+__global__ void __launch_bounds__(kUpThreads, 1)
+    update_oz_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int ka, const unsigned* __restrict__ vmax,
+                     double* Y, int64_t ldy, int j0, const double* __restrict__ T, int ldt, unsigned* bout,
+                     unsigned* bout2, int nb2, const unsigned* bcopy_src, unsigned* bcopy_dst, const SolverState* st,
+                     int gate, long spin, unsigned* err) {
+    using C = UpCfg<KAP>;
+    constexpr int SBO = C::kSbo;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[2], empty[2], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int failed;
+    __shared__ uint32_t exv[32];
+    __shared__ unsigned fmax[KBO];
+    __shared__ int fexp[KBO];
+    static_assert(KBO <= 16, "the B operand has 16 rows");
+    __shared__ int nonfinite;
+    __shared__ double tp[32 * KBO];
+    if (!gate_open(st, gate)) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* Abuf = smem;
+    unsigned char* Bop = smem + 2 * C::kA;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        failed = 0;
+        nonfinite = 0;
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&full[b], kUpSplitWarps);
+            bar_init(&empty[b], 1);
+            bar_init(&tfull[b], 1);
+            bar_init(&tempty[b], kUpSplitWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        if (bcopy_dst && blockIdx.x == 0) *bcopy_dst = *bcopy_src;   // the unchanged column's bound
+    }
+    if (tid < 32) exv[tid] = tid < ka ? oz::bound_exponent(vmax[tid]) : 0u;
+    if (tid < KBO) fmax[tid] = 0u;
+    // zero both A buffers and B: columns KAP > ka and the padded output rows stay zero
+    for (int i = tid; i < C::kSmem / 16; i += kUpThreads) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    // T' = 2^(ea - kFrac) T and the bound of each of its columns
+    for (int e = tid; e < ka * KBO; e += kUpThreads) {
+        const int a = e % ka, j = e / ka;
+        const double t = T[a + (int64_t)(j0 + j) * ldt];
+        const uint32_t ea = exv[a];
+        if (ea == oz::kNonFinite || !isfinite(t)) nonfinite = 1;
+        const double v = ea == 0 ? 0.0 : ldexp(t, (int)ea - oz::kFrac);
+        tp[e] = v;
+        atomicMax(&fmax[j], oz::abs_hiword((uint32_t)((unsigned long long)__double_as_longlong(v) >> 32)));
+    }
+    __syncthreads();
+    if (tid < KBO) fexp[tid] = (int)oz::bound_exponent(fmax[tid]);
+    __syncthreads();
+    // B: row j, K (7 - tb) KAP + a = digit tb of T'_aj (digit order reversed)
+    for (int e = tid; e < ka * KBO; e += kUpThreads) {
+        const int a = e % ka, j = e / ka;
+        const uint64_t bits = (uint64_t)__double_as_longlong(tp[e]);
+        const uint64_t w = oz::fixed_biased((uint32_t)bits, (uint32_t)(bits >> 32), (uint32_t)fexp[j]);
+#pragma unroll
+        for (int tb = 0; tb < oz::kDigits; ++tb)
+            *reinterpret_cast<__half*>(Bop + op_off<SBO>(j, (oz::kDigits - 1 - tb) * KAP + a)) =
+                __int2half_rn(oz::digit(w, tb));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base, sbase = smem_addr(smem);
+    const int64_t ntiles = (n + kUpRows - 1) / kUpRows;
+    const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    const int64_t nt = t1 - t0;
+
+    if (warp == kUpMmaWarp) {
+        // ---------------------------------------------------------------- MMA warp
+        if (lane == 0) {
+            int n_empty[2] = {0, 0}, n_tfull[2] = {0, 0};
+            for (int64_t lt = 0; lt < nt && !failed; ++lt) {
+                const int b = (int)(lt & 1);
+                if (lt >= 2 && !oz_wait(smem_addr(&tempty[b]), (uint32_t)(((lt >> 1) - 1) & 1), spin)) {
+                    failed = 1;
+                    break;
+                }
+                if (!oz_wait(smem_addr(&full[b]), (uint32_t)((lt >> 1) & 1), spin)) {
+                    failed = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t ab = sbase + (uint32_t)(b * C::kA), bb = sbase + (uint32_t)(2 * C::kA);
+#pragma unroll 1
+                for (int d = 0; d < kUpDiags; ++d) {
+                    const int lo = d > oz::kDigits - 1 ? d - (oz::kDigits - 1) : 0;
+                    const int hi = d < oz::kDigits - 1 ? d : oz::kDigits - 1;
+                    const int u0 = oz::kDigits - 1 - d + lo;
+                    const uint32_t dt = tmem + (uint32_t)b * kUpBuf + (uint32_t)(d * 16);
+                    for (int ta = lo; ta <= hi; ++ta)
+#pragma unroll
+                        for (int ks = 0; ks < KAP / 16; ++ks) {
+                            const uint32_t accf = (ta > lo || ks > 0) ? 1u : 0u;
+                            const uint32_t aa = ab + (uint32_t)(ta * KAP * 16 + ks * 256);
+                            const uint32_t ba = bb + (uint32_t)((u0 + ta - lo) * KAP * 16 + ks * 256);
+                            mma_f16(dt, op_desc<SBO>(aa), op_desc<SBO>(ba), oz_idesc(16), accf);
+                        }
+                }
+                mma_commit(&empty[b]);
+                ++n_empty[b];
+                mma_commit(&tfull[b]);
+                ++n_tfull[b];
+            }
+            for (int b = 0; b < 2; ++b) {
+                if (n_empty[b]) oz_wait(smem_addr(&empty[b]), (uint32_t)((n_empty[b] - 1) & 1), kOzSpin);
+                if (n_tfull[b]) oz_wait(smem_addr(&tfull[b]), (uint32_t)((n_tfull[b] - 1) & 1), kOzSpin);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------------- split + epilogue warps
+        // split item k of this warp: row group rg (8 rows) and column octet oct of the tile;
+        // lane: row rr of the group, columns a and a + 1 of the octet (a K-adjacent pair)
+        constexpr int kIt = 2 * (KAP / 8);   // 16 row groups x KAP / 8 octets / 8 warps
+        const int koct = (ka + 7) >> 3, rr = lane & 7, cpair = lane >> 3;
+        // epilogue role: rows 32 q + lane of a tile; warps 0..3 take the outputs j < H, warps
+        // 4..7 the outputs H <= j < KBO (a compile-time offset: registers are not indexed)
+        constexpr int H = (KBO + 1) / 2;
+        const int q = warp & 3;
+        unsigned bm[H];
+#pragma unroll
+        for (int j = 0; j < H; ++j) bm[j] = 0;
+        // per item: the entries of columns a and a + 1 in this CTA's first tile (null: none)
+        const double* pa[kIt];
+        const double* pb[kIt];
+#pragma unroll
+        for (int k = 0; k < kIt; ++k) {
+            const int i = warp + kUpSplitWarps * k, rg = i & 15, oct = i >> 4;
+            const int a = oct * 8 + cpair * 2;
+            const int64_t r0 = t0 * kUpRows + rg * 8 + rr;
+            pa[k] = (oct < koct && a < ka) ? V + (int64_t)a * ldv + r0 : nullptr;
+            pb[k] = (oct < koct && a + 1 < ka) ? V + (int64_t)(a + 1) * ldv + r0 : nullptr;
+        }
+        auto load = [&](int64_t lt, double2 (&buf)[kIt]) {
+            const int64_t off = lt * kUpRows;
+            const bool whole = (t0 + lt + 1) * kUpRows <= n;   // warp-uniform: no row past n
+#pragma unroll
+            for (int k = 0; k < kIt; ++k) {
+                const int i = warp + kUpSplitWarps * k, rg = i & 15;
+                const bool in = whole || (t0 + lt) * kUpRows + rg * 8 + rr < n;
+                buf[k].x = (pa[k] && in) ? __ldg(pa[k] + off) : 0.0;
+                buf[k].y = (pb[k] && in) ? __ldg(pb[k] + off) : 0.0;
+            }
+        };
+        // this thread's Y entries of tile lt (loaded a whole split ahead of their use)
+        const int jo_rt = warp < 4 ? 0 : H;
+        double yv[H];
+        auto load_y = [&](int64_t lt) {
+            const int64_t r = (t0 + lt) * kUpRows + q * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < H; ++j)
+                yv[j] = (r < n && jo_rt + j < KBO) ? Y[(int64_t)(j0 + jo_rt + j) * ldy + r] : 0.0;
+        };
+        // epilogue of tile lt: Yhat = Y - P for this thread's row and outputs (yv: its Y entries)
+        auto epilogue = [&](int64_t lt, auto joc) -> bool {
+            constexpr int jo = decltype(joc)::value;
+            const int b = (int)(lt & 1);
+            const int64_t r = (t0 + lt) * kUpRows + q * 32 + lane;
+            if (!oz_wait(smem_addr(&tfull[b]), (uint32_t)((lt >> 1) & 1), spin)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            long long Ql[H];   // Horner in 64 bits while it fits (5 diagonals: < 2^55)
+            oz::i128 Q[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) Ql[j] = 0;
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * kUpBuf;
+#pragma unroll
+            for (int d = 0; d < kUpDiags; ++d) {
+                uint32_t rv[16];
+                tmem_ld<16>(ta + (uint32_t)(d * 16), rv);
+#pragma unroll
+                for (int j = 0; j < H; ++j) {
+                    const long long S = jo + j < 16 ? __float2int_rn(__uint_as_float(rv[(jo + j) & 15])) : 0;
+                    if (d < 5) Ql[j] = Ql[j] * 256 + S;
+                    else {
+                        if (d == 5) Q[j] = (oz::i128)Ql[j];
+                        Q[j] = (Q[j] << 8) + (oz::i128)S;
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) bar_arrive(&tempty[b]);
+            if (r < n) {
+#pragma unroll
+                for (int j = 0; j < H; ++j) {
+                    if (jo + j < KBO) {
+                        const int fj = fexp[jo + j];
+                        const double P = (nonfinite || fj == (int)oz::kNonFinite)
+                                             ? __longlong_as_double(0x7FF8000000000000ll)
+                                             : oz::i128_to_double_int(Q[j], 8 * (2 * (oz::kDigits - 1) - oz::kCut) + fj -
+                                                                                oz::kFrac);
+                        const double yh = yv[j] - P;
+                        Y[(int64_t)(j0 + jo + j) * ldy + r] = yh;
+                        bm[j] = max(bm[j],
+                                    oz::abs_hiword((uint32_t)((unsigned long long)__double_as_longlong(yh) >> 32)));
+                    }
+                }
+            }
+            return true;
+        };
+        double2 cur[kIt];
+        if (nt > 0) load(0, cur);
+        for (int64_t lt = 0; lt < nt; ++lt) {
+            if (failed) break;
+            double2 nxt[kIt];
+            if (lt + 1 < nt) load(lt + 1, nxt);
+            if (lt >= 1) load_y(lt - 1);   // consumed by the epilogue after this split
+            const int b = (int)(lt & 1);
+            if (lt >= 2 && !oz_wait(smem_addr(&empty[b]), (uint32_t)(((lt >> 1) - 1) & 1), spin)) {
+                failed = 1;
+                break;
+            }
+            unsigned char* ap = Abuf + b * C::kA;
+#pragma unroll
+            for (int k = 0; k < kIt; ++k) {
+                const int i = warp + kUpSplitWarps * k, rg = i & 15, oct = i >> 4;
+                if (oct < koct) {   // warp-uniform
+                    const int a = oct * 8 + cpair * 2;
+                    const uint64_t b0 = (uint64_t)__double_as_longlong(cur[k].x);
+                    const uint64_t b1 = (uint64_t)__double_as_longlong(cur[k].y);
+                    const uint64_t w0 = oz::fixed_biased((uint32_t)b0, (uint32_t)(b0 >> 32), exv[a & 31]);
+                    const uint64_t w1 = oz::fixed_biased((uint32_t)b1, (uint32_t)(b1 >> 32), exv[(a + 1) & 31]);
+                    unsigned char* base = ap + op_off<SBO>(rg * 8 + rr, a);
+                    *reinterpret_cast<uint32_t*>(base + 0 * KAP * 16) = digit_pair<0>(w0, w1);
+                    *reinterpret_cast<uint32_t*>(base + 1 * KAP * 16) = digit_pair<1>(w0, w1);
+                    *reinterpret_cast<uint32_t*>(base + 2 * KAP * 16) = digit_pair<2>(w0, w1);
+                    *reinterpret_cast<uint32_t*>(base + 3 * KAP * 16) = digit_pair<3>(w0, w1);
+                    *reinterpret_cast<uint32_t*>(base + 4 * KAP * 16) = digit_pair<4>(w0, w1);
+                    *reinterpret_cast<uint32_t*>(base + 5 * KAP * 16) = digit_pair<5>(w0, w1);
+                    *reinterpret_cast<uint32_t*>(base + 6 * KAP * 16) = digit_pair<6>(w0, w1);
+                    *reinterpret_cast<uint32_t*>(base + 7 * KAP * 16) = digit_pair<7>(w0, w1);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) bar_arrive(&full[b]);
+#pragma unroll
+            for (int k = 0; k < kIt; ++k) cur[k] = nxt[k];
+            if (lt >= 1) {   // the previous tile, while this tile's MMAs run
+                const bool ok = warp < 4 ? epilogue(lt - 1, std::integral_constant<int, 0>())
+                                         : epilogue(lt - 1, std::integral_constant<int, H>());
+                if (!ok) {
+                    failed = 1;
+                    break;
+                }
+            }
+        }
+        if (!failed && nt > 0) {
+            load_y(nt - 1);
+            const bool ok = warp < 4 ? epilogue(nt - 1, std::integral_constant<int, 0>())
+                                     : epilogue(nt - 1, std::integral_constant<int, H>());
+            if (!ok) failed = 1;
+        }
+        const int jo = warp < 4 ? 0 : H;
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            const unsigned m = __reduce_max_sync(0xffffffffu, bm[j]);
+            if (lane == 0 && m && jo + j < KBO) {
+                if (bout) atomicMax(bout + jo + j, m);
+                if (bout2 && jo + j < nb2) atomicMax(bout2 + jo + j, m);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    if (failed && tid == 0) {
+        if (err) atomicExch(err, 1u);
+        if (st) {
+            SolverState* sw = const_cast<SolverState*>(st);
+            sw->status = SSTEP_ERR_TIMEOUT;
+            sw->building = 0;
+            sw->active = 0;
+        }
+    }
+}
+
+template <int KAP, int KBO>
+void launch_up(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, double* Y, int64_t ldy, int j0,
+               const double* T, int ldt, unsigned* bout, unsigned* bout2, int nb2, const unsigned* bsrc,
+               unsigned* bdst, const SolverState* st, int gate, cudaStream_t stream, unsigned* err) {
+    using C = UpCfg<KAP>;
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr[dev]) {
+        cudaFuncSetAttribute(update_oz_kernel<KAP, KBO>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+        if (dev >= 0 && dev < 64) attr[dev] = true;
+    }
+    const int64_t ntiles = (n + kUpRows - 1) / kUpRows;
+    int grid = device_sms();
+    if (grid > ntiles) grid = (int)std::max<int64_t>(ntiles, 1);
+    update_oz_kernel<KAP, KBO><<<grid, kUpThreads, C::kSmem, stream>>>(n, V, ldv, ka, vmax, Y, ldy, j0, T, ldt, bout,
+                                                                        bout2, nb2, bsrc, bdst, st, gate, g_oz_spin,
+                                                                        err);
+}
+
+}  // namespace
+
+bool launch_update_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, double* Y, int64_t ldy,
+                      int j0, int kbo, const double* T, int ldt, unsigned* bout, unsigned* bout2, int nb2,
+                      const unsigned* bcopy_src, unsigned* bcopy_dst, const SolverState* st, int gate,
+                      cudaStream_t stream, unsigned* err) {
+    if (ka < 1 || ka > 32 || kbo < 1 || kbo > kMaxS + 1 || n < 1 || n > ((int64_t)1 << 27)) return false;
+    const bool k16 = ka <= 16;
+    switch (kbo) {
+#define SSTEP_UP_CASE(KBO)                                                                                      \
+    case KBO:                                                                                                   \
+        if (k16) launch_up<16, KBO>(n, V, ldv, ka, vmax, Y, ldy, j0, T, ldt, bout, bout2, nb2, bcopy_src,       \
+                                    bcopy_dst, st, gate, stream, err);                                          \
+        else launch_up<32, KBO>(n, V, ldv, ka, vmax, Y, ldy, j0, T, ldt, bout, bout2, nb2, bcopy_src,           \
+                                bcopy_dst, st, gate, stream, err);                                              \
+        return true;
+        SSTEP_UP_CASE(1)
+        SSTEP_UP_CASE(2)
+        SSTEP_UP_CASE(3)
+        SSTEP_UP_CASE(4)
+        SSTEP_UP_CASE(5)
+        SSTEP_UP_CASE(6)
+        SSTEP_UP_CASE(7)
+        SSTEP_UP_CASE(8)
+        SSTEP_UP_CASE(9)
+#undef SSTEP_UP_CASE
         default: return false;
     }
 }

@@ -30,6 +30,7 @@
 
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #ifdef __CUDACC__
 #define OZ_HD __host__ __device__ __forceinline__
@@ -101,6 +102,33 @@ OZ_HD double i128_to_double(i128 v, int e2) {
     const double d = (double)top;                        // rounds to 53 bits
     const double r = ldexp(d, 64 - lz + e2);
     return neg ? -r : r;
+}
+
+// The same rounding with integer operations only (no FP64 instruction): normalise, round
+// the top 53 bits to nearest even with a sticky bit, and assemble sign, exponent and
+// significand. Results outside the normal range fall back to i128_to_double.
+OZ_HD double i128_to_double_int(i128 v, int e2) {
+    if (v == 0) return 0.0;
+    const uint64_t sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    u128 u = v < 0 ? (u128)0 - (u128)v : (u128)v;
+    const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+    const int lz = hi ? clz64(hi) : 64 + clz64(lo);
+    u <<= lz;
+    const uint64_t top = (uint64_t)(u >> 64);
+    const bool sticky = (uint64_t)u != 0ull;
+    uint64_t m = top >> 11;                       // 53 bits, the leading one at bit 52
+    const uint64_t r = top & 0x7FFull;
+    if (r > 0x400ull || (r == 0x400ull && (sticky || (m & 1ull)))) ++m;
+    int ex = 127 - lz + e2 + 1023;                // the value is m 2^(127 - lz + e2 - 52)
+    if (m >> 53) {                                // rounding carried into bit 53
+        m >>= 1;
+        ++ex;
+    }
+    if (ex <= 0 || ex >= 2047) return i128_to_double(v, e2);
+    const uint64_t bits = sign | ((uint64_t)ex << 52) | (m & 0xFFFFFFFFFFFFFull);
+    double d;
+    memcpy(&d, &bits, 8);
+    return d;
 }
 
 }  // namespace oz

@@ -65,3 +65,13 @@ void oz_gram(int64_t n, const double* V, int ka, const double* Y, int kb, int cu
     }
 }
 }
+
+extern "C" {
+// both roundings of v 2^e2 for v = hi 2^64 + lo (two's complement): the FP64 reference and
+// the integer-only one the kernels use
+void oz_round_both(uint64_t hi, uint64_t lo, int e2, double* out) {
+    const i128 v = (i128)(((u128)hi << 64) | (u128)lo);
+    out[0] = i128_to_double(v, e2);
+    out[1] = i128_to_double_int(v, e2);
+}
+}

@@ -124,8 +124,10 @@ def test_tc_gram_symmetric_bit_for_bit():
     d = dev()
     n = 200000
     V = np.stack([inputs.x_true(40 + i, n) * 3.0 ** i for i in range(8)], axis=1)
-    G = pkg.sstep_gram_tc(panel(V, d), panel(V, d)).cpu().numpy()
-    assert np.array_equal(G, G.T)
+    P = panel(V, d)
+    G = pkg.sstep_gram_tc(P, P).cpu().numpy()               # one panel: each column split once
+    G2 = pkg.sstep_gram_tc(P, panel(V, d)).cpu().numpy()    # two panels: V and Y split apart
+    assert np.array_equal(G, G.T) and np.array_equal(G, G2)
     check(V, V, G)
 
 
@@ -178,3 +180,44 @@ def test_tc_gram_wait_timeout_gives_nan_and_recovers():
     C = pkg.sstep_gram_tc(Vd, Yd)
     torch.cuda.synchronize()
     check(V, Y, C.cpu().numpy())
+
+
+# ------------------------------------------------------------------ block update on the tensor cores
+@pytest.mark.parametrize("n,ka,kb", [(4096, 12, 5), (5000, 0, 3), (300001, 32, 9), (31, 3, 2), (1, 1, 1),
+                                     (130, 16, 8), (2_097_152, 32, 9)])
+def test_tc_block_update_matches_oracle(n, ka, kb):
+    """Y <- Y - V T and G = Y^T Y on the tensor cores against the oracle's block update:
+    every updated column to 1e-14 relative (the FP64 kernel's bar) and G to 1e-14 of the
+    product of the column norms."""
+    from tests.gpu_util import relerr
+
+    d = dev()
+    V = np.stack([inputs.x_true(20 + i, n) * 2.0 ** (i % 7 - 3) for i in range(ka)], axis=1) if ka else np.zeros((n, 0))
+    Y = np.stack([inputs.x_true(200 + j, n) for j in range(kb)], axis=1)
+    T = np.stack([inputs.x_true(300 + j, ka) * 10.0 ** (j % 4 - 2) for j in range(kb)], axis=1) if ka else np.zeros((0, kb))
+    Yd = panel(Y, d)
+    G = pkg.sstep_block_update(panel(V, d) if ka else None, Yd, to_dev(T, d) if ka else None, tc=True)
+    torch.cuda.synchronize()
+    Yh, Gr = osstep.block_update(Y, V, T)
+    got = Yd.cpu().numpy()
+    for j in range(kb):
+        assert relerr(got[:, j], Yh[:, j]) <= 1e-14, j
+    nrm = np.linalg.norm(Yh, axis=0)
+    assert np.max(np.abs(G.cpu().numpy() - Gr) / np.outer(nrm, nrm)) <= 1e-14
+
+
+def test_tc_block_update_cancellation():
+    """Y almost in the span of V (the s-step projection at large s): the updated columns are
+    tiny against Y, and their error against the oracle is still at the FP64 level of Y."""
+    d = dev()
+    n, ka, kb = 100000, 16, 9
+    V = np.stack([inputs.x_true(500 + i, n) for i in range(ka)], axis=1)
+    T = np.stack([inputs.x_true(600 + j, ka) for j in range(kb)], axis=1)
+    Y = V @ T + 1e-9 * np.stack([inputs.x_true(700 + j, n) for j in range(kb)], axis=1)
+    Yd = panel(Y, d)
+    pkg.sstep_block_update(panel(V, d), Yd, to_dev(T, d), tc=True)
+    torch.cuda.synchronize()
+    Yh, _ = osstep.block_update(Y, V, T)
+    got = Yd.cpu().numpy()
+    for j in range(kb):
+        assert np.linalg.norm(got[:, j] - Yh[:, j]) <= 1e-15 * 8 * np.linalg.norm(Y[:, j]), j

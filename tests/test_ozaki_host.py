@@ -190,3 +190,27 @@ def test_planted_coarse_cut_breaks_the_bound(emu):
     B = error_bound(V, Y)
     C = gram(emu, V, Y, cut=6)
     assert any(abs(Fraction(float(C[a, b])) - ex[a, b]) > B[a, b] for a in range(2) for b in range(2))
+
+
+def test_integer_rounding_equals_fp64_rounding(emu):
+    """The integer-only rounding of a 128-bit integer times 2^e2 (the kernels' epilogue)
+    gives the same double as the reference rounding, and that one is the correctly
+    rounded value (checked with exact rationals), on ties, carries and random values."""
+    emu.oz_round_both.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    rng = np.random.default_rng(4)
+    cases = []
+    for v in [1, -1, 2 ** 53 + 1, 2 ** 53 + 3, (2 ** 53 - 1) * 2 ** 11 + 2 ** 10, (2 ** 53 - 1) * 2 ** 11 + 2 ** 10 + 1,
+              2 ** 120 + 2 ** 67, -(2 ** 100) - 2 ** 47, 2 ** 126 - 1, -(2 ** 126) + 12345]:
+        cases.append(v)
+    for _ in range(300):
+        bits = int(rng.integers(1, 126))
+        v = int(rng.integers(0, 2 ** 62)) * 2 ** max(0, bits - 62) + int(rng.integers(0, 2 ** 30))
+        cases.append(v if rng.random() < 0.5 else -v)
+    out = (ctypes.c_double * 2)()
+    for v in cases:
+        for e2 in (-1100, -200, 0, 37):
+            u = v % (1 << 128)
+            emu.oz_round_both(u >> 64, u & ((1 << 64) - 1), e2, out)
+            exact = Fraction(v) * Fraction(2) ** e2
+            assert out[0] == out[1], (v, e2)
+            assert out[0] == float(exact), (v, e2)   # Python's float() of a Fraction rounds correctly
