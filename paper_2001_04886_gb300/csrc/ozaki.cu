@@ -40,18 +40,24 @@ constexpr long kOzSpin = 1L << 24;                   // bounded mbarrier polls
 // Shapes of one instantiation: G groups of 32 V columns.
 // (14 split warps + the MMA warp: at most 4 warps per SM sub-partition, so 128 registers
 // per thread; a stage of 112 rows is 7 MMA K-steps and 9 stages make a chunk of 1008 rows.)
+// G = 0: at most 16 V columns, one A tile of all 8 digits x 16 columns and 4 stages in
+// flight; G = 1, 2: up to 32 G V columns, two tiles per 32 columns (digits 0-3 and 4-7)
 template <int G>
 struct OzCfg {
-    static constexpr int kSplitWarps = G == 1 ? 14 : 8;
+    static constexpr int kSplitWarps = G <= 1 ? 14 : 8;
     static constexpr int kThreads = (kSplitWarps + 1) * 32;   // + the MMA warp
     static constexpr int kRows = 8 * kSplitWarps;             // rows per stage (one K group per split warp)
     static constexpr int kSbo = kRows * 16;                   // bytes between 8-row groups of an operand
     static constexpr int kTile = 128 * kRows * 2;             // one A tile (FP16)
     static constexpr int kB = kBRows * kRows * 2;             // B
-    static constexpr int kStage = 2 * G * kTile + kB;
-    static constexpr int kSmem = 2 * kStage;                  // two stages
+    static constexpr int kAT = G == 0 ? 1 : 2 * G;            // A tiles per stage
+    static constexpr int kGroups = G == 0 ? 1 : G;            // column groups
+    static constexpr int kColsPer = G == 0 ? 16 : 32;         // V columns per group
+    static constexpr int kStage = kAT * kTile + kB;
+    static constexpr int kNStages = G == 0 ? 4 : 2;
+    static constexpr int kSmem = kNStages * kStage;
     static constexpr int kStagesPerChunk = oz::kChunkRows / kRows;
-    static constexpr int kBuf = G * kGroupCols;               // accumulator columns per buffer
+    static constexpr int kBuf = G == 0 ? 128 : G * kGroupCols;   // accumulator columns per buffer
     static constexpr uint32_t kCols = 2 * kBuf <= 256 ? 256u : 512u;
     static_assert(kRows % 16 == 0 && kStagesPerChunk * kRows <= oz::kChunkRows, "stage shape");
 };
@@ -162,10 +168,10 @@ namespace {
 // integer S is added into acc[b] with weight 256^(kCut - tb); the thread's contribution is
 // acc >> 8 ta (every kept term has kCut - tb >= ta, so that shift is exact).
 template <int KB, int NC>
-__device__ __forceinline__ void drain_tile(uint32_t taddr, int ta, oz::i128 (&acc)[KB]) {
+__device__ __forceinline__ void drain_tile(uint32_t taddr, int ta, int tmin, oz::i128 (&acc)[KB]) {
 #pragma unroll
     for (int c0 = 0; c0 < NC; c0 += 16) {
-        if (c0 >= (oz::kCut + 1 - ta) * KB) break;       // warp-uniform: the rest are dropped pairs
+        if (c0 >= (oz::kCut + 1 - tmin) * KB) break;     // warp-uniform (tmin: the warp's smallest ta)
         uint32_t r[16];
         tmem_ld<16>(taddr + (uint32_t)c0, r);
 #pragma unroll
@@ -185,10 +191,11 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
                    const double* __restrict__ Y, int64_t ldy, const unsigned* __restrict__ ymax, Scratch sc, Epi epi,
                    int gate, long spin, int sym) {
     using C = OzCfg<G>;
-    constexpr int kItems = 4 * G + (KB + 7) / 8;        // column octets per split warp and stage
+    constexpr int kItems = (G == 0 ? 2 : 4 * G) + (KB + 7) / 8;   // column octets per split warp and stage
+    constexpr int NS = C::kNStages, NG = C::kGroups, CP = C::kColsPer;
     constexpr int SBO = C::kSbo;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[2], empty[2], tfull[2], tempty[2];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int failed;
     __shared__ bool last;
@@ -204,9 +211,11 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
     }
     if (tid == 0) {
         failed = 0;
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NS; ++b) {
             bar_init(&full[b], C::kSplitWarps);
             bar_init(&empty[b], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
             bar_init(&tfull[b], 1);
             bar_init(&tempty[b], C::kSplitWarps);
         }
@@ -220,21 +229,25 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
     const int64_t s0 = nst * blockIdx.x / gridDim.x, s1 = nst * (blockIdx.x + 1) / gridDim.x;
     const int64_t nstages = s1 - s0;
 
-    // drain role of split warps 0..7: TMEM lane quarter q, V digit ta
-    const int q = warp & 3, ta = 4 * ((warp >> 2) & 1) + q;
-    const bool drains = warp < kDrainWarps;
-    oz::i128 acc[G][KB];
+    // drain role: G >= 1: split warps 0..7, TMEM lane quarter q, V digit ta, column g 32 +
+    // lane; G = 0: split warps 0..3, lane quarter q holds digits 2q and 2q + 1 of 16 columns
+    const int q = warp & 3;
+    const int ta = G == 0 ? 2 * q + (lane >> 4) : 4 * ((warp >> 2) & 1) + q;
+    const int tmin = G == 0 ? 2 * q : ta;
+    const int al_ = G == 0 ? (lane & 15) : lane;   // column within its group
+    const bool drains = warp < (G == 0 ? 4 : kDrainWarps);
+    oz::i128 acc[NG][KB];
 #pragma unroll
-    for (int g = 0; g < G; ++g)
+    for (int g = 0; g < NG; ++g)
 #pragma unroll
         for (int b = 0; b < KB; ++b) acc[g][b] = 0;
 
     if (warp == C::kSplitWarps) {
         // ---------------------------------------------------------------- MMA warp
         if (lane == 0) {
-            int n_empty[2] = {0, 0}, n_tfull[2] = {0, 0};
+            int n_empty[NS] = {}, n_tfull[2] = {0, 0};
             for (int64_t gs = 0; gs < nstages && !failed; ++gs) {
-                const int sb = (int)(gs & 1);
+                const int sb = (int)(gs % NS);
                 const int chunk = (int)(gs / C::kStagesPerChunk), sic = (int)(gs % C::kStagesPerChunk);
                 const int tb = chunk & 1;
                 if (sic == 0 && chunk >= 2 &&   // the accumulators of chunk - 2 are drained
@@ -242,13 +255,20 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
                     failed = 1;
                     break;
                 }
-                if (!oz_wait(smem_addr(&full[sb]), (uint32_t)((gs >> 1) & 1), spin)) {
+                if (!oz_wait(smem_addr(&full[sb]), (uint32_t)((gs / NS) & 1), spin)) {
                     failed = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t so = sbase + (uint32_t)(sb * C::kStage);
                 const uint32_t dt = tmem + (uint32_t)(tb * C::kBuf);
+                if (G == 0) {   // one tile: all digit pairs of 16 columns against the B digits
+#pragma unroll
+                    for (int ks = 0; ks < C::kRows / 16; ++ks)
+                        mma_f16(dt, op_desc<SBO>(so + (uint32_t)(ks * 256)),
+                                op_desc<SBO>(so + (uint32_t)(C::kTile + ks * 256)), oz_idesc(kN0),
+                                (sic > 0 || ks > 0) ? 1u : 0u);
+                }
 #pragma unroll
                 for (int g = 0; g < G; ++g)
 #pragma unroll
@@ -268,10 +288,10 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
                 }
             }
             // every commit has landed before the CTA leaves (no arrive is left pending)
-            for (int b = 0; b < 2; ++b) {
+            for (int b = 0; b < NS; ++b)
                 if (n_empty[b]) oz_wait(smem_addr(&empty[b]), (uint32_t)((n_empty[b] - 1) & 1), kOzSpin);
+            for (int b = 0; b < 2; ++b)
                 if (n_tfull[b]) oz_wait(smem_addr(&tfull[b]), (uint32_t)((n_tfull[b] - 1) & 1), kOzSpin);
-            }
         }
         __syncwarp();
     } else {
@@ -320,8 +340,8 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
             if (failed) break;
             double2 nxt[kItems];
             if (gs + 1 < nstages) load(gs + 1, nxt);
-            const int sb = (int)(gs & 1);
-            if (gs >= 2 && !oz_wait(smem_addr(&empty[sb]), (uint32_t)(((gs >> 1) - 1) & 1), spin)) {
+            const int sb = (int)(gs % NS);
+            if (gs >= NS && !oz_wait(smem_addr(&empty[sb]), (uint32_t)(((gs / NS) - 1) & 1), spin)) {
                 failed = 1;
                 break;
             }
@@ -345,18 +365,25 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
                     d[7] = digit_pair<7>(w0, w1);
                     const int c = cc[j];
                     if (isv) {   // unused columns of an octet land in unused A rows
-                        unsigned char* base = sp + (c >> 5) * 2 * C::kTile + op_off<SBO>(c & 31, kk);
+                        if (G == 0) {   // row t 16 + c of the one tile
+                            unsigned char* base = sp + op_off<SBO>(c, kk);
 #pragma unroll
-                        for (int t = 0; t < oz::kDigits; ++t)
-                            *reinterpret_cast<uint32_t*>(base + (t >> 2) * C::kTile + (t & 3) * 4 * SBO) = d[t];
+                            for (int t = 0; t < oz::kDigits; ++t)
+                                *reinterpret_cast<uint32_t*>(base + t * 2 * SBO) = d[t];
+                        } else {        // tile 2 (c / 32) + t / 4, row (t % 4) 32 + c % 32
+                            unsigned char* base = sp + (c >> 5) * 2 * C::kTile + op_off<SBO>(c & 31, kk);
+#pragma unroll
+                            for (int t = 0; t < oz::kDigits; ++t)
+                                *reinterpret_cast<uint32_t*>(base + (t >> 2) * C::kTile + (t & 3) * 4 * SBO) = d[t];
+                        }
                         if (sym && cv[j]) {
-                            unsigned char* bb = sp + 2 * G * C::kTile;
+                            unsigned char* bb = sp + C::kAT * C::kTile;
 #pragma unroll
                             for (int t = 0; t < oz::kDigits; ++t)
                                 *reinterpret_cast<uint32_t*>(bb + op_off<SBO>(t * KB + c, kk)) = d[t];
                         }
                     } else if (cv[j]) {
-                        unsigned char* base = sp + 2 * G * C::kTile;
+                        unsigned char* base = sp + C::kAT * C::kTile;
 #pragma unroll
                         for (int t = 0; t < oz::kDigits; ++t)
                             *reinterpret_cast<uint32_t*>(base + op_off<SBO>(t * KB + c, kk)) = d[t];
@@ -366,8 +393,6 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) bar_arrive(&full[sb]);
-#pragma unroll
-            for (int j = 0; j < kItems; ++j) cur[j] = nxt[j];
             const int sic = (int)(gs % C::kStagesPerChunk);
             if (sic == C::kStagesPerChunk - 1 || gs == nstages - 1) {   // drain the chunk's exact sums
                 const int chunk = (int)(gs / C::kStagesPerChunk), tb = chunk & 1;
@@ -378,16 +403,22 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t tb0 = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tb * C::kBuf);
                 if (drains) {
+                    if (G == 0) {
+                        drain_tile<KB, kN0>(tb0, ta, tmin, acc[0]);
+                    } else {
 #pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        if (ta < 4) drain_tile<KB, kN0>(tb0 + (uint32_t)(g * kGroupCols), ta, acc[g]);
-                        else drain_tile<KB, kN1>(tb0 + (uint32_t)(g * kGroupCols + kN0), ta, acc[g]);
+                        for (int g = 0; g < NG; ++g) {
+                            if (ta < 4) drain_tile<KB, kN0>(tb0 + (uint32_t)(g * kGroupCols), ta, ta, acc[g]);
+                            else drain_tile<KB, kN1>(tb0 + (uint32_t)(g * kGroupCols + kN0), ta, ta, acc[g]);
+                        }
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 __syncwarp();
                 if (lane == 0) bar_arrive(&tempty[tb]);
             }
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) cur[j] = nxt[j];
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -399,17 +430,17 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
     // stage buffers are free), summed over the digits, then added
     // into the 128-bit accumulators: atomicAdd of the low words, whose old value gives the
     // carry, then of the high words (addition of integers is exact and order-free)
-    oz::i128* part = reinterpret_cast<oz::i128*>(smem);   // [8 digits][32 G][KB]
+    oz::i128* part = reinterpret_cast<oz::i128*>(smem);   // [8 digits][NG CP columns][KB]
     if (drains)
 #pragma unroll
-        for (int g = 0; g < G; ++g)
+        for (int g = 0; g < NG; ++g)
 #pragma unroll
-            for (int b = 0; b < KB; ++b) part[(ta * 32 * G + g * 32 + lane) * KB + b] = acc[g][b] >> (8 * ta);
+            for (int b = 0; b < KB; ++b) part[(ta * NG * CP + g * CP + al_) * KB + b] = acc[g][b] >> (8 * ta);
     __syncthreads();
     for (int e = tid; e < ka * KB; e += C::kThreads) {
         const int a = e % ka, b = e / ka;
         oz::i128 s = 0;
-        for (int k = 0; k < oz::kDigits; ++k) s += part[(k * 32 * G + a) * KB + b];
+        for (int k = 0; k < oz::kDigits; ++k) s += part[(k * NG * CP + a) * KB + b];
         const unsigned long long lo = (unsigned long long)(uint64_t)s;
         const unsigned long long hi = (unsigned long long)(uint64_t)((oz::u128)s >> 64);
         const unsigned long long old = atomicAdd(sc.acc + 2 * e, lo);
@@ -497,12 +528,12 @@ bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsig
                     cudaStream_t stream) {
     if (ka < 1 || ka > kMaxCols || kb < 1 || kb > kMaxS + 1 || n < 1 || n > ((int64_t)1 << 27) || !sc.acc) return false;
     if (((uintptr_t)V & 7) || ((uintptr_t)Y & 7)) return false;
-    const bool one = ka <= 32;
     const int sym = (V == Y && ldv == ldy && ka == kb) ? 1 : 0;   // V^T V: split each column once
     switch (kb) {
 #define SSTEP_OZ_CASE(KB)                                                                                       \
     case KB:                                                                                                    \
-        if (one) launch_oz<1, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym);    \
+        if (ka <= 16) launch_oz<0, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym); \
+        else if (ka <= 32) launch_oz<1, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym); \
         else launch_oz<2, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym);        \
         return true;
         SSTEP_OZ_CASE(1)
@@ -528,11 +559,12 @@ bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsig
 // scales, T'[a][j] = 2^(ea - kFrac) T[a][j], so V_ra T_aj = q_ra T'_aj, and every column j
 // of T' is in fixed point relative to its own bound: T'_aj = p_aj 2^(Fj - kFrac). Then
 // P_rj = 2^(Fj - kFrac) sum_a q_ra p_aj, an exact integer sum of digit products. The A
-// operand holds V's digit planes (M = 128 rows, K = digit x column), the B operand T's
-// digits with the digit order reversed, so that one digit diagonal ta + tb = d is one
-// contiguous K window of both: each of the 9 kept diagonals is one FP32 accumulator in
-// tensor memory, exact (at most 8 x 32 products of 2^14). The epilogue warps combine the
-// diagonals into a 128-bit integer (Horner in 256), round P once and form Y - P in FP64.
+// operand holds V's digit planes (M = 128 rows, K = digit plane x column), the B operand a
+// banded arrangement of T's digits: row (j, d), K position (ta, a) holds digit d - ta of
+// T'_aj (zero outside 0..7), so one MMA over the whole K gives, for every output j and
+// digit diagonal d = ta + tb <= 8, the exact FP32 sum over the digit pairs of that
+// diagonal (at most 8 x 32 products of 2^14). The epilogue combines the 9 diagonals into
+// a 128-bit integer (Horner in 256), rounds P once and forms Y - P in FP64.
 namespace sstep {
 namespace {
 
@@ -543,15 +575,20 @@ constexpr int kUpThreads = (kUpSplitWarps + 1) * 32;
 
 constexpr int kUpRows = 128;                      // rows per tile (MMA M)
 constexpr int kUpDiags = oz::kCut + 1;            // kept digit diagonals
-constexpr uint32_t kUpBuf = 256;                  // tensor-memory columns per accumulator buffer
+constexpr uint32_t kUpBuf = 128;                  // tensor-memory columns per accumulator buffer
 
-template <int KAP>
+// B rows: (output j, diagonal d) with d fastest, padded to a multiple of 16 (the MMA N)
+__host__ __device__ constexpr int up_n(int kbo) { return (kUpDiags * kbo + 15) / 16 * 16; }
+
+template <int KAP, int KBO>
 struct UpCfg {
     static constexpr int kK = oz::kDigits * KAP;  // K of one row: 8 digit planes of KAP columns
     static constexpr int kSbo = KAP * 128;        // bytes between 8-row groups
+    static constexpr int kN = up_n(KBO);          // MMA N
     static constexpr int kA = kUpRows * kK * 2;   // one A buffer (FP16)
-    static constexpr int kB = 16 * kK * 2;        // B: 16 rows (outputs, padded)
+    static constexpr int kB = kN * kK * 2;        // B: kN rows
     static constexpr int kSmem = 2 * kA + kB;
+    static_assert(kN <= (int)kUpBuf, "accumulator buffer");
 };
 
 __device__ __forceinline__ uint64_t op_desc_rt(uint32_t addr, int sbo) {
@@ -565,7 +602,7 @@ __global__ void __launch_bounds__(kUpThreads, 1)
                      double* Y, int64_t ldy, int j0, const double* __restrict__ T, int ldt, unsigned* bout,
                      unsigned* bout2, int nb2, const unsigned* bcopy_src, unsigned* bcopy_dst, const SolverState* st,
                      int gate, long spin, unsigned* err) {
-    using C = UpCfg<KAP>;
+    using C = UpCfg<KAP, KBO>;
     constexpr int SBO = C::kSbo;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[2], empty[2], tfull[2], tempty[2];
@@ -583,7 +620,7 @@ __global__ void __launch_bounds__(kUpThreads, 1)
     unsigned char* Bop = smem + 2 * C::kA;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
-                     "r"(512));
+                     "r"(2 * kUpBuf));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -616,15 +653,20 @@ __global__ void __launch_bounds__(kUpThreads, 1)
     __syncthreads();
     if (tid < KBO) fexp[tid] = (int)oz::bound_exponent(fmax[tid]);
     __syncthreads();
-    // B: row j, K (7 - tb) KAP + a = digit tb of T'_aj (digit order reversed)
+    // B: row (j, d), K = (digit plane ta of V, column a): digit d - ta of T'_aj where
+    // 0 <= d - ta <= 7, zero elsewhere, so one MMA over all of K sums each digit diagonal d
     for (int e = tid; e < ka * KBO; e += kUpThreads) {
         const int a = e % ka, j = e / ka;
         const uint64_t bits = (uint64_t)__double_as_longlong(tp[e]);
         const uint64_t w = oz::fixed_biased((uint32_t)bits, (uint32_t)(bits >> 32), (uint32_t)fexp[j]);
 #pragma unroll
-        for (int tb = 0; tb < oz::kDigits; ++tb)
-            *reinterpret_cast<__half*>(Bop + op_off<SBO>(j, (oz::kDigits - 1 - tb) * KAP + a)) =
-                __int2half_rn(oz::digit(w, tb));
+        for (int tb = 0; tb < oz::kDigits; ++tb) {
+            const __half e16 = __int2half_rn(oz::digit(w, tb));
+#pragma unroll
+            for (int ta = 0; ta < oz::kDigits; ++ta)
+                if (ta + tb <= oz::kCut)
+                    *reinterpret_cast<__half*>(Bop + op_off<SBO>(j * kUpDiags + ta + tb, ta * KAP + a)) = e16;
+        }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -651,30 +693,20 @@ __global__ void __launch_bounds__(kUpThreads, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t ab = sbase + (uint32_t)(b * C::kA), bb = sbase + (uint32_t)(2 * C::kA);
-#pragma unroll 1
-                for (int d = 0; d < kUpDiags; ++d) {
-                    const int lo = d > oz::kDigits - 1 ? d - (oz::kDigits - 1) : 0;
-                    const int hi = d < oz::kDigits - 1 ? d : oz::kDigits - 1;
-                    const int u0 = oz::kDigits - 1 - d + lo;
-                    const uint32_t dt = tmem + (uint32_t)b * kUpBuf + (uint32_t)(d * 16);
-                    for (int ta = lo; ta <= hi; ++ta)
+                const uint32_t dt = tmem + (uint32_t)b * kUpBuf;
 #pragma unroll
-                        for (int ks = 0; ks < KAP / 16; ++ks) {
-                            const uint32_t accf = (ta > lo || ks > 0) ? 1u : 0u;
-                            const uint32_t aa = ab + (uint32_t)(ta * KAP * 16 + ks * 256);
-                            const uint32_t ba = bb + (uint32_t)((u0 + ta - lo) * KAP * 16 + ks * 256);
-                            mma_f16(dt, op_desc<SBO>(aa), op_desc<SBO>(ba), oz_idesc(16), accf);
-                        }
-                }
+                for (int ks = 0; ks < C::kK / 16; ++ks)
+                    mma_f16(dt, op_desc<SBO>(ab + (uint32_t)(ks * 256)), op_desc<SBO>(bb + (uint32_t)(ks * 256)),
+                            oz_idesc(C::kN), ks > 0 ? 1u : 0u);
                 mma_commit(&empty[b]);
                 ++n_empty[b];
                 mma_commit(&tfull[b]);
                 ++n_tfull[b];
             }
-            for (int b = 0; b < 2; ++b) {
+            for (int b = 0; b < 2; ++b)
                 if (n_empty[b]) oz_wait(smem_addr(&empty[b]), (uint32_t)((n_empty[b] - 1) & 1), kOzSpin);
+            for (int b = 0; b < 2; ++b)
                 if (n_tfull[b]) oz_wait(smem_addr(&tfull[b]), (uint32_t)((n_tfull[b] - 1) & 1), kOzSpin);
-            }
         }
         __syncwarp();
     } else {
@@ -728,25 +760,32 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             const int64_t r = (t0 + lt) * kUpRows + q * 32 + lane;
             if (!oz_wait(smem_addr(&tfull[b]), (uint32_t)((lt >> 1) & 1), spin)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            long long Ql[H];   // Horner in 64 bits while it fits (5 diagonals: < 2^55)
+            // Q = sum_d S_d 256^(8 - d) = Qh 2^32 + Ql: Horner in 64 bits over the diagonals
+            // 0..4 (Qh < 2^54) and 5..8 (Ql < 2^47), then one 128-bit step
+            long long Qh[H], Ql[H];
             oz::i128 Q[H];
 #pragma unroll
-            for (int j = 0; j < H; ++j) Ql[j] = 0;
-            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * kUpBuf;
+            for (int j = 0; j < H; ++j) Qh[j] = Ql[j] = 0;
+            // columns (j, d) = 9 j + d of this thread's outputs, read 16 at a time from the
+            // aligned column c0 below the first one (compile-time offsets)
+            constexpr int c0 = (kUpDiags * jo) / 16 * 16;
+            constexpr int c1 = kUpDiags * (jo + H);
+            constexpr int NR = (c1 - c0 + 15) / 16 * 16;
+            uint32_t rv[NR];
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * kUpBuf + (uint32_t)c0;
+            tmem_ld<NR>(ta, rv);
 #pragma unroll
             for (int d = 0; d < kUpDiags; ++d) {
-                uint32_t rv[16];
-                tmem_ld<16>(ta + (uint32_t)(d * 16), rv);
 #pragma unroll
                 for (int j = 0; j < H; ++j) {
-                    const long long S = jo + j < 16 ? __float2int_rn(__uint_as_float(rv[(jo + j) & 15])) : 0;
-                    if (d < 5) Ql[j] = Ql[j] * 256 + S;
-                    else {
-                        if (d == 5) Q[j] = (oz::i128)Ql[j];
-                        Q[j] = (Q[j] << 8) + (oz::i128)S;
-                    }
+                    const int col = kUpDiags * (jo + j) + d - c0;
+                    const long long S = (jo + j < KBO && col < NR) ? __float2int_rn(__uint_as_float(rv[col])) : 0;
+                    if (d < 5) Qh[j] = Qh[j] * 256 + S;
+                    else Ql[j] = Ql[j] * 256 + S;
                 }
             }
+#pragma unroll
+            for (int j = 0; j < H; ++j) Q[j] = ((oz::i128)Qh[j] << 32) + (oz::i128)Ql[j];
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) bar_arrive(&tempty[b]);
@@ -833,7 +872,7 @@ __global__ void __launch_bounds__(kUpThreads, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kUpBuf));
     if (failed && tid == 0) {
         if (err) atomicExch(err, 1u);
         if (st) {
@@ -849,7 +888,7 @@ template <int KAP, int KBO>
 void launch_up(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, double* Y, int64_t ldy, int j0,
                const double* T, int ldt, unsigned* bout, unsigned* bout2, int nb2, const unsigned* bsrc,
                unsigned* bdst, const SolverState* st, int gate, cudaStream_t stream, unsigned* err) {
-    using C = UpCfg<KAP>;
+    using C = UpCfg<KAP, KBO>;
     static bool attr[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
