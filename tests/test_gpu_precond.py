@@ -8,6 +8,7 @@ from oracle import sstep as osstep
 from oracle import stencil as ostencil
 from paper_2001_04886_gb300 import inputs
 from tests.gpu_util import dev, to_dev, torch
+from tests.parity_bars import first_block_tol
 
 import paper_2001_04886_gb300 as pkg
 
@@ -69,11 +70,11 @@ def test_preconditioned_solve_matches_oracle(shape, beta, s, m, basis):
     x = xd.cpu().numpy()
     assert r["status"] == 0 and ref["status"] == 0
     assert r["cycles"] == ref["cycles"] and r["matvecs"] == ref["matvecs"] and r["iters"] == ref["iters"]
-    # first s estimates: two FP64 implementations differ by about u cond(W_1) (the monomial
-    # first block of A M^-1; at s = 8 cond ~ 1e10)
+    # first s estimates: implementations that round W_1 differently differ by a few
+    # u cond(W_1) (the monomial first block of A M^-1; at s = 8 cond ~ 1e10)
     tr = {}
     osstep.sstep_gmres(Ao, f, np.zeros(Ao.n), s, m, 1e-30, 1.0, 1, trace=tr, precond=P)
-    htol = max(1e-10, 2.0 ** -53 * float(np.linalg.cond(tr["W"][0])))
+    htol = first_block_tol(np.linalg.cond(tr["W"][0]))
     h, hr = np.array(r["history"][1 : s + 1]), np.array(ref["history"][1 : s + 1])
     assert np.max(np.abs(h - hr) / hr) <= htol
     # the solution: to 1e-8, or to u cond(W_1) when the first block is worse conditioned
