@@ -166,9 +166,10 @@ int sstep_set_tc_wait_limit(long limit);
  * all device memory, so that a library allocating behind their back would break
  * their accounting or fail. The paper has no counterpart; this is a property of the
  * library's interface, not of the method.
- *   - Allocates nothing: the scratch is a fixed 700,672-byte array in the library's
- *     device image, present on every GPU that loads the library until the process
- *     exits. ka <= SSTEP_MAX_COLS and kb <= SSTEP_MAX_S + 1, else SSTEP_ERR_ARG.
+ *   - Allocates nothing: the scratch is a fixed 884,992-byte array in the library's
+ *     device image (sized for devices of up to 192 multiprocessors), present on every
+ *     GPU that loads the library until the process exits. ka <= SSTEP_MAX_COLS,
+ *     kb <= SSTEP_MAX_S + 1 and at most 192 multiprocessors, else SSTEP_ERR_ARG.
  *   - The first call on each device looks up the array's device address (with that
  *     device current); make that first call before any stream capture begins. Later
  *     calls on a stream that is not being captured look the address up again, so a

@@ -141,6 +141,8 @@ __device__ __forceinline__ bool publish_partial(const double* red, int nv, doubl
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 
 // ------------------------------------------------------------------ launch helpers
+int device_sms();   // multiprocessors of the current device, queried once per device (ozaki.cu)
+
 inline int grid_for(int64_t n, int max_ctas) {
     int64_t need = (n + kThreads - 1) / kThreads;
     if (need < 1) need = 1;

@@ -9,12 +9,13 @@
 
 namespace sstep {
 
-constexpr int kMaxCtas = 152 * 8;      // 8 CTAs of 256 threads per SM at most
+// 8 CTAs of 256 threads per SM at most, on the current device
+static int max_ctas() { return 8 * device_sms(); }
 constexpr int kGramKA = 8;             // V columns per Gram CTA (grid.y splits ka)
 constexpr int kMaxNV = kGramKA * (kMaxS + 1);   // largest per-CTA partial vector
 
-int fp64_gram_partials_doubles() { return kMaxCtas * kMaxNV; }
-int max_partials_doubles() { return std::max(std::max(kMaxCtas * kMaxNV, oz_partials_doubles()), kOzAccWords); }
+int fp64_gram_partials_doubles() { return max_ctas() * kMaxNV; }
+int max_partials_doubles() { return std::max(std::max(max_ctas() * kMaxNV, oz_partials_doubles()), kOzAccWords); }
 
 // ================================================================== stencil sweep
 __device__ __forceinline__ void grid_xyz(const StencilDesc& A, int64_t p, int& x, int& y, int& z) {
@@ -212,7 +213,7 @@ void launch_stencil(const StencilDesc& A, const double* v, double fy, double* y,
                     const double* u, unsigned* ybnd, unsigned* wbnd, unsigned* ybnd2, unsigned* wbnd2) {
     const int tiles = ((A.nx + 31) / 32) * ((A.ny + 7) / 8);
     // z chunks: about one wave of 8 CTAs per SM, at least one plane per chunk
-    int chunks = kMaxCtas / tiles;
+    int chunks = max_ctas() / tiles;
     chunks = chunks < 1 ? 1 : (chunks > A.nz ? A.nz : chunks);
     const int zchunk = (A.nz + chunks - 1) / chunks;
     chunks = (A.nz + zchunk - 1) / zchunk;
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(kThreads) residual_kernel(StencilDesc A, const
 
 void launch_residual(const StencilDesc& A, const double* f, const double* x, double* out, Scratch sc,
                      const Epi& epi, int gate, cudaStream_t stream) {
-    int grid = grid_for(A.n, kMaxCtas / 2);
+    int grid = grid_for(A.n, max_ctas() / 2);
     residual_kernel<<<grid, kThreads, 0, stream>>>(A, f, x, out, sc, epi, gate);
 }
 
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(int64_t n, const double*
 void launch_gram(int64_t n, const double* V, int64_t ldv, int ka, const double* Y, int64_t ldy, int kb,
                  int win_s, Scratch sc, const Epi& epi, int gate, cudaStream_t stream) {
     const int gy = (ka + kGramKA - 1) / kGramKA;
-    int gx = grid_for(n, kMaxCtas / gy > 0 ? kMaxCtas / gy : 1);
+    int gx = grid_for(n, max_ctas() / gy > 0 ? max_ctas() / gy : 1);
     dim3 grid(gx, gy);
     switch (kb) {
 #define SSTEP_GRAM_CASE(KB) \
@@ -436,7 +437,7 @@ void launch_update(int64_t n, const double* V, int64_t ldv, int ka, const double
                    double* Yout, int64_t ldo, int kb, int j0, const double* T, int ldt, double sgn,
                    bool gram, Scratch sc, const Epi& epi, int gate, cudaStream_t stream, unsigned* bnd,
                    int bnd_hi) {
-    int grid = grid_for(n, kMaxCtas / 2);
+    int grid = grid_for(n, max_ctas() / 2);
     switch (kb) {
 #define SSTEP_UPD_CASE(KB)                                                                                \
     case KB:                                                                                              \
@@ -497,7 +498,7 @@ __global__ void __launch_bounds__(kThreads) omin_xr_kernel(int64_t n, const doub
 
 void launch_omin_xr(int64_t n, const double* P, const double* AP, int64_t ld, int s, double* x, double* r,
                     Scratch sc, const Epi& epi, int gate, cudaStream_t stream) {
-    int grid = grid_for(n, kMaxCtas / 2);
+    int grid = grid_for(n, max_ctas() / 2);
     switch (s) {
 #define SSTEP_XR_CASE(S) \
     case S: omin_xr_kernel<S><<<grid, kThreads, 0, stream>>>(n, P, AP, ld, x, r, sc, epi, gate); break;
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(kThreads) omin_pupdate_kernel(int64_t n, const
 void launch_omin_pupdate(int64_t n, const double* r, const double* AR, const double* Ppanel,
                          const double* APpanel, int64_t ld, int s, double sigma, Scratch sc, const Epi& epi,
                          int gate, cudaStream_t stream) {
-    int grid = grid_for(n, kMaxCtas / 2);
+    int grid = grid_for(n, max_ctas() / 2);
     switch (s) {
 #define SSTEP_PU_CASE(S)                                                                                 \
     case S:                                                                                              \
@@ -641,7 +642,7 @@ __global__ void convdiff_fields_kernel(const double* __restrict__ beta, double h
 }
 
 void launch_convdiff_fields(const double* beta, double h, int64_t n, double* out, cudaStream_t stream) {
-    convdiff_fields_kernel<<<grid_for(n, kMaxCtas), kThreads, 0, stream>>>(beta, h, n, out);
+    convdiff_fields_kernel<<<grid_for(n, max_ctas()), kThreads, 0, stream>>>(beta, h, n, out);
 }
 
 // ================================================================== least squares solve

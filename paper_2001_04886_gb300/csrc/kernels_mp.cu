@@ -23,10 +23,11 @@
 
 namespace sstep {
 
-constexpr int kMpRedCtas = 152 * 2;    // reductions with many accumulators: many rows per thread
-constexpr int kMpCtas = 152 * 4;       // light kernels
+// grid caps per multiprocessor of the current device
+static int mp_red_ctas() { return 2 * device_sms(); }   // reductions with many accumulators: many rows per thread
+static int mp_ctas() { return 4 * device_sms(); }       // light kernels
 constexpr int kRenorm = 8;             // rows between accumulator renormalisations
-constexpr int kMaxCtasMp = 152 * 8;    // grid bound of the reductions (the partials buffer size)
+static int max_ctas_mp() { return 8 * device_sms(); }   // grid bound of the reductions (the partials buffer size)
 constexpr int kChunk = 8;              // basis columns loaded together in the projection
 
 // ------------------------------------------------------------------ storage / arithmetic traits
@@ -153,7 +154,7 @@ int resident_ctas(const void* kernel) {
     int per_sm = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = device_sms();
     cudaGetLastError();
     const int r = per_sm * sms;
     cache[{kernel, dev}] = r;
@@ -239,7 +240,7 @@ void mp_launch_stencil(const StencilDesc& A, const void* v, double fy, void* y, 
     using T = typename Mode<P>::T;
     const int tiles = ((A.nx + 31) / 32) * ((A.ny + 7) / 8);
     // z chunks: about one wave of 8 CTAs per SM, at least one plane per chunk
-    int chunks = (152 * 8) / tiles;
+    int chunks = (8 * device_sms()) / tiles;
     chunks = chunks < 1 ? 1 : (chunks > A.nz ? A.nz : chunks);
     const int zchunk = (A.nz + chunks - 1) / chunks;
     chunks = (A.nz + zchunk - 1) / zchunk;
@@ -375,7 +376,7 @@ bool mp_launch_powers_fused(const StencilDesc& A, const void* u, void* Y, int64_
     const int tiles = ((A.nx + kTile - 1) / kTile) * ((A.ny + kTile - 1) / kTile);
     // z chunks: enough CTAs to fill the GPU, no thinner than S planes (the recomputed halo)
     int zchunk = A.nz;
-    while (zchunk > s && (int64_t)tiles * ((A.nz + zchunk - 1) / zchunk) < 152 * 3) zchunk = (zchunk + 1) / 2;
+    while (zchunk > s && (int64_t)tiles * ((A.nz + zchunk - 1) / zchunk) < 3 * device_sms()) zchunk = (zchunk + 1) / 2;
     dim3 grid(tiles, (A.nz + zchunk - 1) / zchunk);
     switch (s) {
 #define SSTEP_PF(S)                                                                                             \
@@ -430,7 +431,7 @@ template <int P>
 void mp_launch_residual(const StencilDesc& A, const double* f, const double* x, void* out, Scratch sc,
                         const Epi& epi, int gate, cudaStream_t stream) {
     using T = typename Mode<P>::T;
-    int grid = grid_for(A.n, 152 * 4);
+    int grid = grid_for(A.n, 4 * device_sms());
     mp_residual_kernel<P><<<grid, kThreads, 0, stream>>>(A, f, x, (T*)out, sc, epi, gate);
 }
 
@@ -505,7 +506,7 @@ void mp_launch_gram(int64_t n, const void* V, int64_t ldv, int ka, const void* Y
     using T = typename Mode<P>::T;
     const int KAc = kb <= 4 ? 8 : 4;   // V columns per CTA, keeping the accumulators in registers
     const int gy = (ka + KAc - 1) / KAc;
-    int gx = grid_for((n + 1) / 2, kMpRedCtas * 2 / gy > 0 ? kMpRedCtas * 2 / gy : 1);
+    int gx = grid_for((n + 1) / 2, mp_red_ctas() * 2 / gy > 0 ? mp_red_ctas() * 2 / gy : 1);
     dim3 grid(gx, gy);
     const T* Vp = (const T*)V;
     const T* Yp = (const T*)Y;
@@ -830,7 +831,7 @@ void mp_launch_update(int64_t n, const void* V, int64_t ldv, int ka, const void*
     const Tt* Yi = (const Tt*)Yin;
     Tt* Yo = (Tt*)Yout;
     if (!gram) {
-        int grid = grid_for((n + 1) / 2, kMpCtas);
+        int grid = grid_for((n + 1) / 2, mp_ctas());
         switch (kb) {
 #define SSTEP_MPP(KB)                                                                                             \
     case KB:                                                                                                      \
@@ -858,7 +859,7 @@ void mp_launch_update(int64_t n, const void* V, int64_t ldv, int ka, const void*
         switch (kb) {
 #define SSTEP_MPS(KB)                                                                                             \
     case KB: {                                                                                                    \
-        const int wave = std::min(kMaxCtasMp, resident_ctas((const void*)mp_symgram_kernel<P, KB>));             \
+        const int wave = std::min(max_ctas_mp(), resident_ctas((const void*)mp_symgram_kernel<P, KB>));             \
         dim3 grid(grid_for((n + 1) / 2, wave / 2 > 0 ? wave / 2 : 1), 2);                                         \
         mp_symgram_kernel<P, KB><<<grid, kThreads, 0, stream>>>(n, Yo, ldo, sc, epi, gate);                       \
     } break;
@@ -874,15 +875,15 @@ void mp_launch_update(int64_t n, const void* V, int64_t ldv, int ka, const void*
         }
         return;
     }
-    // one wave of CTAs (the partials buffer holds kMaxCtas x kMaxNV doubles)
+    // one wave of CTAs (the partials buffer holds 8 CTAs per multiprocessor x kMaxNV doubles)
     switch (kb) {
         case 1: {
-            const int grid = grid_for((n + 1) / 2, std::min(kMaxCtasMp, resident_ctas((const void*)mp_update_kernel<P, 1, true>)));
+            const int grid = grid_for((n + 1) / 2, std::min(max_ctas_mp(), resident_ctas((const void*)mp_update_kernel<P, 1, true>)));
             mp_update_kernel<P, 1, true><<<grid, kThreads, 0, stream>>>(n, Vp, ldv, ka, Yi, ldy, Yo, ldo, j0, T, ldt, sgn,
                                                                         sc, epi, gate);
         } break;
         case 2: {
-            const int grid = grid_for((n + 1) / 2, std::min(kMaxCtasMp, resident_ctas((const void*)mp_update_kernel<P, 2, true>)));
+            const int grid = grid_for((n + 1) / 2, std::min(max_ctas_mp(), resident_ctas((const void*)mp_update_kernel<P, 2, true>)));
             mp_update_kernel<P, 2, true><<<grid, kThreads, 0, stream>>>(n, Vp, ldv, ka, Yi, ldy, Yo, ldo, j0, T, ldt, sgn,
                                                                         sc, epi, gate);
         } break;
@@ -928,7 +929,7 @@ template <int P>
 void mp_launch_axpy(int64_t n, const void* V, int64_t ldv, double* x, const Epi& epi, int gate,
                     cudaStream_t stream) {
     using T = typename Mode<P>::T;
-    int grid = grid_for(n, kMpCtas * 2);
+    int grid = grid_for(n, mp_ctas() * 2);
     mp_axpy_kernel<P><<<grid, kThreads, 0, stream>>>(n, (const T*)V, ldv, x, epi, gate);
 }
 
@@ -942,7 +943,7 @@ __global__ void split_fields_kernel(const double* __restrict__ src, float2* __re
 }
 
 void launch_split_fields(const double* src, float2* dst, int64_t n, cudaStream_t stream) {
-    split_fields_kernel<<<grid_for(n, 152 * 8), kThreads, 0, stream>>>(src, dst, n);
+    split_fields_kernel<<<grid_for(n, 8 * device_sms()), kThreads, 0, stream>>>(src, dst, n);
 }
 
 // ------------------------------------------------------------------ instantiations

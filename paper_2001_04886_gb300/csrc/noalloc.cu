@@ -16,9 +16,12 @@ using namespace sstep;
 namespace {
 
 // 256 bytes for the arrival counter, then the per-CTA partials of the largest
-// Gram grid (1216 CTAs x 8 x 9 doubles): 700,672 bytes in all.
+// Gram grid on a device of up to 192 multiprocessors (8 CTAs per multiprocessor,
+// 8 x 9 doubles each): 884,992 bytes in all. A device with more multiprocessors
+// is refused (SSTEP_ERR_ARG).
 constexpr size_t kCounterBytes = 256;
-constexpr size_t kPartialDoubles = 152 * 8 * 8 * (SSTEP_MAX_S + 1);
+constexpr size_t kMaxSms = 192;
+constexpr size_t kPartialDoubles = kMaxSms * 8 * 8 * (SSTEP_MAX_S + 1);
 constexpr size_t kScratchBytes = kCounterBytes + kPartialDoubles * sizeof(double);
 
 static __device__ __align__(256) unsigned char g_gram_scratch[kScratchBytes];

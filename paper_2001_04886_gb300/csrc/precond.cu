@@ -113,23 +113,23 @@ __global__ void __launch_bounds__(kThreads) add_kernel(double* __restrict__ x, c
 }
 
 void launch_rbilu_setup(const StencilDesc& A, double* dt, cudaStream_t s) {
-    rbilu_setup_kernel<<<grid_for(A.n, 152 * 8), kThreads, 0, s>>>(A, dt);
+    rbilu_setup_kernel<<<grid_for(A.n, 8 * device_sms()), kThreads, 0, s>>>(A, dt);
 }
 
 void launch_rbilu_apply(const StencilDesc& A, const double* dt, const double* v, double* w, const SolverState* st,
                         int gate, cudaStream_t s) {
-    const int grid = grid_for(A.n, 152 * 8);
+    const int grid = grid_for(A.n, 8 * device_sms());
     rbilu_black_kernel<<<grid, kThreads, 0, s>>>(A, dt, v, w, st, gate);
     rbilu_red_kernel<<<grid, kThreads, 0, s>>>(A, dt, v, w, st, gate);
 }
 
 void launch_scale_copy(const double* src, double* dst, int64_t n, const double* dscale, const SolverState* st,
                        int gate, cudaStream_t s) {
-    scale_copy_kernel<<<grid_for(n, 152 * 8), kThreads, 0, s>>>(src, dst, n, dscale, st, gate);
+    scale_copy_kernel<<<grid_for(n, 8 * device_sms()), kThreads, 0, s>>>(src, dst, n, dscale, st, gate);
 }
 
 void launch_add(double* x, const double* d, int64_t n, const SolverState* st, int gate, cudaStream_t s) {
-    add_kernel<<<grid_for(n, 152 * 8), kThreads, 0, s>>>(x, d, n, st, gate);
+    add_kernel<<<grid_for(n, 8 * device_sms()), kThreads, 0, s>>>(x, d, n, st, gate);
 }
 
 }  // namespace sstep

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_kernel(StencilDesc A, const d
 
 void launch_jacobi(const StencilDesc& A, const double* f, const double* x, double* y, double omega,
                    cudaStream_t stream) {
-    const int grid = grid_for(A.n, 152 * 8);
+    const int grid = grid_for(A.n, 8 * device_sms());
     jacobi_kernel<<<grid, kThreads, 0, stream>>>(A, f, x, y, omega);
 }
 
@@ -61,7 +61,7 @@ int launch_jacobi_batched(const SmoothSys* sys, int nsys, int64_t nmax, int swee
                           cudaStream_t stream) {
     if (nsys < 1 || nsys > 65535) return -1;
     int gx = (int)((nmax + kThreads - 1) / kThreads);
-    const int cap = (152 * 8 + nsys - 1) / nsys;   // about one wave over all systems
+    const int cap = (8 * device_sms() + nsys - 1) / nsys;   // about one wave over all systems
     gx = gx < 1 ? 1 : (gx > cap ? (cap < 1 ? 1 : cap) : gx);
     for (int t = 0; t < sweeps; ++t)
         jacobi_batched_kernel<<<dim3(gx, nsys), kThreads, 0, stream>>>(sys, omega, t & 1);

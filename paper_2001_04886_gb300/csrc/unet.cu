@@ -27,6 +27,10 @@
 
 #include "../../include/sstep.h"
 
+namespace sstep {
+int device_sms();   // multiprocessors of the current device (ozaki.cu)
+}
+
 namespace unet {
 
 constexpr int kT = 256;
@@ -982,7 +986,7 @@ __global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __res
 
 inline int blocks_for(int64_t n) {
     int64_t b = (n + kT - 1) / kT;
-    return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+    return (int)(b < 16 * sstep::device_sms() ? (b < 1 ? 1 : b) : 16 * sstep::device_sms());
 }
 
 // ------------------------------------------------------------------ the network
