@@ -79,6 +79,76 @@ class Stencil:
         return float(tot.max())
 
 
+class NaturalILU0:
+    """ILU(0) of a stencil operator in the natural (lexicographic, x fastest) ordering: the
+    preconditioner of the paper's tables (Sec. 5: right preconditioning with ILU(0)).
+
+    ILU(0) keeps the sparsity of A, so L U equals A on that sparsity. For a (2d+1)-point
+    stencil this fixes the factors row by row in the natural order:
+      * U has A's upper part off the diagonal (U[p, p + e_d] = A[p, p + e_d]) and the
+        pivots d[p] on it;
+      * L is unit lower triangular with L[p, p - e_d] = A[p, p - e_d] / d[p - e_d];
+      * d[p] = A[p, p] - sum_d A[p, p - e_d] A[p - e_d, p] / d[p - e_d], the diagonal of
+        (L U)[p, p] matched to A[p, p]. The other products L[p, p - e_d] U[p - e_d, q] land
+        at q = p - e_d + e_d' (d != d'), outside the sparsity: that is the dropped fill.
+    M^-1 v = U^-1 (L^-1 v): a forward substitution y[p] = v[p] - sum_d L[p, p - e_d] y[p - e_d]
+    in the natural order, then a backward one z[p] = (y[p] - sum_d A[p, p + e_d] z[p + e_d]) / d[p]
+    in the reverse order. The sums run over the dimensions x, y, z in turn; every loop here
+    is the definition, one point at a time (the library sweeps the same arithmetic along
+    hyperplanes, where the points are independent).
+    """
+
+    def __init__(self, A):
+        self.A = A
+        n, dim = A.n, A.dim
+        sh = A.shape[::-1]
+        self.a0 = np.broadcast_to(A._coef(A.a0), sh).reshape(-1).astype(np.float64)
+        self.am = [np.broadcast_to(A._coef(A.am[d]), sh).reshape(-1).astype(np.float64) for d in range(dim)]
+        self.ap = [np.broadcast_to(A._coef(A.ap[d]), sh).reshape(-1).astype(np.float64) for d in range(dim)]
+        self.stride = [1, A.shape[0], A.shape[0] * A.shape[1]][:dim]
+        self.coord = np.indices(sh).reshape(dim, -1)[::-1]     # coord[d][p]: index of p along dimension d
+        d = np.zeros(n)
+        L = [np.zeros(n) for _ in range(dim)]
+        a0, am, ap = self.a0.tolist(), [v.tolist() for v in self.am], [v.tolist() for v in self.ap]
+        coord = [c.tolist() for c in self.coord]
+        for p in range(n):
+            dp = a0[p]
+            for k in range(dim):
+                if coord[k][p] > 0:
+                    q = p - self.stride[k]
+                    dp -= am[k][p] * ap[k][q] / d[q]
+            d[p] = dp
+            for k in range(dim):
+                if coord[k][p] > 0:
+                    L[k][p] = am[k][p] / d[p - self.stride[k]]
+        self.d, self.L = d, L
+
+    def apply_inv(self, v):
+        """z = M^-1 v = U^-1 L^-1 v."""
+        A = self.A
+        n, dim = A.n, A.dim
+        v = np.asarray(v, dtype=np.float64).tolist()
+        L = [x.tolist() for x in self.L]
+        ap = [x.tolist() for x in self.ap]
+        d = self.d.tolist()
+        coord = [c.tolist() for c in self.coord]
+        y = [0.0] * n
+        for p in range(n):
+            t = v[p]
+            for k in range(dim):
+                if coord[k][p] > 0:
+                    t -= L[k][p] * y[p - self.stride[k]]
+            y[p] = t
+        z = [0.0] * n
+        for p in range(n - 1, -1, -1):
+            t = y[p]
+            for k in range(dim):
+                if coord[k][p] < A.shape[k] - 1:
+                    t -= ap[k][p] * z[p + self.stride[k]]
+            z[p] = t / d[p]
+        return np.array(z)
+
+
 def convdiff(shape, beta):
     """Constant-coefficient operator of -Lap u + beta . grad u on the unit square/cube.
 
