@@ -79,8 +79,8 @@ def sources_sha(names):
     return h.hexdigest()[:16]
 
 
-def measured_traffic(precision, kernel):
-    t = TRAFFIC.get(precision)
+def measured_traffic(precision, kernel, tc=True):
+    t = TRAFFIC.get(precision if not (precision == "fp64" and tc) else "fp64_tc")
     if not t or t["kernel"] != kernel or sources_sha(t["sources"]) != t["sha256"]:
         return None
     return t["bytes_per_launch"]
@@ -112,8 +112,9 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32"],
                     help="basis precision of the headline solve")
     ap.add_argument("--no-variants", action="store_true", help="the headline solve only")
-    ap.add_argument("--variants", default="solvers,precision,batched,paper",
-                    help="comma list of the extra measurements: solvers (s = 2/4/8, GMRES, Orthomin, "
+    ap.add_argument("--variants", default="small,solvers,precision,batched,paper",
+                    help="comma list of the extra measurements: small (the 2-D 64^2 system, s = 4, m = 20, "
+                         "against GMRES(20); multi-kernel and one persistent launch), solvers (s = 2/4/8, GMRES, Orthomin, "
                          "mixed-precision bases, Newton basis, red-black ILU(0)), precision (the 256^3 "
                          "FP32-refinement form), batched (512 systems), paper (the paper's test problem, "
                          "Sec. 5), learned (the learned initial guess; minutes)")
@@ -431,14 +432,24 @@ def main():
     flops, bytes_, launches_dom = work[dom]
     achieved = flops / t_dom / 1e12
     issued_dom = kinds[dom][1] / args.steps   # includes launches a converged cycle skips at once
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": measured_traffic(args.precision, dom), "kernel": dom,
-                "launches_per_solve": launches_dom, "launches_issued_per_solve": issued_dom,
-                "algorithmic_bytes_per_launch": bytes_ / launches_dom,
-                "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
-                "hbm_gbs": bytes_ / t_dom / 1e9,
-                "hbm_peak_gbs": HBM_PEAK_GBS, "hbm_frac": bytes_ / t_dom / 1e9 / HBM_PEAK_GBS,
-                "share_of_step": kinds[dom][0] / args.steps / ms}
+    tc = args.precision == "fp64" and os.environ.get("SSTEP_TC_GRAM", "1") != "0"
+    gbs = bytes_ / t_dom / 1e9
+    common = {"kernel": dom, "launches_per_solve": launches_dom, "launches_issued_per_solve": issued_dom,
+              "algorithmic_bytes_per_launch": bytes_ / launches_dom,
+              "traffic": measured_traffic(args.precision, dom, tc),
+              "fp64_equivalent_tflops": achieved, "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+              "share_of_step": kinds[dom][0] / args.steps / ms}
+    if tc:
+        # the Gram and block-update contractions run on the tensor cores in exact fixed point,
+        # off the FP64 pipe: the roof of these streaming kernels is HBM bandwidth
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                    "frac": gbs / HBM_PEAK_GBS,
+                    "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst", **common}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
+                    "hbm_gbs": gbs, "hbm_peak_gbs": HBM_PEAK_GBS, "hbm_frac": gbs / HBM_PEAK_GBS, **common}
 
     # the comparison the metric names: standard GMRES(m) (classical Gram-Schmidt, Alg. 2.2)
     # on the same system and GPU, timed the same way
@@ -503,6 +514,51 @@ def main():
             torch.cuda.synchronize()
             variants[name] = {"ms": e0.elapsed_time(e1) / reps, "status": rv["status"], "cycles": rv["cycles"],
                               "iters": rv["iters"], "matvecs": rv["matvecs"], "relres": rv["relres"]}
+
+    if "small" in args.groups:
+        # the 2-D workload: 64^2 interior grid (n = 4096), beta = (20, 20), s-step GMRES with
+        # s = 4, m = 20 against GMRES(20) on the same system. Its 32 KB columns sit in L2, so
+        # every solve is bound by launch latency and the per-cycle host read; besides the
+        # multi-kernel solvers, the batched solver runs the same system as one persistent
+        # launch (one thread-block cluster, no host round trip per cycle)
+        A2 = pkg.StencilMatrix(2, (64, 64), beta=(20.0, 20.0))
+        xt2 = torch.tensor(inputs.x_true(rank, A2.n), dtype=torch.float64, device=dev)
+        f2 = torch.empty_like(xt2)
+        A2.apply(xt2, f2)
+        x2 = torch.zeros_like(f2)
+        small = {"workload": "2-D convection-diffusion 64^2 (n=4,096), beta=(20,20), 5-point, FP64, x0=0, tol 1e-8"}
+        reps = 10
+        for name, fn in (("sstep_gmres_s4_m20", lambda xv: pkg.sstep_gmres_solve(A2, f2, xv, 4, 20, TOL, max_cycles=2000,
+                                                                                 history_cap=0)),
+                         ("gmres_m20", lambda xv: pkg.gmres_solve(A2, f2, xv, 20, TOL, max_cycles=2000, history_cap=0))):
+            x2.zero_()
+            fn(x2)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                x2.zero_()
+                r2s = fn(x2)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            small[name] = {"ms": e0.elapsed_time(e1) / reps, "status": r2s["status"], "cycles": r2s["cycles"],
+                           "matvecs": r2s["matvecs"], "relres": r2s["relres"]}
+        for s_, name in ((4, "persistent_sstep_gmres_s4_m20"), (1, "persistent_gmres_m20_s1")):
+            Bs = pkg.BatchSolver([A2], s_, 20, TOL, max_cycles=2000)
+            cfg = Bs.tune([f2], [x2])
+            x2.zero_()
+            Bs.solve([f2], [x2])
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                x2.zero_()
+                rb = Bs.solve([f2], [x2])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            small[name] = {"ms": e0.elapsed_time(e1) / reps, "status": rb[0]["status"], "cycles": rb[0]["cycles"],
+                           "matvecs": rb[0]["matvecs"], "relres": rb[0]["relres"], "tuned": cfg}
+            Bs.close()
+        variants["small_2d_64_s4_m20"] = small
+        del A2, xt2, f2, x2
 
     if "precision" in args.groups:
         # the precision form: 3-D 256^3, beta = (50, 0, 0), s = 8, m = 32, to 1e-10; FP32
@@ -645,6 +701,11 @@ def main():
                                        if v[1] > 0 and k in work and v[0] > 0},
             "variants": variants,
         }
+        if "small_2d_64_s4_m20" in variants:   # the 2-D 64^2 workload, compact, ahead of the variants
+            sm = variants["small_2d_64_s4_m20"]
+            line = {**{k: v for k, v in line.items() if k != "variants"},
+                    "small_2d_64_ms": {k: round(v["ms"], 3) for k, v in sm.items() if isinstance(v, dict)},
+                    "variants": variants}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

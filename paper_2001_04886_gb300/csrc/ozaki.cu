@@ -32,18 +32,24 @@
 namespace sstep {
 namespace {
 
-constexpr int kBRows = 80;                           // B rows: 8 digits x up to 9 columns, padded
-constexpr int kN0 = 80, kN1 = 48;                    // MMA N of the digit-0..3 and digit-4..7 tiles
+constexpr int kN0 = 80, kN1 = 48;                    // MMA N of the digit-0..3 and digit-4..7 tiles (G >= 1)
 constexpr int kGroupCols = kN0 + kN1;                // tensor-memory columns per 32 V columns
 constexpr long kOzSpin = 1L << 24;                   // bounded mbarrier polls
 
-// Shapes of one instantiation: G groups of 32 V columns.
+// Shapes of one instantiation: G groups of 32 V columns, KB Y columns.
 // (14 split warps + the MMA warp: at most 4 warps per SM sub-partition, so 128 registers
 // per thread; a stage of 112 rows is 7 MMA K-steps and 9 stages make a chunk of 1008 rows.)
-// G = 0: at most 16 V columns, one A tile of all 8 digits x 16 columns and 4 stages in
-// flight; G = 1, 2: up to 32 G V columns, two tiles per 32 columns (digits 0-3 and 4-7)
-template <int G>
+// G = 0: at most 16 V columns, one A tile of all 8 digits x 16 columns; G = 1, 2: up to
+// 32 G V columns, two tiles per 32 columns (digits 0-3 and 4-7). B row t BST + b holds
+// digit t of Y column b: BST = 8 for KB <= 8, and for KB = 9 16 (G = 0) or 9 (G >= 1), so
+// that, except in the last case, a digit's rows start on an 8-row core-matrix boundary and
+// an octet's unused columns fall in rows that no kept sum reads.
+template <int G, int KB>
 struct OzCfg {
+    static constexpr int kBst = KB <= 8 ? 8 : (G == 0 ? 16 : KB);
+    static constexpr bool kFastB = kBst % 8 == 0;               // digit t's B rows at t kBst / 8 row groups
+    static constexpr int kBRows = G == 0 ? 8 * kBst : 80;       // B rows allocated
+    static constexpr int kN0 = G == 0 ? 8 * kBst : 80;          // MMA N of the digit-0..3 (G = 0: all) tile
     static constexpr int kSplitWarps = G <= 1 ? 14 : 8;
     static constexpr int kThreads = (kSplitWarps + 1) * 32;   // + the MMA warp
     static constexpr int kRows = 8 * kSplitWarps;             // rows per stage (one K group per split warp)
@@ -54,12 +60,14 @@ struct OzCfg {
     static constexpr int kGroups = G == 0 ? 1 : G;            // column groups
     static constexpr int kColsPer = G == 0 ? 16 : 32;         // V columns per group
     static constexpr int kStage = kAT * kTile + kB;
-    static constexpr int kNStages = G == 0 ? 4 : 2;
+    static constexpr int kNStages = G == 0 ? (kBst > 8 ? 3 : 4) : 2;
     static constexpr int kSmem = kNStages * kStage;
     static constexpr int kStagesPerChunk = oz::kChunkRows / kRows;
     static constexpr int kBuf = G == 0 ? 128 : G * kGroupCols;   // accumulator columns per buffer
     static constexpr uint32_t kCols = 2 * kBuf <= 256 ? 256u : 512u;
     static_assert(kRows % 16 == 0 && kStagesPerChunk * kRows <= oz::kChunkRows, "stage shape");
+    static_assert(kN0 <= 128 && 8 * kBst <= kBRows && (G == 0 || 5 * kBst <= kN1), "B shape");
+    static_assert(kSmem <= 227 * 1024, "shared memory");
 };
 constexpr int kDrainWarps = 8;   // split warps 0..7 drain: TMEM lane quarter warp % 4, tile warp / 4
 
@@ -113,6 +121,47 @@ __device__ __forceinline__ uint32_t digit_pair(uint64_t w0, uint64_t w1) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+// digits T and T + 1 (T even: bytes i = 7 - T and i - 1 of the same 32-bit word) of two
+// rows as two FP16 pairs: one byte permute gathers the four bytes, two more interleave
+// them with the FP16 exponent byte 0x64 (1024 + byte), and 1152 is subtracted
+template <int T>
+__device__ __forceinline__ void digit_pairs2(uint32_t a, uint32_t b, uint32_t& dt, uint32_t& dt1) {
+    constexpr int k = (oz::kDigits - 1 - T) & 3;   // byte of digit T within its word; k - 1 holds digit T + 1
+    constexpr uint32_t sel = (uint32_t)(k | ((4 + k) << 4) | ((k - 1) << 8) | ((3 + k) << 12));
+    const uint32_t p = __byte_perm(a, b, sel);                 // [a_k, b_k, a_k-1, b_k-1]
+    const uint32_t x0 = __byte_perm(p, 0x64646464u, 0x4140u);  // [a_k, 0x64, b_k, 0x64]
+    const uint32_t x1 = __byte_perm(p, 0x64646464u, 0x4342u);  // [a_k-1, 0x64, b_k-1, 0x64]
+    const __half2 off = __halves2half2(__float2half(1152.f), __float2half(1152.f));
+    const __half2 h0 = __hsub2(*reinterpret_cast<const __half2*>(&x0), off);
+    const __half2 h1 = __hsub2(*reinterpret_cast<const __half2*>(&x1), off);
+    dt = *reinterpret_cast<const uint32_t*>(&h0);
+    dt1 = *reinterpret_cast<const uint32_t*>(&h1);
+}
+
+// the 8 digits (top first) of one entry as FP16, in one 16-byte row: pairs (t, t + 1) from
+// one byte permute each (bytes i and i - 1 of a word, interleaved with the exponent byte
+// 0x64), 1152 subtracted
+__device__ __forceinline__ void digit_row8(uint32_t wl, uint32_t wh, uint4& v) {
+    const __half2 off = __halves2half2(__float2half(1152.f), __float2half(1152.f));
+    uint32_t x[4] = {__byte_perm(wh, 0x64646464u, 0x4243u), __byte_perm(wh, 0x64646464u, 0x4041u),
+                     __byte_perm(wl, 0x64646464u, 0x4243u), __byte_perm(wl, 0x64646464u, 0x4041u)};
+    uint32_t r[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&x[i]), off);
+        r[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    v = make_uint4(r[0], r[1], r[2], r[3]);
+}
+
+// the 8 digit pairs (top first) of two rows of one column from their biased words
+__device__ __forceinline__ void digits8(uint32_t l0, uint32_t h0, uint32_t l1, uint32_t h1, uint32_t (&d)[oz::kDigits]) {
+    digit_pairs2<0>(h0, h1, d[0], d[1]);
+    digit_pairs2<2>(h0, h1, d[2], d[3]);
+    digit_pairs2<4>(l0, l1, d[4], d[5]);
+    digit_pairs2<6>(l0, l1, d[6], d[7]);
+}
+
 __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, long limit) {
     uint32_t done = 0;
     for (long it = 0; it < limit && !done; ++it)
@@ -120,6 +169,21 @@ __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, long limi
                      : "=r"(done)
                      : "r"(bar), "r"(parity)
                      : "memory");
+    return done != 0;
+}
+
+// the same bounded wait with a short sleep between polls (the MMA-issue thread, which
+// otherwise polls for the whole time the split warps fill a stage)
+__device__ __forceinline__ bool oz_wait_sleep(uint32_t bar, uint32_t parity, long limit) {
+    uint32_t done = 0;
+    for (long it = 0; it < limit; ++it) {
+        asm volatile("{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\nselp.b32 %0, 1, 0, P;\n}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) break;
+        __nanosleep(32);
+    }
     return done != 0;
 }
 
@@ -164,20 +228,21 @@ namespace sstep {
 namespace {
 
 // The digit-pair sums of one drained tile: TMEM lane (warp quarter, lane) is the V digit
-// ta of column a; its columns are (tb, b), b fastest, read 16 at a time. Each exact FP32
-// integer S is added into acc[b] with weight 256^(kCut - tb); the thread's contribution is
-// acc >> 8 ta (every kept term has kCut - tb >= ta, so that shift is exact).
-template <int KB, int NC>
+// ta of column a; its column tb BST + b holds the sum against digit tb of Y column b, read
+// 16 at a time (columns with b >= KB hold nothing kept). Each exact FP32 integer S is added
+// into acc[b] with weight 256^(kCut - tb); the thread's contribution is acc >> 8 ta (every
+// kept term has kCut - tb >= ta, so that shift is exact).
+template <int KB, int BST, int NC>
 __device__ __forceinline__ void drain_tile(uint32_t taddr, int ta, int tmin, oz::i128 (&acc)[KB]) {
 #pragma unroll
     for (int c0 = 0; c0 < NC; c0 += 16) {
-        if (c0 >= (oz::kCut + 1 - tmin) * KB) break;     // warp-uniform (tmin: the warp's smallest ta)
+        if (c0 >= (oz::kCut + 1 - tmin) * BST) break;     // warp-uniform (tmin: the warp's smallest ta)
         uint32_t r[16];
         tmem_ld<16>(taddr + (uint32_t)c0, r);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int col = c0 + j, tb = col / KB, b = col % KB;
-            if (col < NC && tb < oz::kDigits && tb <= oz::kCut - ta) {
+            const int col = c0 + j, tb = col / BST, b = col % BST;
+            if (col < NC && b < KB && tb < oz::kDigits && tb <= oz::kCut - ta) {
                 const int S = __float2int_rn(__uint_as_float(r[j]));
                 acc[b] += (oz::i128)S << (8 * (oz::kCut - tb));
             }
@@ -186,11 +251,12 @@ __device__ __forceinline__ void drain_tile(uint32_t taddr, int ta, int tmin, oz:
 }
 
 template <int G, int KB>
-__global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
+__global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
     gram_oz_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int ka, const unsigned* __restrict__ vmax,
                    const double* __restrict__ Y, int64_t ldy, const unsigned* __restrict__ ymax, Scratch sc, Epi epi,
                    int gate, long spin, int sym) {
-    using C = OzCfg<G>;
+    using C = OzCfg<G, KB>;
+    constexpr int BST = C::kBst;
     constexpr int kItems = (G == 0 ? 2 : 4 * G) + (KB + 7) / 8;   // column octets per split warp and stage
     constexpr int NS = C::kNStages, NG = C::kGroups, CP = C::kColsPer;
     constexpr int SBO = C::kSbo;
@@ -251,11 +317,11 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
                 const int chunk = (int)(gs / C::kStagesPerChunk), sic = (int)(gs % C::kStagesPerChunk);
                 const int tb = chunk & 1;
                 if (sic == 0 && chunk >= 2 &&   // the accumulators of chunk - 2 are drained
-                    !oz_wait(smem_addr(&tempty[tb]), (uint32_t)(((chunk >> 1) - 1) & 1), spin)) {
+                    !oz_wait_sleep(smem_addr(&tempty[tb]), (uint32_t)(((chunk >> 1) - 1) & 1), spin)) {
                     failed = 1;
                     break;
                 }
-                if (!oz_wait(smem_addr(&full[sb]), (uint32_t)((gs / NS) & 1), spin)) {
+                if (!oz_wait_sleep(smem_addr(&full[sb]), (uint32_t)((gs / NS) & 1), spin)) {
                     failed = 1;
                     break;
                 }
@@ -266,7 +332,7 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
 #pragma unroll
                     for (int ks = 0; ks < C::kRows / 16; ++ks)
                         mma_f16(dt, op_desc<SBO>(so + (uint32_t)(ks * 256)),
-                                op_desc<SBO>(so + (uint32_t)(C::kTile + ks * 256)), oz_idesc(kN0),
+                                op_desc<SBO>(so + (uint32_t)(C::kTile + ks * 256)), oz_idesc(C::kN0),
                                 (sic > 0 || ks > 0) ? 1u : 0u);
                 }
 #pragma unroll
@@ -303,33 +369,51 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
         const int c8 = lane >> 2, kk = warp * 8 + (lane & 3) * 2;
         // per item: the entry (row kk of this CTA's first stage) and whether it is 16-byte
         // aligned (kk and the stage height are even, so that holds for every stage)
+        // per item: the entry in row kk of this CTA's first stage (a column past ka or kb reads
+        // column 0 of its operand instead, so every lane loads, and its digits are stored
+        // where no kept sum reads them), its bound exponent and its shared-memory offsets
         const double* cp[kItems];
         uint32_t ce[kItems];
-        int cc[kItems];
-        bool cv[kItems], al[kItems];
+        uint32_t aoff[kItems], boff[kItems];   // byte offsets of digit 0 in A and in B (none: ~0u)
+        int bcol[kItems];
+        bool cv[kItems];
+        bool al = true;                        // every item's entries 16-byte aligned
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             const bool isv = j < noct_v;
             const int c = isv ? j * 8 + c8 : (j - noct_v) * 8 + c8;
             cv[j] = j < noct && c < (isv ? ka : KB);
-            cc[j] = c;
-            cp[j] = cv[j] ? (isv ? V + (int64_t)c * ldv : Y + (int64_t)c * ldy) + s0 * C::kRows + kk : nullptr;
-            al[j] = ((uintptr_t)cp[j] & 15) == 0;
-            ce[j] = cv[j] ? ex[isv ? c : ka + c] : 0u;
+            const int cl = cv[j] ? c : 0;
+            cp[j] = (isv ? V + (int64_t)cl * ldv : Y + (int64_t)cl * ldy) + s0 * C::kRows + kk;
+            al = al && ((uintptr_t)cp[j] & 15) == 0;
+            ce[j] = ex[isv ? cl : ka + cl];
+            // B: digit t of column c in row t BST + c (C::kFastB: the octet's unused columns land
+            // in rows no drain reads); otherwise (BST = 9) the row is formed per digit
+            if (isv) {
+                aoff[j] = G == 0 ? op_off<SBO>(c, kk) : (uint32_t)((c >> 5) * 2 * C::kTile) + op_off<SBO>(c & 31, kk);
+                boff[j] = sym ? (uint32_t)(C::kAT * C::kTile) + op_off<SBO>(c, kk) : ~0u;
+            } else {
+                aoff[j] = ~0u;
+                boff[j] = (uint32_t)(C::kAT * C::kTile) + (C::kFastB ? op_off<SBO>(c, kk) : 0u);
+            }
+            bcol[j] = c;
         }
+        al = __all_sync(0xffffffffu, al);
         auto load = [&](int64_t st, double2 (&buf)[kItems]) {
             const int64_t off = st * C::kRows, r = (s0 + st) * C::kRows + kk;
             const bool whole = (s0 + st + 1) * C::kRows <= n;   // warp-uniform: no row past n
+            if (whole && al) {
 #pragma unroll
-            for (int j = 0; j < kItems; ++j) {
-                buf[j] = make_double2(0.0, 0.0);
-                if (cv[j]) {
-                    const double* p = cp[j] + off;
-                    if (whole || r + 1 < n) {
-                        if (al[j]) buf[j] = __ldg(reinterpret_cast<const double2*>(p));
-                        else buf[j] = make_double2(__ldg(p), __ldg(p + 1));
-                    } else if (r < n) {
-                        buf[j].x = __ldg(p);
+                for (int j = 0; j < kItems; ++j)
+                    if (j < noct) buf[j] = __ldg(reinterpret_cast<const double2*>(cp[j] + off));
+            } else {
+#pragma unroll
+                for (int j = 0; j < kItems; ++j) {
+                    buf[j] = make_double2(0.0, 0.0);
+                    if (j < noct) {
+                        const double* p = cp[j] + off;
+                        if (r < n) buf[j].x = __ldg(p);
+                        if (r + 1 < n) buf[j].y = __ldg(p + 1);
                     }
                 }
             }
@@ -352,41 +436,40 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
                     const bool isv = j < noct_v;
                     const uint64_t b0 = (uint64_t)__double_as_longlong(cur[j].x);
                     const uint64_t b1 = (uint64_t)__double_as_longlong(cur[j].y);
-                    const uint64_t w0 = oz::fixed_biased((uint32_t)b0, (uint32_t)(b0 >> 32), ce[j]);
-                    const uint64_t w1 = oz::fixed_biased((uint32_t)b1, (uint32_t)(b1 >> 32), ce[j]);
+                    uint32_t l0, h0, l1, h1;
+                    oz::fixed_biased_words((uint32_t)b0, (uint32_t)(b0 >> 32), ce[j], l0, h0);
+                    oz::fixed_biased_words((uint32_t)b1, (uint32_t)(b1 >> 32), ce[j], l1, h1);
                     uint32_t d[oz::kDigits];
-                    d[0] = digit_pair<0>(w0, w1);
-                    d[1] = digit_pair<1>(w0, w1);
-                    d[2] = digit_pair<2>(w0, w1);
-                    d[3] = digit_pair<3>(w0, w1);
-                    d[4] = digit_pair<4>(w0, w1);
-                    d[5] = digit_pair<5>(w0, w1);
-                    d[6] = digit_pair<6>(w0, w1);
-                    d[7] = digit_pair<7>(w0, w1);
-                    const int c = cc[j];
+                    digits8(l0, h0, l1, h1, d);
                     if (isv) {   // unused columns of an octet land in unused A rows
+                        unsigned char* base = sp + aoff[j];
                         if (G == 0) {   // row t 16 + c of the one tile
-                            unsigned char* base = sp + op_off<SBO>(c, kk);
 #pragma unroll
                             for (int t = 0; t < oz::kDigits; ++t)
                                 *reinterpret_cast<uint32_t*>(base + t * 2 * SBO) = d[t];
                         } else {        // tile 2 (c / 32) + t / 4, row (t % 4) 32 + c % 32
-                            unsigned char* base = sp + (c >> 5) * 2 * C::kTile + op_off<SBO>(c & 31, kk);
 #pragma unroll
                             for (int t = 0; t < oz::kDigits; ++t)
                                 *reinterpret_cast<uint32_t*>(base + (t >> 2) * C::kTile + (t & 3) * 4 * SBO) = d[t];
                         }
-                        if (sym && cv[j]) {
-                            unsigned char* bb = sp + C::kAT * C::kTile;
+                        if (sym) {      // warp-uniform; sym implies G = 0, so C::kFastB
+                            unsigned char* bb = sp + boff[j];
 #pragma unroll
                             for (int t = 0; t < oz::kDigits; ++t)
-                                *reinterpret_cast<uint32_t*>(bb + op_off<SBO>(t * KB + c, kk)) = d[t];
+                                *reinterpret_cast<uint32_t*>(bb + (uint32_t)(t * (BST / 8)) * SBO) = d[t];
                         }
-                    } else if (cv[j]) {
-                        unsigned char* base = sp + C::kAT * C::kTile;
+                    } else if (C::kFastB) {
+                        unsigned char* bb = sp + boff[j];
 #pragma unroll
                         for (int t = 0; t < oz::kDigits; ++t)
-                            *reinterpret_cast<uint32_t*>(base + op_off<SBO>(t * KB + c, kk)) = d[t];
+                            *reinterpret_cast<uint32_t*>(bb + (uint32_t)(t * (BST / 8)) * SBO) = d[t];
+                    } else {           // BST = KB = 9: unused columns go to the spare rows 72..79
+                        unsigned char* bb = sp + boff[j];
+#pragma unroll
+                        for (int t = 0; t < oz::kDigits; ++t) {
+                            const int row = cv[j] ? t * BST + bcol[j] : 8 * BST + (bcol[j] & 7);
+                            *reinterpret_cast<uint32_t*>(bb + op_off<SBO>(row, kk)) = d[t];
+                        }
                     }
                 }
             }
@@ -404,12 +487,12 @@ __global__ void __launch_bounds__(OzCfg<G>::kThreads, 1)
                 const uint32_t tb0 = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tb * C::kBuf);
                 if (drains) {
                     if (G == 0) {
-                        drain_tile<KB, kN0>(tb0, ta, tmin, acc[0]);
+                        drain_tile<KB, BST, C::kN0>(tb0, ta, tmin, acc[0]);
                     } else {
 #pragma unroll
                         for (int g = 0; g < NG; ++g) {
-                            if (ta < 4) drain_tile<KB, kN0>(tb0 + (uint32_t)(g * kGroupCols), ta, ta, acc[g]);
-                            else drain_tile<KB, kN1>(tb0 + (uint32_t)(g * kGroupCols + kN0), ta, ta, acc[g]);
+                            if (ta < 4) drain_tile<KB, BST, kN0>(tb0 + (uint32_t)(g * kGroupCols), ta, ta, acc[g]);
+                            else drain_tile<KB, BST, kN1>(tb0 + (uint32_t)(g * kGroupCols + kN0), ta, ta, acc[g]);
                         }
                     }
                 }
@@ -505,7 +588,7 @@ namespace {
 template <int G, int KB>
 void launch_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, const double* Y, int64_t ldy,
                const unsigned* ymax, Scratch sc, const Epi& epi, int gate, cudaStream_t stream, long spin, int sym) {
-    using C = OzCfg<G>;
+    using C = OzCfg<G, KB>;
     static bool attr[64] = {false};   // once per device
     int dev = 0;
     cudaGetDevice(&dev);
@@ -568,9 +651,10 @@ bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsig
 namespace sstep {
 namespace {
 
-// warps 0..7 split tile t and then run the epilogue of tile t - 1 (warps w and w + 4 share
-// tensor-memory lane quarter w % 4 and take half of the outputs each); warp 8 issues the MMAs
-constexpr int kUpSplitWarps = 8, kUpMmaWarp = 8;
+// warps 0..15 split tile t and then run the epilogue of tile t - 1 (warps w, w + 4, w + 8 and
+// w + 12 share tensor-memory lane quarter w % 4 and take a quarter of the outputs each); warp
+// 16 issues the MMAs
+constexpr int kUpSplitWarps = 16, kUpMmaWarp = 16;
 constexpr int kUpThreads = (kUpSplitWarps + 1) * 32;
 
 constexpr int kUpRows = 128;                      // rows per tile (MMA M)
@@ -590,11 +674,6 @@ struct UpCfg {
     static constexpr int kSmem = 2 * kA + kB;
     static_assert(kN <= (int)kUpBuf, "accumulator buffer");
 };
-
-__device__ __forceinline__ uint64_t op_desc_rt(uint32_t addr, int sbo) {
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) |
-           ((uint64_t)1 << 46);
-}
 
 template <int KAP, int KBO>
 __global__ void __launch_bounds__(kUpThreads, 1)
@@ -653,7 +732,7 @@ __global__ void __launch_bounds__(kUpThreads, 1)
     __syncthreads();
     if (tid < KBO) fexp[tid] = (int)oz::bound_exponent(fmax[tid]);
     __syncthreads();
-    // B: row (j, d), K = (digit plane ta of V, column a): digit d - ta of T'_aj where
+    // B: row (j, d), K = 8 a + ta (column a of V, its digit ta): digit d - ta of T'_aj where
     // 0 <= d - ta <= 7, zero elsewhere, so one MMA over all of K sums each digit diagonal d
     for (int e = tid; e < ka * KBO; e += kUpThreads) {
         const int a = e % ka, j = e / ka;
@@ -665,7 +744,7 @@ __global__ void __launch_bounds__(kUpThreads, 1)
 #pragma unroll
             for (int ta = 0; ta < oz::kDigits; ++ta)
                 if (ta + tb <= oz::kCut)
-                    *reinterpret_cast<__half*>(Bop + op_off<SBO>(j * kUpDiags + ta + tb, ta * KAP + a)) = e16;
+                    *reinterpret_cast<__half*>(Bop + op_off<SBO>(j * kUpDiags + ta + tb, 8 * a + ta)) = e16;
         }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -683,21 +762,23 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             int n_empty[2] = {0, 0}, n_tfull[2] = {0, 0};
             for (int64_t lt = 0; lt < nt && !failed; ++lt) {
                 const int b = (int)(lt & 1);
-                if (lt >= 2 && !oz_wait(smem_addr(&tempty[b]), (uint32_t)(((lt >> 1) - 1) & 1), spin)) {
+                if (lt >= 2 && !oz_wait_sleep(smem_addr(&tempty[b]), (uint32_t)(((lt >> 1) - 1) & 1), spin)) {
                     failed = 1;
                     break;
                 }
-                if (!oz_wait(smem_addr(&full[b]), (uint32_t)((lt >> 1) & 1), spin)) {
+                if (!oz_wait_sleep(smem_addr(&full[b]), (uint32_t)((lt >> 1) & 1), spin)) {
                     failed = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t ab = sbase + (uint32_t)(b * C::kA), bb = sbase + (uint32_t)(2 * C::kA);
                 const uint32_t dt = tmem + (uint32_t)b * kUpBuf;
+                const int nks = (ka + 1) >> 1;   // K steps of 16 = two columns; the rest is zero in B
 #pragma unroll
                 for (int ks = 0; ks < C::kK / 16; ++ks)
-                    mma_f16(dt, op_desc<SBO>(ab + (uint32_t)(ks * 256)), op_desc<SBO>(bb + (uint32_t)(ks * 256)),
-                            oz_idesc(C::kN), ks > 0 ? 1u : 0u);
+                    if (ks < nks)
+                        mma_f16(dt, op_desc<SBO>(ab + (uint32_t)(ks * 256)), op_desc<SBO>(bb + (uint32_t)(ks * 256)),
+                                oz_idesc(C::kN), ks > 0 ? 1u : 0u);
                 mma_commit(&empty[b]);
                 ++n_empty[b];
                 mma_commit(&tfull[b]);
@@ -711,51 +792,51 @@ __global__ void __launch_bounds__(kUpThreads, 1)
         __syncwarp();
     } else {
         // ---------------------------------------------------------------- split + epilogue warps
-        // split item k of this warp: row group rg (8 rows) and column octet oct of the tile;
-        // lane: row rr of the group, columns a and a + 1 of the octet (a K-adjacent pair)
-        constexpr int kIt = 2 * (KAP / 8);   // 16 row groups x KAP / 8 octets / 8 warps
-        const int koct = (ka + 7) >> 3, rr = lane & 7, cpair = lane >> 3;
-        // epilogue role: rows 32 q + lane of a tile; warps 0..3 take the outputs j < H, warps
-        // 4..7 the outputs H <= j < KBO (a compile-time offset: registers are not indexed)
-        constexpr int H = (KBO + 1) / 2;
-        const int q = warp & 3;
+        // split: warp w owns rows 8 w .. 8 w + 7 of every tile; item i holds columns 4 i .. 4 i + 3,
+        // lane: row 8 w + (lane & 7) of column 4 i + (lane >> 3). With K = 8 a + t, the 8 digits
+        // of one entry are one 16-byte row of a core matrix: one store per entry. Columns past
+        // ka read column 0 (finite digits against B's zeros); items past them are skipped and
+        // stay zero from the initial clear.
+        constexpr int kIt = KAP / 4;
+        const int rr = warp * 8 + (lane & 7), csub = lane >> 3;
+        const int nit = (ka + 3) >> 2;   // items with a column < ka (warp-uniform)
+        const double* pa[kIt];
+        uint32_t ea[kIt];
+        // byte offset of the entry's digit row in an A buffer: item i adds 4 columns of 128 B
+        const uint32_t soff0 = op_off<SBO>(rr, 8 * csub);
+#pragma unroll
+        for (int i = 0; i < kIt; ++i) {
+            const int a = 4 * i + csub, ac = a < ka ? a : 0;
+            pa[i] = V + (int64_t)ac * ldv + t0 * kUpRows + rr;
+            ea[i] = exv[ac];
+        }
+        // epilogue: rows 32 q + lane of a tile; warp group g = warp / 4 takes the outputs
+        // g H .. g H + H - 1 (compile-time offsets through one instantiation per group)
+        constexpr int H = (KBO + 3) / 4;
+        const int q = warp & 3, g = warp >> 2;
         unsigned bm[H];
 #pragma unroll
         for (int j = 0; j < H; ++j) bm[j] = 0;
-        // per item: the entries of columns a and a + 1 in this CTA's first tile (null: none)
-        const double* pa[kIt];
-        const double* pb[kIt];
-#pragma unroll
-        for (int k = 0; k < kIt; ++k) {
-            const int i = warp + kUpSplitWarps * k, rg = i & 15, oct = i >> 4;
-            const int a = oct * 8 + cpair * 2;
-            const int64_t r0 = t0 * kUpRows + rg * 8 + rr;
-            pa[k] = (oct < koct && a < ka) ? V + (int64_t)a * ldv + r0 : nullptr;
-            pb[k] = (oct < koct && a + 1 < ka) ? V + (int64_t)(a + 1) * ldv + r0 : nullptr;
-        }
-        auto load = [&](int64_t lt, double2 (&buf)[kIt]) {
+        auto load = [&](int64_t lt, double (&buf)[kIt]) {
             const int64_t off = lt * kUpRows;
-            const bool whole = (t0 + lt + 1) * kUpRows <= n;   // warp-uniform: no row past n
+            const bool in = (t0 + lt) * kUpRows + rr < n;
 #pragma unroll
-            for (int k = 0; k < kIt; ++k) {
-                const int i = warp + kUpSplitWarps * k, rg = i & 15;
-                const bool in = whole || (t0 + lt) * kUpRows + rg * 8 + rr < n;
-                buf[k].x = (pa[k] && in) ? __ldg(pa[k] + off) : 0.0;
-                buf[k].y = (pb[k] && in) ? __ldg(pb[k] + off) : 0.0;
-            }
+            for (int i = 0; i < kIt; ++i)
+                if (i < nit) buf[i] = in ? __ldg(pa[i] + off) : 0.0;
         };
         // this thread's Y entries of tile lt (loaded a whole split ahead of their use)
-        const int jo_rt = warp < 4 ? 0 : H;
         double yv[H];
         auto load_y = [&](int64_t lt) {
             const int64_t r = (t0 + lt) * kUpRows + q * 32 + lane;
 #pragma unroll
-            for (int j = 0; j < H; ++j)
-                yv[j] = (r < n && jo_rt + j < KBO) ? Y[(int64_t)(j0 + jo_rt + j) * ldy + r] : 0.0;
+            for (int j = 0; j < H; ++j) {
+                const int jj = g * H + j;
+                yv[j] = (r < n && jj < KBO) ? Y[(int64_t)(j0 + jj) * ldy + r] : 0.0;
+            }
         };
-        // epilogue of tile lt: Yhat = Y - P for this thread's row and outputs (yv: its Y entries)
-        auto epilogue = [&](int64_t lt, auto joc) -> bool {
-            constexpr int jo = decltype(joc)::value;
+        // epilogue of tile lt: Yhat = Y - P for this thread's row and outputs
+        auto epilogue = [&](int64_t lt, auto goc) -> bool {
+            constexpr int jo = decltype(goc)::value * H;
             const int b = (int)(lt & 1);
             const int64_t r = (t0 + lt) * kUpRows + q * 32 + lane;
             if (!oz_wait(smem_addr(&tfull[b]), (uint32_t)((lt >> 1) & 1), spin)) return false;
@@ -763,14 +844,13 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             // Q = sum_d S_d 256^(8 - d) = Qh 2^32 + Ql: Horner in 64 bits over the diagonals
             // 0..4 (Qh < 2^54) and 5..8 (Ql < 2^47), then one 128-bit step
             long long Qh[H], Ql[H];
-            oz::i128 Q[H];
 #pragma unroll
             for (int j = 0; j < H; ++j) Qh[j] = Ql[j] = 0;
             // columns (j, d) = 9 j + d of this thread's outputs, read 16 at a time from the
             // aligned column c0 below the first one (compile-time offsets)
             constexpr int c0 = (kUpDiags * jo) / 16 * 16;
-            constexpr int c1 = kUpDiags * (jo + H);
-            constexpr int NR = (c1 - c0 + 15) / 16 * 16;
+            constexpr int c1 = kUpDiags * (jo + H) < kUpDiags * KBO ? kUpDiags * (jo + H) : kUpDiags * KBO;
+            constexpr int NR = c1 > c0 ? (c1 - c0 + 15) / 16 * 16 : 16;
             uint32_t rv[NR];
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * kUpBuf + (uint32_t)c0;
             tmem_ld<NR>(ta, rv);
@@ -784,8 +864,6 @@ __global__ void __launch_bounds__(kUpThreads, 1)
                     else Ql[j] = Ql[j] * 256 + S;
                 }
             }
-#pragma unroll
-            for (int j = 0; j < H; ++j) Q[j] = ((oz::i128)Qh[j] << 32) + (oz::i128)Ql[j];
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) bar_arrive(&tempty[b]);
@@ -793,11 +871,12 @@ __global__ void __launch_bounds__(kUpThreads, 1)
 #pragma unroll
                 for (int j = 0; j < H; ++j) {
                     if (jo + j < KBO) {
+                        const oz::i128 Q = ((oz::i128)Qh[j] << 32) + (oz::i128)Ql[j];
                         const int fj = fexp[jo + j];
                         const double P = (nonfinite || fj == (int)oz::kNonFinite)
                                              ? __longlong_as_double(0x7FF8000000000000ll)
-                                             : oz::i128_to_double_int(Q[j], 8 * (2 * (oz::kDigits - 1) - oz::kCut) + fj -
-                                                                                oz::kFrac);
+                                             : oz::i128_to_double_int(Q, 8 * (2 * (oz::kDigits - 1) - oz::kCut) + fj -
+                                                                             oz::kFrac);
                         const double yh = yv[j] - P;
                         Y[(int64_t)(j0 + jo + j) * ldy + r] = yh;
                         bm[j] = max(bm[j],
@@ -807,11 +886,19 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             }
             return true;
         };
-        double2 cur[kIt];
+        auto run_epilogue = [&](int64_t lt) -> bool {
+            switch (g) {
+                case 0: return epilogue(lt, std::integral_constant<int, 0>());
+                case 1: return epilogue(lt, std::integral_constant<int, 1>());
+                case 2: return epilogue(lt, std::integral_constant<int, 2>());
+                default: return epilogue(lt, std::integral_constant<int, 3>());
+            }
+        };
+        double cur[kIt];
         if (nt > 0) load(0, cur);
         for (int64_t lt = 0; lt < nt; ++lt) {
             if (failed) break;
-            double2 nxt[kIt];
+            double nxt[kIt];
             if (lt + 1 < nt) load(lt + 1, nxt);
             if (lt >= 1) load_y(lt - 1);   // consumed by the epilogue after this split
             const int b = (int)(lt & 1);
@@ -821,52 +908,37 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             }
             unsigned char* ap = Abuf + b * C::kA;
 #pragma unroll
-            for (int k = 0; k < kIt; ++k) {
-                const int i = warp + kUpSplitWarps * k, rg = i & 15, oct = i >> 4;
-                if (oct < koct) {   // warp-uniform
-                    const int a = oct * 8 + cpair * 2;
-                    const uint64_t b0 = (uint64_t)__double_as_longlong(cur[k].x);
-                    const uint64_t b1 = (uint64_t)__double_as_longlong(cur[k].y);
-                    const uint64_t w0 = oz::fixed_biased((uint32_t)b0, (uint32_t)(b0 >> 32), exv[a & 31]);
-                    const uint64_t w1 = oz::fixed_biased((uint32_t)b1, (uint32_t)(b1 >> 32), exv[(a + 1) & 31]);
-                    unsigned char* base = ap + op_off<SBO>(rg * 8 + rr, a);
-                    *reinterpret_cast<uint32_t*>(base + 0 * KAP * 16) = digit_pair<0>(w0, w1);
-                    *reinterpret_cast<uint32_t*>(base + 1 * KAP * 16) = digit_pair<1>(w0, w1);
-                    *reinterpret_cast<uint32_t*>(base + 2 * KAP * 16) = digit_pair<2>(w0, w1);
-                    *reinterpret_cast<uint32_t*>(base + 3 * KAP * 16) = digit_pair<3>(w0, w1);
-                    *reinterpret_cast<uint32_t*>(base + 4 * KAP * 16) = digit_pair<4>(w0, w1);
-                    *reinterpret_cast<uint32_t*>(base + 5 * KAP * 16) = digit_pair<5>(w0, w1);
-                    *reinterpret_cast<uint32_t*>(base + 6 * KAP * 16) = digit_pair<6>(w0, w1);
-                    *reinterpret_cast<uint32_t*>(base + 7 * KAP * 16) = digit_pair<7>(w0, w1);
+            for (int i = 0; i < kIt; ++i) {
+                if (i < nit) {   // warp-uniform
+                    const uint64_t bits = (uint64_t)__double_as_longlong(cur[i]);
+                    uint32_t wl, wh;
+                    oz::fixed_biased_words((uint32_t)bits, (uint32_t)(bits >> 32), ea[i], wl, wh);
+                    uint4 v;
+                    digit_row8(wl, wh, v);
+                    *reinterpret_cast<uint4*>(ap + soff0 + i * 4 * 128) = v;
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) bar_arrive(&full[b]);
 #pragma unroll
-            for (int k = 0; k < kIt; ++k) cur[k] = nxt[k];
-            if (lt >= 1) {   // the previous tile, while this tile's MMAs run
-                const bool ok = warp < 4 ? epilogue(lt - 1, std::integral_constant<int, 0>())
-                                         : epilogue(lt - 1, std::integral_constant<int, H>());
-                if (!ok) {
-                    failed = 1;
-                    break;
-                }
+            for (int i = 0; i < kIt; ++i) cur[i] = nxt[i];
+            if (lt >= 1 && !run_epilogue(lt - 1)) {   // the previous tile, while this tile's MMAs run
+                failed = 1;
+                break;
             }
         }
         if (!failed && nt > 0) {
             load_y(nt - 1);
-            const bool ok = warp < 4 ? epilogue(nt - 1, std::integral_constant<int, 0>())
-                                     : epilogue(nt - 1, std::integral_constant<int, H>());
-            if (!ok) failed = 1;
+            if (!run_epilogue(nt - 1)) failed = 1;
         }
-        const int jo = warp < 4 ? 0 : H;
 #pragma unroll
         for (int j = 0; j < H; ++j) {
+            const int jj = g * H + j;
             const unsigned m = __reduce_max_sync(0xffffffffu, bm[j]);
-            if (lane == 0 && m && jo + j < KBO) {
-                if (bout) atomicMax(bout + jo + j, m);
-                if (bout2 && jo + j < nb2) atomicMax(bout2 + jo + j, m);
+            if (lane == 0 && m && jj < KBO) {
+                if (bout) atomicMax(bout + jj, m);
+                if (bout2 && jj < nb2) atomicMax(bout2 + jj, m);
             }
         }
     }

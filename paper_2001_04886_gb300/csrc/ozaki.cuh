@@ -66,6 +66,46 @@ OZ_HD uint64_t fixed_biased(uint32_t lo, uint32_t hi, uint32_t ex_max) {
     return (q ^ s) + kBias + (s & 1ull);                          // two's complement sign, then the bias
 }
 
+// Funnel shifts on 32-bit words: the low word of (hi:lo) >> min(sh, 32), and the high
+// word of (hi:lo) << sh for sh < 32 (one instruction each on the device)
+OZ_HD uint32_t fshr_clamp(uint32_t lo, uint32_t hi, uint32_t sh) {
+#ifdef __CUDA_ARCH__
+    return __funnelshift_rc(lo, hi, sh);
+#else
+    const uint64_t v = ((uint64_t)hi << 32) | lo;
+    return (uint32_t)(v >> (sh < 32u ? sh : 32u));
+#endif
+}
+OZ_HD uint32_t fshl(uint32_t lo, uint32_t hi, uint32_t sh) {
+#ifdef __CUDA_ARCH__
+    return __funnelshift_l(lo, hi, sh);
+#else
+    const uint64_t v = ((uint64_t)hi << 32) | lo;
+    return (uint32_t)((v << (sh & 31u)) >> 32);
+#endif
+}
+
+// fixed_biased in 32-bit words (the kernels' form): the same w = q + kBias, returned as
+// its low and high words. The significand moved up 8 bits is (h:l); it moves down by
+// sh = ex_max - ex in two clamped steps of at most 32 (sh = 64 for a zero exponent field,
+// which leaves 0); a negative entry is complemented into the bias add (w = (q ^ s) + kBias
+// + (s & 1) with s the sign mask), one 32-bit add with carry per word.
+OZ_HD void fixed_biased_words(uint32_t lo, uint32_t hi, uint32_t ex_max, uint32_t& wlo, uint32_t& whi) {
+    const uint32_t ex = (hi >> 20) & 0x7FFu;
+    const uint32_t sh = ex ? ex_max - ex : 64u;
+    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+    uint32_t h = fshl(lo, mh, 8u), l = lo << 8;
+    const uint32_t s1 = sh < 32u ? sh : 32u, s2 = sh - s1;
+    l = fshr_clamp(l, h, s1);
+    h = fshr_clamp(h, 0u, s1);
+    l = fshr_clamp(l, h, s2);
+    h = fshr_clamp(h, 0u, s2);
+    const uint32_t sm = (uint32_t)((int32_t)hi >> 31);   // all ones for a negative entry
+    const uint64_t lo_sum = (uint64_t)(l ^ sm) + 0x80808080u + (sm & 1u);
+    wlo = (uint32_t)lo_sum;
+    whi = (h ^ sm) + 0x80808080u + (uint32_t)(lo_sum >> 32);
+}
+
 // digit t (0 = top) of a biased word
 OZ_HD int digit(uint64_t w, int t) { return (int)((w >> (8 * (kDigits - 1 - t))) & 0xFFu) - 128; }
 

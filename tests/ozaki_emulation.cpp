@@ -67,6 +67,18 @@ void oz_gram(int64_t n, const double* V, int ka, const double* Y, int kb, int cu
 }
 
 extern "C" {
+// the 64-bit and the 32-bit-word forms of the biased fixed-point word of each entry
+void oz_biased_both(const double* x, int64_t n, uint32_t ex, uint64_t* out) {
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t b;
+        memcpy(&b, x + i, 8);
+        out[2 * i] = fixed_biased((uint32_t)b, (uint32_t)(b >> 32), ex);
+        uint32_t wl, wh;
+        fixed_biased_words((uint32_t)b, (uint32_t)(b >> 32), ex, wl, wh);
+        out[2 * i + 1] = ((uint64_t)wh << 32) | wl;
+    }
+}
+
 // both roundings of v 2^e2 for v = hi 2^64 + lo (two's complement): the FP64 reference and
 // the integer-only one the kernels use
 void oz_round_both(uint64_t hi, uint64_t lo, int e2, double* out) {

@@ -184,7 +184,7 @@ def test_tc_gram_wait_timeout_gives_nan_and_recovers():
 
 # ------------------------------------------------------------------ block update on the tensor cores
 @pytest.mark.parametrize("n,ka,kb", [(4096, 12, 5), (5000, 0, 3), (300001, 32, 9), (31, 3, 2), (1, 1, 1),
-                                     (130, 16, 8), (2_097_152, 32, 9)])
+                                     (130, 16, 8), (2_097_152, 32, 9), (4099, 13, 8), (50000, 27, 4), (777, 17, 9)])
 def test_tc_block_update_matches_oracle(n, ka, kb):
     """Y <- Y - V T and G = Y^T Y on the tensor cores against the oracle's block update:
     every updated column to 1e-14 relative (the FP64 kernel's bar) and G to 1e-14 of the

@@ -214,3 +214,20 @@ def test_integer_rounding_equals_fp64_rounding(emu):
             exact = Fraction(v) * Fraction(2) ** e2
             assert out[0] == out[1], (v, e2)
             assert out[0] == float(exact), (v, e2)   # Python's float() of a Fraction rounds correctly
+
+
+def test_word_form_equals_64_bit_form(emu):
+    """The kernels' 32-bit-word fixed-point conversion equals the 64-bit definition for
+    every entry: signs, zeros, subnormals, entries at the bound and far below it."""
+    emu.oz_biased_both.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_uint32,
+                                   ctypes.POINTER(ctypes.c_uint64)]
+    rng = np.random.default_rng(7)
+    x = np.concatenate([rng.standard_normal(4000) * np.exp2(rng.integers(-80, 8, 4000)),
+                        [0.0, -0.0, 5e-324, -5e-324, 2.2e-308, 1.0, -1.0, 0.5, np.nextafter(2.0, 0.0), -1.9999999]])
+    out = np.zeros(2 * x.size, dtype=np.uint64)
+    for ex in (1023, 1024, 1030, 1100, 1500, 2000):
+        m = np.abs(x) < np.exp2(ex - 1022)          # entries within the bound of this exponent
+        xs = np.ascontiguousarray(x[m])
+        o = np.zeros(2 * xs.size, dtype=np.uint64)
+        emu.oz_biased_both(_p(xs), xs.size, ex, o.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        assert np.array_equal(o[0::2], o[1::2]), ex
