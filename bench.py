@@ -620,7 +620,8 @@ def main():
         # the paper's test problem (Sec. 5): variable coefficients, gamma = 50, beta = 1,
         # the paper's initial guess, to 1e-8 relative; Table 6.1's settings: GMRES(10),
         # 2-step GMRES(10) (the paper's 2-GMRES(5): m = 10 Krylov vectors per cycle), Omin(4)
-        # and 2-step Omin(2); GMRES with red-black ILU(0) (the paper: natural-ordering ILU(0))
+        # and 2-step Omin(2); unpreconditioned, with the paper's ILU(0) (natural ordering,
+        # hyperplane sweeps) and with the red-black ILU(0)
         paper = {}
         for Np in (64, 128, 192, 256):
             Pp = inputs.paper_problem(Np)
@@ -632,7 +633,11 @@ def main():
                              ("sstep2_gmres10", dict(s=2, m=10)),
                              ("omin4", dict(omin=True, s=1, k=4)), ("sstep2_omin2", dict(omin=True, s=2, k=2)),
                              ("omin4_rbilu0", dict(omin=True, s=1, k=4, precond="rbilu0")),
-                             ("sstep2_omin2_rbilu0", dict(omin=True, s=2, k=2, precond="rbilu0"))):
+                             ("sstep2_omin2_rbilu0", dict(omin=True, s=2, k=2, precond="rbilu0")),
+                             ("gmres10_ilu0", dict(s=1, m=10, precond="ilu0")),
+                             ("sstep2_gmres10_ilu0", dict(s=2, m=10, precond="ilu0")),
+                             ("omin4_ilu0", dict(omin=True, s=1, k=4, precond="ilu0")),
+                             ("sstep2_omin2_ilu0", dict(omin=True, s=2, k=2, precond="ilu0"))):
                 xp = torch.tensor(Pp["x0"], device=dev)
                 for rep in range(2):
                     xp.copy_(torch.tensor(Pp["x0"], device=dev))

@@ -81,6 +81,17 @@ int stencil_matrix_info(sstep_matrix A, int64_t* n, double* norm_inf);
  * distinct. Stream-ordered. */
 int stencil_matrix_rbilu0_apply(sstep_matrix A, const double* v, double* w, void* stream);
 
+/* w = M^-1 v for ILU(0) of A in the natural ordering (Sec. 5: the paper's right
+ * preconditioner; the preconditioner of SSTEP_PRECOND_ILU0). With no fill outside A's
+ * sparsity, L U = A there: U = diag(d) + the upper part of A, L = I + A[p, p - e_k] / d[p - e_k]
+ * below it, d[p] = A[p,p] - sum_k A[p, p - e_k] A[p - e_k, p] / d[p - e_k]. The factors
+ * ((dim + 1) n doubles) are built on first use and kept with A. Both substitutions run as
+ * sweeps over the hyperplanes x + y (+ z) = c, one CTA with a barrier between hyperplanes
+ * (2N - 1 of them in 2-D, 3N - 2 in 3-D), every operation rounded as written, so the
+ * result is that of the plain point-by-point substitutions in the natural order. v, w:
+ * DEVICE arrays of n, distinct. Stream-ordered. */
+int stencil_matrix_ilu0_apply(sstep_matrix A, const double* v, double* w, void* stream);
+
 /* The Newton-basis shifts theta_1..theta_s of the last s-step GMRES solve on A with
  * basis = SSTEP_BASIS_NEWTON (HOST output, up to cap values). Returns their number (0
  * when the last solve kept the monomial powers), or SSTEP_ERR_ARG. */
@@ -242,8 +253,9 @@ typedef struct {
                            ordering (the sparsity pattern of A, d~_b = a0_b - sum_r A[b,r] A[r,b] /
                            a0_r); powers of A M^-1, x = x0 + M^-1 V y (Orthomin: the steps P a
                            accumulate and x += M^-1 of them before every explicit residual), true
-                           restart residual; sigma defaults to 1. The paper uses ILU(0) in the
-                           natural ordering. */
+                           restart residual; sigma defaults to 1.
+                           SSTEP_PRECOND_ILU0: the same right preconditioning with ILU(0) in the
+                           natural ordering (the paper's, Sec. 5; see stencil_matrix_ilu0_apply). */
 } sstep_params;
 
 #define SSTEP_BASIS_MONOMIAL 0
@@ -252,6 +264,7 @@ typedef struct {
 
 #define SSTEP_PRECOND_NONE 0
 #define SSTEP_PRECOND_RBILU0 1
+#define SSTEP_PRECOND_ILU0 2
 
 #define SSTEP_PREC_FP64 0
 #define SSTEP_PREC_DF64 1

@@ -43,6 +43,7 @@ SIGNATURES = {
     "stencil_matrix_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "sstep_last_shifts": (c_int, [c_void_p, P(c_double), c_int]),
     "stencil_matrix_rbilu0_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "stencil_matrix_ilu0_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "sstep_newton_shifts": (c_int, [P(c_double), c_int, c_int, c_int, P(c_double)]),
     "sstep_set_workspace_limit": (c_int, [c_int64]),
     "stencil_matrix_smooth": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_void_p]),
@@ -223,6 +224,12 @@ class StencilMatrix:
                       lib().stencil_matrix_rbilu0_apply(self.handle, _vec(v, self.n, "v"), _vec(w, self.n, "w"),
                                                         _stream(stream)))
 
+    def ilu0_apply(self, v, w, stream=None):
+        """w = M^-1 v, M the natural-ordering ILU(0) of this operator (the paper's)."""
+        return _check("stencil_matrix_ilu0_apply",
+                      lib().stencil_matrix_ilu0_apply(self.handle, _vec(v, self.n, "v"), _vec(w, self.n, "w"),
+                                                      _stream(stream)))
+
     def smooth(self, f, x, work, sweeps, omega, stream=None):
         return stencil_matrix_smooth(self, f, x, work, sweeps, omega, stream)
 
@@ -346,7 +353,7 @@ def sstep_block_update(V, Y, T, work=None, stream=None, tc=False):
 
 
 BASES = {"monomial": 0, "newton": 1, "ortho": 2}
-PRECONDS = {None: 0, "none": 0, "rbilu0": 1}
+PRECONDS = {None: 0, "none": 0, "rbilu0": 1, "ilu0": 2}
 
 
 def _solve(name, A, f, x, s=1, m=20, k=1, tol=1e-8, max_cycles=1000, max_iters=100000, sigma=0.0,
@@ -373,7 +380,8 @@ def sstep_gmres_solve(A, f, x, s, m, tol, max_cycles=1000, sigma=0.0, history_ca
 
     precision: "fp64", "df64" (double-float basis) or "fp32" (FP32 basis, FP32 iterative refinement).
     basis: "monomial" (as printed) or "newton" (shifts from the first cycle's Ritz values).
-    precond: None or "rbilu0" (right ILU(0) in red-black ordering; FP64 basis).
+    precond: None, "rbilu0" (right ILU(0) in red-black ordering) or "ilu0" (right ILU(0) in the
+    natural ordering, the paper's); FP64 basis.
     """
     r = _solve("sstep_gmres_solve", A, f, x, s=s, m=m, tol=tol, max_cycles=max_cycles, sigma=sigma,
                history_cap=history_cap, stream=stream, precision=precision, x0_guard=x0_guard, basis=basis,
@@ -392,7 +400,7 @@ def gmres_solve(A, f, x, m, tol, max_cycles=1000, history_cap=4096, stream=None,
 
 def sstep_omin_solve(A, f, x, s, k, tol, max_iters=100000, sigma=0.0, history_cap=4096, stream=None, precond=None,
                      basis="monomial"):
-    """s-step Orthomin(k) (Alg. 3.1); s = 1 is Orthomin(k). precond: None or "rbilu0".
+    """s-step Orthomin(k) (Alg. 3.1); s = 1 is Orthomin(k). precond: None, "rbilu0" or "ilu0".
     basis: "monomial" (as printed) or "ortho" (A^T A-orthonormal direction blocks, Sec. 3)."""
     return _solve("sstep_omin_solve", A, f, x, s=s, k=k, tol=tol, max_iters=max_iters, sigma=sigma,
                   history_cap=history_cap, stream=stream, precond=precond, basis=basis)
@@ -439,13 +447,31 @@ def trace_read():
     return out
 
 
-def tune_cache_key(shapes, s, m, device):
-    """The key of a batch's tuned launch configuration: the device name, s, m and a hash
-    of the systems' grid shapes in batch order (what the timing depends on)."""
+def library_build_id():
+    """A hash of the kernel sources this package builds libsstep.so from (its csrc files
+    and the C header): tuned timings are only valid for the kernels they were taken on."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    names = sorted(os.listdir(csrc)) if os.path.isdir(csrc) else []
+    for nm in names:
+        with open(os.path.join(csrc, nm), "rb") as fh:
+            h.update(nm.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def tune_cache_key(shapes, s, m, device, tol=1e-8, sigma=0.0, x0_guard=False, build=None):
+    """The key of a batch's tuned launch configuration: what the timing depends on. The
+    device name, s, m, the tolerance, sigma and the x0 guard (they change the cycle counts),
+    a hash of the systems' grid shapes in batch order and the library build
+    (library_build_id)."""
     import hashlib
 
     h = hashlib.sha256(repr([tuple(int(v) for v in sh) for sh in shapes]).encode()).hexdigest()[:16]
-    return f"{device}|s={int(s)}|m={int(m)}|n={len(shapes)}|{h}"
+    b = library_build_id() if build is None else build
+    return (f"{device}|s={int(s)}|m={int(m)}|tol={float(tol)!r}|sigma={float(sigma)!r}|guard={int(bool(x0_guard))}"
+            f"|n={len(shapes)}|{h}|build={b}")
 
 
 def tune_cache_get(path, key):
@@ -464,21 +490,29 @@ def tune_cache_get(path, key):
 
 
 def tune_cache_put(path, key, cfg):
-    """Adds (or replaces) key's configuration, rewriting the file atomically."""
+    """Adds (or replaces) key's configuration, rewriting the file atomically. The
+    read-modify-write holds an exclusive lock on path + ".lock", so processes that write
+    at the same time keep each other's entries."""
+    import fcntl
     import json
 
-    try:
-        with open(path) as fh:
-            data = json.load(fh)
-        if not isinstance(data, dict):
-            data = {}
-    except (OSError, ValueError):
-        data = {}
-    data[key] = dict(cfg)
-    tmp = f"{path}.{os.getpid()}.tmp"
-    with open(tmp, "w") as fh:
-        json.dump(data, fh, indent=1, sort_keys=True)
-    os.replace(tmp, path)
+    with open(path + ".lock", "a") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            try:
+                with open(path) as fh:
+                    data = json.load(fh)
+                if not isinstance(data, dict):
+                    data = {}
+            except (OSError, ValueError):
+                data = {}
+            data[key] = dict(cfg)
+            tmp = f"{path}.{os.getpid()}.tmp"
+            with open(tmp, "w") as fh:
+                json.dump(data, fh, indent=1, sort_keys=True)
+            os.replace(tmp, path)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
 
 
 class BatchSolver:
@@ -495,6 +529,7 @@ class BatchSolver:
         self.mats = list(mats)
         self.n = len(self.mats)
         self.s, self.m = s, m
+        self.tol, self.sigma, self.x0_guard = tol, sigma, bool(x0_guard)
         h = c_void_p()
         arr = (c_void_p * self.n)(*[A.handle.value for A in self.mats])
         p = SStepParams(s=s, m=m, k=0, tol=tol, max_cycles=max_cycles, max_iters=0, sigma=sigma, history=None,
@@ -523,7 +558,8 @@ class BatchSolver:
         if cache:
             import torch
 
-            key = tune_cache_key([A.shape for A in self.mats], self.s, self.m, torch.cuda.get_device_name())
+            key = tune_cache_key([A.shape for A in self.mats], self.s, self.m, torch.cuda.get_device_name(),
+                                 tol=self.tol, sigma=self.sigma, x0_guard=self.x0_guard)
             hit = tune_cache_get(cache, key)
             if hit is not None:
                 self.configure(**hit)

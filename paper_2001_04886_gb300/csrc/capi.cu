@@ -24,6 +24,7 @@ struct sstep_matrix_s {
     StencilDesc A;
     std::vector<double> shifts;      // Newton-basis shifts of the last s-step GMRES solve (host)
     double* rbilu = nullptr;         // red-black ILU(0) reciprocal pivots (device, n), built on first use
+    double* nilu = nullptr;          // natural-ordering ILU(0) factors (device, (dim + 1) n), built on first use
     double norm_inf = 0.0;
     double* fields = nullptr;        // owned copies of variable coefficients (7 x n)
     float2* fields_df = nullptr;     // the same as float pairs (mixed-precision kernels)
@@ -200,6 +201,17 @@ std::vector<double> newton_shifts_from_device(const double* G_dev, int m, int K,
 bool tc_gram_enabled() {
     static const bool on = [] {
         const char* v = getenv("SSTEP_TC_GRAM");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+// The tensor-core passes read the basis from its kept fixed-point words (a second panel
+// written by the Gram pass of each block) unless SSTEP_TC_WORDS=0 makes them convert the
+// FP64 columns every time (for comparisons).
+bool tc_words_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("SSTEP_TC_WORDS");
         return !(v && v[0] == '0');
     }();
     return on;
@@ -879,6 +891,7 @@ int stencil_matrix_destroy(sstep_matrix M) {
     if (M->ws) cudaFree(M->ws);
     if (M->hdr) cudaFreeHost(M->hdr);
     if (M->rbilu) cudaFree(M->rbilu);
+    if (M->nilu) cudaFree(M->nilu);
     delete M;
     return SSTEP_OK;
 }
@@ -960,10 +973,10 @@ int sstep_newton_shifts(const double* G, int ldg, int K, int s, double* theta) {
     return SSTEP_OK;
 }
 
-int stencil_matrix_rbilu0_apply(sstep_matrix M, const double* v, double* w, void* stream) {
-    if (!M || !v || !w || v == w) return SSTEP_ERR_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (!M->rbilu) {
+namespace {
+// the factors of the right preconditioner `kind`, built on first use and kept with A
+int ensure_precond(sstep_matrix M, int kind, cudaStream_t st) {
+    if (kind == SSTEP_PRECOND_RBILU0 && !M->rbilu) {
         if (cudaMalloc((void**)&M->rbilu, sizeof(double) * M->A.n) != cudaSuccess) {
             cudaGetLastError();
             M->rbilu = nullptr;
@@ -971,7 +984,40 @@ int stencil_matrix_rbilu0_apply(sstep_matrix M, const double* v, double* w, void
         }
         launch_rbilu_setup(M->A, M->rbilu, st);
     }
-    launch_rbilu_apply(M->A, M->rbilu, v, w, nullptr, GATE_NONE, st);
+    if (kind == SSTEP_PRECOND_ILU0 && !M->nilu) {
+        if (cudaMalloc((void**)&M->nilu, sizeof(double) * (M->A.dim + 1) * M->A.n) != cudaSuccess) {
+            cudaGetLastError();
+            M->nilu = nullptr;
+            return SSTEP_ERR_OOM;
+        }
+        launch_nilu_setup(M->A, M->nilu, st);
+    }
+    return SSTEP_OK;
+}
+
+// w = M^-1 v for the preconditioner `kind` (its factors exist), gated like the solver's kernels
+void precond_apply(sstep_matrix M, int kind, const double* v, double* w, const SolverState* st, int gate,
+                   cudaStream_t s) {
+    if (kind == SSTEP_PRECOND_ILU0) launch_nilu_apply(M->A, M->nilu, v, w, st, gate, s);
+    else launch_rbilu_apply(M->A, M->rbilu, v, w, st, gate, s);
+}
+}  // namespace
+
+int stencil_matrix_rbilu0_apply(sstep_matrix M, const double* v, double* w, void* stream) {
+    if (!M || !v || !w || v == w) return SSTEP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_precond(M, SSTEP_PRECOND_RBILU0, st);
+    if (rc) return rc;
+    precond_apply(M, SSTEP_PRECOND_RBILU0, v, w, nullptr, GATE_NONE, st);
+    return check_launch();
+}
+
+int stencil_matrix_ilu0_apply(sstep_matrix M, const double* v, double* w, void* stream) {
+    if (!M || !v || !w || v == w) return SSTEP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_precond(M, SSTEP_PRECOND_ILU0, st);
+    if (rc) return rc;
+    precond_apply(M, SSTEP_PRECOND_ILU0, v, w, nullptr, GATE_NONE, st);
     return check_launch();
 }
 
@@ -1117,25 +1163,24 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     const int s = p->s, m = p->m;
     if (s < 1 || s > SSTEP_MAX_S || m < s || m > SSTEP_MAX_M || m % s != 0 || p->max_cycles < 0) return SSTEP_ERR_ARG;
     if (p->basis != SSTEP_BASIS_MONOMIAL && p->basis != SSTEP_BASIS_NEWTON) return SSTEP_ERR_ARG;
-    if (p->precond != SSTEP_PRECOND_NONE && (p->precond != SSTEP_PRECOND_RBILU0 || p->precision != SSTEP_PREC_FP64))
+    if (p->precond != SSTEP_PRECOND_NONE &&
+        ((p->precond != SSTEP_PRECOND_RBILU0 && p->precond != SSTEP_PRECOND_ILU0) || p->precision != SSTEP_PREC_FP64))
         return SSTEP_ERR_ARG;
-    const bool pre = p->precond == SSTEP_PRECOND_RBILU0;
+    const int pk = p->precond;
+    const bool pre = pk != SSTEP_PRECOND_NONE;
     cudaStream_t stream_ = (cudaStream_t)stream;
     if (p->precision == SSTEP_PREC_DF64) return sstep_gmres_mp<PREC_DF64>(M, f, x, p, res, stream_);
     if (p->precision == SSTEP_PREC_FP32) return sstep_gmres_mp<PREC_FP32>(M, f, x, p, res, stream_);
     if (p->precision != SSTEP_PREC_FP64) return SSTEP_ERR_ARG;
     const int64_t n = M->A.n, ld = col_ld(n);
-    // columns: U (m+1), the raw start vector and, preconditioned, M^-1 of a power
-    Layout l = plan(n, m + 2 + (pre ? 1 : 0), m, p->history ? p->history_cap : 0);
+    // tensor-core Gram pass and block update (off with a preconditioner)
+    const bool tcg = !pre && tc_gram_enabled();
+    // columns: U (m+1), the raw start vector and, preconditioned, M^-1 of a power; with the
+    // tensor-core passes also m columns of the basis in fixed-point words
+    const int ncols0 = m + 2 + (pre ? 1 : 0);
+    Layout l = plan(n, ncols0 + (tcg ? m : 0), m, p->history ? p->history_cap : 0);
     if ((rc = ensure_workspace(M, l.total))) return rc;
-    if (pre && !M->rbilu) {   // d~ of the red-black ILU(0), once per matrix
-        if (cudaMalloc((void**)&M->rbilu, sizeof(double) * n) != cudaSuccess) {
-            cudaGetLastError();
-            M->rbilu = nullptr;
-            return SSTEP_ERR_OOM;
-        }
-        launch_rbilu_setup(M->A, M->rbilu, stream_);
-    }
+    if (pre && (rc = ensure_precond(M, pk, stream_))) return rc;   // the factors, once per matrix
     SolverState h = init_state(l, M->ws, p, s, m, 0);
     // sigma: 1 / ||A||_inf; preconditioned, A M^-1 has its spectrum near 1 and sigma = 1
     h.sigma = p->sigma > 0.0 ? p->sigma : (pre ? 1.0 : 1.0 / M->norm_inf);
@@ -1156,8 +1201,11 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     const double sigma = h.sigma;
     const int nb = m / s;
     // tensor-core Gram pass: the producers of every basis and power column record its bound
-    // (bnd[c] for basis column c, pbnd(k)[j] for power j of block k), zeroed per cycle
-    const bool tcg = !pre && tc_gram_enabled();
+    // (bnd[c] for basis column c, pbnd(k)[j] for power j of block k), zeroed per cycle. The
+    // pass that forms block k's Gram matrix also keeps the block's columns as fixed-point
+    // words (Wp, relative to the same bounds), which the later inner products and updates
+    // of the cycle read instead of converting the FP64 columns again.
+    uint64_t* Wp = (tcg && tc_words_enabled()) ? (uint64_t*)(U + (int64_t)ncols0 * ld) : nullptr;
     unsigned* bnd = (unsigned*)(M->ws + l.bnd);
     auto pbnd = [&](int k) { return tcg ? bnd + (m + 1) + k * (s + 1) : nullptr; };
     auto ubnd = [&](int k) { return tcg ? bnd + (m + 1) + (nb + k) * (s + 1) : nullptr; };
@@ -1170,6 +1218,7 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
     M->shifts.clear();
     for (;;) {
         if (tcg) CUDA_TRY(cudaMemsetAsync(bnd, 0, sizeof(unsigned) * kBndSlots, stream_));
+        int wcols = 0;   // basis columns of this cycle whose words are in Wp
         e = Epi();
         e.st = st;
         e.mode = EPI_RESTART;
@@ -1194,8 +1243,8 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
             } else {   // right preconditioning: y^{j+1} = sigma (A M^-1 y^j - theta_j y^j)
                 launch_scale_copy(uraw, U + o * ld, n, &st->vscale, st, GATE_BUILDING, stream_);
                 for (int j = 1; j <= s; ++j) {
-                    TRACED(K_PRECOND, stream_, launch_rbilu_apply(M->A, M->rbilu, U + (o + j - 1) * ld, ptmp, st,
-                                                                  GATE_BUILDING, stream_));
+                    TRACED(K_PRECOND, stream_, precond_apply(M, pk, U + (o + j - 1) * ld, ptmp, st, GATE_BUILDING,
+                                                             stream_));
                     TRACED(K_STENCIL, stream_, launch_stencil(M->A, ptmp, sigma, U + (o + j) * ld, 0.0, nullptr,
                                                               nullptr, st, GATE_BUILDING, stream_, theta[j - 1],
                                                               U + (o + j - 1) * ld));
@@ -1206,9 +1255,10 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
                 e.st = st;
                 e.mode = EPI_GM_T;
                 e.o = o;
+                const bool vw = wcols >= o;   // every earlier column's words are kept
                 TRACED(K_GRAM, stream_,
-                       if (!tcg || !launch_gram_oz(n, U, ld, o, bnd, U + (o + 1) * ld, ld, s, pb + 1, sc, e,
-                                                   GATE_BUILDING, stream_))
+                       if (!tcg || !launch_gram_oz(n, vw ? (const double*)Wp : U, ld, o, bnd, U + (o + 1) * ld, ld, s,
+                                                   pb + 1, sc, e, GATE_BUILDING, stream_, vw ? 1 : 0))
                            launch_gram(n, U, ld, o, U + (o + 1) * ld, ld, s, 0, sc, e, GATE_BUILDING, stream_));
             }
             // step 7 and Scalar1: project, then Gram of the projected block
@@ -1219,15 +1269,20 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
             bool done = false;
             if (tcg) {   // tensor cores: projection (k > 0), then the Gram pass of the s + 1 columns
                 bool proj = k == 0;
-                if (k > 0)
+                if (k > 0) {
+                    const bool vw = wcols >= o;
                     TRACED(K_UPDATE, stream_,
-                           proj = launch_update_oz(n, U, ld, o, bnd, U + o * ld, ld, 1, s, h.T, m, ub + 1, bnd + o + 1,
-                                                   s - 1, pb, ub, st, GATE_BUILDING, stream_));
+                           proj = launch_update_oz(n, vw ? (const double*)Wp : U, ld, o, bnd, U + o * ld, ld, 1, s, h.T,
+                                                   m, ub + 1, bnd + o + 1, s - 1, pb, ub, st, GATE_BUILDING, stream_,
+                                                   nullptr, vw ? 1 : 0));
+                }
                 unsigned* yb = k > 0 ? ub : pb;
                 if (proj)
                     TRACED(K_UPDATE, stream_,
                            done = launch_gram_oz(n, U + o * ld, ld, s + 1, yb, U + o * ld, ld, s + 1, yb, sc, e,
-                                                 GATE_BUILDING, stream_));
+                                                 GATE_BUILDING, stream_, 0, Wp ? Wp + (int64_t)o * ld : nullptr, ld,
+                                                 Wp ? s : 0));
+                if (done && Wp && wcols == o) wcols = o + s;   // this block's words are kept
                 if (proj && !done)   // projected on the tensor cores; Gram in FP64
                     TRACED(K_UPDATE, stream_, launch_update(n, U, ld, 0, U + o * ld, ld, U + o * ld, ld, s + 1, 1, h.T, m,
                                                             -1.0, true, sc, e, GATE_BUILDING, stream_));
@@ -1257,7 +1312,7 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
             CUDA_TRY(cudaMemsetAsync(ptmp, 0, sizeof(double) * n, stream_));
             TRACED(K_AXPY, stream_, launch_update(n, U, ld, -1, ptmp, ld, ptmp, ld, 1, 0, nullptr, 0, 1.0, false, sc,
                                                   e, GATE_ACTIVE, stream_));
-            TRACED(K_PRECOND, stream_, launch_rbilu_apply(M->A, M->rbilu, ptmp, uraw, st, GATE_ACTIVE, stream_));
+            TRACED(K_PRECOND, stream_, precond_apply(M, pk, ptmp, uraw, st, GATE_ACTIVE, stream_));
             launch_add(x, uraw, n, st, GATE_ACTIVE, stream_);
         }
         CUDA_TRY(cudaGetLastError());
@@ -1342,10 +1397,12 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
     if (rc) return rc;
     const int s = p->s, k = p->k;
     if (s < 1 || s > SSTEP_MAX_S || k < 0 || (int64_t)k * s > SSTEP_MAX_COLS || p->max_iters < 0) return SSTEP_ERR_ARG;
-    if (p->precision != SSTEP_PREC_FP64 || (p->precond != SSTEP_PRECOND_NONE && p->precond != SSTEP_PRECOND_RBILU0))
+    if (p->precision != SSTEP_PREC_FP64 || (p->precond != SSTEP_PRECOND_NONE && p->precond != SSTEP_PRECOND_RBILU0 &&
+                                             p->precond != SSTEP_PRECOND_ILU0))
         return SSTEP_ERR_ARG;
     if (p->basis != SSTEP_BASIS_MONOMIAL && p->basis != SSTEP_BASIS_ORTHO) return SSTEP_ERR_ARG;
-    const bool pre = p->precond == SSTEP_PRECOND_RBILU0;
+    const int pk = p->precond;
+    const bool pre = pk != SSTEP_PRECOND_NONE;
     const int ortho = p->basis == SSTEP_BASIS_ORTHO;
     if (ortho && (int64_t)(k + 1) * s > SSTEP_MAX_COLS) return SSTEP_ERR_ARG;
     cudaStream_t stream_ = (cudaStream_t)stream;
@@ -1356,14 +1413,7 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
     // accumulated correction du (the method runs on A M^-1: x = x0 + M^-1 du) and a scratch
     Layout l = plan(n, 2 * nslots * s + s + 1 + (pre ? 2 : 0), 1, p->history ? p->history_cap : 0);
     if ((rc = ensure_workspace(M, l.total))) return rc;
-    if (pre && !M->rbilu) {
-        if (cudaMalloc((void**)&M->rbilu, sizeof(double) * n) != cudaSuccess) {
-            cudaGetLastError();
-            M->rbilu = nullptr;
-            return SSTEP_ERR_OOM;
-        }
-        launch_rbilu_setup(M->A, M->rbilu, stream_);
-    }
+    if (pre && (rc = ensure_precond(M, pk, stream_))) return rc;
     SolverState h = init_state(l, M->ws, p, s, 1, k);
     h.sigma = p->sigma > 0.0 ? p->sigma : (pre ? 1.0 : 1.0 / M->norm_inf);
     SolverState* st = (SolverState*)(M->ws + l.state);
@@ -1392,8 +1442,8 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
             return;
         }
         for (int j = 0; j < s; ++j) {
-            TRACED(K_PRECOND, stream_, launch_rbilu_apply(M->A, M->rbilu, j == 0 ? r : AR + (j - 1) * ld, ptmp, st,
-                                                          GATE_BUILDING, stream_));
+            TRACED(K_PRECOND, stream_, precond_apply(M, pk, j == 0 ? r : AR + (j - 1) * ld, ptmp, st, GATE_BUILDING,
+                                                     stream_));
             TRACED(K_STENCIL, stream_, launch_stencil(M->A, ptmp, j == 0 ? 1.0 : sigma, AR + j * ld, 0.0, nullptr,
                                                       nullptr, st, GATE_BUILDING, stream_));
         }
@@ -1401,7 +1451,7 @@ int sstep_omin_solve(sstep_matrix M, const double* f, double* x, const sstep_par
     // x += M^-1 du, du = 0 (at a restart the solve is active, so the gated kernels run)
     auto fold = [&](int gate) -> int {
         if (!pre) return SSTEP_OK;
-        TRACED(K_PRECOND, stream_, launch_rbilu_apply(M->A, M->rbilu, du, ptmp, st, gate, stream_));
+        TRACED(K_PRECOND, stream_, precond_apply(M, pk, du, ptmp, st, gate, stream_));
         launch_add(x, ptmp, n, st, gate, stream_);
         return cudaMemsetAsync(du, 0, sizeof(double) * n, stream_) == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA;
     };

@@ -89,9 +89,13 @@ void launch_update(int64_t n, const double* V, int64_t ldv, int ka, const double
 // word of |x| per column, launch_colmax or the producing kernel). Returns false, launching
 // nothing, for shapes it does not take (ka > 64, kb > 9, n > 2^27, V or Y not 8-byte
 // aligned, no Scratch::acc). A bounded wait that runs out gives NaN entries.
+// vw = 1: V holds, in place of each FP64 entry, its biased fixed-point word (the
+// fixed_biased value for the column's bound vmax), as kept by an earlier pass. wout: keep
+// the words of V's first nw columns there (leading dimension ldw, even; 16-byte aligned),
+// for later passes to read with vw = 1.
 bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, const double* Y,
                     int64_t ldy, int kb, const unsigned* ymax, Scratch sc, const Epi& epi, int gate,
-                    cudaStream_t stream);
+                    cudaStream_t stream, int vw = 0, uint64_t* wout = nullptr, int64_t ldw = 0, int nw = 0);
 // Yhat[:, j] = Y[:, j] - V T[:, j], j0 <= j < j0 + kbo, in place, on the tensor cores (exact
 // 61-bit fixed-point products, one rounding of V T, then the FP64 difference); vmax: the
 // bounds of the ka V columns. bout[j - j0] (and bout2[j - j0] for j - j0 < nb2) receive the
@@ -101,7 +105,7 @@ bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsig
 bool launch_update_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, double* Y, int64_t ldy,
                       int j0, int kbo, const double* T, int ldt, unsigned* bout, unsigned* bout2, int nb2,
                       const unsigned* bcopy_src, unsigned* bcopy_dst, const SolverState* st, int gate,
-                      cudaStream_t stream, unsigned* err = nullptr);
+                      cudaStream_t stream, unsigned* err = nullptr, int vw = 0);   // vw: as launch_gram_oz
 // out[c] = column bound of column c (out must be zeroed first)
 void launch_colmax(int64_t n, const double* X, int64_t ld, int ncols, unsigned* out, cudaStream_t stream);
 int oz_partials_doubles();      // per-CTA partials of the tensor-core Gram pass (none: sums go to Scratch::acc)
@@ -133,6 +137,11 @@ void launch_convdiff_fields(const double* beta, double h, int64_t n, double* out
 void launch_rbilu_setup(const StencilDesc& A, double* dt, cudaStream_t s);
 void launch_rbilu_apply(const StencilDesc& A, const double* dt, const double* v, double* w, const SolverState* st,
                         int gate, cudaStream_t s);
+// ILU(0) in the natural ordering (precond.cu): the factors f = [d | L_x | L_y | L_z] ((dim + 1)
+// arrays of n; 2-D: three) by one hyperplane sweep, and w = M^-1 v (w != v) by two
+void launch_nilu_setup(const StencilDesc& A, double* f, cudaStream_t s);
+void launch_nilu_apply(const StencilDesc& A, const double* f, const double* v, double* w, const SolverState* st,
+                       int gate, cudaStream_t s);
 void launch_scale_copy(const double* src, double* dst, int64_t n, const double* dscale, const SolverState* st,
                        int gate, cudaStream_t s);
 void launch_add(double* x, const double* d, int64_t n, const SolverState* st, int gate, cudaStream_t s);

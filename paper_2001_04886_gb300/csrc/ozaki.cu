@@ -254,7 +254,7 @@ template <int G, int KB>
 __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
     gram_oz_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int ka, const unsigned* __restrict__ vmax,
                    const double* __restrict__ Y, int64_t ldy, const unsigned* __restrict__ ymax, Scratch sc, Epi epi,
-                   int gate, long spin, int sym) {
+                   int gate, long spin, int sym, int vw, uint64_t* __restrict__ wout, int64_t ldw, int nw) {
     using C = OzCfg<G, KB>;
     constexpr int BST = C::kBst;
     constexpr int kItems = (G == 0 ? 2 : 4 * G) + (KB + 7) / 8;   // column octets per split warp and stage
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
         // ---------------------------------------------------------------- MMA warp
         if (lane == 0) {
             int n_empty[NS] = {}, n_tfull[2] = {0, 0};
-            for (int64_t gs = 0; gs < nstages && !failed; ++gs) {
+            for (unsigned gs = 0; gs < (unsigned)nstages && !failed; ++gs) {
                 const int sb = (int)(gs % NS);
                 const int chunk = (int)(gs / C::kStagesPerChunk), sic = (int)(gs % C::kStagesPerChunk);
                 const int tb = chunk & 1;
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
                     }
                 mma_commit(&empty[sb]);
                 ++n_empty[sb];
-                if (sic == C::kStagesPerChunk - 1 || gs == nstages - 1) {
+                if (sic == C::kStagesPerChunk - 1 || gs + 1 == (unsigned)nstages) {
                     mma_commit(&tfull[tb]);
                     ++n_tfull[tb];
                 }
@@ -365,8 +365,18 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
         // item j: column octet j (V octets first, then Y octets) of this warp's K group of 8
         // rows; lane: column c8 of the octet, rows kk and kk + 1 of the stage
         // sym (V = Y): the V columns only, each digit stored into A and B
-        const int noct_v = (ka + 7) >> 3, noct = noct_v + (sym ? 0 : (KB + 7) / 8);
+        // zmode (the 9-column V^T V of the s-step block, s = 8): columns 0..7 as one octet in
+        // every warp, and column 8 as one item of 28 row pairs in each of warps 2 and 3 (the
+        // two sub-partitions with three split warps), instead of a second octet with one
+        // column in use in every warp; its stores meet bank conflicts, the issue slots are fewer
+        const bool zmode = G == 0 && KB == 9 && sym && ka == 9 && C::kSplitWarps == 14;
+        const int noct_v = zmode ? 1 : (ka + 7) >> 3, noct = noct_v + (sym ? 0 : (KB + 7) / 8);
         const int c8 = lane >> 2, kk = warp * 8 + (lane & 3) * 2;
+        const bool zw = zmode && (warp == 2 || warp == 3);            // warp-uniform
+        const int zrow = (warp - 2) * 56 + 2 * lane;                   // stage row of a z lane
+        const bool zl = zw && lane < 28;
+        const double* zp = Y + 8 * ldy + s0 * C::kRows + (zl ? zrow : 0);
+        const uint32_t ze = ex[ka + (KB > 8 ? 8 : 0)];
         // per item: the entry (row kk of this CTA's first stage) and whether it is 16-byte
         // aligned (kk and the stage height are even, so that holds for every stage)
         // per item: the entry in row kk of this CTA's first stage (a column past ka or kb reads
@@ -398,7 +408,18 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
             }
             bcol[j] = c;
         }
-        al = __all_sync(0xffffffffu, al);
+        al = __all_sync(0xffffffffu, al);   // (the z column is aligned with column 0, in every warp's test)
+        auto zload = [&](int64_t st, double2& z) {
+            z = make_double2(0.0, 0.0);
+            if (!zl) return;
+            const int64_t r = (s0 + st) * C::kRows + zrow;
+            if ((s0 + st + 1) * C::kRows <= n && al) {
+                z = __ldg(reinterpret_cast<const double2*>(zp + st * C::kRows));
+            } else {
+                if (r < n) z.x = __ldg(zp + st * C::kRows);
+                if (r + 1 < n) z.y = __ldg(zp + st * C::kRows + 1);
+            }
+        };
         auto load = [&](int64_t st, double2 (&buf)[kItems]) {
             const int64_t off = st * C::kRows, r = (s0 + st) * C::kRows + kk;
             const bool whole = (s0 + st + 1) * C::kRows <= n;   // warp-uniform: no row past n
@@ -418,12 +439,19 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
                 }
             }
         };
-        double2 cur[kItems];
-        if (nstages > 0) load(0, cur);
-        for (int64_t gs = 0; gs < nstages; ++gs) {
+        double2 cur[kItems], zcur = make_double2(0.0, 0.0);
+        if (nstages > 0) {
+            load(0, cur);
+            if (zw) zload(0, zcur);
+        }
+        for (unsigned gs = 0; gs < (unsigned)nstages; ++gs) {
             if (failed) break;
-            double2 nxt[kItems];
-            if (gs + 1 < nstages) load(gs + 1, nxt);
+            double2 nxt[kItems], znxt = make_double2(0.0, 0.0);
+            if (gs + 1 < (unsigned)nstages) {
+                load(gs + 1, nxt);
+                if (zw) zload(gs + 1, znxt);
+            }
+
             const int sb = (int)(gs % NS);
             if (gs >= NS && !oz_wait(smem_addr(&empty[sb]), (uint32_t)(((gs / NS) - 1) & 1), spin)) {
                 failed = 1;
@@ -437,8 +465,24 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
                     const uint64_t b0 = (uint64_t)__double_as_longlong(cur[j].x);
                     const uint64_t b1 = (uint64_t)__double_as_longlong(cur[j].y);
                     uint32_t l0, h0, l1, h1;
-                    oz::fixed_biased_words((uint32_t)b0, (uint32_t)(b0 >> 32), ce[j], l0, h0);
-                    oz::fixed_biased_words((uint32_t)b1, (uint32_t)(b1 >> 32), ce[j], l1, h1);
+                    if (isv && vw) {   // warp-uniform: V holds the biased fixed-point words already
+                        l0 = (uint32_t)b0;
+                        h0 = (uint32_t)(b0 >> 32);
+                        l1 = (uint32_t)b1;
+                        h1 = (uint32_t)(b1 >> 32);
+                    } else {
+                        oz::fixed_biased_words((uint32_t)b0, (uint32_t)(b0 >> 32), ce[j], l0, h0);
+                        oz::fixed_biased_words((uint32_t)b1, (uint32_t)(b1 >> 32), ce[j], l1, h1);
+                    }
+                    if (isv && wout) {   // keep the words of the first nw V columns (warp-uniform test)
+                        const int c = j * 8 + c8;
+                        const int64_t r = (s0 + (int64_t)gs) * C::kRows + kk;
+                        if (cv[j] && c < nw) {
+                            uint64_t* wp = wout + (int64_t)c * ldw + r;
+                            if (r + 1 < n) *reinterpret_cast<uint4*>(wp) = make_uint4(l0, h0, l1, h1);
+                            else if (r < n) *reinterpret_cast<uint2*>(wp) = make_uint2(l0, h0);
+                        }
+                    }
                     uint32_t d[oz::kDigits];
                     digits8(l0, h0, l1, h1, d);
                     if (isv) {   // unused columns of an octet land in unused A rows
@@ -473,11 +517,28 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
                     }
                 }
             }
+            if (zw) {   // column 8 of this stage's rows zrow, zrow + 1: A row t 16 + 8 and B row t BST + 8
+                const uint64_t b0 = (uint64_t)__double_as_longlong(zcur.x);
+                const uint64_t b1 = (uint64_t)__double_as_longlong(zcur.y);
+                uint32_t l0, h0, l1, h1;
+                oz::fixed_biased_words((uint32_t)b0, (uint32_t)(b0 >> 32), ze, l0, h0);
+                oz::fixed_biased_words((uint32_t)b1, (uint32_t)(b1 >> 32), ze, l1, h1);
+                uint32_t d[oz::kDigits];
+                digits8(l0, h0, l1, h1, d);
+                if (zl) {
+#pragma unroll
+                    for (int t = 0; t < oz::kDigits; ++t) {
+                        *reinterpret_cast<uint32_t*>(sp + op_off<SBO>(t * 16 + 8, zrow)) = d[t];
+                        *reinterpret_cast<uint32_t*>(sp + C::kAT * C::kTile + op_off<SBO>(t * BST + 8, zrow)) = d[t];
+                    }
+                }
+                zcur = znxt;
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) bar_arrive(&full[sb]);
             const int sic = (int)(gs % C::kStagesPerChunk);
-            if (sic == C::kStagesPerChunk - 1 || gs == nstages - 1) {   // drain the chunk's exact sums
+            if (sic == C::kStagesPerChunk - 1 || gs + 1 == (unsigned)nstages) {   // drain the chunk's exact sums
                 const int chunk = (int)(gs / C::kStagesPerChunk), tb = chunk & 1;
                 if (!oz_wait(smem_addr(&tfull[tb]), (uint32_t)((chunk >> 1) & 1), spin)) {
                     failed = 1;
@@ -587,7 +648,8 @@ void launch_colmax(int64_t n, const double* X, int64_t ld, int ncols, unsigned* 
 namespace {
 template <int G, int KB>
 void launch_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, const double* Y, int64_t ldy,
-               const unsigned* ymax, Scratch sc, const Epi& epi, int gate, cudaStream_t stream, long spin, int sym) {
+               const unsigned* ymax, Scratch sc, const Epi& epi, int gate, cudaStream_t stream, long spin, int sym,
+               int vw, uint64_t* wout, int64_t ldw, int nw) {
     using C = OzCfg<G, KB>;
     static bool attr[64] = {false};   // once per device
     int dev = 0;
@@ -600,7 +662,7 @@ void launch_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* 
     int grid = device_sms();
     if (grid > nst) grid = (int)std::max<int64_t>(nst, 1);
     gram_oz_kernel<G, KB><<<grid, C::kThreads, C::kSmem, stream>>>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate,
-                                                                    spin, sym);
+                                                                    spin, sym, vw, wout, ldw, nw);
 }
 }  // namespace
 
@@ -608,16 +670,21 @@ long g_oz_spin = kOzSpin;
 
 bool launch_gram_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, const double* Y,
                     int64_t ldy, int kb, const unsigned* ymax, Scratch sc, const Epi& epi, int gate,
-                    cudaStream_t stream) {
+                    cudaStream_t stream, int vw, uint64_t* wout, int64_t ldw, int nw) {
     if (ka < 1 || ka > kMaxCols || kb < 1 || kb > kMaxS + 1 || n < 1 || n > ((int64_t)1 << 27) || !sc.acc) return false;
     if (((uintptr_t)V & 7) || ((uintptr_t)Y & 7)) return false;
-    const int sym = (V == Y && ldv == ldy && ka == kb) ? 1 : 0;   // V^T V: split each column once
+    const int sym = (V == Y && ldv == ldy && ka == kb && !vw) ? 1 : 0;   // V^T V: split each column once
+    // kept words: 16-byte stores of row pairs (even leading dimension, aligned panel)
+    if (wout && (((uintptr_t)wout & 15) || (ldw & 1) || ldw < n || vw)) return false;
     switch (kb) {
 #define SSTEP_OZ_CASE(KB)                                                                                       \
     case KB:                                                                                                    \
-        if (ka <= 16) launch_oz<0, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym); \
-        else if (ka <= 32) launch_oz<1, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym); \
-        else launch_oz<2, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym);        \
+        if (ka <= 16) launch_oz<0, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym, vw, \
+                                       wout, ldw, nw);                                                          \
+        else if (ka <= 32) launch_oz<1, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym, \
+                                            vw, wout, ldw, nw);                                                 \
+        else launch_oz<2, KB>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, stream, g_oz_spin, sym, vw, wout, \
+                              ldw, nw);                                                                         \
         return true;
         SSTEP_OZ_CASE(1)
         SSTEP_OZ_CASE(2)
@@ -680,7 +747,7 @@ __global__ void __launch_bounds__(kUpThreads, 1)
     update_oz_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int ka, const unsigned* __restrict__ vmax,
                      double* Y, int64_t ldy, int j0, const double* __restrict__ T, int ldt, unsigned* bout,
                      unsigned* bout2, int nb2, const unsigned* bcopy_src, unsigned* bcopy_dst, const SolverState* st,
-                     int gate, long spin, unsigned* err) {
+                     int gate, long spin, unsigned* err, int vw) {
     using C = UpCfg<KAP, KBO>;
     constexpr int SBO = C::kSbo;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -843,7 +910,11 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;");
             // Q = sum_d S_d 256^(8 - d) = Qh 2^32 + Ql: Horner in 64 bits over the diagonals
             // 0..4 (Qh < 2^54) and 5..8 (Ql < 2^47), then one 128-bit step
-            long long Qh[H], Ql[H];
+            // Each S is an exact integer with |S| <= 2^22, so S + 1.5 2^23 is exact and its FP32
+            // bits are 0x4B400000 + S: the sums run over those bits (FP32 add, integer Horner)
+            // and the constant they add is taken off at the end.
+            constexpr unsigned kMagic = 0x4B400000u;
+            unsigned long long Qh[H], Ql[H];
 #pragma unroll
             for (int j = 0; j < H; ++j) Qh[j] = Ql[j] = 0;
             // columns (j, d) = 9 j + d of this thread's outputs, read 16 at a time from the
@@ -859,9 +930,11 @@ __global__ void __launch_bounds__(kUpThreads, 1)
 #pragma unroll
                 for (int j = 0; j < H; ++j) {
                     const int col = kUpDiags * (jo + j) + d - c0;
-                    const long long S = (jo + j < KBO && col < NR) ? __float2int_rn(__uint_as_float(rv[col])) : 0;
-                    if (d < 5) Qh[j] = Qh[j] * 256 + S;
-                    else Ql[j] = Ql[j] * 256 + S;
+                    const unsigned mS = (jo + j < KBO && col < NR)
+                                            ? (unsigned)__float_as_int(__uint_as_float(rv[col]) + 12582912.0f)
+                                            : kMagic;
+                    if (d < 5) Qh[j] = Qh[j] * 256 + mS;
+                    else Ql[j] = Ql[j] * 256 + mS;
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -871,7 +944,9 @@ __global__ void __launch_bounds__(kUpThreads, 1)
 #pragma unroll
                 for (int j = 0; j < H; ++j) {
                     if (jo + j < KBO) {
-                        const oz::i128 Q = ((oz::i128)Qh[j] << 32) + (oz::i128)Ql[j];
+                        const long long qh = (long long)(Qh[j] - (unsigned long long)kMagic * 0x0101010101ull);
+                        const long long ql = (long long)(Ql[j] - (unsigned long long)kMagic * 0x01010101ull);
+                        const oz::i128 Q = ((oz::i128)qh << 32) + (oz::i128)ql;
                         const int fj = fexp[jo + j];
                         const double P = (nonfinite || fj == (int)oz::kNonFinite)
                                              ? __longlong_as_double(0x7FF8000000000000ll)
@@ -900,6 +975,7 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             if (failed) break;
             double nxt[kIt];
             if (lt + 1 < nt) load(lt + 1, nxt);
+
             if (lt >= 1) load_y(lt - 1);   // consumed by the epilogue after this split
             const int b = (int)(lt & 1);
             if (lt >= 2 && !oz_wait(smem_addr(&empty[b]), (uint32_t)(((lt >> 1) - 1) & 1), spin)) {
@@ -911,8 +987,8 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             for (int i = 0; i < kIt; ++i) {
                 if (i < nit) {   // warp-uniform
                     const uint64_t bits = (uint64_t)__double_as_longlong(cur[i]);
-                    uint32_t wl, wh;
-                    oz::fixed_biased_words((uint32_t)bits, (uint32_t)(bits >> 32), ea[i], wl, wh);
+                    uint32_t wl = (uint32_t)bits, wh = (uint32_t)(bits >> 32);   // vw: the words already
+                    if (!vw) oz::fixed_biased_words((uint32_t)bits, (uint32_t)(bits >> 32), ea[i], wl, wh);
                     uint4 v;
                     digit_row8(wl, wh, v);
                     *reinterpret_cast<uint4*>(ap + soff0 + i * 4 * 128) = v;
@@ -959,7 +1035,7 @@ __global__ void __launch_bounds__(kUpThreads, 1)
 template <int KAP, int KBO>
 void launch_up(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, double* Y, int64_t ldy, int j0,
                const double* T, int ldt, unsigned* bout, unsigned* bout2, int nb2, const unsigned* bsrc,
-               unsigned* bdst, const SolverState* st, int gate, cudaStream_t stream, unsigned* err) {
+               unsigned* bdst, const SolverState* st, int gate, cudaStream_t stream, unsigned* err, int vw) {
     using C = UpCfg<KAP, KBO>;
     static bool attr[64] = {false};
     int dev = 0;
@@ -973,7 +1049,7 @@ void launch_up(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* 
     if (grid > ntiles) grid = (int)std::max<int64_t>(ntiles, 1);
     update_oz_kernel<KAP, KBO><<<grid, kUpThreads, C::kSmem, stream>>>(n, V, ldv, ka, vmax, Y, ldy, j0, T, ldt, bout,
                                                                         bout2, nb2, bsrc, bdst, st, gate, g_oz_spin,
-                                                                        err);
+                                                                        err, vw);
 }
 
 }  // namespace
@@ -981,16 +1057,16 @@ void launch_up(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* 
 bool launch_update_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* vmax, double* Y, int64_t ldy,
                       int j0, int kbo, const double* T, int ldt, unsigned* bout, unsigned* bout2, int nb2,
                       const unsigned* bcopy_src, unsigned* bcopy_dst, const SolverState* st, int gate,
-                      cudaStream_t stream, unsigned* err) {
+                      cudaStream_t stream, unsigned* err, int vw) {
     if (ka < 1 || ka > 32 || kbo < 1 || kbo > kMaxS + 1 || n < 1 || n > ((int64_t)1 << 27)) return false;
     const bool k16 = ka <= 16;
     switch (kbo) {
 #define SSTEP_UP_CASE(KBO)                                                                                      \
     case KBO:                                                                                                   \
         if (k16) launch_up<16, KBO>(n, V, ldv, ka, vmax, Y, ldy, j0, T, ldt, bout, bout2, nb2, bcopy_src,       \
-                                    bcopy_dst, st, gate, stream, err);                                          \
+                                    bcopy_dst, st, gate, stream, err, vw);                                      \
         else launch_up<32, KBO>(n, V, ldv, ka, vmax, Y, ldy, j0, T, ldt, bout, bout2, nb2, bcopy_src,           \
-                                bcopy_dst, st, gate, stream, err);                                              \
+                                bcopy_dst, st, gate, stream, err, vw);                                          \
         return true;
         SSTEP_UP_CASE(1)
         SSTEP_UP_CASE(2)

@@ -13,7 +13,7 @@ from oracle import sstep as osstep
 from oracle import stencil as ostencil
 from paper_2001_04886_gb300 import inputs
 from tests.gpu_util import dev, to_dev, torch
-from tests.parity_bars import first_block_tol
+from tests.parity_bars import cycle_abs_tol, cycle_x_tol, first_block_tol
 
 import paper_2001_04886_gb300 as pkg
 
@@ -48,7 +48,10 @@ def test_first_cycle(big, s):
     History over the first s-steps to max(1e-10, 4 u cond(W_1)) (tests/parity_bars.py):
     implementations that round the first block's Gram matrix differently differ there by
     a few u cond(W_1), which is ~1e11 for the scaled monomial block at s = 8 (u = 2^-53).
-    The iterate after the cycle to 1e-8 relative.
+    The rest of the cycle's history to 0.1 u cond(W_1) of its first entry (or 1e-6
+    relative), and the iterate after the cycle to max(1e-8, u cond(W_1)) relative: the
+    oracle's own first-cycle results move by less than that when its sums are taken in
+    extended precision (tests/test_parity_bar.py).
     """
     d, Ao, A, f = big
     sigma = 1.0 / Ao.norm_inf()
@@ -60,9 +63,10 @@ def test_first_cycle(big, s):
     h, hr = np.array(res["history"]), np.array(ref["history"])
     assert len(h) == len(hr) == 42
     assert np.max(np.abs(h[: s + 1] - hr[: s + 1]) / hr[: s + 1]) <= hist_tol
-    assert np.max(np.abs(h - hr) / hr) <= 1e-6
+    cond = float(np.linalg.cond(tr["W"][0]))
+    assert np.all(np.abs(h - hr) <= np.maximum(1e-6 * hr, cycle_abs_tol(cond) * hr[0]))
     x = xd.cpu().numpy()
-    assert np.linalg.norm(x - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+    assert np.linalg.norm(x - ref["x"]) <= cycle_x_tol(cond) * np.linalg.norm(ref["x"])
 
 
 def test_headline_solve_matches_oracle(big):

@@ -15,6 +15,33 @@ def test_key_depends_on_device_shape_and_method():
     assert k != B.tune_cache_key(shapes, 8, 40, "NVIDIA GB300")
     assert k != B.tune_cache_key(shapes, 4, 20, "another device")
     assert k != B.tune_cache_key(shapes[:2], 4, 20, "NVIDIA GB300")
+    # the stopping test, sigma, the x0 guard and the library build change what was timed
+    assert k != B.tune_cache_key(shapes, 4, 20, "NVIDIA GB300", tol=1e-10)
+    assert k != B.tune_cache_key(shapes, 4, 20, "NVIDIA GB300", sigma=0.25)
+    assert k != B.tune_cache_key(shapes, 4, 20, "NVIDIA GB300", x0_guard=True)
+    assert k != B.tune_cache_key(shapes, 4, 20, "NVIDIA GB300", build="0" * 16)
+    assert k == B.tune_cache_key(shapes, 4, 20, "NVIDIA GB300", build=B.library_build_id())
+
+
+def test_concurrent_writers_keep_each_others_entries(tmp_path):
+    """Writers in separate processes serialise their read-modify-write on a lock file."""
+    import multiprocessing as mp
+
+    p = str(tmp_path / "tune.json")
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_put_many, args=(p, i)) for i in range(4)]
+    for pr in procs:
+        pr.start()
+    for pr in procs:
+        pr.join(60)
+        assert pr.exitcode == 0
+    data = json.load(open(p))
+    assert sorted(data) == sorted(f"w{i}-{j}" for i in range(4) for j in range(25))
+
+
+def _put_many(path, i):
+    for j in range(25):
+        B.tune_cache_put(path, f"w{i}-{j}", CFG)
 
 
 def test_round_trip_and_replacement(tmp_path):

@@ -1,16 +1,19 @@
-"""The allocation-free Gram entry point against the allocating one.
+"""The allocation-free Gram entry point against the allocating one and the oracle.
 
 sstep_gram_noalloc serves callers that cannot allocate device memory when they
-call it (stream capture in progress, a fixed device-memory budget, a host that
-owns the allocator). It keeps its scratch in a fixed device array shared by all
-calls, so this test also runs it twice in a row: the second call must not see
-the first call's leftovers. This file is collected last on purpose.
+call it: applications that fix their device-memory budget at start-up, and hosts
+whose own allocator owns all device memory. It keeps its scratch in a fixed device
+array shared by all calls, so this test also runs it twice in a row: the second
+call must not see the first call's leftovers. The file is named to be collected
+last, so that a run which stops at its first failure has run every other test
+before this one.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle import sstep as osstep
 from paper_2001_04886_gb300 import inputs
 from tests.gpu_util import dev, to_dev, torch
 
@@ -35,12 +38,14 @@ def test_noalloc_matches_gram_twice(n, ka, kb):
     Y = np.stack([inputs.x_true(100 + j, n) for j in range(kb)], axis=1)
     Vd, Yd = to_dev(V.T, d).t(), to_dev(Y.T, d).t()
     ref = pkg.sstep_gram(Vd, Yd).cpu().numpy()
+    oracle = osstep.inner_products(V, Y)
     scale = np.outer(np.linalg.norm(V, axis=0), np.linalg.norm(Y, axis=0))
     for _ in range(2):
         got = call_noalloc(Vd, Yd, n, ka, kb)
         torch.cuda.synchronize()
         got = got.cpu().numpy()
         assert np.max(np.abs(got - ref) / scale) <= 1e-14
+        assert np.max(np.abs(got - oracle) / scale) <= 1e-14
 
 
 def test_noalloc_rejects_sizes_beyond_the_maximum():
