@@ -378,6 +378,21 @@ int x0net_get_params(x0net X, float* params, void* stream);
 int x0net_get_state(x0net X, float* params, float* m, float* v, int64_t* step, void* stream);
 int x0net_set_state(x0net X, const float* params, const float* m, const float* v, int64_t step, void* stream);
 int x0net_forward(x0net X, const float* input, float* output, int batch, void* stream);
+/* The scalings of the learned form, on the device (the network works on O(1) data):
+ *   x0net_features: for each of `batch` systems on an H x W grid (f, beta: DEVICE, batch x H x W
+ *     doubles, system b at offset b H W), f_scale[b] = s_f = sqrt(mean f_b^2) (1 when f_b = 0;
+ *     DEVICE, batch doubles) and input[b] = (f_b / s_f, beta_b / 20) as float32
+ *     (DEVICE, (batch, 2, H, W)).
+ *   x0net_targets: target[b] = x_b / (kappa s_f[b]) as float32 (training pairs), kappa =
+ *     1 / (2 pi^2 h^2), h = 1 / (H + 1): the inverse of the smallest eigenvalue of the h^2-scaled
+ *     Laplacian, so the targets are O(1) on any grid.
+ *   x0net_predict: the forward pass and x0[b] = kappa s_f[b] out[b] (DEVICE, batch x H x W
+ *     doubles): the initial guess the solver takes.
+ * Stream-ordered; SSTEP_ERR_ARG for null pointers, sizes below 1 or batch > batch_max. */
+int x0net_features(int H, int W, int batch, const double* f, const double* beta, float* input, double* f_scale,
+                   void* stream);
+int x0net_targets(int H, int W, int batch, const double* x, const double* f_scale, float* target, void* stream);
+int x0net_predict(x0net X, const float* input, const double* f_scale, int batch, double* x0, void* stream);
 /* loss = mean over batch*H*W of (out - target)^2 and its gradient with respect to
  * every parameter (host or device outputs; either may be NULL). Synchronises. */
 int x0net_gradient(x0net X, const float* input, const float* target, int batch, float* loss, float* grads,

@@ -35,6 +35,8 @@ from ._binding import (  # noqa: F401
     trace_enable,
     trace_read,
     trace_select,
+    x0net_features,
+    x0net_targets,
 )
 
 __all__ = [
@@ -58,5 +60,7 @@ __all__ = [
     "trace_enable",
     "trace_read",
     "trace_select",
+    "x0net_features",
+    "x0net_targets",
     "lib",
 ]

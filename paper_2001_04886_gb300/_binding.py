@@ -81,6 +81,9 @@ SIGNATURES = {
     "x0net_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P(c_int64), c_void_p]),
     "x0net_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "x0net_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "x0net_features": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "x0net_targets": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "x0net_predict": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
     "x0net_gradient": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "x0net_set_tensor_cores": (c_int, [c_void_p, c_int]),
     "x0net_status": (c_int, [c_void_p, c_void_p]),
@@ -515,6 +518,40 @@ def tune_cache_put(path, key, cfg):
             fcntl.flock(lk, fcntl.LOCK_UN)
 
 
+def _f64(t, count, name):
+    """Pointer of a contiguous float64 CUDA tensor of `count` elements."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() \
+            or t.numel() != count:
+        raise TypeError(f"{name}: expected a contiguous float64 CUDA tensor of {count} elements")
+    return c_void_p(t.data_ptr())
+
+
+def x0net_features(H, W, f, beta, stream=None):
+    """The learned form's inputs, on the device: f and beta (B, H*W float64 CUDA) ->
+    (features (B, 2, H, W) float32 = (f / s_f, beta / 20), f_scale (B,) float64 = s_f)."""
+    import torch
+
+    B = f.shape[0]
+    inp = torch.empty((B, 2, H, W), dtype=torch.float32, device=f.device)
+    sf = torch.empty(B, dtype=torch.float64, device=f.device)
+    _check("x0net_features", lib().x0net_features(H, W, B, _f64(f, B * H * W, "f"), _f64(beta, B * H * W, "beta"),
+                                                   c_void_p(inp.data_ptr()), c_void_p(sf.data_ptr()), _stream(stream)))
+    return inp, sf
+
+
+def x0net_targets(H, W, x, f_scale, stream=None):
+    """Training targets x / (kappa s_f) (B, 1, H, W) float32 from solutions x (B, H*W float64)."""
+    import torch
+
+    B = x.shape[0]
+    t = torch.empty((B, 1, H, W), dtype=torch.float32, device=x.device)
+    _check("x0net_targets", lib().x0net_targets(H, W, B, _f64(x, B * H * W, "x"), _f64(f_scale, B, "f_scale"),
+                                                 c_void_p(t.data_ptr()), _stream(stream)))
+    return t
+
+
 class BatchSolver:
     """Batched s-step GMRES over many systems (include/sstep.h, batched solves).
 
@@ -667,6 +704,16 @@ class X0Net:
         pi, po = self._io(inp, out, "output")
         _check("x0net_forward", lib().x0net_forward(self.handle, pi, po, inp.shape[0],
                                                     _stream(stream)))
+
+    def predict(self, inp, f_scale, x0, stream=None):
+        """x0 (B, H*W float64 CUDA) = kappa s_f * the network's output for input (B, 2, H, W):
+        the initial guesses (x0net_predict)."""
+        pi = self._f32(inp)
+        B = inp.shape[0]
+        if tuple(inp.shape) != (B, 2, self.H, self.W):
+            raise ValueError(f"expected input (B, 2, {self.H}, {self.W}), got {tuple(inp.shape)}")
+        _check("x0net_predict", lib().x0net_predict(self.handle, pi, _f64(f_scale, B, "f_scale"),
+                                                    B, _f64(x0, B * self.H * self.W, "x0"), _stream(stream)))
 
     def gradient(self, inp, target, stream=None):
         import numpy as np

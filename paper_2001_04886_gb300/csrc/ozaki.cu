@@ -32,8 +32,7 @@
 namespace sstep {
 namespace {
 
-constexpr int kN0 = 80, kN1 = 48;                    // MMA N of the digit-0..3 and digit-4..7 tiles (G >= 1)
-constexpr int kGroupCols = kN0 + kN1;                // tensor-memory columns per 32 V columns
+constexpr int kN1 = 48;                              // MMA N of the digit-4..7 tile (G >= 1): digits tb <= 4
 constexpr long kOzSpin = 1L << 24;                   // bounded mbarrier polls
 
 // Shapes of one instantiation: G groups of 32 V columns, KB Y columns.
@@ -48,8 +47,11 @@ template <int G, int KB>
 struct OzCfg {
     static constexpr int kBst = KB <= 8 ? 8 : (G == 0 ? 16 : KB);
     static constexpr bool kFastB = kBst % 8 == 0;               // digit t's B rows at t kBst / 8 row groups
-    static constexpr int kBRows = G == 0 ? 8 * kBst : 80;       // B rows allocated
-    static constexpr int kN0 = G == 0 ? 8 * kBst : 80;          // MMA N of the digit-0..3 (G = 0: all) tile
+    // MMA N of the digit-0..3 tile (G = 0: the one tile): every B row, rounded up to 16;
+    // B rows allocated: those, plus the spare rows 72..79 of BST = 9
+    static constexpr int kN0 = (8 * kBst + 15) / 16 * 16;
+    static constexpr int kBRows = kN0;
+    static constexpr int kGroupCols = kN0 + kN1;                // tensor-memory columns per 32 V columns (G >= 1)
     static constexpr int kSplitWarps = G <= 1 ? 14 : 8;
     static constexpr int kThreads = (kSplitWarps + 1) * 32;   // + the MMA warp
     static constexpr int kRows = 8 * kSplitWarps;             // rows per stage (one K group per split warp)
@@ -64,6 +66,7 @@ struct OzCfg {
     static constexpr int kSmem = kNStages * kStage;
     static constexpr int kStagesPerChunk = oz::kChunkRows / kRows;
     static constexpr int kBuf = G == 0 ? 128 : G * kGroupCols;   // accumulator columns per buffer
+    static_assert(2 * kBuf <= 512, "tensor memory");
     static constexpr uint32_t kCols = 2 * kBuf <= 256 ? 256u : 512u;
     static_assert(kRows % 16 == 0 && kStagesPerChunk * kRows <= oz::kChunkRows, "stage shape");
     static_assert(kN0 <= 128 && 8 * kBst <= kBRows && (G == 0 || 5 * kBst <= kN1), "B shape");
@@ -342,8 +345,8 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
                         const uint32_t accf = (sic > 0 || ks > 0) ? 1u : 0u;
                         const uint32_t a0 = so + (uint32_t)(2 * g * C::kTile + ks * 256);
                         const uint64_t db = op_desc<SBO>(so + (uint32_t)(2 * G * C::kTile + ks * 256));
-                        mma_f16(dt + (uint32_t)(g * kGroupCols), op_desc<SBO>(a0), db, oz_idesc(kN0), accf);
-                        mma_f16(dt + (uint32_t)(g * kGroupCols + kN0), op_desc<SBO>(a0 + C::kTile), db, oz_idesc(kN1),
+                        mma_f16(dt + (uint32_t)(g * C::kGroupCols), op_desc<SBO>(a0), db, oz_idesc(C::kN0), accf);
+                        mma_f16(dt + (uint32_t)(g * C::kGroupCols + C::kN0), op_desc<SBO>(a0 + C::kTile), db, oz_idesc(kN1),
                                 accf);
                     }
                 mma_commit(&empty[sb]);
@@ -552,8 +555,8 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
                     } else {
 #pragma unroll
                         for (int g = 0; g < NG; ++g) {
-                            if (ta < 4) drain_tile<KB, BST, kN0>(tb0 + (uint32_t)(g * kGroupCols), ta, ta, acc[g]);
-                            else drain_tile<KB, BST, kN1>(tb0 + (uint32_t)(g * kGroupCols + kN0), ta, ta, acc[g]);
+                            if (ta < 4) drain_tile<KB, BST, C::kN0>(tb0 + (uint32_t)(g * C::kGroupCols), ta, ta, acc[g]);
+                            else drain_tile<KB, BST, kN1>(tb0 + (uint32_t)(g * C::kGroupCols + C::kN0), ta, ta, acc[g]);
                         }
                     }
                 }

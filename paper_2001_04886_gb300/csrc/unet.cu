@@ -1217,6 +1217,63 @@ int loss_and_grad(Net& n, const float* input, const float* target, int B, cudaSt
     return 0;
 }
 
+// ------------------------------------------------------------------ the form's scalings
+// The network sees each system scaled to O(1): features (f / s_f, beta / 20) with s_f the
+// RMS of f, and it predicts x / (kappa s_f) with kappa = 1 / (2 pi^2 h^2) (the inverse of
+// the smallest eigenvalue of the h^2-scaled Laplacian), so the targets are O(1) on any grid.
+
+constexpr double kBetaScale = 20.0;
+
+// one CTA per system: s_f = sqrt(mean f^2) (FP64, summed in a fixed order; 1 when f = 0)
+// and the two feature planes
+__global__ void __launch_bounds__(kT) features_kernel(const double* __restrict__ f, const double* __restrict__ beta,
+                                                      int64_t hw, float* __restrict__ input, double* __restrict__ fscale) {
+    __shared__ double part[kT / 32];
+    const int64_t b = blockIdx.x;
+    const double* fb = f + b * hw;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < hw; i += kT) acc = fma(fb[i], fb[i], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    __shared__ double sf;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kT / 32; ++w) t += part[w];
+        const double v = sqrt(t / (double)hw);
+        sf = v > 0.0 ? v : 1.0;
+        fscale[b] = sf;
+    }
+    __syncthreads();
+    const double inv = 1.0 / sf;
+    float* in0 = input + b * 2 * hw;
+    float* in1 = in0 + hw;
+    const double* bb = beta + b * hw;
+    for (int64_t i = threadIdx.x; i < hw; i += kT) {
+        in0[i] = (float)(fb[i] * inv);
+        in1[i] = (float)(bb[i] / kBetaScale);
+    }
+}
+
+// target = x / (kappa s_f) as FP32 (training pairs)
+__global__ void __launch_bounds__(kT) targets_kernel(const double* __restrict__ x, const double* __restrict__ fscale,
+                                                     int64_t hw, int64_t total, double kappa, float* __restrict__ target) {
+    for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < total; i += (int64_t)gridDim.x * kT)
+        target[i] = (float)(x[i] / (kappa * fscale[i / hw]));
+}
+
+// x0 = kappa s_f out (FP64)
+__global__ void __launch_bounds__(kT) unscale_kernel(const float* __restrict__ out, const double* __restrict__ fscale,
+                                                     int64_t hw, int64_t total, double kappa, double* __restrict__ x0) {
+    for (int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x; i < total; i += (int64_t)gridDim.x * kT)
+        x0[i] = kappa * fscale[i / hw] * (double)out[i];
+}
+
+inline double kappa_of(int H) {
+    const double h = 1.0 / (double)(H + 1);
+    return 1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846 * h * h);
+}
+
 }  // namespace unet
 
 using namespace unet;
@@ -1397,6 +1454,34 @@ int x0net_forward(x0net X, const float* input, float* output, int batch, void* s
     else forward<float>(n, input, batch, s);
     if (cudaMemcpyAsync(output, n.out, sizeof(float) * batch * n.H * n.W, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return SSTEP_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA;
+}
+
+int x0net_features(int H, int W, int batch, const double* f, const double* beta, float* input, double* f_scale,
+                   void* stream) {
+    if (H < 1 || W < 1 || batch < 1 || !f || !beta || !input || !f_scale) return SSTEP_ERR_ARG;
+    const int64_t hw = (int64_t)H * W;
+    unet::features_kernel<<<batch, unet::kT, 0, (cudaStream_t)stream>>>(f, beta, hw, input, f_scale);
+    return cudaGetLastError() == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA;
+}
+
+int x0net_targets(int H, int W, int batch, const double* x, const double* f_scale, float* target, void* stream) {
+    if (H < 1 || W < 1 || batch < 1 || !x || !f_scale || !target) return SSTEP_ERR_ARG;
+    const int64_t hw = (int64_t)H * W, total = hw * batch;
+    unet::targets_kernel<<<unet::blocks_for(total), unet::kT, 0, (cudaStream_t)stream>>>(x, f_scale, hw, total,
+                                                                                      unet::kappa_of(H), target);
+    return cudaGetLastError() == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA;
+}
+
+int x0net_predict(x0net X, const float* input, const double* f_scale, int batch, double* x0, void* stream) {
+    if (!X || !input || !f_scale || !x0 || batch < 1 || batch > X->n.Bmax) return SSTEP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    unet::Net& n = X->n;
+    if (n.bf16) unet::forward<__nv_bfloat16>(n, input, batch, s);
+    else unet::forward<float>(n, input, batch, s);
+    const int64_t hw = (int64_t)n.H * n.W, total = hw * batch;
+    unet::unscale_kernel<<<unet::blocks_for(total), unet::kT, 0, s>>>(n.out, f_scale, hw, total, unet::kappa_of(n.H),
+                                                                       x0);
     return cudaGetLastError() == cudaSuccess ? SSTEP_OK : SSTEP_ERR_CUDA;
 }
 

@@ -13,7 +13,8 @@ amplifies the rough part of the prediction's error by up to ~1/(2 pi^2 h^2), and
 the sweeps remove that part while keeping the smooth part the network gets right.
 The same sweeps applied to x0 = 0 are reported as a control.
 
-Scaling: the network sees f / s_f and beta / 20 (s_f = rms of f) and predicts
+Scaling (done on the device by the library: x0net_features, x0net_targets,
+x0net_predict): the network sees f / s_f and beta / 20 (s_f = rms of f) and predicts
 x / (kappa s_f) with kappa = 1 / (2 pi^2 h^2), the inverse of the smallest
 eigenvalue scale of the h^2-scaled operator, so that targets are O(1) on every
 grid; since A x = f is linear in f for fixed beta, scaling f scales x.
@@ -25,9 +26,9 @@ import time
 import numpy as np
 
 from . import inputs
-from ._binding import BatchSolver, StencilMatrix, X0Net, stencil_matrix_smooth_batched
+from ._binding import (BatchSolver, StencilMatrix, X0Net, stencil_matrix_smooth_batched, x0net_features,
+                       x0net_targets)
 
-BETA_SCALE = 20.0
 SWEEPS = 32          # damped Jacobi sweeps on the predicted x0
 OMEGA = 0.8          # their damping (the smoothing optimum for the 2-D 5-point Laplacian)
 
@@ -38,19 +39,19 @@ def kappa(N):
 
 
 def make_systems(seeds, N, device):
-    """Operators, right-hand sides (FP64, device), features (FP32, device) and f scales."""
+    """Operators, right-hand sides (FP64, device), features (FP32, device) and f scales
+    (FP64, device): the features and scales come from the library (x0net_features)."""
     import torch
 
-    mats, fs, feats, scales = [], [], [], []
+    mats, fs, betas = [], [], []
     for sd in seeds:
         beta, f = inputs.fourier_fields(int(sd), N)
-        sf = float(np.sqrt(np.mean(f * f)))
-        mats.append(StencilMatrix(2, (N, N), beta_field=torch.tensor(beta, dtype=torch.float64, device=device)))
+        bd = torch.tensor(beta, dtype=torch.float64, device=device)
+        mats.append(StencilMatrix(2, (N, N), beta_field=bd))
         fs.append(torch.tensor(f, dtype=torch.float64, device=device))
-        feat = np.stack([f / sf, beta / BETA_SCALE]).astype(np.float32).reshape(2, N, N)
-        feats.append(torch.tensor(feat, device=device))
-        scales.append(sf)
-    return mats, fs, torch.stack(feats), np.array(scales)
+        betas.append(bd)
+    feats, scales = x0net_features(N, N, torch.stack(fs).contiguous(), torch.stack(betas).contiguous())
+    return mats, fs, feats, scales
 
 
 def solve_batch(mats, fs, x0s, s=4, m=20, tol=1e-8, guard=False, tune=False):
@@ -84,19 +85,20 @@ def generate(seeds, N, device, chunk=1024, report=None):
         mats, fs, ft, sc = make_systems(part, N, device)
         xs = [torch.zeros_like(f) for f in fs]
         res, _ = solve_batch(mats, fs, xs)
-        k = kappa(N)
         keep = []
-        for i, (x, s_, r) in enumerate(zip(xs, sc, res)):
+        for i, r in enumerate(res):
             if r["status"] != 0:
                 dropped.append((int(part[i]), r["status"], r["cycles"]))
                 continue
             keep.append(i)
-            targets.append((x / (k * s_)).to(torch.float32).reshape(1, N, N))
-        feats.append(ft[torch.tensor(keep, device=device, dtype=torch.long)])
+        idx = torch.tensor(keep, device=device, dtype=torch.long)
+        if keep:   # x / (kappa s_f), by the library (x0net_targets)
+            targets.append(x0net_targets(N, N, torch.stack([xs[i] for i in keep]).contiguous(), sc[idx].contiguous()))
+        feats.append(ft[idx])
         del mats, fs, xs
     if report is not None:
         report["dropped"] = dropped
-    return torch.cat(feats), torch.stack(targets)
+    return torch.cat(feats), torch.cat(targets)
 
 
 # checkpoint file: magic, format version, then little-endian int64 num_params, Adam
@@ -185,17 +187,16 @@ def train(net, feats, targets, epochs, batch=32, lr=1e-3, seed=0, log=None, chec
 
 
 def predict(net, feats, scales, batch=32):
-    """x0 = kappa s_f net(features): FP64 device vectors, the rows of one (S, N*N) tensor."""
+    """x0 = kappa s_f net(features) by the library (x0net_predict): FP64 device vectors, the
+    rows of one (S, N*N) tensor."""
     import torch
 
     N = feats.shape[-1]
     S = feats.shape[0]
     assert feats.dim() == 4 and feats.shape[-2] == N, "features must be (S, 2, N, N)"
-    out = torch.empty((S, 1, N, N), dtype=torch.float32, device=feats.device)
+    x0 = torch.empty((S, N * N), dtype=torch.float64, device=feats.device)
     for b0 in range(0, S, batch):
-        net.forward(feats[b0 : b0 + batch].contiguous(), out[b0 : b0 + batch])
-    k = torch.tensor(np.asarray(scales, dtype=np.float64) * kappa(N), device=feats.device)
-    x0 = out.reshape(S, N * N).to(torch.float64) * k[:, None]
+        net.predict(feats[b0 : b0 + batch].contiguous(), scales[b0 : b0 + batch].contiguous(), x0[b0 : b0 + batch])
     return list(x0.unbind(0))
 
 

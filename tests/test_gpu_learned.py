@@ -57,6 +57,40 @@ def test_x0_guard_falls_back_to_zero():
     assert rb[0]["status"] == 0 and rb[0]["cycles"] == ref["cycles"]
 
 
+def test_scalings_on_the_device():
+    """The form's scalings by the library against their definitions: s_f = rms of f, the
+    features (f / s_f, beta / 20) in FP32, targets x / (kappa s_f) and the initial guess
+    kappa s_f * output, kappa = 1 / (2 pi^2 h^2)."""
+    d = dev()
+    N, B = 24, 3
+    fields = [inputs.fourier_fields(30 + i, N) for i in range(B)]
+    beta = np.stack([b for b, _ in fields])
+    f = np.stack([f_ for _, f_ in fields])
+    f[2] = 0.0                                    # f = 0: the scale is taken as 1
+    feats, sf = pkg.x0net_features(N, N, to_dev(f, d), to_dev(beta, d))
+    torch.cuda.synchronize()
+    rms = np.sqrt(np.mean(f * f, axis=1))
+    want_sf = np.where(rms > 0, rms, 1.0)
+    np.testing.assert_allclose(sf.cpu().numpy(), want_sf, rtol=1e-14, atol=0)
+    ft = feats.cpu().numpy()
+    np.testing.assert_array_equal(ft[:, 0].reshape(B, -1), (f / want_sf[:, None]).astype(np.float32))
+    np.testing.assert_array_equal(ft[:, 1].reshape(B, -1), (beta / 20.0).astype(np.float32))
+    kap = 1.0 / (2.0 * np.pi ** 2 * (1.0 / (N + 1)) ** 2)
+    x = np.stack([inputs.x_true(40 + i, N * N) for i in range(B)])
+    t = pkg.x0net_targets(N, N, to_dev(x, d), sf).cpu().numpy()
+    np.testing.assert_allclose(t.reshape(B, -1), (x / (kap * want_sf[:, None])).astype(np.float32), rtol=1e-7, atol=0)
+    net = pkg.X0Net(N, N, B, bf16=False, smooth=0)
+    net.set_params(np.random.default_rng(0).standard_normal(net.num_params).astype(np.float32) * 0.05)
+    out = torch.empty((B, 1, N, N), dtype=torch.float32, device=d)
+    net.forward(feats, out)
+    x0 = torch.empty((B, N * N), dtype=torch.float64, device=d)
+    net.predict(feats, sf, x0)
+    torch.cuda.synchronize()
+    want = kap * want_sf[:, None] * out.cpu().numpy().reshape(B, -1).astype(np.float64)
+    np.testing.assert_allclose(x0.cpu().numpy(), want, rtol=1e-15, atol=0)
+    net.close()
+
+
 def test_trained_network_reduces_krylov_steps():
     dev()
     # training is deterministic (seeded order, fixed-order reductions, no atomics)
