@@ -58,14 +58,21 @@ def _hbm_peak_gbs():
 HBM_PEAK_GBS = _hbm_peak_gbs()   # the algorithmic GB/s of the dominant kernel are reported against it
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
-# kernel, averaged over the launches of one solve in an ncu capture of this bench
-# (profiles/sstep_gmres_fp64_128cube_traffic.md has the command and the per-kernel table).
-# Keyed by precision mode, with a hash of the kernel sources it was taken on: once the
+# kernel kind, averaged over the launches of one solve, from an ncu capture of this bench
+# (the profiles directory has the command and the per-kernel table). Keyed by precision
+# mode ("fp64_tc": the tensor-core Gram and block-update passes; "fp64": the FP64-pipe
+# kernels, SSTEP_TC_GRAM=0), with a hash of the kernel sources it was taken on: once the
 # sources change, the figure no longer describes the kernel and the bench reports null.
+# A "launch" is one block of the cycle, as in sstep_gmres_work: for the tensor-core path
+# the projection (blocks k > 0) and the Gram pass of the s + 1 new columns together,
+# (10 full cycles + the 2 blocks of the last) / 52 blocks of the 128^3 solve.
 TRAFFIC = {
     "fp64": {"kernel": "block_update", "bytes_per_launch": 471.3e6,
              "sources": ("common.cuh", "kernels.cuh", "epilogue.cuh", "kernels.cu"),
              "sha256": "42dddf2a1f6c61fa"},
+    "fp64_tc": {"kernel": "block_update", "bytes_per_launch": 694.5e6,
+                "sources": ("ozaki.cu", "ozaki.cuh"),
+                "sha256": "5921731962ab3337"},
 }
 
 

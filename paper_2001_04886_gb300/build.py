@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "libsstep.so")
 SOURCES = ["kernels.cu", "kernels_mp.cu", "batched.cu", "capi.cu", "noalloc.cu", "unet.cu", "smooth.cu", "precond.cu",
-           "ozaki.cu"]
+           "ozaki.cu", "powers.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -195,7 +195,9 @@ std::vector<double> newton_shifts_from_device(const double* G_dev, int m, int K,
 // The fused matrix-powers kernel (one launch for the s powers of a block) is off by
 // default: on GB300 the 16.8 MB columns of a 128^3 solve stay in the 129 MB L2 between
 // separate sweeps, so fusion saves only L2 reads while its tile halos recompute ~4x the
-// points (measured slower). SSTEP_FUSED_POWERS=1 turns it on.
+// points (measured slower). SSTEP_FUSED_POWERS=1 turns it on, in the mixed-precision solver
+// and in the FP64 one (powers.cu; there the halos' extra multiply-adds fall on the FP64 pipe,
+// which already bounds the separate sweeps).
 // The Gram pass of the FP64 s-step GMRES runs on the tensor cores (exact fixed point,
 // ozaki.cu) unless SSTEP_TC_GRAM=0 selects the FP64 CUDA-core kernel (for comparisons).
 bool tc_gram_enabled() {
@@ -1230,8 +1232,25 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
             // bounds: the copy v_k^1 -> bnd[o] and pb[0]; power j -> pb[j]; in the first block
             // the powers 1..s-1 are final basis columns as they stand -> bnd[o + j] too
             auto fin = [&](int j) { return (tcg && k == 0 && j < s) ? bnd + o + j : nullptr; };
-            // Alg. 4.1 step 3: v_k^1 = u / ||u|| and its s scaled powers
-            if (!pre) {
+            // Alg. 4.1 step 3: v_k^1 = u / ||u|| and its s scaled powers (in one fused launch with
+            // TMA-staged tiles when SSTEP_FUSED_POWERS=1: the same columns, bit for bit)
+            bool fusedp = false;
+            if (!pre && fused_powers_enabled()) {
+                unsigned* b1[kMaxS + 1] = {};
+                unsigned* b2[kMaxS + 1] = {};
+                if (tcg) {
+                    b1[0] = bnd + o;   // the copy v_k^1: basis column o and power 0 of the block
+                    b2[0] = pb;
+                    for (int j = 1; j <= s; ++j) {
+                        b1[j] = pb + j;
+                        b2[j] = fin(j);
+                    }
+                }
+                TRACED(K_STENCIL, stream_,
+                       fusedp = launch_powers_fused(M->A, uraw, sigma, &st->vscale, U + o * ld, ld, s, theta.data(), b1,
+                                                    b2, st, GATE_BUILDING, stream_));
+            }
+            if (!pre && !fusedp) {
                 TRACED(K_STENCIL, stream_, launch_stencil(M->A, uraw, sigma, U + (o + 1) * ld, 1.0, U + o * ld,
                                                           &st->vscale, st, GATE_BUILDING, stream_, theta[0], nullptr,
                                                           tcg ? pb + 1 : nullptr, tcg ? bnd + o : nullptr, fin(1),
@@ -1240,7 +1259,7 @@ int sstep_gmres_solve(sstep_matrix M, const double* f, double* x, const sstep_pa
                     TRACED(K_STENCIL, stream_, launch_stencil(M->A, U + (o + j - 1) * ld, sigma, U + (o + j) * ld, 0.0,
                                                               nullptr, nullptr, st, GATE_BUILDING, stream_, theta[j - 1],
                                                               nullptr, tcg ? pb + j : nullptr, nullptr, fin(j)));
-            } else {   // right preconditioning: y^{j+1} = sigma (A M^-1 y^j - theta_j y^j)
+            } else if (pre) {   // right preconditioning: y^{j+1} = sigma (A M^-1 y^j - theta_j y^j)
                 launch_scale_copy(uraw, U + o * ld, n, &st->vscale, st, GATE_BUILDING, stream_);
                 for (int j = 1; j <= s; ++j) {
                     TRACED(K_PRECOND, stream_, precond_apply(M, pk, U + (o + j - 1) * ld, ptmp, st, GATE_BUILDING,

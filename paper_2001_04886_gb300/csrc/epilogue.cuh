@@ -38,9 +38,9 @@ __device__ bool chol_upper(const double* W, int ldw, int s, double* L) {
     return true;
 }
 
-// x = (L^T L)^{-1} b (forward with L^T, then backward with L); b and x may alias.
+// x = (L^T L)^{-1} b (forward with L^T, then backward with L); b and x may alias; s <= kMaxS.
 __device__ void chol_solve(const double* L, int s, const double* b, double* x) {
-    double z[kMaxCols];
+    double z[kMaxS];
     for (int i = 0; i < s; ++i) {
         double t = 0.0;
         for (int q = 0; q < i; ++q) t = add(t, mul(L[q + i * s], z[q]));
@@ -51,6 +51,87 @@ __device__ void chol_solve(const double* L, int s, const double* b, double* x) {
         for (int q = i + 1; q < s; ++q) t = add(t, mul(L[i + q * s], x[q]));
         x[i] = sub(z[i], t) / L[i + i * s];
     }
+}
+
+// The same solves spread over lanes, with the divisions taken off the dependent chain.
+// An FP64 division or square root is a long dependent sequence of FP64 operations, which
+// GB300 issues slowly (about 1.5k cycles each, measured in these epilogues); one thread
+// doing an s x s factorization and its two substitutions one operation after another
+// waits for each in turn, in the last CTA of a reduction, while the rest of the GPU is
+// idle. So the factorization divides a whole row of L at once (one lane per entry, the
+// same quotients as chol_upper: a singular block still gives a zero or negative pivot
+// exactly where the sequential factorization does), and the substitutions multiply by
+// reciprocals of the diagonal formed off their dependent chain (each product differs
+// from the quotient by at most an ulp; the solves stay backward stable).
+//
+// Forward substitution z = L^{-T} b for an aligned group of G lanes (G a power of two,
+// s <= G; lane r of the group brings b_r and gets z_r; rd[q] = 1 / L_qq): column by
+// column, z_q by lane q and then every lane r > q adds L[q, r] z_q to its sum, so each sum
+// runs over q in ascending order, as in chol_solve. Every lane of the warp calls it.
+__device__ double tri_fwd_group(const double* L, const double* rd, int s, double b_r, int r, int G) {
+    double t = 0.0, z = 0.0;
+    for (int q = 0; q < s; ++q) {
+        if (r == q) z = mul(sub(b_r, t), rd[q]);
+        const double zq = __shfl_sync(0xffffffffu, z, q, G);
+        if (r > q && r < s) t = add(t, mul(L[q + r * s], zq));
+    }
+    return z;
+}
+
+// Backward substitution x = L^{-1} z for the same lanes: x_q from q = s - 1 down; lane r < q
+// adds L[r, q] x_q to its sum (so in descending q; chol_solve sums in ascending q).
+__device__ double tri_bwd_group(const double* L, const double* rd, int s, double z_r, int r, int G) {
+    double t = 0.0, x = 0.0;
+    for (int q = s - 1; q >= 0; --q) {
+        if (r == q) x = mul(sub(z_r, t), rd[q]);
+        const double xq = __shfl_sync(0xffffffffu, x, q, G);
+        if (r < q) t = add(t, mul(L[r + q * s], xq));
+    }
+    return x;
+}
+
+// One warp (every lane calls it): W = L^T L (L upper, col-major ld s, into shared Ls) with
+// z = L^{-T} b formed in the same sweep as column s of the factor of [W b] (row i of L,
+// columns i + 1 .. s, one lane each, after its pivot: chol_upper's and chol_solve's
+// forward pass, operation for operation), then x = L^{-1} z; lane r < s gets x_r. false
+// (warp-uniform: every lane computes the pivots) on a non-positive pivot, with Ls as
+// chol_upper leaves it. zs, rs: s doubles of shared scratch each (z, 1 / L_ii).
+__device__ bool chol_solve_warp(const double* W, int ldw, const double* b, int s, double* Ls, double* zs, double* rs,
+                                double& x) {
+    const int lane = threadIdx.x & 31;
+    for (int t = lane; t < s * s; t += 32) Ls[t] = 0.0;
+    __syncwarp();
+    bool ok = true;
+    for (int i = 0; i < s; ++i) {
+        double t = 0.0;
+        for (int q = 0; q < i; ++q) t = add(t, mul(Ls[q + i * s], Ls[q + i * s]));
+        const double d = sub(W[i + i * ldw], t);
+        if (!(d > 0.0)) {
+            ok = false;
+            break;
+        }
+        const double lii = sqrt(d);
+        // one division by every lane at once: lanes 0 .. s-1-i the entries of row i (the last
+        // of them z_i), lane 31 the reciprocal 1 / L_ii
+        const int j = i + 1 + lane;
+        double num = 1.0;
+        if (j <= s) {
+            const double* cj = j < s ? Ls + j * s : zs;   // column j of L, or z
+            double u = 0.0;
+            for (int q = 0; q < i; ++q) u = add(u, mul(Ls[q + i * s], cj[q]));
+            num = sub(j < s ? W[i + j * ldw] : b[i], u);
+        }
+        const double qv = num / lii;
+        if (j < s) Ls[i + j * s] = qv;
+        else if (j == s) zs[i] = qv;
+        if (lane == 31) rs[i] = qv;
+        if (lane == 0) Ls[i + i * s] = lii;
+        __syncwarp();
+    }
+    x = 0.0;
+    if (!ok) return false;
+    x = tri_bwd_group(Ls, rs, s, lane < s ? zs[lane] : 0.0, lane, 32);
+    return true;
 }
 
 __device__ void hist_push(SolverState* st, double v) {
@@ -116,35 +197,50 @@ __device__ void epi_restart(SolverState* st, double rr) {
 __device__ void epi_gm_T(const Epi& e, const double* C) {
     SolverState* st = e.st;
     const int s = st->s, m = st->m, o = e.o, nblk = o / s;
-    __shared__ double sL[kMaxCols * kMaxS];
+    __shared__ double sL[kMaxCols * kMaxS], sR[kMaxCols];   // the factors, the reciprocals of their diagonals
     for (int t = threadIdx.x; t < nblk * s * s; t += blockDim.x) sL[t] = st->L[t];
-    __syncthreads();
     for (int t = threadIdx.x; t < nblk * s; t += blockDim.x) {
-        const int b = t / s, j = t % s;
-        double rhs[kMaxS], x[kMaxS];
-        for (int q = 0; q < s; ++q) rhs[q] = C[(b * s + q) + j * o];
-        chol_solve(sL + b * s * s, s, rhs, x);
-        for (int q = 0; q < s; ++q) st->T[(b * s + q) + (j + 1) * m] = x[q];
+        const int b = t / s, i = t % s;
+        sR[t] = 1.0 / st->L[b * s * s + i + i * s];
+    }
+    __syncthreads();
+    // one solve per group of 8 lanes (s <= 8): lane r holds row r; whole warps take part
+    const int nsol = nblk * s, nwarp = (int)(blockDim.x >> 5);
+    for (int w0 = (int)(threadIdx.x >> 5) * 4; w0 < nsol; w0 += nwarp * 4) {
+        const int sol = w0 + (int)((threadIdx.x & 31) >> 3), r = threadIdx.x & 7;
+        const bool act = sol < nsol && r < s;
+        const int b = sol < nsol ? sol / s : 0, j = sol < nsol ? sol % s : 0;
+        const double* Lb = sL + b * s * s;
+        const double z = tri_fwd_group(Lb, sR + b * s, s, act ? C[(b * s + r) + j * o] : 0.0, r, 8);
+        const double x = tri_bwd_group(Lb, sR + b * s, s, z, r, 8);
+        if (act) st->T[(b * s + r) + (j + 1) * m] = x;
     }
     for (int i = threadIdx.x; i < o; i += blockDim.x) st->T[i] = 0.0;   // first column: 0 (step 7)
 }
 
 // Scalar1 of Alg. 4.1 on the projected block: W_k = V_k^T V_k, S = W_k^{-1} V_k^T z.
+// The factor and the solution are formed in shared memory and then stored: formed in
+// place in global memory, every read of an entry just written would wait for L2.
 __device__ void epi_gm_W(const Epi& e, const double* G2) {
     SolverState* st = e.st;
-    if (threadIdx.x != 0) return;
-    const int s = st->s, o = e.o, ld = s + 1;
-    st->matvecs += s;
+    __shared__ double sLk[kMaxS * kMaxS], sz[kMaxS], sr[kMaxS];
+    if (threadIdx.x >= 32) return;   // one warp
+    const int s = st->s, o = e.o, ld = s + 1, lane = threadIdx.x;
     double* Lk = st->L + (o / s) * s * s;
-    if (!chol_upper(G2, ld, s, Lk)) {
-        st->building = 0;
-        if (o == 0) {
-            st->status = SSTEP_ERR_BREAKDOWN;
-            st->active = 0;
+    double x;
+    const bool ok = chol_solve_warp(G2, ld, G2 + s * ld, s, sLk, sz, sr, x);
+    for (int t = lane; t < s * s; t += 32) Lk[t] = sLk[t];
+    if (lane == 0) {
+        st->matvecs += s;
+        if (!ok) {
+            st->building = 0;
+            if (o == 0) {
+                st->status = SSTEP_ERR_BREAKDOWN;
+                st->active = 0;
+            }
         }
-        return;
     }
-    chol_solve(Lk, s, G2 + s * ld, st->S);
+    if (ok && lane < s) st->S[lane] = x;
 }
 
 // u = z - V_k S has been formed; nu = ||u||. Columns o..o+s-1 of G hold A v_k^j in
@@ -243,8 +339,8 @@ __device__ void epi_gm_nu(const Epi& e, const double* red) {
                 h[i] = t;
             }
             const double a = h[c], b = h[c + 1];
-            const double d = sqrt(add(mul(a, a), mul(b, b)));
-            const double cc = a / d, sn = b / d;
+            const double h2 = add(mul(a, a), mul(b, b)), rh = rsqrt(h2);   // one reciprocal square root
+            const double d = mul(h2, rh), cc = mul(a, rh), sn = mul(b, rh);
             sc_[c] = cc;
             ss_[c] = sn;
             h[c] = d;
@@ -425,25 +521,29 @@ __device__ void epi_om_B(const Epi& e, const double* C) {
 // Orthomin Scalar1 (Alg. 3.1 steps 1-2): W = L^T L, a = W^{-1} m for the new block.
 __device__ void epi_om_W(const Epi& e, const double* red) {
     SolverState* st = e.st;
-    if (threadIdx.x != 0) return;
-    const int s = st->s;
-    st->matvecs += s;
-    double W[kMaxS * kMaxS];
-    int idx = 0;
-    for (int q = 0; q < s; ++q)
-        for (int p = 0; p <= q; ++p) {
-            W[p + q * s] = red[idx];
-            W[q + p * s] = red[idx];
-            ++idx;
-        }
-    double* Ln = st->L + e.slot * s * s;
-    if (!chol_upper(W, s, s, Ln)) {
-        st->status = SSTEP_ERR_BREAKDOWN;
-        st->active = 0;
-        st->building = 0;
-        return;
+    __shared__ double sW[kMaxS * kMaxS], sLn[kMaxS * kMaxS], sz[kMaxS], sr[kMaxS];   // the factor: formed here, then stored
+    if (threadIdx.x >= 32) return;   // one warp
+    const int s = st->s, lane = threadIdx.x;
+    // W from the packed upper triangle (column q: rows 0..q), then the right-hand side
+    for (int t = lane; t < s * s; t += 32) {
+        const int p = t % s, q = t / s, lo = p < q ? p : q, hi = p < q ? q : p;
+        sW[t] = red[hi * (hi + 1) / 2 + lo];
     }
-    chol_solve(Ln, s, red + idx, st->a);
+    __syncwarp();
+    const int idx = s * (s + 1) / 2;
+    double* Ln = st->L + e.slot * s * s;
+    double x;
+    const bool ok = chol_solve_warp(sW, s, red + idx, s, sLn, sz, sr, x);
+    for (int t = lane; t < s * s; t += 32) Ln[t] = sLn[t];
+    if (lane == 0) {
+        st->matvecs += s;
+        if (!ok) {
+            st->status = SSTEP_ERR_BREAKDOWN;
+            st->active = 0;
+            st->building = 0;
+        }
+    }
+    if (ok && lane < s) st->a[lane] = x;
 }
 
 __device__ __noinline__ void run_epilogue(const Epi& e, const double* red, int ka, int kb) {

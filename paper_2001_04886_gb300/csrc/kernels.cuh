@@ -106,6 +106,16 @@ bool launch_update_oz(int64_t n, const double* V, int64_t ldv, int ka, const uns
                       int j0, int kbo, const double* T, int ldt, unsigned* bout, unsigned* bout2, int nb2,
                       const unsigned* bcopy_src, unsigned* bcopy_dst, const SolverState* st, int gate,
                       cudaStream_t stream, unsigned* err = nullptr, int vw = 0);   // vw: as launch_gram_oz
+// Fused matrix powers of the FP64 s-step block (powers.cu): Y[:, 0] = d u, Y[:, j] = sigma
+// (A - theta[j-1] I) Y[:, j-1], j = 1..s, d = *dscale, in one launch whose start-vector
+// tiles come in by TMA; the same columns as s separate launch_stencil sweeps, bit for bit.
+// b1[j], b2[j] (either may be null): column-bound records of column j. Returns false,
+// launching nothing, unless the coefficients are constant, s is 2, 4 or 8, nx is even and
+// u is 16-byte aligned (or the driver has no tensor-map encoder). A bounded wait that runs
+// out sets st->status to SSTEP_ERR_TIMEOUT and *err.
+bool launch_powers_fused(const StencilDesc& A, const double* u, double sigma, const double* dscale, double* Y,
+                         int64_t ldy, int s, const double* theta, unsigned* const* b1, unsigned* const* b2,
+                         const SolverState* st, int gate, cudaStream_t stream, unsigned* err = nullptr);
 // out[c] = column bound of column c (out must be zeroed first)
 void launch_colmax(int64_t n, const double* X, int64_t ld, int ncols, unsigned* out, cudaStream_t stream);
 int oz_partials_doubles();      // per-CTA partials of the tensor-core Gram pass (none: sums go to Scratch::acc)

@@ -253,18 +253,39 @@ __device__ __forceinline__ void drain_tile(uint32_t taddr, int ta, int tmin, oz:
     }
 }
 
+// ZS: the symmetric 9-column pass V^T V of the s-step block at s = 8 (the z mode below,
+// one column octet per warp). Its rows come into shared memory by TMA bulk copies (a
+// producer warp keeps kZRawSlots stages of the 9 columns in flight) and the split warps
+// read them from there: a split warp then has no global load outstanding when it fences
+// and arrives on a stage, which would otherwise wait for its loads of later stages. The
+// other forms load their entries straight into registers one stage ahead.
+constexpr int kZRawSlots = 8;                 // stages of raw rows in flight (ZS)
 template <int G, int KB>
-__global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
+struct ZRaw {
+    static constexpr int kCol = OzCfg<G, KB>::kRows + 8;   // doubles between columns: 960 B, half a bank row off
+    static constexpr int kSlot = 9 * kCol * 8;             // bytes per slot: the 9 columns of one stage
+    static constexpr int kNS = 2;                           // digit stages (room for the raw slots)
+    static constexpr int kSmem = kNS * OzCfg<G, KB>::kStage + kZRawSlots * kSlot;
+    static_assert(kSmem <= 200 * 1024, "shared memory (static use besides)");
+};
+template <int G, int KB, bool ZS>
+__global__ void __launch_bounds__(OzCfg<G, KB>::kThreads + (ZS ? 32 : 0), 1)
     gram_oz_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int ka, const unsigned* __restrict__ vmax,
                    const double* __restrict__ Y, int64_t ldy, const unsigned* __restrict__ ymax, Scratch sc, Epi epi,
                    int gate, long spin, int sym, int vw, uint64_t* __restrict__ wout, int64_t ldw, int nw) {
     using C = OzCfg<G, KB>;
+    static_assert(!ZS || (G == 0 && KB == 9 && C::kSplitWarps == 14), "z mode shape");
     constexpr int BST = C::kBst;
-    constexpr int kItems = (G == 0 ? 2 : 4 * G) + (KB + 7) / 8;   // column octets per split warp and stage
-    constexpr int NS = C::kNStages, NG = C::kGroups, CP = C::kColsPer;
+    constexpr int kItems = ZS ? 1 : (G == 0 ? 2 : 4 * G) + (KB + 7) / 8;   // column octets per split warp and stage
+    constexpr int PD = 1;                                          // stages of register loads in flight
+    static_assert(C::kStagesPerChunk % PD == 0, "a chunk ends in the ring's last slot");
+    constexpr int NT = C::kThreads + (ZS ? 32 : 0);                // + the producer warp (ZS)
+    constexpr int RS = ZS ? kZRawSlots : 1;
+    using R = ZRaw<0, 9>;
+    constexpr int NS = ZS ? R::kNS : C::kNStages, NG = C::kGroups, CP = C::kColsPer;
     constexpr int SBO = C::kSbo;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[2], tempty[2];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[2], tempty[2], rfull[RS], rempty[RS];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int failed;
     __shared__ bool last;
@@ -272,7 +293,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
     __shared__ double res[kMaxCols * (kMaxS + 1)];
     if (!gate_open(epi.st, gate)) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int c = tid; c < ka + KB; c += C::kThreads) ex[c] = oz::bound_exponent(c < ka ? vmax[c] : ymax[c - ka]);
+    for (int c = tid; c < ka + KB; c += NT) ex[c] = oz::bound_exponent(c < ka ? vmax[c] : ymax[c - ka]);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
                      "r"(C::kCols));
@@ -288,6 +309,11 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
             bar_init(&tfull[b], 1);
             bar_init(&tempty[b], C::kSplitWarps);
         }
+        if (ZS)
+            for (int b = 0; b < RS; ++b) {
+                bar_init(&rfull[b], 1);
+                bar_init(&rempty[b], C::kSplitWarps);
+            }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -363,6 +389,39 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
                 if (n_tfull[b]) oz_wait(smem_addr(&tfull[b]), (uint32_t)((n_tfull[b] - 1) & 1), kOzSpin);
         }
         __syncwarp();
+    } else if (ZS && warp == C::kSplitWarps + 1) {
+        // ---------------------------------------------------------------- producer warp (ZS)
+        // stage gs: rows r0 .. r0 + 111 of the 9 columns into raw slot gs % RS, one bulk copy
+        // per column (an even row count: a last odd row is read by its split lane directly)
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t gs = 0; gs < nstages && !failed; ++gs) {
+                const int slot = (int)(gs % RS);
+                if (gs >= RS && !oz_wait_sleep(smem_addr(&rempty[slot]), (uint32_t)(((gs / RS) - 1) & 1), spin)) {
+                    failed = 1;
+                    break;
+                }
+                const int64_t r0 = (s0 + gs) * C::kRows, left = n - r0;
+                const uint32_t bytes = (uint32_t)(left >= C::kRows ? C::kRows : (left & ~1ll)) * 8u;
+                const uint32_t bar = smem_addr(&rfull[slot]);
+                const uint32_t dst = sbase + (uint32_t)(NS * C::kStage + slot * R::kSlot);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(9u * bytes)
+                             : "memory");
+                if (bytes)
+                    for (int c = 0; c < 9; ++c)
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                            ::"r"(dst + (uint32_t)(c * R::kCol * 8)), "l"(V + (int64_t)c * ldv + r0), "r"(bytes),
+                            "r"(bar)
+                            : "memory");
+                issued = gs + 1;
+            }
+            // every copy has landed before the CTA goes on (the split warps waited for all of
+            // them unless they stopped early)
+            for (int64_t gs = issued > RS ? issued - RS : 0; gs < issued; ++gs)
+                oz_wait(smem_addr(&rfull[gs % RS]), (uint32_t)((gs / RS) & 1), kOzSpin);
+        }
+        __syncwarp();
     } else {
         // ---------------------------------------------------------------- split warps
         // item j: column octet j (V octets first, then Y octets) of this warp's K group of 8
@@ -372,7 +431,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
         // every warp, and column 8 as one item of 28 row pairs in each of warps 2 and 3 (the
         // two sub-partitions with three split warps), instead of a second octet with one
         // column in use in every warp; its stores meet bank conflicts, the issue slots are fewer
-        const bool zmode = G == 0 && KB == 9 && sym && ka == 9 && C::kSplitWarps == 14;
+        const bool zmode = ZS;   // (chosen at launch: sym, ka = KB = 9)
         const int noct_v = zmode ? 1 : (ka + 7) >> 3, noct = noct_v + (sym ? 0 : (KB + 7) / 8);
         const int c8 = lane >> 2, kk = warp * 8 + (lane & 3) * 2;
         const bool zw = zmode && (warp == 2 || warp == 3);            // warp-uniform
@@ -442,22 +501,87 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
                 }
             }
         };
-        double2 cur[kItems], zcur = make_double2(0.0, 0.0);
-        if (nstages > 0) {
-            load(0, cur);
-            if (zw) zload(0, zcur);
+        // the chunk's exact sums out of tensor memory into the 128-bit accumulators
+        auto drain_chunk = [&](int chunk) -> bool {
+            const int tb = chunk & 1;
+            if (!oz_wait(smem_addr(&tfull[tb]), (uint32_t)((chunk >> 1) & 1), spin)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t tb0 = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tb * C::kBuf);
+            if (drains) {
+                if (G == 0) {
+                    drain_tile<KB, BST, C::kN0>(tb0, ta, tmin, acc[0]);
+                } else {
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) {
+                        if (ta < 4) drain_tile<KB, BST, C::kN0>(tb0 + (uint32_t)(g * C::kGroupCols), ta, ta, acc[g]);
+                        else drain_tile<KB, BST, kN1>(tb0 + (uint32_t)(g * C::kGroupCols + C::kN0), ta, ta, acc[g]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) bar_arrive(&tempty[tb]);
+            return true;
+        };
+        // A ring of PD stages of loads in registers: stage gs + PD is requested as stage gs
+        // is taken out of its slot, so PD stages of loads are in flight per warp. The slot
+        // index is static (the loop is unrolled by PD): a register move would wait for its load.
+        double2 ring[PD][kItems], zring[PD];
+#pragma unroll
+        for (int u = 0; u < PD; ++u) {
+            zring[u] = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) ring[u][j] = make_double2(0.0, 0.0);
+            if (!ZS && (int64_t)u < nstages) {
+                load(u, ring[u]);
+                if (zw) zload(u, zring[u]);
+            }
         }
-        for (unsigned gs = 0; gs < (unsigned)nstages; ++gs) {
-            if (failed) break;
-            double2 nxt[kItems], znxt = make_double2(0.0, 0.0);
-            if (gs + 1 < (unsigned)nstages) {
-                load(gs + 1, nxt);
-                if (zw) zload(gs + 1, znxt);
+        bool stop = false;
+        for (unsigned gs0 = 0; gs0 < (unsigned)nstages && !stop; gs0 += PD) {
+#pragma unroll
+          for (int u = 0; u < PD; ++u) {
+            const unsigned gs = gs0 + (unsigned)u;
+            if (gs >= (unsigned)nstages || failed) {
+                stop = true;
+                break;
+            }
+            double2 cur[kItems], zcur = zring[u];
+            if constexpr (ZS) {
+                // this lane's entries from the raw slot: column c8, rows kk and kk + 1; column 8,
+                // rows zrow and zrow + 1 (z lanes); rows past n are 0
+                const int slot = (int)(gs % RS);
+                if (!oz_wait(smem_addr(&rfull[slot]), (uint32_t)((gs / RS) & 1), spin)) {
+                    failed = 1;
+                    stop = true;
+                    break;
+                }
+                const double* raw = reinterpret_cast<const double*>(smem + NS * C::kStage + slot * R::kSlot);
+                const int64_t r0 = (s0 + (int64_t)gs) * C::kRows, left = n - r0;
+                const int copied = (int)(left >= C::kRows ? C::kRows : (left & ~1ll));
+                cur[0] = make_double2(0.0, 0.0);
+                if (kk < copied) cur[0] = *reinterpret_cast<const double2*>(raw + c8 * R::kCol + kk);
+                else if (kk < left) cur[0].x = __ldg(V + (int64_t)c8 * ldv + r0 + kk);
+                zcur = make_double2(0.0, 0.0);
+                if (zl) {
+                    if (zrow < copied) zcur = *reinterpret_cast<const double2*>(raw + 8 * R::kCol + zrow);
+                    else if (zrow < left) zcur.x = __ldg(V + 8 * ldv + r0 + zrow);
+                }
+                __syncwarp();
+                if (lane == 0) bar_arrive(&rempty[slot]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < kItems; ++j) cur[j] = ring[u][j];
+                if (gs + PD < (unsigned)nstages) {
+                    load(gs + PD, ring[u]);
+                    if (zw) zload(gs + PD, zring[u]);
+                }
             }
 
             const int sb = (int)(gs % NS);
             if (gs >= NS && !oz_wait(smem_addr(&empty[sb]), (uint32_t)(((gs / NS) - 1) & 1), spin)) {
                 failed = 1;
+                stop = true;
                 break;
             }
             unsigned char* sp = smem + sb * C::kStage;
@@ -535,38 +659,25 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
                         *reinterpret_cast<uint32_t*>(sp + C::kAT * C::kTile + op_off<SBO>(t * BST + 8, zrow)) = d[t];
                     }
                 }
-                zcur = znxt;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) bar_arrive(&full[sb]);
+            // drain at the end of each chunk (kStagesPerChunk is a multiple of PD, so a chunk
+            // ends in the last slot); with PD > 1 a last, partial chunk is drained after the loop
             const int sic = (int)(gs % C::kStagesPerChunk);
-            if (sic == C::kStagesPerChunk - 1 || gs + 1 == (unsigned)nstages) {   // drain the chunk's exact sums
-                const int chunk = (int)(gs / C::kStagesPerChunk), tb = chunk & 1;
-                if (!oz_wait(smem_addr(&tfull[tb]), (uint32_t)((chunk >> 1) & 1), spin)) {
-                    failed = 1;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t tb0 = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tb * C::kBuf);
-                if (drains) {
-                    if (G == 0) {
-                        drain_tile<KB, BST, C::kN0>(tb0, ta, tmin, acc[0]);
-                    } else {
-#pragma unroll
-                        for (int g = 0; g < NG; ++g) {
-                            if (ta < 4) drain_tile<KB, BST, C::kN0>(tb0 + (uint32_t)(g * C::kGroupCols), ta, ta, acc[g]);
-                            else drain_tile<KB, BST, kN1>(tb0 + (uint32_t)(g * C::kGroupCols + C::kN0), ta, ta, acc[g]);
-                        }
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncwarp();
-                if (lane == 0) bar_arrive(&tempty[tb]);
+            if ((PD == 1 || u == PD - 1) &&
+                (sic == C::kStagesPerChunk - 1 || (PD == 1 && gs + 1 == (unsigned)nstages)) &&
+                !drain_chunk((int)(gs / C::kStagesPerChunk))) {
+                failed = 1;
+                stop = true;
+                break;
             }
-#pragma unroll
-            for (int j = 0; j < kItems; ++j) cur[j] = nxt[j];
+          }
         }
+        if (PD > 1 && !failed && nstages > 0 && nstages % C::kStagesPerChunk != 0 &&
+            !drain_chunk((int)((nstages - 1) / C::kStagesPerChunk)))
+            failed = 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -584,7 +695,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
 #pragma unroll
             for (int b = 0; b < KB; ++b) part[(ta * NG * CP + g * CP + al_) * KB + b] = acc[g][b] >> (8 * ta);
     __syncthreads();
-    for (int e = tid; e < ka * KB; e += C::kThreads) {
+    for (int e = tid; e < ka * KB; e += NT) {
         const int a = e % ka, b = e / ka;
         oz::i128 s = 0;
         for (int k = 0; k < oz::kDigits; ++k) s += part[(k * NG * CP + a) * KB + b];
@@ -601,7 +712,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads, 1)
     __threadfence();
     // last CTA: one rounding per entry, then the accumulators go back to zero for the next launch
     const bool err = ((volatile unsigned*)sc.counter)[1] != 0u;
-    for (int e = tid; e < ka * KB; e += C::kThreads) {
+    for (int e = tid; e < ka * KB; e += NT) {
         const uint64_t lo = __ldcg(sc.acc + 2 * e), hi = __ldcg(sc.acc + 2 * e + 1);
         sc.acc[2 * e] = 0ull;
         sc.acc[2 * e + 1] = 0ull;
@@ -654,18 +765,27 @@ void launch_oz(int64_t n, const double* V, int64_t ldv, int ka, const unsigned* 
                const unsigned* ymax, Scratch sc, const Epi& epi, int gate, cudaStream_t stream, long spin, int sym,
                int vw, uint64_t* wout, int64_t ldw, int nw) {
     using C = OzCfg<G, KB>;
-    static bool attr[64] = {false};   // once per device
+    constexpr bool kZ = G == 0 && KB == 9 && C::kSplitWarps == 14;   // the z-mode form exists
+    static bool attr[64][2] = {};     // once per device and form
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !attr[dev]) {
-        cudaFuncSetAttribute(gram_oz_kernel<G, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
-        if (dev >= 0 && dev < 64) attr[dev] = true;
+    // the z-mode form: V^T V of 9 columns whose starts are 16-byte aligned (bulk copies)
+    const bool z = kZ && sym && ka == 9 && ((uintptr_t)V & 15) == 0 && (ldv & 1) == 0;
+    if (dev < 0 || dev >= 64 || !attr[dev][z]) {
+        if (z) cudaFuncSetAttribute(gram_oz_kernel<G, KB, kZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    ZRaw<0, 9>::kSmem);
+        else cudaFuncSetAttribute(gram_oz_kernel<G, KB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+        if (dev >= 0 && dev < 64) attr[dev][z] = true;
     }
     const int64_t nst = (n + C::kRows - 1) / C::kRows;
     int grid = device_sms();
     if (grid > nst) grid = (int)std::max<int64_t>(nst, 1);
-    gram_oz_kernel<G, KB><<<grid, C::kThreads, C::kSmem, stream>>>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate,
-                                                                    spin, sym, vw, wout, ldw, nw);
+    if (z)
+        gram_oz_kernel<G, KB, kZ><<<grid, C::kThreads + 32, ZRaw<0, 9>::kSmem, stream>>>(
+            n, V, ldv, ka, vmax, Y, ldy, ymax, sc, epi, gate, spin, sym, vw, wout, ldw, nw);
+    else
+        gram_oz_kernel<G, KB, false><<<grid, C::kThreads, C::kSmem, stream>>>(n, V, ldv, ka, vmax, Y, ldy, ymax, sc,
+                                                                               epi, gate, spin, sym, vw, wout, ldw, nw);
 }
 }  // namespace
 

@@ -95,7 +95,13 @@ def test_fp32_refinement_256cube():
 
 
 def test_fused_powers_match_separate_sweeps():
-    """The fused matrix-powers launch (opt-in) gives the separate sweeps' solve, in a fresh process."""
+    """The fused matrix-powers launch (opt-in) gives the separate sweeps' solve, in a fresh process.
+
+    All of x is compared. The double-float basis rounds the same operations in the same
+    order either way: x to 1e-8 relative. The FP32 basis rounds the powers in a different
+    order (2^-24 per operation), so the two solves are two different solutions that each
+    meet the 1e-8 residual test; what they must share is that bound: A (x1 - x2) = r2 - r1,
+    so ||A (x1 - x2)|| <= 2e-8 ||f||, checked with the oracle's operator."""
     import json
     import os
     import subprocess
@@ -116,7 +122,7 @@ for shape, beta in [((24, 24, 24), (30.0, 20.0, 10.0)), ((48, 48), (20.0, 20.0))
     for prec in ('df64', 'fp32'):
         x = torch.zeros_like(f)
         r = pkg.sstep_gmres_solve(A, f, x, 4, 20, 1e-8, precision=prec)
-        out[str(shape) + prec] = [r['cycles'], r['relres'], x.cpu().numpy().tolist()[:50]]
+        out[str(shape) + prec] = [r['cycles'], r['relres'], x.cpu().numpy().tolist()]
 print(json.dumps(out))
 """
     res = {}
@@ -125,8 +131,63 @@ print(json.dumps(out))
         p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
         assert p.returncode == 0, p.stderr[-2000:]
         res[flag] = json.loads(p.stdout.strip().splitlines()[-1])
+    for shape, beta in [((24, 24, 24), (30.0, 20.0, 10.0)), ((48, 48), (20.0, 20.0))]:
+        Ao = ostencil.convdiff(shape, beta)
+        nf = np.linalg.norm(Ao.apply(inputs.x_true(0, Ao.n)))
+        for prec in ("df64", "fp32"):
+            key = str(shape) + prec
+            c0, r0, x0 = res["0"][key]
+            c1, r1, x1 = res["1"][key]
+            assert c0 == c1 and r0 <= 1e-8 and r1 <= 1e-8
+            dx = np.array(x0) - np.array(x1)
+            if prec == "df64":
+                assert np.linalg.norm(dx) <= 1e-8 * np.linalg.norm(x0), key
+            else:
+                assert np.linalg.norm(Ao.apply(dx)) <= 2e-8 * nf, key
+
+
+def test_fused_powers_fp64_bit_for_bit():
+    """The FP64 fused matrix-powers launch (TMA-staged tiles, opt-in) gives the separate
+    sweeps' solve bit for bit: the same coefficients and the same order of multiply-adds at
+    every point, so the same history and the same x. Cases span s = 2, 4, 8, partial tiles in
+    x and y, z chunks thinner than the grid, 2-D, and the Newton basis (shifts in the powers)."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    dev()
+    code = r"""
+import json, sys
+import numpy as np, torch
+sys.path.insert(0, '.')
+import paper_2001_04886_gb300 as pkg
+from paper_2001_04886_gb300 import inputs
+out = {}
+cases = [((24, 24, 24), (30.0, 20.0, 10.0), 2, 20, 'monomial'), ((24, 24, 24), (30.0, 20.0, 10.0), 4, 20, 'monomial'),
+         ((38, 22, 70), (30.0, 20.0, 10.0), 8, 40, 'monomial'), ((38, 22, 30), (30.0, 20.0, 10.0), 8, 40, 'newton'),
+         ((66, 50), (20.0, 20.0), 4, 20, 'monomial'), ((66, 50), (20.0, 20.0), 8, 40, 'newton')]
+for shape, beta, s, m, basis in cases:
+    c = [b / (2.0 * (shape[0] + 1)) for b in beta]   # convection-diffusion coefficients, h = 1 / (nx + 1)
+    coef = [2.0 * len(shape)] + sum([[-1.0 - ci, -1.0 + ci] for ci in c], []) + [0.0] * (6 - 2 * len(shape))
+    A = pkg.StencilMatrix(len(shape), shape, coef=coef)
+    xt = torch.tensor(inputs.x_true(0, A.n), device='cuda')
+    f = torch.empty_like(xt); A.apply(xt, f)
+    x = torch.zeros_like(f)
+    r = pkg.sstep_gmres_solve(A, f, x, s, m, 1e-8, basis=basis)
+    out[str((shape, s, basis))] = [r['status'], r['history'], x.cpu().numpy().tolist()]
+print(json.dumps(out))
+"""
+    res = {}
+    for flag in ("0", "1"):
+        env = dict(os.environ, SSTEP_FUSED_POWERS=flag)
+        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        assert p.returncode == 0, p.stderr[-2000:]
+        res[flag] = json.loads(p.stdout.strip().splitlines()[-1])
+    assert res["0"].keys() == res["1"].keys()
     for key in res["0"]:
-        c0, r0, x0 = res["0"][key]
-        c1, r1, x1 = res["1"][key]
-        assert c0 == c1 and r0 <= 1e-8 and r1 <= 1e-8
-        assert np.linalg.norm(np.array(x0) - x1) <= 1e-6 * np.linalg.norm(x0)
+        st0, h0, x0 = res["0"][key]
+        st1, h1, x1 = res["1"][key]
+        assert st0 == 0 and st1 == 0, key
+        assert h0 == h1, key
+        assert np.array_equal(np.array(x0), np.array(x1)), key

@@ -131,6 +131,40 @@ def test_tc_gram_symmetric_bit_for_bit():
     check(V, V, G)
 
 
+@pytest.mark.parametrize("n", [1, 113, 9077, 153216, 300001, 2_097_152])
+def test_tc_gram_symmetric_nine_columns(emu, n):
+    """The 9-column V^T V of the s-step block at s = 8 (its own kernel form, loads three
+    stages ahead): bit for bit the same as V and Y split apart, and as the exact emulation.
+    The sizes give CTAs of one stage, whole chunks of 9 stages only (153216 = 152 x 9 x 112
+    rows) and partial last chunks."""
+    d = dev()
+    V = spread_columns(n, 9, 3)
+    P = panel(V, d)
+    G = pkg.sstep_gram_tc(P, P).cpu().numpy()
+    G2 = pkg.sstep_gram_tc(P, panel(V, d)).cpu().numpy()
+    assert np.array_equal(G, G2) and np.array_equal(G, G.T)
+    if n <= 300001:
+        assert np.array_equal(G, emulate(emu, V, V))
+    check(V, V, G)
+
+
+def test_tc_gram_symmetric_nine_columns_wait_timeout():
+    """The bounded waits of the 9-column form: a poll limit of 0 gives NaN and a normal
+    end; the next call with the default limit is exact."""
+    d = dev()
+    V = spread_columns(300001, 9, 4)
+    P = panel(V, d)
+    try:
+        pkg.set_tc_wait_limit(0)
+        bad = pkg.sstep_gram_tc(P, P)
+        torch.cuda.synchronize()
+        bad = bad.cpu().numpy()
+    finally:
+        pkg.set_tc_wait_limit(-1)
+    assert np.all(np.isnan(bad))
+    check(V, V, pkg.sstep_gram_tc(P, P).cpu().numpy())
+
+
 def test_tc_gram_nonfinite_and_zero():
     d = dev()
     n = 3000
