@@ -256,16 +256,17 @@ __device__ __forceinline__ void drain_tile(uint32_t taddr, int ta, int tmin, oz:
 // ZS: the symmetric 9-column pass V^T V of the s-step block at s = 8 (the z mode below,
 // one column octet per warp). Its rows come into shared memory by TMA bulk copies (a
 // producer warp keeps kZRawSlots stages of the 9 columns in flight) and the split warps
-// read them from there: a split warp then has no global load outstanding when it fences
-// and arrives on a stage, which would otherwise wait for its loads of later stages. The
-// other forms load their entries straight into registers one stage ahead.
+// read them from there; its B operand is its A tile (V = Y: the same digits in the same
+// rows), so a digit stage is one tile and four of them fit. The other forms load their
+// entries straight into registers one stage ahead.
 constexpr int kZRawSlots = 8;                 // stages of raw rows in flight (ZS)
 template <int G, int KB>
 struct ZRaw {
     static constexpr int kCol = OzCfg<G, KB>::kRows + 8;   // doubles between columns: 960 B, half a bank row off
     static constexpr int kSlot = 9 * kCol * 8;             // bytes per slot: the 9 columns of one stage
-    static constexpr int kNS = 2;                           // digit stages (room for the raw slots)
-    static constexpr int kSmem = kNS * OzCfg<G, KB>::kStage + kZRawSlots * kSlot;
+    // digit stages: the A tile only (V^T V: the B operand is the same tile)
+    static constexpr int kNS = 4;
+    static constexpr int kSmem = kNS * OzCfg<G, KB>::kTile + kZRawSlots * kSlot;
     static_assert(kSmem <= 200 * 1024, "shared memory (static use besides)");
 };
 template <int G, int KB, bool ZS>
@@ -283,6 +284,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads + (ZS ? 32 : 0), 1)
     constexpr int RS = ZS ? kZRawSlots : 1;
     using R = ZRaw<0, 9>;
     constexpr int NS = ZS ? R::kNS : C::kNStages, NG = C::kGroups, CP = C::kColsPer;
+    constexpr int STG = ZS ? C::kTile : C::kStage;   // bytes per digit stage
     constexpr int SBO = C::kSbo;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[2], tempty[2], rfull[RS], rempty[RS];
@@ -355,13 +357,13 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads + (ZS ? 32 : 0), 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t so = sbase + (uint32_t)(sb * C::kStage);
+                const uint32_t so = sbase + (uint32_t)(sb * STG);
                 const uint32_t dt = tmem + (uint32_t)(tb * C::kBuf);
                 if (G == 0) {   // one tile: all digit pairs of 16 columns against the B digits
 #pragma unroll
                     for (int ks = 0; ks < C::kRows / 16; ++ks)
                         mma_f16(dt, op_desc<SBO>(so + (uint32_t)(ks * 256)),
-                                op_desc<SBO>(so + (uint32_t)(C::kTile + ks * 256)), oz_idesc(C::kN0),
+                                op_desc<SBO>(so + (uint32_t)((ZS ? 0 : C::kTile) + ks * 256)), oz_idesc(C::kN0),
                                 (sic > 0 || ks > 0) ? 1u : 0u);
                 }
 #pragma unroll
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads + (ZS ? 32 : 0), 1)
                 const int64_t r0 = (s0 + gs) * C::kRows, left = n - r0;
                 const uint32_t bytes = (uint32_t)(left >= C::kRows ? C::kRows : (left & ~1ll)) * 8u;
                 const uint32_t bar = smem_addr(&rfull[slot]);
-                const uint32_t dst = sbase + (uint32_t)(NS * C::kStage + slot * R::kSlot);
+                const uint32_t dst = sbase + (uint32_t)(NS * STG + slot * R::kSlot);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(9u * bytes)
                              : "memory");
                 if (bytes)
@@ -556,7 +558,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads + (ZS ? 32 : 0), 1)
                     stop = true;
                     break;
                 }
-                const double* raw = reinterpret_cast<const double*>(smem + NS * C::kStage + slot * R::kSlot);
+                const double* raw = reinterpret_cast<const double*>(smem + NS * STG + slot * R::kSlot);
                 const int64_t r0 = (s0 + (int64_t)gs) * C::kRows, left = n - r0;
                 const int copied = (int)(left >= C::kRows ? C::kRows : (left & ~1ll));
                 cur[0] = make_double2(0.0, 0.0);
@@ -584,7 +586,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads + (ZS ? 32 : 0), 1)
                 stop = true;
                 break;
             }
-            unsigned char* sp = smem + sb * C::kStage;
+            unsigned char* sp = smem + sb * STG;
 #pragma unroll
             for (int j = 0; j < kItems; ++j) {
                 if (j < noct) {   // warp-uniform
@@ -623,7 +625,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads + (ZS ? 32 : 0), 1)
                             for (int t = 0; t < oz::kDigits; ++t)
                                 *reinterpret_cast<uint32_t*>(base + (t >> 2) * C::kTile + (t & 3) * 4 * SBO) = d[t];
                         }
-                        if (sym) {      // warp-uniform; sym implies G = 0, so C::kFastB
+                        if (sym && !ZS) {   // warp-uniform; sym implies G = 0, so C::kFastB (ZS: B is A)
                             unsigned char* bb = sp + boff[j];
 #pragma unroll
                             for (int t = 0; t < oz::kDigits; ++t)
@@ -656,7 +658,8 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads + (ZS ? 32 : 0), 1)
 #pragma unroll
                     for (int t = 0; t < oz::kDigits; ++t) {
                         *reinterpret_cast<uint32_t*>(sp + op_off<SBO>(t * 16 + 8, zrow)) = d[t];
-                        *reinterpret_cast<uint32_t*>(sp + C::kAT * C::kTile + op_off<SBO>(t * BST + 8, zrow)) = d[t];
+                        if (!ZS)
+                            *reinterpret_cast<uint32_t*>(sp + C::kAT * C::kTile + op_off<SBO>(t * BST + 8, zrow)) = d[t];
                     }
                 }
             }
