@@ -603,6 +603,7 @@ def main():
             mats.append(Ab)
             fs.append(fb)
             xs.append(torch.zeros_like(fb))
+            xts.append(xb)
         Bs = pkg.BatchSolver(mats, 4, 20, TOL, max_cycles=2000)
         t0 = time.perf_counter()
         cfg = Bs.tune(fs, xs)
@@ -619,8 +620,25 @@ def main():
             out[name] = {"ms": e0.elapsed_time(e1), "all_converged": all(r["status"] == 0 for r in rb),
                          "cycles_total": int(sum(r["cycles"] for r in rb)),
                          "max_relres": float(max(r["relres"] for r in rb))}
-        variants["batched_512_s4_m20"] = out
         Bs.close()
+        # the same batch with the FP32 basis (FP64 residual, x and scalar work), tuned apart
+        Bf = pkg.BatchSolver(mats, 4, 20, TOL, max_cycles=2000, precision="fp32")
+        for x_ in xs:
+            x_.zero_()   # tuned on the solve it will time (tune() restores these guesses)
+        out["fp32_basis_tuned"] = Bf.tune(fs, xs)
+        for x_ in xs:
+            x_.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rb = Bf.solve(fs, xs, mode=Bf.PERSISTENT)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["fp32_basis_persistent_graph"] = {
+            "ms": e0.elapsed_time(e1), "all_converged": all(r["status"] == 0 for r in rb),
+            "cycles_total": int(sum(r["cycles"] for r in rb)), "max_relres": float(max(r["relres"] for r in rb)),
+            "max_x_err_vs_x_true": float(max(float((x_ - xt_).norm() / xt_.norm()) for x_, xt_ in zip(xs, xts)))}
+        variants["batched_512_s4_m20"] = out
+        Bf.close()
         del mats, fs, xs
 
     if "paper" in args.groups:

@@ -315,7 +315,11 @@ int sstep_omin_solve(sstep_matrix A, const double* f, double* x, const sstep_par
  * otherwise) and runs its entire solve with CTA-wide reductions. Mode
  * SSTEP_BATCH_PER_SYSTEM calls sstep_gmres_solve once per system (the comparison).
  * The handle keeps references to the matrices, which must outlive it.
- * p: s in {1, 2, 4, 8}, m <= 40 and a multiple of s, FP64 only; p->history is
+ * p: s in {1, 2, 4, 8}, m <= 40 and a multiple of s; p->precision SSTEP_PREC_FP64 or
+ * SSTEP_PREC_FP32 (the persistent kernel then keeps the basis in FP32, adds exact FP32
+ * products in double-float and keeps the restart residual, x and the scalar work in
+ * FP64: FP32 iterative refinement per system, as sstep_gmres_solve's FP32 mode, with
+ * the same FP64 stopping test); monomial basis, no preconditioner; p->history is
  * ignored. */
 #define SSTEP_BATCH_PERSISTENT 0
 #define SSTEP_BATCH_PER_SYSTEM 1

@@ -464,17 +464,18 @@ def library_build_id():
     return h.hexdigest()[:16]
 
 
-def tune_cache_key(shapes, s, m, device, tol=1e-8, sigma=0.0, x0_guard=False, build=None):
+def tune_cache_key(shapes, s, m, device, tol=1e-8, sigma=0.0, x0_guard=False, build=None, precision="fp64"):
     """The key of a batch's tuned launch configuration: what the timing depends on. The
     device name, s, m, the tolerance, sigma and the x0 guard (they change the cycle counts),
-    a hash of the systems' grid shapes in batch order and the library build
-    (library_build_id)."""
+    the basis precision (another kernel), a hash of the systems' grid shapes in batch order
+    and the library build (library_build_id)."""
     import hashlib
 
     h = hashlib.sha256(repr([tuple(int(v) for v in sh) for sh in shapes]).encode()).hexdigest()[:16]
     b = library_build_id() if build is None else build
+    prec = "" if precision == "fp64" else f"|prec={precision}"   # (FP64 keys as before)
     return (f"{device}|s={int(s)}|m={int(m)}|tol={float(tol)!r}|sigma={float(sigma)!r}|guard={int(bool(x0_guard))}"
-            f"|n={len(shapes)}|{h}|build={b}")
+            f"{prec}|n={len(shapes)}|{h}|build={b}")
 
 
 def tune_cache_get(path, key):
@@ -562,15 +563,19 @@ class BatchSolver:
     PERSISTENT = 0
     PER_SYSTEM = 1
 
-    def __init__(self, mats, s, m, tol, max_cycles=1000, sigma=0.0, x0_guard=False):
+    def __init__(self, mats, s, m, tol, max_cycles=1000, sigma=0.0, x0_guard=False, precision="fp64"):
+        """precision: "fp64" (FP64 basis) or "fp32" (FP32 basis, double-float sums, FP64
+        residual, x and scalar work: FP32 iterative refinement per system)."""
+        if precision not in ("fp64", "fp32"):
+            raise ValueError("precision: fp64 or fp32")
         self.mats = list(mats)
         self.n = len(self.mats)
         self.s, self.m = s, m
-        self.tol, self.sigma, self.x0_guard = tol, sigma, bool(x0_guard)
+        self.tol, self.sigma, self.x0_guard, self.precision = tol, sigma, bool(x0_guard), precision
         h = c_void_p()
         arr = (c_void_p * self.n)(*[A.handle.value for A in self.mats])
         p = SStepParams(s=s, m=m, k=0, tol=tol, max_cycles=max_cycles, max_iters=0, sigma=sigma, history=None,
-                        history_cap=0, precision=0, x0_guard=1 if x0_guard else 0)
+                        history_cap=0, precision=PRECISIONS[precision], x0_guard=1 if x0_guard else 0)
         _check("sstep_batch_create", lib().sstep_batch_create(ctypes.byref(h), self.n, arr, ctypes.byref(p)))
         self.handle = h
 
@@ -596,7 +601,7 @@ class BatchSolver:
             import torch
 
             key = tune_cache_key([A.shape for A in self.mats], self.s, self.m, torch.cuda.get_device_name(),
-                                 tol=self.tol, sigma=self.sigma, x0_guard=self.x0_guard)
+                                 tol=self.tol, sigma=self.sigma, x0_guard=self.x0_guard, precision=self.precision)
             hit = tune_cache_get(cache, key)
             if hit is not None:
                 self.configure(**hit)

@@ -17,6 +17,9 @@
 // rate of its SM, so without clusters the largest system alone sets the batch time.
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
+#include "df64.cuh"
 #include "epilogue.cuh"
 
 namespace sstep {
@@ -44,10 +47,12 @@ __device__ __forceinline__ void step_sync() {
     else __syncthreads();
 }
 
+// a vector entry that this kernel may have written: from L2 when another CTA of the
+// cluster wrote it (after a cluster barrier), else a plain (coherent) load
 template <bool CO>
 __device__ __forceinline__ double ldv(const double* p) {
     if constexpr (CO) return __ldcg(p);
-    else return __ldg(p);
+    else return *p;
 }
 
 __device__ __forceinline__ void cta_grid_xyz(const StencilDesc& A, int64_t p, int& x, int& y, int& z) {
@@ -240,15 +245,188 @@ __device__ void cta_lsq(SolverState* st) {
 
 __device__ __forceinline__ int flag(const SolverState* st, int which) { return ((volatile const int*)st)[which]; }
 
+// ================================================================== FP32 basis
+// The precision form of the batched solver (precision SSTEP_PREC_FP32): the basis and its
+// powers are FP32 columns; every inner product and every projection Y - V T adds exact
+// FP32 products in double-float (df64.cuh) and is rounded once; the restart residual, x
+// and all scalar work stay FP64. Each restart is then a step of FP32 iterative refinement
+// with an FP64 stopping test, as in the single-system FP32 mode. The FP64 pipe, which a
+// CTA of the FP64 form keeps busy, is left with the residual and the x update.
+
+template <bool CO>
+__device__ __forceinline__ float ldf(const float* p) {
+    if constexpr (CO) return __ldcg(p);
+    else return *p;
+}
+
+__device__ __forceinline__ float coef32(const StencilDesc& A, int q, int64_t p) {
+    return A.variable ? __ldg(A.fdf[q] + p).x : A.ch[q];
+}
+
+// (A v)_p in FP32 (the coefficients' high parts), the same order as row_at
+template <bool CO>
+__device__ __forceinline__ float row32(const StencilDesc& A, const float* v, int64_t p, int x, int y, int z) {
+    float acc = __fmul_rn(coef32(A, 0, p), ldf<CO>(v + p));
+    if (x > 0) acc = __fmaf_rn(coef32(A, 1, p), ldf<CO>(v + p - 1), acc);
+    if (x < A.nx - 1) acc = __fmaf_rn(coef32(A, 2, p), ldf<CO>(v + p + 1), acc);
+    if (y > 0) acc = __fmaf_rn(coef32(A, 3, p), ldf<CO>(v + p - A.nx), acc);
+    if (y < A.ny - 1) acc = __fmaf_rn(coef32(A, 4, p), ldf<CO>(v + p + A.nx), acc);
+    if (A.dim == 3) {
+        const int64_t pl = (int64_t)A.nx * A.ny;
+        if (z > 0) acc = __fmaf_rn(coef32(A, 5, p), ldf<CO>(v + p - pl), acc);
+        if (z < A.nz - 1) acc = __fmaf_rn(coef32(A, 6, p), ldf<CO>(v + p + pl), acc);
+    }
+    return acc;
+}
+
+// y = fy (A v); w = fw v when w is set; then a barrier (as cta_stencil)
+template <bool CO>
+__device__ void cta_stencil32(const StencilDesc& A, Rows R, const float* v, float fy, float* y, float fw, float* w) {
+    for (int64_t p = R.r0 + threadIdx.x; p < R.r1; p += blockDim.x) {
+        int x, yy, z;
+        cta_grid_xyz(A, p, x, yy, z);
+        y[p] = __fmul_rn(fy, row32<CO>(A, v, p, x, yy, z));
+        if (w) w[p] = __fmul_rn(fw, ldf<CO>(v + p));
+    }
+    step_sync<CO>();
+}
+
+// r = f - A x in FP64, stored rounded to FP32 into out; ||r||^2 (FP64) in res[0]
+template <bool CO>
+__device__ void cta_residual32(const StencilDesc& A, Rows R, const double* f, const double* xv, float* out,
+                               double* scratch, double* res) {
+    double acc[1] = {0.0};
+    for (int64_t p = R.r0 + threadIdx.x; p < R.r1; p += blockDim.x) {
+        int x, yy, z;
+        cta_grid_xyz(A, p, x, yy, z);
+        const double r = f[p] - row_at<CO>(A, xv, p, x, yy, z);
+        out[p] = __double2float_rn(r);
+        acc[0] = fma(r, r, acc[0]);
+    }
+    cta_reduce<1, CO>(acc, scratch, res);
+}
+
+// s += a b (a FP32, b a float pair): the product's two parts exactly, then TwoSum into s
+__device__ __forceinline__ void acc_fd(DfAcc& s, float a, df64 b) {
+    const float p = __fmul_rn(a, b.hi);
+    float e = __fmaf_rn(a, b.hi, -p);
+    e = __fmaf_rn(a, b.lo, e);
+    float h, t;
+    two_sum(s.hi, p, h, t);
+    s.hi = h;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(t, e));
+}
+
+// C = V^T Y (FP32 columns, double-float sums, FP64 across threads); as cta_gram
+template <int S, bool CO>
+__device__ void cta_gram32(Rows R, const float* V, int64_t ld, int ka, const float* Y, double* scratch, double* res) {
+    constexpr int KA = 4;
+    for (int a0 = 0; a0 < ka; a0 += KA) {
+        const int na = min(KA, ka - a0);
+        DfAcc acc[KA * S];
+        int cnt = 0;
+        for (int64_t p = R.r0 + threadIdx.x; p < R.r1; p += blockDim.x) {
+            float yv[S];
+#pragma unroll
+            for (int j = 0; j < S; ++j) yv[j] = Y[p + j * ld];
+#pragma unroll
+            for (int i = 0; i < KA; ++i)
+                if (i < na) {
+                    const float a = V[p + (int64_t)(a0 + i) * ld];
+#pragma unroll
+                    for (int j = 0; j < S; ++j) acc[i * S + j].add_prod(a, yv[j]);
+                }
+            if (++cnt == 32) {   // keep each error term within a few ulps of its sum
+                cnt = 0;
+#pragma unroll
+                for (int v = 0; v < KA * S; ++v) acc[v].normalize();
+            }
+        }
+        double accd[KA * S];
+#pragma unroll
+        for (int v = 0; v < KA * S; ++v) accd[v] = acc[v].value();
+        __shared__ double part[KA * S];
+        cta_reduce<KA * S, CO>(accd, scratch, part);
+        for (int t = threadIdx.x; t < na * S; t += blockDim.x) {
+            const int i = t / S, j = t % S;
+            res[(a0 + i) + j * ka] = part[i * S + j];
+        }
+        __syncthreads();
+    }
+}
+
+// Y[:, j] -= V T[:, j] for j >= j0 (in place, or into Yout): y + sum_a V_a (-T_aj) in
+// double-float, rounded once to FP32; then the Gram of the KB output columns as stored
+template <int KB, bool CO>
+__device__ void cta_update32(Rows R, const float* V, int64_t ld, int ka, float* Yin, float* Yout, int j0,
+                             const double* T, int ldt, double* scratch, double* res) {
+    constexpr int NV = KB * (KB + 1) / 2;
+    __shared__ df64 Ts[kBatchMaxM * KB];
+    for (int t = threadIdx.x; t < ka * KB; t += blockDim.x)
+        Ts[(t % ka) * KB + t / ka] = df_from_double(-T[(t % ka) + (t / ka) * ldt]);
+    __syncthreads();
+    DfAcc acc[NV];
+    int cnt = 0;
+    for (int64_t p = R.r0 + threadIdx.x; p < R.r1; p += blockDim.x) {
+        float yv[KB];
+        DfAcc sum[KB];
+#pragma unroll
+        for (int j = 0; j < KB; ++j) {
+            yv[j] = Yin[p + j * ld];
+            sum[j].hi = yv[j];
+        }
+        for (int i = 0; i < ka; ++i) {
+            const float a = V[p + (int64_t)i * ld];
+#pragma unroll
+            for (int j = 0; j < KB; ++j)
+                if (j >= j0) acc_fd(sum[j], a, Ts[i * KB + j]);
+        }
+#pragma unroll
+        for (int j = 0; j < KB; ++j) {
+            if (j >= j0 && ka > 0) yv[j] = __fadd_rn(sum[j].hi, sum[j].lo);
+            if (Yout != Yin || (j >= j0 && ka > 0)) Yout[p + j * ld] = yv[j];
+        }
+        int idx = 0;
+#pragma unroll
+        for (int q = 0; q < KB; ++q)
+#pragma unroll
+            for (int pp = 0; pp <= q; ++pp) {
+                acc[idx].add_prod(yv[pp], yv[q]);
+                ++idx;
+            }
+        if (++cnt == 32) {
+            cnt = 0;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[v].normalize();
+        }
+    }
+    double accd[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) accd[v] = acc[v].value();
+    __shared__ double packed[NV];
+    cta_reduce<NV, CO>(accd, scratch, packed);
+    for (int t = threadIdx.x; t < KB * KB; t += blockDim.x) {
+        int pp = t % KB, q = t / KB;
+        if (pp > q) {
+            const int tmp = pp;
+            pp = q;
+            q = tmp;
+        }
+        res[t] = packed[q * (q + 1) / 2 + pp];
+    }
+    __syncthreads();
+}
+
 // One whole s-step GMRES solve of one system, by one CTA (CO = false) or by the CTAs
 // of a cluster (CO = true; st is this CTA's own copy of the state).
-template <int S, bool CO>
+template <int S, bool CO, bool F32>
 __device__ void cta_solve(const BatchSys& b, SolverState* st, Rows R, double* scratch) {
+    using T = typename std::conditional<F32, float, double>::type;   // the basis type
     const StencilDesc& A = b.A;
     const int64_t ld = b.ld;
     const int m = st->m, nb = m / S;
-    double* U = b.U;
-    double* uraw = U + (int64_t)(m + 1) * ld;
+    T* U = reinterpret_cast<T*>(b.U);
+    T* uraw = U + (int64_t)(m + 1) * ld;
     __shared__ double res[kBatchMaxM * (kBatchMaxS + 1)];
     Epi e;
     e.st = st;
@@ -265,7 +443,8 @@ __device__ void cta_solve(const BatchSys& b, SolverState* st, Rows R, double* sc
         step_sync<CO>();
     }
     for (;;) {
-        cta_residual<CO>(A, R, b.f, b.x, uraw, scratch, res);
+        if constexpr (F32) cta_residual32<CO>(A, R, b.f, b.x, uraw, scratch, res);
+        else cta_residual<CO>(A, R, b.f, b.x, uraw, scratch, res);
         e.mode = EPI_RESTART;
         run_epilogue(e, res, 1, 1);
         __syncthreads();
@@ -274,23 +453,34 @@ __device__ void cta_solve(const BatchSys& b, SolverState* st, Rows R, double* sc
             if (!flag(st, 1)) break;
             const int o = k * S;
             const double vs = st->vscale, sigma = st->sigma;
-            cta_stencil<CO>(A, R, uraw, sigma * vs, U + (o + 1) * ld, vs, U + o * ld);
-            for (int j = 2; j <= S; ++j)
-                cta_stencil<CO>(A, R, U + (o + j - 1) * ld, sigma, U + (o + j) * ld, 0.0, nullptr);
+            if constexpr (F32) {
+                cta_stencil32<CO>(A, R, uraw, __double2float_rn(sigma * vs), U + (o + 1) * ld, __double2float_rn(vs),
+                                  U + o * ld);
+                for (int j = 2; j <= S; ++j)
+                    cta_stencil32<CO>(A, R, U + (o + j - 1) * ld, __double2float_rn(sigma), U + (o + j) * ld, 0.f,
+                                      nullptr);
+            } else {
+                cta_stencil<CO>(A, R, uraw, sigma * vs, U + (o + 1) * ld, vs, U + o * ld);
+                for (int j = 2; j <= S; ++j)
+                    cta_stencil<CO>(A, R, U + (o + j - 1) * ld, sigma, U + (o + j) * ld, 0.0, nullptr);
+            }
             if (k > 0) {
-                cta_gram<S, CO>(R, U, ld, o, U + (o + 1) * ld, scratch, res);
+                if constexpr (F32) cta_gram32<S, CO>(R, U, ld, o, U + (o + 1) * ld, scratch, res);
+                else cta_gram<S, CO>(R, U, ld, o, U + (o + 1) * ld, scratch, res);
                 e.mode = EPI_GM_T;
                 e.o = o;
                 run_epilogue(e, res, o, S);
                 __syncthreads();
             }
-            cta_update<S + 1, CO>(R, U, ld, o, U + o * ld, U + o * ld, 1, st->T, m, scratch, res);
+            if constexpr (F32) cta_update32<S + 1, CO>(R, U, ld, o, U + o * ld, U + o * ld, 1, st->T, m, scratch, res);
+            else cta_update<S + 1, CO>(R, U, ld, o, U + o * ld, U + o * ld, 1, st->T, m, scratch, res);
             e.mode = EPI_GM_W;
             e.o = o;
             run_epilogue(e, res, S + 1, S + 1);
             __syncthreads();
             if (!flag(st, 1)) break;
-            cta_update<1, CO>(R, U + o * ld, ld, S, U + (o + S) * ld, uraw, 0, st->S, S, scratch, res);
+            if constexpr (F32) cta_update32<1, CO>(R, U + o * ld, ld, S, U + (o + S) * ld, uraw, 0, st->S, S, scratch, res);
+            else cta_update<1, CO>(R, U + o * ld, ld, S, U + (o + S) * ld, uraw, 0, st->S, S, scratch, res);
             e.mode = EPI_GM_NU;
             e.o = o;
             e.lastblock = (k == nb - 1);
@@ -301,10 +491,21 @@ __device__ void cta_solve(const BatchSys& b, SolverState* st, Rows R, double* sc
         __syncthreads();
         // x += U y
         const int K = st->K;
-        for (int64_t p = R.r0 + threadIdx.x; p < R.r1; p += blockDim.x) {
-            double acc = 0.0;
-            for (int i = 0; i < K; ++i) acc = fma(U[p + (int64_t)i * ld], st->y[i], acc);
-            b.x[p] = b.x[p] + acc;
+        if constexpr (F32) {   // y as float pairs; the sum in double-float, added to x in FP64
+            __shared__ df64 ys[kBatchMaxM];
+            for (int i = threadIdx.x; i < K; i += blockDim.x) ys[i] = df_from_double(st->y[i]);
+            __syncthreads();
+            for (int64_t p = R.r0 + threadIdx.x; p < R.r1; p += blockDim.x) {
+                DfAcc acc;
+                for (int i = 0; i < K; ++i) acc_fd(acc, U[p + (int64_t)i * ld], ys[i]);
+                b.x[p] = b.x[p] + acc.value();
+            }
+        } else {
+            for (int64_t p = R.r0 + threadIdx.x; p < R.r1; p += blockDim.x) {
+                double acc = 0.0;
+                for (int i = 0; i < K; ++i) acc = fma(U[p + (int64_t)i * ld], st->y[i], acc);
+                b.x[p] = b.x[p] + acc;
+            }
         }
         step_sync<CO>();   // the next residual reads halo rows of x
     }
@@ -321,7 +522,7 @@ __device__ void cta_solve(const BatchSys& b, SolverState* st, Rows R, double* sc
 // independent round have similar sizes. Every cluster barrier below is reached by all
 // CTAs of the cluster: the round's items are read from rank 0, and the cooperative
 // solve's branches come from identical state copies.
-template <int S>
+template <int S, bool F32>
 __global__ void __launch_bounds__(256) batched_sstep_gmres_kernel(const BatchSys* __restrict__ sys,
                                                                   const int* __restrict__ order, int nsys,
                                                                   unsigned* queue, int64_t nbig) {
@@ -357,10 +558,10 @@ __global__ void __launch_bounds__(256) batched_sstep_gmres_kernel(const BatchSys
             const int64_t n = b.A.n;
             const Rows R{n * rank / G, n * (rank + 1) / G};
             SolverState* st = (SolverState*)((char*)b.st + (int64_t)rank * b.st_stride);
-            cta_solve<S, true>(b, st, R, scratch);
+            cta_solve<S, true, F32>(b, st, R, scratch);
         } else if (item < nsys) {
             const BatchSys& b = sys[order ? order[item] : item];
-            cta_solve<S, false>(b, b.st, Rows{0, b.A.n}, scratch);
+            cta_solve<S, false, F32>(b, b.st, Rows{0, b.A.n}, scratch);
         }
         cl.sync();   // the round is over in every CTA before rank 0 takes the next items
     }
@@ -397,12 +598,13 @@ cudaLaunchConfig_t batched_config(int threads, int grid, int cluster, cudaLaunch
     return cfg;
 }
 
-template <int S>
+template <int S, bool F32>
 int batched_grid_s(int threads, int ctas, int cluster) {
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = batched_config<S>(threads, (ctas / cluster) * cluster, cluster, at, nullptr);
     int maxc = 0;
-    if (cfg.gridDim.x < 1 || cudaOccupancyMaxActiveClusters(&maxc, batched_sstep_gmres_kernel<S>, &cfg) != cudaSuccess) {
+    if (cfg.gridDim.x < 1 ||
+        cudaOccupancyMaxActiveClusters(&maxc, batched_sstep_gmres_kernel<S, F32>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return -1;
     }
@@ -411,35 +613,44 @@ int batched_grid_s(int threads, int ctas, int cluster) {
     return nclu >= 1 ? nclu * cluster : -1;
 }
 
-int batched_grid(int s, int threads, int ctas, int cluster) {
+int batched_grid(int s, int threads, int ctas, int cluster, bool f32) {
     if (cluster < 1 || cluster > kBatchCopies || threads > 256 || threads % 32) return -1;
     switch (s) {
-        case 1: return batched_grid_s<1>(threads, ctas, cluster);
-        case 2: return batched_grid_s<2>(threads, ctas, cluster);
-        case 4: return batched_grid_s<4>(threads, ctas, cluster);
-        case 8: return batched_grid_s<8>(threads, ctas, cluster);
+#define SSTEP_BG(S_) \
+    case S_: return f32 ? batched_grid_s<S_, true>(threads, ctas, cluster) : batched_grid_s<S_, false>(threads, ctas, cluster);
+        SSTEP_BG(1)
+        SSTEP_BG(2)
+        SSTEP_BG(4)
+        SSTEP_BG(8)
+#undef SSTEP_BG
         default: return -1;
     }
 }
 
-template <int S>
+template <int S, bool F32>
 int launch_batched_s(const BatchSys* sys, const int* order, int nsys, unsigned* queue, int threads, int grid,
                      int cluster, int64_t nbig, cudaStream_t stream) {
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = batched_config<S>(threads, grid, cluster, at, stream);
-    return cudaLaunchKernelEx(&cfg, batched_sstep_gmres_kernel<S>, sys, order, nsys, queue, nbig) == cudaSuccess ? 0
-                                                                                                           : -1;
+    return cudaLaunchKernelEx(&cfg, batched_sstep_gmres_kernel<S, F32>, sys, order, nsys, queue, nbig) == cudaSuccess
+               ? 0
+               : -1;
 }
 
 int launch_batched(const BatchSys* sys, const int* order, int nsys, unsigned* queue, int s, int threads, int grid,
-                   int cluster, int64_t nbig, cudaStream_t stream) {
+                   int cluster, int64_t nbig, bool f32, cudaStream_t stream) {
     if (cluster < 1 || cluster > kBatchCopies || threads > 256 || threads % 32 || grid < cluster || grid % cluster)
         return -1;
     switch (s) {
-        case 1: return launch_batched_s<1>(sys, order, nsys, queue, threads, grid, cluster, nbig, stream);
-        case 2: return launch_batched_s<2>(sys, order, nsys, queue, threads, grid, cluster, nbig, stream);
-        case 4: return launch_batched_s<4>(sys, order, nsys, queue, threads, grid, cluster, nbig, stream);
-        case 8: return launch_batched_s<8>(sys, order, nsys, queue, threads, grid, cluster, nbig, stream);
+#define SSTEP_LB(S_)                                                                                           \
+    case S_:                                                                                                   \
+        return f32 ? launch_batched_s<S_, true>(sys, order, nsys, queue, threads, grid, cluster, nbig, stream)  \
+                   : launch_batched_s<S_, false>(sys, order, nsys, queue, threads, grid, cluster, nbig, stream);
+        SSTEP_LB(1)
+        SSTEP_LB(2)
+        SSTEP_LB(4)
+        SSTEP_LB(8)
+#undef SSTEP_LB
         default: return -1;
     }
 }

@@ -681,7 +681,8 @@ int batch_graph(sstep_batch B, cudaStream_t stream) {
     int dev = 0, sms = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int grid = batched_grid(B->s, B->threads, sms * B->ctas_per_sm, B->cluster);
+    const bool f32 = B->p.precision == SSTEP_PREC_FP32;
+    const int grid = batched_grid(B->s, B->threads, sms * B->ctas_per_sm, B->cluster, f32);
     if (grid < 1) return SSTEP_ERR_ARG;
     cudaStream_t cap;
     CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -692,7 +693,7 @@ int batch_graph(sstep_batch B, cudaStream_t stream) {
         cudaMemsetAsync(B->d_queue, 0, sizeof(unsigned), cap);
         launch_batch_init(B->d_init, B->d_sys, B->nsys, cap);
         if (launch_batched(B->d_sys, B->largest_first ? B->d_order : nullptr, B->nsys, B->d_queue, B->s, B->threads,
-                           grid, B->cluster, B->nbig, cap))
+                           grid, B->cluster, B->nbig, f32, cap))
             rc = SSTEP_ERR_ARG;
         if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = SSTEP_ERR_CUDA;
     }
@@ -1543,7 +1544,8 @@ int sstep_batch_create(sstep_batch* out, int nsys, const sstep_matrix* A, const 
     *out = nullptr;
     const int s = p->s, m = p->m;
     if (!(s == 1 || s == 2 || s == 4 || s == 8) || m < s || m > kBatchMaxM || m % s || p->max_cycles < 0 ||
-        !(p->tol > 0.0) || p->sigma < 0.0 || p->precision != SSTEP_PREC_FP64 || p->basis != SSTEP_BASIS_MONOMIAL ||
+        !(p->tol > 0.0) || p->sigma < 0.0 || (p->precision != SSTEP_PREC_FP64 && p->precision != SSTEP_PREC_FP32) ||
+        p->basis != SSTEP_BASIS_MONOMIAL ||
         p->precond != SSTEP_PRECOND_NONE)
         return SSTEP_ERR_ARG;
     for (int i = 0; i < nsys; ++i)
@@ -1566,7 +1568,8 @@ int sstep_batch_create(sstep_batch* out, int nsys, const sstep_matrix* A, const 
     }
     for (int i = 0; i < nsys; ++i) {
         col_off[i] = total;
-        total += align_up(sizeof(double) * (size_t)col_ld(A[i]->A.n) * (m + 2));
+        const size_t elem = p->precision == SSTEP_PREC_FP32 ? sizeof(float) : sizeof(double);
+        total += align_up(elem * (size_t)col_ld(A[i]->A.n) * (m + 2));
     }
     int rc = SSTEP_OK;
     if (cudaMalloc((void**)&B->ws, total) != cudaSuccess || cudaMalloc((void**)&B->d_sys, sizeof(BatchSys) * nsys) !=

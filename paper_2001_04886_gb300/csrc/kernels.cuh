@@ -209,7 +209,7 @@ struct BatchSys {
     StencilDesc A;
     const double* f;
     double* x;
-    double* U;           // m+2 columns of ld doubles: basis, raw start vector
+    double* U;           // m+2 columns of ld entries (double, or float for the FP32 basis): basis, raw start vector
     SolverState* st;     // state copy 0; copy g (cooperative solves) at st + g * st_stride bytes
     int64_t ld;
     int64_t st_stride;
@@ -219,9 +219,10 @@ size_t batched_scratch_bytes(int threads);
 // the persistent kernel; cluster = CTAs per cluster (1..8), systems with n >= nbig are
 // solved cooperatively by a whole cluster. batched_grid: the grid for about `ctas` CTAs
 // with no more clusters than can be resident at once (-1: the configuration cannot run).
-int batched_grid(int s, int threads, int ctas, int cluster);
+// f32: the FP32-basis form (double-float sums, FP64 residual, x and scalar work).
+int batched_grid(int s, int threads, int ctas, int cluster, bool f32);
 int launch_batched(const BatchSys* sys, const int* order, int nsys, unsigned* queue, int s, int threads, int grid,
-                   int cluster, int64_t nbig, cudaStream_t stream);
+                   int cluster, int64_t nbig, bool f32, cudaStream_t stream);
 // copies the initial state images src[i * kBatchCopies + g] into every state copy
 void launch_batch_init(const SolverState* src, const BatchSys* sys, int nsys, cudaStream_t stream);
 }  // namespace sstep

@@ -119,3 +119,51 @@ def test_tune_cache_configures_without_timing(tmp_path):
     assert cfg2 == cfg and time.perf_counter() - t0 < 0.5
     res = B2.solve(fs, xs, mode=B2.PERSISTENT)
     assert all(r["status"] == 0 for r in res)
+
+
+@pytest.mark.parametrize("cluster,coop", [(1, "none"), (4, "all"), (4, "half")])
+def test_fp32_basis_batch_reaches_fp64_tolerance(cluster, coop):
+    """The FP32-basis form of the persistent solver (FP32 powers and basis, double-float
+    sums, FP64 residual, x and scalar work) meets the FP64 stopping test at 1e-10 on
+    every system, one CTA per system and cluster-cooperative alike, and lands on the
+    oracle's FP64 solution: both have residuals <= 1e-10 ||f||, so they differ by at most
+    cond(A) 2e-10 relative (cond(A) < 1e3 at these sizes: 1e-6 is the bar)."""
+    d = dev()
+    mats, ora, fs, xs = batch(3, 24, 6, 40, d)
+    nmed = int(np.median([A.n for A in mats]))
+    B = pkg.BatchSolver(mats, 4, 20, 1e-10, max_cycles=400, precision="fp32")
+    B.configure(threads=256, ctas_per_sm=1, largest_first=1, cluster=cluster,
+                coop_min_n={"none": 1 << 40, "all": 0, "half": nmed}[coop])
+    res = B.solve(fs, xs, mode=B.PERSISTENT)
+    torch.cuda.synchronize()
+    for i, ((Ao, f), r) in enumerate(zip(ora, res)):
+        ref = osstep.sstep_gmres(Ao, f, np.zeros(Ao.n), 4, 20, 1e-10, 1.0 / Ao.norm_inf(), 400)
+        x = xs[i].cpu().numpy()
+        assert r["status"] == 0 and ref["status"] == 0, (i, r)
+        assert r["relres"] <= 1e-10, (i, r)
+        assert np.linalg.norm(f - Ao.apply(x)) <= 1e-10 * np.linalg.norm(f) * (1 + 1e-6), i
+        assert np.linalg.norm(x - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"]), i
+        assert r["cycles"] <= ref["cycles"] + 3, (i, r["cycles"], ref["cycles"])
+
+
+def test_fp32_basis_batch_matches_per_system_fp32_solves():
+    """The FP32-basis persistent solve and the single-system FP32 mode, system by system:
+    both reach 1e-10 and the same solution to the bound above; two solves with one handle
+    give the same cycle counts (the graph resets every state)."""
+    d = dev()
+    mats, ora, fs, xs = batch(11, 30, 16, 64, d)
+    xs2 = [torch.zeros_like(x) for x in xs]
+    B = pkg.BatchSolver(mats, 4, 20, 1e-10, max_cycles=400, precision="fp32")
+    r1 = B.solve(fs, xs, mode=B.PERSISTENT)
+    r2 = B.solve(fs, xs2, mode=B.PER_SYSTEM)
+    torch.cuda.synchronize()
+    for i in range(len(xs)):
+        assert r1[i]["status"] == r2[i]["status"] == 0, i
+        a, b = xs[i].cpu().numpy(), xs2[i].cpu().numpy()
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b), i
+    for x in xs:
+        x.zero_()
+    r3 = B.solve(fs, xs, mode=B.PERSISTENT)
+    assert [r["cycles"] for r in r3] == [r["cycles"] for r in r1]
+    with pytest.raises(ValueError):
+        pkg.BatchSolver(mats, 4, 20, 1e-10, precision="df64")

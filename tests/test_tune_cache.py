@@ -20,6 +20,8 @@ def test_key_depends_on_device_shape_and_method():
     assert k != B.tune_cache_key(shapes, 4, 20, "NVIDIA GB300", sigma=0.25)
     assert k != B.tune_cache_key(shapes, 4, 20, "NVIDIA GB300", x0_guard=True)
     assert k != B.tune_cache_key(shapes, 4, 20, "NVIDIA GB300", build="0" * 16)
+    assert k != B.tune_cache_key(shapes, 4, 20, "NVIDIA GB300", precision="fp32")
+    assert k == B.tune_cache_key(shapes, 4, 20, "NVIDIA GB300", precision="fp64")
     assert k == B.tune_cache_key(shapes, 4, 20, "NVIDIA GB300", build=B.library_build_id())
 
 
