@@ -230,17 +230,27 @@ __device__ void cta_update(Rows R, const double* V, int64_t ld, int ka, double* 
     __syncthreads();
 }
 
-// back substitution y = R^{-1} g by one warp (the dot products as warp reductions)
+// back substitution y = R^{-1} g by one warp, column by column from the last (as
+// lsq_solve_kernel): lane l owns rows l and l + 32; the reciprocals of the diagonal are
+// formed first, off the dependent chain
 __device__ void cta_lsq(SolverState* st) {
     if (threadIdx.x >= 32) return;
-    const int K = st->K, ld = st->m + 1, lane = threadIdx.x;
-    for (int i = K - 1; i >= 0; --i) {
-        double t = 0.0;
-        for (int q = i + 1 + lane; q < K; q += 32) t = fma(st->R[i + q * ld], st->y[q], t);
-        t = warp_sum(t);
-        if (lane == 0) st->y[i] = sub(st->g[i], t) / st->R[i + i * ld];
-        __syncwarp();
+    static_assert(kBatchMaxM <= 64, "two rows per lane");
+    const int K = st->K, ld = st->m + 1, lane = threadIdx.x, i0 = lane, i1 = lane + 32;
+    const double* R = st->R;
+    const double r0 = i0 < K ? 1.0 / R[i0 + i0 * ld] : 0.0, r1 = i1 < K ? 1.0 / R[i1 + i1 * ld] : 0.0;
+    const double g0 = i0 < K ? st->g[i0] : 0.0, g1 = i1 < K ? st->g[i1] : 0.0;
+    double t0 = 0.0, t1 = 0.0, y0 = 0.0, y1 = 0.0;
+    for (int q = K - 1; q >= 0; --q) {
+        const double a0 = i0 < q ? R[i0 + q * ld] : 0.0, a1 = i1 < q ? R[i1 + q * ld] : 0.0;
+        if (q == i0) y0 = mul(sub(g0, t0), r0);
+        if (q == i1) y1 = mul(sub(g1, t1), r1);
+        const double yq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31);
+        if (i0 < q) t0 = fma(a0, yq, t0);
+        if (i1 < q) t1 = fma(a1, yq, t1);
     }
+    if (i0 < K) st->y[i0] = y0;
+    if (i1 < K) st->y[i1] = y1;
 }
 
 __device__ __forceinline__ int flag(const SolverState* st, int which) { return ((volatile const int*)st)[which]; }

@@ -281,9 +281,20 @@ __device__ void epi_gm_nu(const Epi& e, const double* red) {
             if (j > 0 && r < o) rj = st->T[r + j * m];
             val = fma(st->theta[j], rj, val);
         }
-        if (o > 0) {
+        if (o > 0) {   // the same multiply-adds in order; the loads of 8 terms issued together
             double acc = 0.0;
-            for (int i = 0; i < o; ++i) acc = fma(st->G[r + i * ldg], st->T[i + j * m], acc);
+            for (int i0 = 0; i0 < o; i0 += 8) {
+                double gv[8], tv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const bool in = i0 + u < o;
+                    gv[u] = in ? st->G[r + (i0 + u) * ldg] : 0.0;
+                    tv[u] = in ? st->T[(i0 + u) + j * m] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + u < o) acc = fma(gv[u], tv[u], acc);
+            }
             val = sub(val, acc);
         }
         st->G[r + (o + j) * ldg] = val;
@@ -297,8 +308,16 @@ __device__ void epi_gm_nu(const Epi& e, const double* red) {
         if (r < o + s) {
             const int b = r / s, rl = r % s;
             const double* Lb = st->L + b * s * s;
+            double lv[kMaxS], gv[kMaxS];   // the loads first, then the multiply-adds in order
+#pragma unroll
+            for (int q = 0; q < kMaxS; ++q) {
+                lv[q] = q < s ? Lb[rl + q * s] : 0.0;
+                gv[q] = q < s ? st->G[(b * s + q) + c * ldg] : 0.0;
+            }
             double acc = 0.0;
-            for (int q = 0; q < s; ++q) acc = fma(Lb[rl + q * s], st->G[(b * s + q) + c * ldg], acc);
+#pragma unroll
+            for (int q = 0; q < kMaxS; ++q)
+                if (q < s) acc = fma(lv[q], gv[q], acc);
             v = acc;
         } else {
             v = st->G[r + c * ldg];

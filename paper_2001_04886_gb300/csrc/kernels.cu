@@ -651,20 +651,29 @@ void launch_convdiff_fields(const double* beta, double h, int64_t n, double* out
 // short steps instead of K^2/2 global-memory round trips.
 __global__ void lsq_solve_kernel(SolverState* st, int gate) {
     __shared__ double sR[(kMaxM + 1) * kMaxM];
-    __shared__ double sy[kMaxM], sg[kMaxM];
+    __shared__ double sg[kMaxM];
     if (!gate_open(st, gate)) return;
     const int K = st->K, ld = st->m + 1, lane = threadIdx.x;
     for (int t = lane; t < K * K; t += blockDim.x) sR[(t % K) + (t / K) * K] = st->R[(t % K) + (t / K) * ld];
     for (int t = lane; t < K; t += blockDim.x) sg[t] = st->g[t];
     __syncwarp();
-    for (int i = K - 1; i >= 0; --i) {
-        double t = 0.0;
-        for (int q = i + 1 + lane; q < K; q += 32) t = fma(sR[i + q * K], sy[q], t);
-        t = warp_sum(t);
-        if (lane == 0) sy[i] = sub(sg[i], t) / sR[i + i * K];
-        __syncwarp();
+    // column by column from the last: y_q by the lane that owns row q (rows lane and
+    // lane + 32), then every lane folds R[i, q] y_q into the sums of its rows i < q. The
+    // reciprocals of the diagonal are formed first, all at once, so no division sits on
+    // the dependent chain of K steps (each product differs from the quotient by at most an ulp).
+    static_assert(kMaxM <= 64, "two rows per lane");
+    const int i0 = lane, i1 = lane + 32;
+    const double r0 = i0 < K ? 1.0 / sR[i0 + i0 * K] : 0.0, r1 = i1 < K ? 1.0 / sR[i1 + i1 * K] : 0.0;
+    double t0 = 0.0, t1 = 0.0, y0 = 0.0, y1 = 0.0;
+    for (int q = K - 1; q >= 0; --q) {
+        if (q == i0) y0 = mul(sub(sg[q], t0), r0);
+        if (q == i1) y1 = mul(sub(sg[q], t1), r1);
+        const double yq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31);
+        if (i0 < q) t0 = fma(sR[i0 + q * K], yq, t0);
+        if (i1 < q) t1 = fma(sR[i1 + q * K], yq, t1);
     }
-    for (int i = lane; i < K; i += 32) st->y[i] = sy[i];
+    if (i0 < K) st->y[i0] = y0;
+    if (i1 < K) st->y[i1] = y1;
 }
 
 void launch_lsq_solve(SolverState* st, int gate, cudaStream_t stream) {
