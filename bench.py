@@ -549,8 +549,10 @@ def main():
             torch.cuda.synchronize()
             small[name] = {"ms": e0.elapsed_time(e1) / reps, "status": r2s["status"], "cycles": r2s["cycles"],
                            "matvecs": r2s["matvecs"], "relres": r2s["relres"]}
-        for s_, name in ((4, "persistent_sstep_gmres_s4_m20"), (1, "persistent_gmres_m20_s1")):
-            Bs = pkg.BatchSolver([A2], s_, 20, TOL, max_cycles=2000)
+        for s_, name, prec in ((4, "persistent_sstep_gmres_s4_m20", "fp64"), (1, "persistent_gmres_m20_s1", "fp64"),
+                               (4, "persistent_sstep_gmres_s4_m20_fp32_basis", "fp32")):
+            Bs = pkg.BatchSolver([A2], s_, 20, TOL, max_cycles=2000, precision=prec)
+            x2.zero_()   # tuned on the solve it will time (tune() restores this guess)
             cfg = Bs.tune([f2], [x2])
             x2.zero_()
             Bs.solve([f2], [x2])
