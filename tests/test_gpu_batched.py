@@ -167,3 +167,27 @@ def test_fp32_basis_batch_matches_per_system_fp32_solves():
     assert [r["cycles"] for r in r3] == [r["cycles"] for r in r1]
     with pytest.raises(ValueError):
         pkg.BatchSolver(mats, 4, 20, 1e-10, precision="df64")
+
+
+def test_fp32_basis_batch_variable_coefficients():
+    """The FP32-basis persistent solver on variable-coefficient systems (the learned form's
+    8-mode fields, coefficients read per point as float pairs), against the oracle's FP64
+    solve to 1e-10: every residual recomputed by the oracle's operator, x to 1e-6."""
+    d = dev()
+    mats, ora, fs, xs = [], [], [], []
+    for k, N in enumerate((17, 32, 45, 64)):
+        beta, f = inputs.fourier_fields(300 + k, N)
+        Ao = ostencil.convdiff_variable(N, beta)
+        mats.append(pkg.StencilMatrix(2, (N, N), beta_field=to_dev(beta, d)))
+        ora.append((Ao, f))
+        fs.append(to_dev(f, d))
+        xs.append(torch.zeros(N * N, dtype=torch.float64, device=d))
+    B = pkg.BatchSolver(mats, 4, 20, 1e-10, max_cycles=2000, precision="fp32")
+    res = B.solve(fs, xs, mode=B.PERSISTENT)
+    torch.cuda.synchronize()
+    for i, ((Ao, f), r) in enumerate(zip(ora, res)):
+        ref = osstep.sstep_gmres(Ao, f, np.zeros(Ao.n), 4, 20, 1e-10, 1.0 / Ao.norm_inf(), 2000)
+        x = xs[i].cpu().numpy()
+        assert r["status"] == 0 and ref["status"] == 0, (i, r)
+        assert np.linalg.norm(f - Ao.apply(x)) <= 1e-10 * np.linalg.norm(f) * (1 + 1e-6), i
+        assert np.linalg.norm(x - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"]), i
