@@ -70,9 +70,9 @@ TRAFFIC = {
     "fp64": {"kernel": "block_update", "bytes_per_launch": 471.3e6,
              "sources": ("common.cuh", "kernels.cuh", "epilogue.cuh", "kernels.cu"),
              "sha256": "42dddf2a1f6c61fa"},
-    "fp64_tc": {"kernel": "block_update", "bytes_per_launch": 690.2e6,
+    "fp64_tc": {"kernel": "block_update", "bytes_per_launch": 690.7e6,
                 "sources": ("ozaki.cu", "ozaki.cuh"),
-                "sha256": "ccb77edff093c73c"},
+                "sha256": "457d6bc7ac8cb1d2"},
 }
 
 

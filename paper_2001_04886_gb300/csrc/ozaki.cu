@@ -854,8 +854,14 @@ constexpr int kUpRows = 128;                      // rows per tile (MMA M)
 constexpr int kUpDiags = oz::kCut + 1;            // kept digit diagonals
 constexpr uint32_t kUpBuf = 128;                  // tensor-memory columns per accumulator buffer
 
-// B rows: (output j, diagonal d) with d fastest, padded to a multiple of 16 (the MMA N)
-__host__ __device__ constexpr int up_n(int kbo) { return (kUpDiags * kbo + 15) / 16 * 16; }
+// B rows: the outputs in groups of H = ceil(KBO / 4), one group per warp of a tensor-memory
+// lane quarter; group g takes rows (accumulator columns) 32 g .. 32 g + 9 H - 1, output
+// j = g H + i at 32 g + 9 i + d (d the diagonal, fastest). Every group starts on the same
+// boundary, so one epilogue serves all four warps of a quarter (the MMA's N grows to 32
+// per group; the tensor pipe has room).
+__host__ __device__ constexpr int up_h(int kbo) { return (kbo + 3) / 4; }
+__host__ __device__ constexpr int up_n(int kbo) { return 32 * ((kbo + up_h(kbo) - 1) / up_h(kbo)); }
+__host__ __device__ constexpr int up_row(int kbo, int j) { return 32 * (j / up_h(kbo)) + kUpDiags * (j % up_h(kbo)); }
 
 template <int KAP, int KBO>
 struct UpCfg {
@@ -865,7 +871,8 @@ struct UpCfg {
     static constexpr int kA = kUpRows * kK * 2;   // one A buffer (FP16)
     static constexpr int kB = kN * kK * 2;        // B: kN rows
     static constexpr int kSmem = 2 * kA + kB;
-    static_assert(kN <= (int)kUpBuf, "accumulator buffer");
+    static_assert(kN <= (int)kUpBuf && kUpDiags * up_h(KBO) <= 32, "accumulator buffer");
+    static_assert(kSmem + 4096 <= 227 * 1024, "shared memory");
 };
 
 template <int KAP, int KBO>
@@ -937,7 +944,7 @@ __global__ void __launch_bounds__(kUpThreads, 1)
 #pragma unroll
             for (int ta = 0; ta < oz::kDigits; ++ta)
                 if (ta + tb <= oz::kCut)
-                    *reinterpret_cast<__half*>(Bop + op_off<SBO>(j * kUpDiags + ta + tb, 8 * a + ta)) = e16;
+                    *reinterpret_cast<__half*>(Bop + op_off<SBO>(up_row(KBO, j) + ta + tb, 8 * a + ta)) = e16;
         }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1004,7 +1011,7 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             ea[i] = exv[ac];
         }
         // epilogue: rows 32 q + lane of a tile; warp group g = warp / 4 takes the outputs
-        // g H .. g H + H - 1 (compile-time offsets through one instantiation per group)
+        // g H .. g H + H - 1, whose accumulators start at column 32 g (one code path for all)
         constexpr int H = (KBO + 3) / 4;
         const int q = warp & 3, g = warp >> 2;
         unsigned bm[H];
@@ -1028,8 +1035,8 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             }
         };
         // epilogue of tile lt: Yhat = Y - P for this thread's row and outputs
-        auto epilogue = [&](int64_t lt, auto goc) -> bool {
-            constexpr int jo = decltype(goc)::value * H;
+        auto epilogue = [&](int64_t lt) -> bool {
+            const int jo = g * H;   // this warp's outputs jo .. jo + H - 1, columns 32 g + 9 i + d
             const int b = (int)(lt & 1);
             const int64_t r = (t0 + lt) * kUpRows + q * 32 + lane;
             if (!oz_wait(smem_addr(&tfull[b]), (uint32_t)((lt >> 1) & 1), spin)) return false;
@@ -1043,21 +1050,19 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             unsigned long long Qh[H], Ql[H];
 #pragma unroll
             for (int j = 0; j < H; ++j) Qh[j] = Ql[j] = 0;
-            // columns (j, d) = 9 j + d of this thread's outputs, read 16 at a time from the
-            // aligned column c0 below the first one (compile-time offsets)
-            constexpr int c0 = (kUpDiags * jo) / 16 * 16;
-            constexpr int c1 = kUpDiags * (jo + H) < kUpDiags * KBO ? kUpDiags * (jo + H) : kUpDiags * KBO;
-            constexpr int NR = c1 > c0 ? (c1 - c0 + 15) / 16 * 16 : 16;
+            // the group's 32 accumulator columns from 32 g (output jo + i, diagonal d at 9 i + d)
+            constexpr int NR = 32;
             uint32_t rv[NR];
-            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * kUpBuf + (uint32_t)c0;
-            tmem_ld<NR>(ta, rv);
+            if (jo < KBO) {   // warp-uniform (a warp past the last group has no outputs)
+                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * kUpBuf + (uint32_t)(32 * g);
+                tmem_ld<NR>(ta, rv);
+            }
 #pragma unroll
             for (int d = 0; d < kUpDiags; ++d) {
 #pragma unroll
                 for (int j = 0; j < H; ++j) {
-                    const int col = kUpDiags * (jo + j) + d - c0;
-                    const unsigned mS = (jo + j < KBO && col < NR)
-                                            ? (unsigned)__float_as_int(__uint_as_float(rv[col]) + 12582912.0f)
+                    const unsigned mS = jo + j < KBO
+                                            ? (unsigned)__float_as_int(__uint_as_float(rv[kUpDiags * j + d]) + 12582912.0f)
                                             : kMagic;
                     if (d < 5) Qh[j] = Qh[j] * 256 + mS;
                     else Ql[j] = Ql[j] * 256 + mS;
@@ -1087,14 +1092,7 @@ __global__ void __launch_bounds__(kUpThreads, 1)
             }
             return true;
         };
-        auto run_epilogue = [&](int64_t lt) -> bool {
-            switch (g) {
-                case 0: return epilogue(lt, std::integral_constant<int, 0>());
-                case 1: return epilogue(lt, std::integral_constant<int, 1>());
-                case 2: return epilogue(lt, std::integral_constant<int, 2>());
-                default: return epilogue(lt, std::integral_constant<int, 3>());
-            }
-        };
+        auto run_epilogue = [&](int64_t lt) -> bool { return epilogue(lt); };
         double cur[kIt];
         if (nt > 0) load(0, cur);
         for (int64_t lt = 0; lt < nt; ++lt) {
