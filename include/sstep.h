@@ -18,6 +18,17 @@
  *     C++ exception crosses the ABI. Argument errors return SSTEP_ERR_ARG before
  *     any work is enqueued.
  *   - A handle may run one solve at a time (its workspace is reused).
+ *
+ * Environment switches (read once per process, at the first solve; all default to the
+ * fastest measured path):
+ *   SSTEP_TC_GRAM=0       FP64 s-step GMRES forms its inner products and block updates
+ *                         on the FP64 CUDA cores instead of the tensor cores (exact fixed
+ *                         point); for comparisons.
+ *   SSTEP_TC_WORDS=0      the tensor-core passes convert every basis column again instead
+ *                         of reading the fixed-point words the block's Gram pass kept.
+ *   SSTEP_FUSED_POWERS=1  the s powers of a block in one fused launch with s-deep halos
+ *                         (FP64: start-vector tiles staged by TMA; the same columns bit for
+ *                         bit); measured slower than the separate sweeps on GB300.
  */
 #ifndef SSTEP_H
 #define SSTEP_H
