@@ -320,8 +320,6 @@ __global__ void __launch_bounds__(kThreads) mp_powers_fused_kernel(StencilDesc A
             const int z = zc - j;
             const bool active = z >= 0 && z < A.nz && z >= zb - (S - j) && z < ze + (S - j);
             if (active) {
-                constexpr int dummy = 0;
-                (void)dummy;
                 const int wp = lvl_w<S>(j - 1), wj = lvl_w<S>(j);
                 const Vt* prev = ring + lvl_off<S>(j - 1);
                 const Vt* pc = prev + (z % 3) * wp * wp;

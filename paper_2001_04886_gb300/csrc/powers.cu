@@ -13,9 +13,10 @@
 // every level is computed with the separate sweep's coefficients and in its order of
 // multiply-adds, neighbours outside the grid skipped, so the columns equal the separate
 // sweeps' (stencil_const_kernel) bit for bit; the tile's points of each level are stored
-// and their column bound recorded. The halos recompute points: about 1.8x the sweeps'
-// multiply-adds at S = 8 on a 32 x 16 tile, which the FP64 pipe pays (see the solver's
-// notes on when this path is used).
+// and their column bound recorded. The halos recompute points (at S = 8 on a 32 x 16 tile
+// about 1.8x the sweeps' multiply-adds in x-y, 2.7x with the z halo of 16-plane chunks),
+// which the FP64 pipe pays: at 128^3 this launch takes about 3x the separate sweeps, so
+// the solver uses it only when SSTEP_FUSED_POWERS=1.
 #include <cuda.h>
 
 #include "kernels.cuh"
