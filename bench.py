@@ -72,7 +72,7 @@ TRAFFIC = {
              "sha256": "42dddf2a1f6c61fa"},
     "fp64_tc": {"kernel": "block_update", "bytes_per_launch": 690.7e6,
                 "sources": ("ozaki.cu", "ozaki.cuh"),
-                "sha256": "457d6bc7ac8cb1d2"},
+                "sha256": "d9ce67d97ba559a1"},
 }
 
 

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads + (ZS ? 32 : 0), 1)
         }
         for (int b = 0; b < 2; ++b) {
             bar_init(&tfull[b], 1);
-            bar_init(&tempty[b], C::kSplitWarps);
+            bar_init(&tempty[b], G == 0 ? 4 : kDrainWarps);   // the warps that drain (see drains)
         }
         if (ZS)
             for (int b = 0; b < RS; ++b) {
@@ -504,7 +504,10 @@ __global__ void __launch_bounds__(OzCfg<G, KB>::kThreads + (ZS ? 32 : 0), 1)
             }
         };
         // the chunk's exact sums out of tensor memory into the 128-bit accumulators
+        // (only the draining warps wait for the chunk's sums; the others go on splitting the
+        // next chunk's stages into the other accumulator buffer)
         auto drain_chunk = [&](int chunk) -> bool {
+            if (!drains) return true;
             const int tb = chunk & 1;
             if (!oz_wait(smem_addr(&tfull[tb]), (uint32_t)((chunk >> 1) & 1), spin)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;");
